@@ -1,0 +1,318 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/dd_oracle.c) against something other than
+itself: brute-force dense linear algebra in numpy, scipy's LU, the
+Banachiewicz form of B (Lemma 1), the spectral theorem for C B^-1 (Theorem 2
+and the right-preconditioning remark), the paper's worked MSCN example
+(Section 3.2), and textbook special cases.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from paper_1104_3349_gb300 import workload as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(20240601)
+
+
+# --------------------------------------------------------------------------
+# LU
+# --------------------------------------------------------------------------
+def _unpack(lu, piv):
+    n = lu.shape[0]
+    L = np.tril(lu, -1) + np.eye(n)
+    U = np.triu(lu)
+    perm = np.arange(n)
+    for k in range(n):
+        perm[[k, piv[k]]] = perm[[piv[k], k]]
+    return L, U, perm
+
+
+@pytest.mark.parametrize("n", [1, 7, 40])
+def test_dense_lu_backward_error_and_scipy(n):
+    A = rng.standard_normal((n, n))
+    lu, piv, rc = O.dense_lu(A)
+    assert rc == 0
+    L, U, perm = _unpack(lu, piv)
+    assert np.abs(A[perm] - L @ U).max() <= 1e-14 * n * np.abs(A).max()
+    P, Ls, Us = sla.lu(A)
+    assert np.allclose(L, Ls, atol=1e-12) and np.allclose(U, Us, atol=1e-12)
+    assert np.array_equal(P.T @ np.arange(n), perm.astype(float))
+
+
+def test_dense_lu_first_max_pivot_and_singular():
+    A = np.array([[1.0, 2.0], [-1.0, 0.0]])
+    _, piv, rc = O.dense_lu(A)
+    assert rc == 0 and piv[0] == 0  # |1| == |-1|: the first row wins
+    S = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [0.0, 0.0, 1.0]])
+    _, _, rc = O.dense_lu(S)
+    assert rc == 2  # column 1 has no acceptable pivot
+
+
+@pytest.mark.parametrize("n,kl,ku", [(60, 3, 2), (120, 9, 5), (50, 1, 7)])
+def test_band_lu_equals_dense_lu(n, kl, ku):
+    A = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - kl), min(n, i + ku + 1)):
+            A[i, j] = rng.standard_normal()
+    A[np.arange(n), np.arange(n)] *= 0.1  # force pivoting
+    b = rng.standard_normal(n)
+    x, piv_b, rc = O.band_lu_solve(A, kl, ku, b)
+    assert rc == 0
+    lu, piv_d, rc2 = O.dense_lu(A)
+    assert rc2 == 0
+    assert np.array_equal(piv_b, piv_d)
+    xd = O.dense_lu_solve(lu, piv_d, b)
+    assert np.abs(x - xd).max() <= 1e-12 * np.abs(xd).max()
+    assert np.abs(x - np.linalg.solve(A, b)).max() <= 1e-10 * np.abs(xd).max()
+
+
+# --------------------------------------------------------------------------
+# Blocks of P^T C P and brute-force Schur complements
+# --------------------------------------------------------------------------
+def _small(n=8, m=4, nu=0.02, wind=W.WIND_FOURIER, seed=9, sz=16):
+    A, _ = W.mac_system(n, nu=nu, wind=wind, wind_seed=seed)
+    part, perm, _ = W.partition(A, m)
+    agg = W.aggregates(A, part, perm, sz)
+    return A, part, perm, agg
+
+
+def _perm_blocks(A, part, perm):
+    C = A.to_dense()
+    Cp = C[np.ix_(perm, perm)]
+    nI = int((part >= 0).sum())
+    return Cp, nI, Cp[:nI, :nI], Cp[:nI, nI:], Cp[nI:, :nI], Cp[nI:, nI:]
+
+
+def _brute_S(D, E, F, G):
+    return G - F @ np.linalg.solve(D, E)
+
+
+def _brute_blocks(kind, D, E, F, G, agg):
+    S = _brute_S(D, E, F, G)
+    out = []
+    for i in range(len(agg) - 1):
+        a, e = agg[i], agg[i + 1]
+        if kind in (O.MSCE_INF, O.EXACT):
+            out.append(S[a:e, a:e])
+        elif kind == O.LUM:
+            out.append(G[a:e, a:e])
+        else:
+            Dii, Eii, Fii = D[a:e, a:e], E[a:e, a:e], F[a:e, a:e]
+            if not Eii.any() or not Fii.any():
+                out.append(G[a:e, a:e].copy())
+                continue
+            X = np.linalg.solve(Dii, Eii)
+            if kind == O.MSCN:
+                out.append(G[a:e, a:e] - Fii @ X)
+            else:
+                out.append(G[a:e, a:e] - np.diag(Fii @ X @ np.ones(e - a)))
+    return out
+
+
+def test_exact_schur_equals_brute_force():
+    A, part, perm, agg = _small()
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, O.EXACT, perm=perm)
+    S = P.schur_block(0)
+    Sb = _brute_S(D, E, F, G)
+    assert np.abs(S - Sb).max() <= 1e-12 * np.abs(Sb).max()
+
+
+@pytest.mark.parametrize("kind", [O.MSCE_INF, O.MSCN, O.MSCNR, O.LUM])
+def test_schur_blocks_equal_brute_force(kind):
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, kind, perm=perm, agg_offsets=agg)
+    ref = _brute_blocks(kind, D, E, F, G, agg)
+    for i, Sb in enumerate(ref):
+        S = P.schur_block(i)
+        assert np.abs(S - Sb).max() <= 1e-11 * max(1.0, np.abs(Sb).max()), (kind, i)
+
+
+def test_mscn_paper_example_index_mapping():
+    """Section 3.2 worked example: aggregate {10,11} of G pairs with D-local
+    {10,11}, i.e. C_4 is built from global rows/columns {10,11,26,27}."""
+    g = json.load(open(os.path.join(GOLDEN, "mscn_toy_example.json")))
+    nD, nG = g["n_D"], g["n_G"]
+    n = nD + nG
+    C = rng.standard_normal((n, n)) * 0.3 + np.eye(n) * 4.0
+    rows, cols = np.nonzero(C)
+    A = W.CSR(n, np.concatenate([[0], np.cumsum(np.count_nonzero(C, axis=1))]).astype(np.int32),
+              cols.astype(np.int32), C[rows, cols])
+    part = np.array([0] * nD + [-1] * nG, np.int32)
+    sizes = [len(a) for a in g["aggregates_1based"]]
+    agg = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    k = g["checked_aggregate_1based"] - 1
+    idx = np.array(g["C4_global_rows_cols_1based"]) - 1
+    C4 = C[np.ix_(idx, idx)]
+    D4, E4, F4, G4 = C4[:2, :2], C4[:2, 2:], C4[2:, :2], C4[2:, 2:]
+    P = O.OracleDD(A, part, 1, O.MSCN, agg_offsets=agg)
+    assert np.abs(P.schur_block(k) - (G4 - F4 @ np.linalg.solve(D4, E4))).max() <= 1e-13
+    P = O.OracleDD(A, part, 1, O.MSCNR, agg_offsets=agg)
+    ref = G4 - np.diag(F4 @ np.linalg.solve(D4, E4) @ np.ones(2))
+    assert np.abs(P.schur_block(k) - ref).max() <= 1e-13
+    P = O.OracleDD(A, part, 1, O.LUM, agg_offsets=agg)
+    assert np.abs(P.schur_block(k) - G4).max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# Apply (Algorithm 2) against the factored form of B
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [O.EXACT, O.MSCE_INF, O.MSCN, O.MSCNR, O.LUM])
+def test_apply_equals_inverse_of_factored_B(kind):
+    A, part, perm, agg = _small(n=8, m=4, sz=14)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, kind, perm=perm, agg_offsets=None if kind == O.EXACT else agg)
+    a = P.agg_offsets()
+    Sh = sla.block_diag(*[P.schur_block(i) for i in range(len(a) - 1)])
+    nG = G.shape[0]
+    Z = np.zeros
+    L1 = np.block([[D, Z((nI, nG))], [F, Sh]])
+    M = np.block([[np.linalg.inv(D), Z((nI, nG))], [Z((nG, nI)), np.linalg.inv(Sh)]])
+    U1 = np.block([[D, E], [Z((nG, nI)), Sh]])
+    Bp = L1 @ M @ U1
+    # B = [D E; F, F D^-1 E + S_hat] (the product of the three factors)
+    assert np.abs(Bp[nI:, nI:] - (F @ np.linalg.solve(D, E) + Sh)).max() <= 1e-10 * np.abs(Bp).max()
+    y = W.uniform(1, A.n)
+    x = P.apply(y)
+    xp = np.linalg.solve(Bp, y[perm])
+    ref = np.zeros(A.n)
+    ref[perm] = xp
+    assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_apply_solves_B_with_F_forward_and_E_backward():
+    """Algorithm 2 printed with (E z1) forward and (F x2) backward is not even
+    well-typed (E is n_I x n_G); with F forward and E backward the apply
+    solves B x = y for B = C with its (2,2) block replaced by F D^-1 E + S_hat."""
+    A, part, perm, agg = _small(n=8, m=2, sz=10)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 2, O.LUM, perm=perm, agg_offsets=agg)
+    C = A.to_dense()
+    y = W.uniform(2, A.n)
+    x = P.apply(y)
+    # B x = y with B = C except its (2,2) block is F D^-1 E + S_hat
+    a = P.agg_offsets()
+    Sh = sla.block_diag(*[P.schur_block(i) for i in range(len(a) - 1)])
+    Bp = Cp.copy()
+    Bp[nI:, nI:] = F @ np.linalg.solve(D, E) + Sh
+    r = Bp @ x[perm] - y[perm]
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(y)
+
+
+# --------------------------------------------------------------------------
+# Spectrum: eig(C B^-1) = {1 (n_I times)} U eig(S S_hat^-1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [O.MSCE_INF, O.MSCN, O.LUM])
+def test_right_preconditioned_spectrum(kind):
+    A, part, perm, agg = _small(n=7, m=2, sz=12, seed=4)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 2, kind, perm=perm, agg_offsets=agg)
+    C = A.to_dense()
+    Binv = np.column_stack([P.apply(e) for e in np.eye(A.n)])
+    ev = np.linalg.eigvals(C @ Binv)
+    a = P.agg_offsets()
+    Sh = sla.block_diag(*[P.schur_block(i) for i in range(len(a) - 1)])
+    S = _brute_S(D, E, F, G)
+    ev_s = np.linalg.eigvals(S @ np.linalg.inv(Sh))
+    expect = np.concatenate([np.ones(nI), ev_s])
+    # match each expected eigenvalue to a distinct computed one
+    remaining = list(ev)
+    for lam in sorted(expect, key=lambda z: (z.real, z.imag)):
+        d = [abs(lam - mu) for mu in remaining]
+        k = int(np.argmin(d))
+        assert d[k] <= 1e-8 * max(1.0, abs(lam)), (lam, d[k])
+        remaining.pop(k)
+
+
+# --------------------------------------------------------------------------
+# GMRES
+# --------------------------------------------------------------------------
+def test_exact_schur_converges_in_one_iteration():
+    w = W.cavity32()
+    P = O.OracleDD(w.A, w.part, w.m, O.EXACT, perm=w.perm)
+    r = P.fgmres(w.b, tol=1e-8, restart=50)
+    assert r["status"] == 0 and r["iters"] == 1 and r["relres"] <= 1e-8
+
+
+def test_single_aggregate_msce_is_exact():
+    A, part, perm, agg = _small(n=8, m=4)
+    nG = int((part < 0).sum())
+    b = W.uniform(0, A.n)
+    r1 = O.OracleDD(A, part, 4, O.EXACT, perm=perm).fgmres(b)
+    r2 = O.OracleDD(A, part, 4, O.MSCE_INF, perm=perm, sz=nG).fgmres(b)
+    assert r1["iters"] == r2["iters"] == 1
+    assert np.abs(r1["x"] - r2["x"]).max() <= 1e-12 * np.abs(r1["x"]).max()
+
+
+def test_unpreconditioned_gmres_terminates_in_n_steps():
+    A, _ = W.mac_system(4, nu=0.05, wind=W.WIND_POLY)
+    part = np.zeros(A.n, np.int32)
+    P = O.OracleDD(A, part, 1, O.IDENTITY)
+    b = W.uniform(3, A.n)
+    r = P.fgmres(b, tol=1e-12, restart=A.n, maxit=A.n)
+    assert r["status"] == 0 and r["iters"] <= A.n
+    x = np.linalg.solve(A.to_dense(), b)
+    assert np.abs(r["x"] - x).max() <= 1e-8 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("kind", [O.MSCE_INF, O.MSCN, O.LUM])
+def test_gmres_solution_matches_dense_solve(kind):
+    w = W.cavity32()
+    P = O.OracleDD(w.A, w.part, w.m, kind, perm=w.perm, agg_offsets=w.agg)
+    r = P.fgmres(w.b, tol=1e-8, restart=50)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
+    C = w.A.to_dense()
+    x = np.linalg.solve(C, w.b)
+    cond = np.linalg.cond(C)
+    assert np.linalg.norm(r["x"] - x) <= cond * 1e-8 * np.linalg.norm(x)
+    assert np.linalg.norm(w.b - C @ r["x"]) <= 1e-8 * np.linalg.norm(w.b)
+    h = r["history"]
+    assert np.all(np.diff(h[: min(len(h), 50)]) <= 1e-15)  # non-increasing within a cycle
+
+
+def test_lum_equals_mscn_when_coupling_blocks_vanish():
+    """Section 5 observation: with E_ii, F_ii zero, MSCN reduces to LUM."""
+    w = W.cavity32()
+    r_l = O.OracleDD(w.A, w.part, w.m, O.LUM, perm=w.perm, agg_offsets=w.agg).fgmres(w.b)
+    r_n = O.OracleDD(w.A, w.part, w.m, O.MSCN, perm=w.perm, agg_offsets=w.agg).fgmres(w.b)
+    assert abs(r_l["iters"] - r_n["iters"]) <= 1
+
+
+def test_stokes_pressure_schur_is_spd():
+    """m = 1, interface = all pressures, w = 0: D is SPD (Theorem 1 applies) and
+    S = G - F D^-1 E is the (pinned) pressure Schur complement, SPD."""
+    n = 6
+    A, _ = W.mac_system(n, nu=0.05, wind=W.WIND_NONE, scale=False)
+    kind, _ = W.mac_layout(n)
+    part = np.where(kind == 0, -1, 0).astype(np.int32)
+    P = O.OracleDD(A, part, 1, O.EXACT)
+    S = P.schur_block(0)
+    assert np.abs(S - S.T).max() <= 1e-12 * np.abs(S).max()
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+
+
+def test_invalid_partition_detected():
+    A, part, perm, agg = _small(n=8, m=4)
+    bad = part.copy()
+    bad[perm[-1]] = 0  # an interface node joins subdomain 0 although it couples others
+    with pytest.raises(O.OracleError) as e:
+        O.OracleDD(A, bad, 4, O.LUM)
+    assert e.value.status == 2
+
+
+def test_singular_lum_block_reported():
+    """LUM with plain chunks can hit a zero row of G_ii (a pressure node whose
+    interface neighbours fall in another chunk): reported, not shifted."""
+    A, _ = W.mac_system(16, nu=0.01, wind=W.WIND_POLY)
+    kind, _ = W.mac_layout(16)
+    part = np.where(kind == 0, -1, 0).astype(np.int32)
+    with pytest.raises(O.OracleError) as e:
+        O.OracleDD(A, part, 1, O.LUM, sz=8)
+    assert e.value.status == 4 and e.value.bad_block == 0
