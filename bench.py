@@ -1,0 +1,321 @@
+"""Benchmark: time to a 1e-8 relative residual of the algebraic-DD
+preconditioned FGMRES solve on the 256x256 MAC Oseen system (196,096
+unknowns, nu = 1e-3, seeded 8-mode Fourier wind, 64 subdomains, MSCE
+aggregates of nominal size 2048, FGMRES(50)).
+
+One step = dd_setup (interior LU, Schur blocks, their inverses) + gmres_solve
+to 1e-8, through the library's C ABI.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual & GMRES iters (learned/FP32 vs FP64 plain); apply GB/s"
+WORKLOAD = "oseen_mac_256x256_uniform_nu1e-3_fourier8_m64_msce_sz2048_fgmres50_tol1e-8"
+TOL, RESTART, MAXIT, SZ = 1e-8, 50, 3000, 2048
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def make_inputs():
+    from paper_1104_3349_gb300 import workload as W
+    w = W.fourier256()
+    agg = W.aggregates(w.A, w.part, w.perm, SZ)
+    return w, agg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx = float(f[2].split()[0])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def apply_bytes(st, elem):
+    """Algorithmic bytes of one dd_apply: both interior sweeps read L and U
+    (in-band entries), the S_hat^-1 blocks, the couplings E and F
+    (12 B per entry), y and x, the interior and interface vectors."""
+    n, nI, nG = st["n"], st["n_interior"], st["n_interface"]
+    return (2 * (elem * st["factor_nonzeros"] + 4 * nI) + st["schur_bytes"] + 12 * st["coupling_nnz"]
+            + 8 * 2 * n + elem * (4 * nI + 4 * nG))
+
+
+def run_ours(args):
+    import torch
+    from paper_1104_3349_gb300 import dd
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    dd.build()
+    dd.load()
+    w, agg = make_inputs()
+    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    b_host = torch.from_numpy(w.b).pin_memory()
+    b = b_host.to(dev)
+    x = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=precision)
+        r = P.gmres(b, x, tol=TOL, restart=RESTART, maxit=MAXIT)
+        return P, r
+
+    for _ in range(args.warmup):
+        P, r = step(prec)
+        P.close()
+    torch.cuda.synchronize()
+    barrier(ws)
+    iters, statuses, relres = [], [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            P, r = step(prec)
+            iters.append(r["iters"]); statuses.append(r["status"]); relres.append(r["relres"])
+            P.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    total_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    ms_per_step = total_ms / args.steps
+    value = ms_per_step / ws  # whole-job: ms per solved system over all ranks
+
+    # end to end through the public API with host buffers
+    x_host = torch.empty_like(b_host).pin_memory()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        bd = b_host.to(dev, non_blocking=True)
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+        r2 = P.gmres(bd, x, tol=TOL, restart=RESTART, maxit=MAXIT)
+        x_host.copy_(x, non_blocking=True)
+        P.close()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws, dev) / e2e_steps / ws
+
+    # the dominant kernels: dd_apply (two interior sweeps + interface solve)
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+    st = P.stats()
+    y = torch.from_numpy(w.b).to(dev)
+    xa = torch.empty_like(y)
+    for _ in range(5):
+        P.apply(y, xa)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    g0.record(stream)
+    for _ in range(reps):
+        P.apply(y, xa)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = g0.elapsed_time(g1) / reps
+    elem = 4 if prec == dd.DD_FP32 else 8
+    abytes = apply_bytes(st, elem)
+    P.close()
+
+    # the plain FP64 method on the same input, for comparison
+    fp64 = None
+    if prec != dd.DD_FP64 and not args.skip_fp64:
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        P, r64 = step(dd.DD_FP64)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms": h0.elapsed_time(h1), "iters": r64["iters"], "setup_ms": r64["setup_ms"],
+                "solve_ms": r64["solve_ms"], "status": r64["status"]}
+        P.close()
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = abytes / (apply_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "dd_apply (band sweeps + interface solve)",
+            "algorithmic_bytes": int(abytes), "launch_ms": round(apply_ms, 4),
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(w, agg)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dd.DD_FP32 else "f64",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": WORKLOAD, "n": int(w.A.n), "nnz": int(w.A.nnz), "subdomains": w.m,
+                       "interface": int(st["n_interface"]), "aggregates": int(st["n_agg"]),
+                       "preconditioner": f"{args.prec} factors, FP64 FGMRES(50)",
+                       "l2": "inputs larger than L2 (factors %.0f MB)" % (2 * st["factor_bytes"] / 1e6),
+                       "parallelism": f"replicas x{ws}"},
+            "gmres_iters": iters[0] if iters else None, "gmres_iters_all": iters,
+            "relres_true": max(relres) if relres else None, "status": statuses,
+            "apply_ms": round(apply_ms, 4), "apply_gbs": round(achieved, 1),
+            "fp64_plain": fp64,
+            "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(8 * w.A.n),
+                    "d2h_bytes_per_step": int(8 * w.A.n),
+                    "note": "C, partition and aggregates enter dd_setup as host arrays in both numbers"},
+            "roofline": roof, "clocks": clk.summary(), "gpu_launches": None,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, agg):
+    """The FP64 oracle on the host cores: full setup + FGMRES(50) to 1e-8."""
+    import oracle as O
+    t0 = time.perf_counter()
+    R = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=agg)
+    t1 = time.perf_counter()
+    r = R.fgmres(w.b, tol=TOL, restart=RESTART, maxit=MAXIT)
+    t2 = time.perf_counter()
+    R.close()
+    return {"value": round(1e3 * (t2 - t0), 1), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "the full workload: one oracle setup + FGMRES(50) solve to 1e-8",
+            "setup_ms": round(1e3 * (t1 - t0), 1), "solve_ms": round(1e3 * (t2 - t1), 1),
+            "iters": r["iters"], "status": r["status"]}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    w, agg = make_inputs()
+    for _ in range(min(args.warmup, 1)):
+        cpu_baseline(w, agg)
+    vals, its = [], []
+    for _ in range(args.steps):
+        c = cpu_baseline(w, agg)
+        vals.append(c["value"]); its.append(c["iters"])
+    import oracle as O
+    v = sum(vals) / len(vals)
+    line = {"metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": int(w.A.n), "subdomains": w.m},
+            "gmres_iters": its[0],
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "full oracle setup + FGMRES(50) solve per step; warm-up capped at 1"},
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

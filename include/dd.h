@@ -1,0 +1,183 @@
+/*
+ * dd.h - C ABI of the GB300 (sm_103a) library for algebraic domain-decomposition
+ * preconditioned GMRES on saddle-point systems C = [D E^T; -E 0] (linearised
+ * Picard/Oseen Navier-Stokes, Section 1 of Kumar, "Purely algebraic domain
+ * decomposition methods for the incompressible Navier-Stokes equations").
+ *
+ * Conventions for every entry point:
+ *   - Plain pointers and sizes only.  "host" pointers are read during the call
+ *     and copied; "device" pointers must be CUDA device memory of the current
+ *     device, 8-byte aligned, and stay owned by the caller.
+ *   - All device work is ordered on the caller's stream (a cudaStream_t passed
+ *     as void*; NULL means the legacy default stream).
+ *   - Errors are returned as dd_status codes; nothing aborts or throws across
+ *     the ABI.  dd_last_error(h) gives a one-line description of the last error
+ *     on a handle (or of the last failed dd_setup when h is NULL).
+ *   - A handle is not thread-safe; distinct handles may be used concurrently on
+ *     distinct streams.
+ *   - Device memory is allocated only inside dd_setup (stream-ordered) and
+ *     released by dd_destroy; dd_apply and gmres_solve allocate nothing.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DD_OK = 0,
+  DD_ERR_INVALID_ARG = 1,       /* bad sizes, pointers, kinds or options       */
+  DD_ERR_INVALID_PARTITION = 2, /* part/perm inconsistent, or an entry couples
+                                   two different interiors (the separator
+                                   property of Section 1 is violated)          */
+  DD_ERR_SINGULAR_BLOCK = 3,    /* an interior block A_jj failed the pivot test */
+  DD_ERR_SINGULAR_SCHUR = 4,    /* a block S_ii of S_hat (or the D_ii of MSCN)
+                                   failed the pivot test                       */
+  DD_ERR_NOT_CONVERGED = 5,     /* maxit reached; x holds the last iterate     */
+  DD_ERR_NONFINITE = 6,         /* NaN/Inf in the input or in a residual       */
+  DD_ERR_TIMEOUT = 7,           /* a bounded device wait gave up               */
+  DD_ERR_OOM = 8,               /* device or host allocation failed            */
+  DD_ERR_CUDA = 9               /* a CUDA runtime call failed                  */
+} dd_status;
+
+/* Approximation of the interface Schur complement S = G - F D^-1 E
+ * (Section 3, Algorithm 1).  Aggregates R_i are runs of consecutive
+ * interface indices (eq. aggrV). */
+typedef enum {
+  DD_EXACT = 0,    /* S itself (one aggregate holding the whole interface)     */
+  DD_MSCE_INF = 1, /* S(R_i,R_i): mini Schur complements over every interior
+                      adjacent to the aggregate (MSCE with unbounded radius,
+                      the block-Jacobi reading that ends Section 3.3)          */
+  DD_MSCN = 2,     /* G_ii - F_ii D_ii^-1 E_ii, principal blocks with the same
+                      local index range (Algorithm 1, MSCN)                    */
+  DD_MSCNR = 3,    /* G_ii - diag(F_ii D_ii^-1 E_ii 1) (Algorithm 1, MSCNR)     */
+  DD_LUM = 4       /* G_ii (Definition of LUM)                                  */
+} dd_approx;
+
+typedef enum {
+  DD_FP64 = 0,     /* preconditioner factors and apply in FP64                 */
+  DD_FP32 = 1      /* factors and apply in FP32 (FP64 in/out); Krylov in FP64  */
+} dd_prec;
+
+/* C in CSR form, original numbering (host, copied). */
+typedef struct {
+  int64_t n;               /* number of rows = columns                      */
+  int64_t nnz;             /* rowptr[n]                                     */
+  const int32_t *rowptr;   /* n+1 entries, rowptr[0] = 0, non-decreasing    */
+  const int32_t *col;      /* nnz column indices in [0, n)                  */
+  const double *val;       /* nnz values, finite                            */
+} dd_csr;
+
+/* The algebraic partition P^T C P (Section 1; Section 3.2, matrix view). */
+typedef struct {
+  int32_t m;                   /* number of subdomains (interiors), >= 1         */
+  const int32_t *part;         /* n entries: 0..m-1 interior, -1 interface       */
+  const int32_t *perm;         /* optional n entries, new->old: the interiors of
+                                  subdomain 0 in their local order, then 1, ...,
+                                  then the interface; NULL = ascending original
+                                  index inside each group                        */
+  int32_t sz;                  /* nominal aggregate size (eq. aggrV) used when
+                                  agg_offsets is NULL; ignored for DD_EXACT      */
+  const int32_t *agg_offsets;  /* optional n_agg+1 offsets into the interface
+                                  numbering, strictly increasing from 0 to n_G   */
+  int32_t n_agg;
+} dd_partition;
+
+typedef struct {
+  dd_prec prec;       /* DD_FP64 or DD_FP32                                    */
+  double pivot_tol;   /* relative pivot test |pivot| <= tol * max|block|;
+                         <= 0 selects 1e-14 (FP64) / 1e-7 (FP32)              */
+  int32_t use_graph;  /* 1: gmres_solve replays one captured CUDA graph per
+                         Arnoldi step; 0: plain launches                       */
+  int32_t max_restart;/* largest restart length gmres_solve will be called
+                         with (its Krylov workspace is allocated by dd_setup);
+                         <= 0 selects 50                                       */
+  int32_t reserved[4];
+} dd_opts;
+
+typedef struct {
+  int32_t iters;        /* Arnoldi steps over all restarts                    */
+  int32_t restarts;
+  int32_t bad_block;    /* index of the failing block for SINGULAR_* statuses */
+  int32_t pad;
+  double relres_true;   /* ||b - C x|| / ||b|| at return                      */
+  double setup_ms;      /* device time of dd_setup (set by dd_setup's handle) */
+  double solve_ms;      /* device time of gmres_solve                         */
+  double *history;      /* optional host array: Givens residual estimate
+                           |g_{j+1}| / ||b|| after every Arnoldi step          */
+  int32_t history_cap;
+  int32_t pad2;
+} dd_info;
+
+/* Sizes and byte counts of a built preconditioner (host struct filled by
+ * dd_get_stats). */
+typedef struct {
+  int64_t n, n_interior, n_interface, nnz;
+  int32_t m, n_agg, max_agg, kl_max, ku_max, tile;
+  int64_t factor_bytes;      /* bytes of interior factors read by one band solve */
+  int64_t factor_nonzeros;   /* in-band entries of L and U (no padding)          */
+  int64_t schur_bytes;       /* bytes of S_hat^-1 blocks read by one apply       */
+  int64_t coupling_nnz;      /* nnz(E) + nnz(F)                                  */
+  double setup_ms;           /* device time of the last dd_setup                 */
+} dd_stats;
+
+/*
+ * Build the preconditioner B = [D 0; F S_hat][D^-1 0; 0 S_hat^-1][D E; 0 S_hat]
+ * (Definition of B_MSCN, eq. NDfactor) with S_hat per `approx` (Algorithm 1).
+ * Every interior block A_jj is factored exactly with partial pivoting
+ * (Section 4), S_hat's blocks are formed and inverted on the device.
+ *   csr, part: host, copied.  opts may be NULL (FP64, default pivot test).
+ *   stream: cudaStream_t as void*.  handle: receives an opaque handle owning all
+ *   device workspace.  Returns DD_OK or an error; on SINGULAR_* errors the
+ *   handle is still returned (dd_get_bad_block reports the block) and must be
+ *   destroyed; on other errors *handle is NULL.  The call synchronises the
+ *   stream once at its end (to read the pivot status).
+ */
+dd_status dd_setup(const dd_csr *csr, const dd_partition *partition, dd_approx approx,
+                   const dd_opts *opts, void *stream, void **handle);
+
+/*
+ * x = B^-1 y (Algorithm 2; the lower-left block F acts in the forward sweep
+ * and the upper-right block E in the backward sweep).  y, x: device, n
+ * doubles, original numbering; may not alias.  Asynchronous on stream.
+ */
+dd_status dd_apply(void *handle, const double *y, double *x, void *stream);
+
+/*
+ * Solve C x = b with right-preconditioned restarted flexible GMRES
+ * (Section 5): x0 = 0, restart length `restart`, classical Gram-Schmidt
+ * applied twice, Givens rotations, stop when the Givens estimate
+ * |g_{j+1}|/||b|| <= tol and the true residual ||b - Cx||/||b|| <= tol.
+ *   b, x: device, n doubles.  info: host, may be NULL.  Krylov vectors, SpMV
+ *   and the Hessenberg least squares are FP64 whatever the preconditioner's
+ *   precision.  Synchronises the stream once per Arnoldi step (to read the
+ *   residual estimate).  Returns DD_OK, DD_ERR_NOT_CONVERGED (x = last
+ *   iterate) or DD_ERR_NONFINITE.
+ */
+dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int32_t restart,
+                      int32_t maxit, dd_info *info, void *stream);
+
+/* y = C x with the handle's copy of C (device pointers, n doubles). */
+dd_status dd_spmv(void *handle, const double *x, double *y, void *stream);
+
+/* Fill *stats (host). */
+dd_status dd_get_stats(void *handle, dd_stats *stats);
+
+/* Block index behind the last SINGULAR_* status of this handle, or -1. */
+int32_t dd_get_bad_block(void *handle);
+
+/* Release every device allocation of the handle (stream-ordered on the
+ * handle's setup stream, then synchronised). */
+dd_status dd_destroy(void *handle);
+
+/* One-line description of the last error (handle NULL: last dd_setup). */
+const char *dd_last_error(void *handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

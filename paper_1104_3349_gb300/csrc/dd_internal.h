@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libdd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dd.h"
+
+// Tile width of the blocked band sweeps: one warp owns a tile's columns.
+#define DD_NB 32
+
+// Per-subdomain geometry of the interior factors (device-visible).
+struct BandInfo {
+  int32_t n;        // rows of A_jj
+  int32_t kl, ku;   // lower / upper bandwidth of A_jj in its local order
+  int32_t ntiles;   // ceil(n / DD_NB)
+  int64_t band_off; // offset of the band rows (elements): row i at band_off + i*wd
+  int64_t lm_off;   // offset of the unpermuted multipliers, n*kl entries
+  int64_t piv_off;  // offset into the pivot array (n entries)
+  int64_t ltile_off;// offset of the forward tiles (elements)
+  int64_t utile_off;// offset of the backward tiles (elements)
+  int64_t src_off;  // offset of the forward window permutations (int32)
+  int32_t row0;     // first row in the permuted interior numbering
+  int32_t pad;
+};
+
+__host__ __device__ inline int bi_wd(const BandInfo &b) { return 2 * b.kl + b.ku + 1; }
+__host__ __device__ inline int bi_ku2(const BandInfo &b) { return b.kl + b.ku; }
+// window length of a forward tile and its element count:
+//   Linv (NB x NB, column-major) + L21 (kl x NB, column-major)
+__host__ __device__ inline int64_t bi_ltile_elems(const BandInfo &b) {
+  return (int64_t)DD_NB * DD_NB + (int64_t)b.kl * DD_NB;
+}
+//   Uinv (NB x NB, column-major) + U12 (ku2 x NB, stored [q][i])
+__host__ __device__ inline int64_t bi_utile_elems(const BandInfo &b) {
+  return (int64_t)DD_NB * DD_NB + (int64_t)bi_ku2(b) * DD_NB;
+}
+
+// Device-side error word: first failure wins.
+struct DevStatus {
+  int32_t code;   // 0 ok, else a dd_status
+  int32_t block;  // failing block
+};
+
+struct Workspace;  // defined in dd_api.cu
+
+// ---- kernels exposed to dd_api.cu (implemented in k_band.cu / k_dense.cu /
+// ---- k_krylov.cu).  All return cudaGetLastError() of their launch.
+size_t band_sweep_smem_bytes(int max_n, int max_kl, int max_ku2, int threads, int elem_size);
+template <typename T>
+cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *lm,
+                           int32_t *piv, double pivtol, DevStatus *st, int threads, cudaStream_t s);
+template <typename T>
+cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
+                              const T *band, const T *lm, const int32_t *piv, T *ltile, T *utile,
+                              int32_t *src, cudaStream_t s);
+// z = A_jj^-1 y_j per subdomain; y gathered through perm (original
+// numbering), z in the interior numbering.
+template <typename T>
+cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
+                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
+                                  const double *y, const int32_t *perm, T *z, int threads,
+                                  cudaStream_t s);
+// x1 = z1 - A^-1 (E z2) per subdomain, scattered to x (original numbering).
+template <typename T>
+cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
+                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
+                                  const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
+                                  const T *z2, const T *z1, const int32_t *perm, double *x,
+                                  int threads, cudaStream_t s);
+// X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
+// at x_off[j], ncols[j] columns.
+template <typename T>
+cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t *ncols,
+                                    const int64_t *x_off, int max_cols, int max_kl, int max_ku2,
+                                    const T *ltile, const T *utile, const int32_t *src, T *X,
+                                    cudaStream_t s);
+
+// Dense blocks (k_dense.cu): block b of size p[b] at offset off[b], row-major.
+template <typename T>
+cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off, const T *A,
+                              T *amax, cudaStream_t s);
+// In-place explicit inverses (Gauss-Jordan, partial pivoting); ipiv holds
+// p[b] entries per block at poff[b]; failing blocks are flagged and reported
+// through st with status_code.
+template <typename T>
+cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
+                              int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
+                              double pivtol, DevStatus *st, int status_code, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *val, T *dst,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_schur_accumulate(int m, const int32_t *fr_ptr, const int32_t *fr_row,
+                                    const int32_t *fr_agg, const int32_t *f_ptr,
+                                    const int32_t *f_col, const T *f_val, const int32_t *gam_ptr,
+                                    const int32_t *gam_idx, const int32_t *gam_agg,
+                                    const int64_t *x_off, const BandInfo *d_info, const T *X,
+                                    const int32_t *agg_off, const int64_t *s_off, T *S,
+                                    int max_fr, int max_gam, cudaStream_t s);
+template <typename T>
+cudaError_t launch_block_gemm(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
+                              const T *A, const T *B, T *C, T alpha, T beta, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mscnr_diag(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
+                              const T *Dinv, const T *E, const T *F, T *S, cudaStream_t s);
+// z2 = S_hat^-1 (y2 - F z1) with explicit inverses; also writes x2 = z2 to x
+// (original numbering).
+template <typename T>
+cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
+                               const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
+                               const T *f_val, const double *y, const int32_t *perm_iface,
+                               const T *z1, T *z2, double *x, cudaStream_t s);
+
+// Krylov (k_krylov.cu), FP64
+cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                        const double *x, double *y, cudaStream_t s);
+cudaError_t launch_residual(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                            const double *x, const double *b, double *r, cudaStream_t s);
+cudaError_t launch_multidot(int n, int k, const double *V, int64_t ldv, const double *w,
+                            double *partial, int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_cols(int nblocks, int k, const double *partial, double *out,
+                               int accumulate, cudaStream_t s);
+cudaError_t launch_gemv_sub(int n, int k, const double *V, int64_t ldv, const double *h,
+                            double *w, cudaStream_t s);
+cudaError_t launch_copy_scaled(int n, const double *src, const double *nrm_sq, double *dst,
+                               cudaStream_t s);
+cudaError_t launch_scale_by(int n, const double *scal, double *w, cudaStream_t s);
+cudaError_t launch_givens2(int j, int R, double *H, const double *hc1, const double *hc2,
+                           const double *nsq, double *cs, double *sn, double *g, double bnorm,
+                           double *out, cudaStream_t s);
+cudaError_t launch_hess_solve_update(int n, int jlast, int R, const double *H, const double *g,
+                                     double *y, const double *Z, int64_t ldz, double *x,
+                                     cudaStream_t s);
+cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s);
+cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);

@@ -1,0 +1,404 @@
+// Interface blocks: assembly of the mini Schur complements S_ii (Algorithm 1),
+// their explicit inverses (Gauss-Jordan with partial pivoting, the same pivot
+// sequence as LU with partial pivoting), and the interface step of the apply
+// z2_i = S_ii^-1 (y2 - F z1)_i (Algorithm 2).
+//
+// Dense blocks are stored row-major, block b at offset off[b], size p[b].
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dd_internal.h"
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
+
+__device__ void set_status2(DevStatus *st, int code, int block) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->block = block;
+}
+
+template <typename T>
+__global__ void block_amax_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                  const T *__restrict__ A, T *amax) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  const T *a = A + off[b];
+  T mx = T(0);
+  for (int64_t q = threadIdx.x; q < (int64_t)p * p; q += blockDim.x) mx = fmax(mx, tabs(a[q]));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ T red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m2 = T(0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
+    amax[b] = m2;
+  }
+}
+
+// Step k, part 1 (one CTA per block): pivot = first row >= k holding the
+// largest |A(i,k)|, exchange rows, normalise the pivot row in place.
+template <typename T>
+__global__ void gj_pivot_kernel(int k, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                T *A, int32_t *ipiv, const int64_t *__restrict__ poff,
+                                const T *__restrict__ amax, double pivtol, int32_t *failed,
+                                DevStatus *st, int code) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  if (k >= p || failed[b]) return;
+  T *a = A + off[b];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ T bv[32];
+  __shared__ int bi[32];
+  __shared__ int s_piv;
+  T best = T(-1);
+  int besti = p;
+  for (int i = k + tid; i < p; i += blockDim.x) {
+    T v = tabs(a[(int64_t)i * p + k]);
+    if (v > best) { best = v; besti = i; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+    if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
+  }
+  if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
+  __syncthreads();
+  if (tid == 0) {
+    T bb = bv[0];
+    int ii = bi[0];
+    for (int w = 1; w < nw; ++w)
+      if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
+    if (!(bb > T(pivtol) * amax[b])) {
+      failed[b] = 1;
+      set_status2(st, code, b);
+      ii = -1;
+    }
+    s_piv = ii;
+    if (ii >= 0) ipiv[poff[b] + k] = ii;
+  }
+  __syncthreads();
+  const int pr = s_piv;
+  if (pr < 0) return;
+  if (pr != k)
+    for (int c = tid; c < p; c += blockDim.x) {
+      T t = a[(int64_t)k * p + c];
+      a[(int64_t)k * p + c] = a[(int64_t)pr * p + c];
+      a[(int64_t)pr * p + c] = t;
+    }
+  __syncthreads();
+  const T pv = a[(int64_t)k * p + k];
+  __syncthreads();
+  for (int c = tid; c < p; c += blockDim.x) {
+    T v = (c == k) ? T(1) : a[(int64_t)k * p + c];
+    a[(int64_t)k * p + c] = v / pv;
+  }
+}
+
+// Step k, part 2: eliminate column k from every other row (one warp per row).
+template <typename T>
+__global__ void gj_update_kernel(int k, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                 T *A, const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k >= p || failed[b]) return;
+  T *a = A + off[b];
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= p || row == k) return;
+  const T f = a[(int64_t)row * p + k];
+  __syncwarp();
+  if (f == T(0)) return;
+  const T *pk = a + (int64_t)k * p;
+  T *ar = a + (int64_t)row * p;
+  for (int c = lane; c < p; c += 32) {
+    T v = (c == k) ? T(0) : ar[c];
+    ar[c] = v - f * pk[c];
+  }
+}
+
+// Undo the row exchanges as column exchanges in reverse order.
+template <typename T>
+__global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                     T *A, const int32_t *__restrict__ ipiv,
+                                     const int64_t *__restrict__ poff,
+                                     const int32_t *__restrict__ failed) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  if (failed[b]) return;
+  T *a = A + off[b];
+  for (int k = p - 1; k >= 0; --k) {
+    const int q = ipiv[poff[b] + k];
+    if (q != k)
+      for (int r = threadIdx.x; r < p; r += blockDim.x) {
+        T t = a[(int64_t)r * p + k];
+        a[(int64_t)r * p + k] = a[(int64_t)r * p + q];
+        a[(int64_t)r * p + q] = t;
+      }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void scatter_coo_kernel(int64_t nnz, const int64_t *__restrict__ idx,
+                                   const double *__restrict__ val, T *dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nnz) dst[idx[i]] += T(val[i]);
+}
+
+// S(R_a, R_a) -= F(r, I_j) X_j(:, c) for every interface pair (r, c) that
+// the subdomain j couples (r: rows of F into I_j, c: columns of E from I_j)
+// and that fall into the same aggregate a.
+template <typename T>
+__global__ void schur_accumulate_kernel(const int32_t *__restrict__ fr_ptr,
+                                        const int32_t *__restrict__ fr_row,
+                                        const int32_t *__restrict__ fr_agg,
+                                        const int32_t *__restrict__ f_ptr,
+                                        const int32_t *__restrict__ f_col,
+                                        const T *__restrict__ f_val,
+                                        const int32_t *__restrict__ gam_ptr,
+                                        const int32_t *__restrict__ gam_idx,
+                                        const int32_t *__restrict__ gam_agg,
+                                        const int64_t *__restrict__ x_off,
+                                        const BandInfo *__restrict__ info, const T *__restrict__ X,
+                                        const int32_t *__restrict__ agg_off,
+                                        const int64_t *__restrict__ s_off, T *S) {
+  const int j = blockIdx.x;
+  const int r_lo = fr_ptr[j], r_hi = fr_ptr[j + 1];
+  const int rr = r_lo + blockIdx.y;
+  if (rr >= r_hi) return;
+  const int g_lo = gam_ptr[j], g_hi = gam_ptr[j + 1];
+  const int nj = info[j].n;
+  const T *Xj = X + x_off[j];
+  const int a = fr_agg[rr];
+  const int row = fr_row[rr];
+  const int p = agg_off[a + 1] - agg_off[a];
+  T *Sa = S + s_off[a];
+  for (int g = g_lo + threadIdx.x; g < g_hi; g += blockDim.x) {
+    if (gam_agg[g] != a) continue;
+    const int col = gam_idx[g];
+    const T *xc = Xj + (int64_t)(g - g_lo) * nj;
+    T s = T(0);
+    for (int k = f_ptr[rr]; k < f_ptr[rr + 1]; ++k) s += f_val[k] * xc[f_col[k]];
+    atomicAdd(&Sa[(int64_t)(row - agg_off[a]) * p + (col - agg_off[a])], -s);
+  }
+}
+
+// C = alpha * A B + beta * C for square blocks (row-major), 16x16 tiles.
+template <typename T>
+__global__ void block_gemm_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                  const T *__restrict__ A, const T *__restrict__ B, T *C, T alpha,
+                                  T beta) {
+  const int b = blockIdx.z;
+  const int p = P[b];
+  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+  if (r0 >= p || c0 >= p) return;
+  const T *a = A + off[b];
+  const T *bb = B + off[b];
+  T *c = C + off[b];
+  __shared__ T As[16][17], Bs[16][17];
+  const int tr = threadIdx.y, tc = threadIdx.x;
+  T acc = T(0);
+  for (int k0 = 0; k0 < p; k0 += 16) {
+    As[tr][tc] = (r0 + tr < p && k0 + tc < p) ? a[(int64_t)(r0 + tr) * p + k0 + tc] : T(0);
+    Bs[tr][tc] = (k0 + tr < p && c0 + tc < p) ? bb[(int64_t)(k0 + tr) * p + c0 + tc] : T(0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc += As[tr][q] * Bs[q][tc];
+    __syncthreads();
+  }
+  if (r0 + tr < p && c0 + tc < p) {
+    T *o = &c[(int64_t)(r0 + tr) * p + c0 + tc];
+    *o = alpha * acc + beta * *o;
+  }
+}
+
+// MSCNR: S -= diag(F Dinv E 1), one CTA per block.
+template <typename T>
+__global__ void mscnr_diag_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                  const T *__restrict__ Dinv, const T *__restrict__ E,
+                                  const T *__restrict__ F, T *S) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  extern __shared__ unsigned char smraw[];
+  T *v = reinterpret_cast<T *>(smraw);
+  T *w = v + p;
+  const T *e = E + off[b], *d = Dinv + off[b], *f = F + off[b];
+  T *s = S + off[b];
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    T acc = T(0);
+    for (int c = 0; c < p; ++c) acc += e[(int64_t)r * p + c];
+    v[r] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    T acc = T(0);
+    for (int c = 0; c < p; ++c) acc += d[(int64_t)r * p + c] * v[c];
+    w[r] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    T acc = T(0);
+    for (int c = 0; c < p; ++c) acc += f[(int64_t)r * p + c] * w[c];
+    s[(int64_t)r * p + r] -= acc;
+  }
+}
+
+// z2 = S_hat^-1 (y2 - F z1): each CTA rebuilds t for its aggregate in shared
+// memory, then computes DD_SROWS rows of the block product (warp per row).
+#define DD_SROWS 32
+template <typename T>
+__global__ void schur_apply_kernel(const int32_t *__restrict__ agg_off,
+                                   const int64_t *__restrict__ s_off, const T *__restrict__ Sinv,
+                                   const int32_t *__restrict__ f_ptr, const int32_t *__restrict__ f_col,
+                                   const T *__restrict__ f_val, const double *__restrict__ y,
+                                   const int32_t *__restrict__ perm_iface, const T *__restrict__ z1,
+                                   T *z2, double *x) {
+  const int a = blockIdx.y;
+  const int g0 = agg_off[a], p = agg_off[a + 1] - g0;
+  const int rbase = blockIdx.x * DD_SROWS;
+  if (rbase >= p) return;
+  extern __shared__ unsigned char smraw[];
+  T *t = reinterpret_cast<T *>(smraw);
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    const int g = g0 + r;
+    T s = T(y[perm_iface[g]]);
+    for (int k = f_ptr[g]; k < f_ptr[g + 1]; ++k) s -= f_val[k] * z1[f_col[k]];
+    t[r] = s;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T *Sa = Sinv + s_off[a];
+  for (int rr = warp; rr < DD_SROWS; rr += nw) {
+    const int r = rbase + rr;
+    if (r >= p) break;
+    const T *row = Sa + (int64_t)r * p;
+    T acc = T(0);
+    for (int c = lane; c < p; c += 32) acc += row[c] * t[c];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      z2[g0 + r] = acc;
+      x[perm_iface[g0 + r]] = double(acc);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off, const T *A,
+                              T *amax, cudaStream_t s) {
+  if (nblk <= 0) return cudaSuccess;
+  block_amax_kernel<T><<<nblk, 256, 0, s>>>(d_p, d_off, A, amax);
+  return cudaGetLastError();
+}
+
+// Explicit inverse of every block (in place); blocks that fail the pivot test
+// are flagged and reported through st with the given status code.
+template <typename T>
+cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
+                              int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
+                              double pivtol, DevStatus *st, int status_code, cudaStream_t s) {
+  if (nblk <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(failed, 0, sizeof(int32_t) * nblk, s);
+  if (e != cudaSuccess) return e;
+  const int rows_per_cta = 8;
+  dim3 ug((pmax + rows_per_cta - 1) / rows_per_cta, nblk);
+  for (int k = 0; k < pmax; ++k) {
+    gj_pivot_kernel<T><<<nblk, 256, 0, s>>>(k, d_p, d_off, A, ipiv, d_poff, amax, pivtol, failed,
+                                            st, status_code);
+    gj_update_kernel<T><<<ug, 32 * rows_per_cta, 0, s>>>(k, d_p, d_off, A, failed);
+  }
+  gj_unscramble_kernel<T><<<nblk, 256, 0, s>>>(d_p, d_off, A, ipiv, d_poff, failed);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *val, T *dst,
+                               cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  scatter_coo_kernel<T><<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nnz, idx, val, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_schur_accumulate(int m, const int32_t *fr_ptr, const int32_t *fr_row,
+                                    const int32_t *fr_agg, const int32_t *f_ptr,
+                                    const int32_t *f_col, const T *f_val, const int32_t *gam_ptr,
+                                    const int32_t *gam_idx, const int32_t *gam_agg,
+                                    const int64_t *x_off, const BandInfo *d_info, const T *X,
+                                    const int32_t *agg_off, const int64_t *s_off, T *S,
+                                    int max_fr, int max_gam, cudaStream_t s) {
+  if (m <= 0 || max_fr <= 0 || max_gam <= 0) return cudaSuccess;
+  dim3 grid(m, max_fr);
+  schur_accumulate_kernel<T><<<grid, 128, 0, s>>>(fr_ptr, fr_row, fr_agg, f_ptr, f_col, f_val,
+                                                  gam_ptr, gam_idx, gam_agg, x_off, d_info, X,
+                                                  agg_off, s_off, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_block_gemm(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
+                              const T *A, const T *B, T *C, T alpha, T beta, cudaStream_t s) {
+  if (nblk <= 0) return cudaSuccess;
+  dim3 grid((pmax + 15) / 16, (pmax + 15) / 16, nblk);
+  block_gemm_kernel<T><<<grid, dim3(16, 16), 0, s>>>(d_p, d_off, A, B, C, alpha, beta);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mscnr_diag(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
+                              const T *Dinv, const T *E, const T *F, T *S, cudaStream_t s) {
+  if (nblk <= 0) return cudaSuccess;
+  size_t smem = sizeof(T) * 2 * (size_t)pmax;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(mscnr_diag_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  mscnr_diag_kernel<T><<<nblk, 256, smem, s>>>(d_p, d_off, Dinv, E, F, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
+                               const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
+                               const T *f_val, const double *y, const int32_t *perm_iface,
+                               const T *z1, T *z2, double *x, cudaStream_t s) {
+  if (nagg <= 0) return cudaSuccess;
+  size_t smem = sizeof(T) * (size_t)pmax;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(schur_apply_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((pmax + DD_SROWS - 1) / DD_SROWS, nagg);
+  schur_apply_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, f_ptr, f_col, f_val, y,
+                                                perm_iface, z1, z2, x);
+  return cudaGetLastError();
+}
+
+#define DD_INST_DENSE(T)                                                                          \
+  template cudaError_t launch_block_amax<T>(int, const int32_t *, const int64_t *, const T *, T *, \
+                                            cudaStream_t);                                         \
+  template cudaError_t launch_gj_inverse<T>(int, const int32_t *, const int64_t *, int, T *,      \
+                                            int32_t *, const int64_t *, const T *, int32_t *,     \
+                                            double, DevStatus *, int, cudaStream_t);              \
+  template cudaError_t launch_scatter_coo<T>(int64_t, const int64_t *, const double *, T *,       \
+                                             cudaStream_t);                                        \
+  template cudaError_t launch_schur_accumulate<T>(                                                \
+      int, const int32_t *, const int32_t *, const int32_t *, const int32_t *, const int32_t *,   \
+      const T *, const int32_t *, const int32_t *, const int32_t *, const int64_t *,              \
+      const BandInfo *, const T *, const int32_t *, const int64_t *, T *, int, int, cudaStream_t); \
+  template cudaError_t launch_block_gemm<T>(int, const int32_t *, const int64_t *, int, const T *, \
+                                            const T *, T *, T, T, cudaStream_t);                   \
+  template cudaError_t launch_mscnr_diag<T>(int, const int32_t *, const int64_t *, int, const T *, \
+                                            const T *, const T *, T *, cudaStream_t);              \
+  template cudaError_t launch_schur_apply<T>(int, const int32_t *, const int64_t *, int, const T *, \
+                                             const int32_t *, const int32_t *, const T *,          \
+                                             const double *, const int32_t *, const T *, T *,      \
+                                             double *, cudaStream_t);
+
+DD_INST_DENSE(double)
+DD_INST_DENSE(float)

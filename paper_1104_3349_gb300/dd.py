@@ -1,0 +1,229 @@
+"""ctypes binding of libdd (include/dd.h): argument marshalling only.
+
+Every step of the setup, the apply and the GMRES solve runs in the library's
+CUDA kernels; PyTorch supplies device memory and streams.  There is no CPU
+fallback: without the compiled library every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INCLUDE = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_ROOT, "_build")
+LIB_PATH = os.path.join(_PKG, "libdd.so")
+SOURCES = ["dd_api.cu", "k_band.cu", "k_dense.cu", "k_krylov.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
+
+DD_EXACT, DD_MSCE_INF, DD_MSCN, DD_MSCNR, DD_LUM = 0, 1, 2, 3, 4
+DD_FP64, DD_FP32 = 0, 1
+STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_INVALID_ARG", 2: "DD_ERR_INVALID_PARTITION",
+                3: "DD_ERR_SINGULAR_BLOCK", 4: "DD_ERR_SINGULAR_SCHUR", 5: "DD_ERR_NOT_CONVERGED",
+                6: "DD_ERR_NONFINITE", 7: "DD_ERR_TIMEOUT", 8: "DD_ERR_OOM", 9: "DD_ERR_CUDA"}
+KINDS = {"exact": DD_EXACT, "msce_inf": DD_MSCE_INF, "mscn": DD_MSCN, "mscnr": DD_MSCNR, "lum": DD_LUM}
+
+
+def _nvcc():
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (in parallel) and link libdd.so in-tree."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, "dd_internal.h"), os.path.join(_INCLUDE, "dd.h")]
+    if not force and os.path.exists(LIB_PATH):
+        t = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return LIB_PATH
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.basename(src) + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call([nvcc, "-shared", "-o", tmp, *objs, "-lcudart"])
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class dd_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class dd_partition(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("part", ctypes.c_void_p), ("perm", ctypes.c_void_p),
+                ("sz", ctypes.c_int32), ("agg_offsets", ctypes.c_void_p), ("n_agg", ctypes.c_int32)]
+
+
+class dd_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("max_restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class dd_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("bad_block", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("relres_true", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int32),
+                ("pad2", ctypes.c_int32)]
+
+
+class dd_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_interior", ctypes.c_int64), ("n_interface", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("m", ctypes.c_int32), ("n_agg", ctypes.c_int32),
+                ("max_agg", ctypes.c_int32), ("kl_max", ctypes.c_int32), ("ku_max", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("factor_bytes", ctypes.c_int64), ("factor_nonzeros", ctypes.c_int64),
+                ("schur_bytes", ctypes.c_int64), ("coupling_nnz", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+
+
+EXPORTS = ["dd_setup", "dd_apply", "gmres_solve", "dd_spmv", "dd_get_stats", "dd_get_bad_block",
+           "dd_destroy", "dd_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdd.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdd.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.dd_setup.restype = ctypes.c_int
+    lib.dd_setup.argtypes = [ctypes.POINTER(dd_csr), ctypes.POINTER(dd_partition), ctypes.c_int,
+                             ctypes.POINTER(dd_opts), vp, ctypes.POINTER(vp)]
+    lib.dd_apply.restype = ctypes.c_int
+    lib.dd_apply.argtypes = [vp, vp, vp, vp]
+    lib.gmres_solve.restype = ctypes.c_int
+    lib.gmres_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.POINTER(dd_info), vp]
+    lib.dd_spmv.restype = ctypes.c_int
+    lib.dd_spmv.argtypes = [vp, vp, vp, vp]
+    lib.dd_get_stats.restype = ctypes.c_int
+    lib.dd_get_stats.argtypes = [vp, ctypes.POINTER(dd_stats)]
+    lib.dd_get_bad_block.restype = ctypes.c_int32
+    lib.dd_get_bad_block.argtypes = [vp]
+    lib.dd_destroy.restype = ctypes.c_int
+    lib.dd_destroy.argtypes = [vp]
+    lib.dd_last_error.restype = ctypes.c_char_p
+    lib.dd_last_error.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, msg: str, bad_block: int = -1):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.bad_block = bad_block
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class DD:
+    """One preconditioner B built by dd_setup; owns the library handle."""
+
+    def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
+                 pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True):
+        lib = load()
+        self._lib = lib
+        self.n = int(A.n)
+        self._arrs = [np.ascontiguousarray(A.rowptr, np.int32), np.ascontiguousarray(A.col, np.int32),
+                      np.ascontiguousarray(A.val, np.float64), np.ascontiguousarray(part, np.int32),
+                      None if perm is None else np.ascontiguousarray(perm, np.int32),
+                      None if agg_offsets is None else np.ascontiguousarray(agg_offsets, np.int32)]
+        rp, col, val, pa, pe, ag = self._arrs
+        csr = dd_csr(self.n, int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
+        pt = dd_partition(int(m), _ptr(pa), _ptr(pe), int(sz), _ptr(ag), 0 if ag is None else len(ag) - 1)
+        o = dd_opts(int(prec), float(pivot_tol), 0, int(max_restart))
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        h = ctypes.c_void_p()
+        rc = lib.dd_setup(ctypes.byref(csr), ctypes.byref(pt), k, ctypes.byref(o), _stream_handle(stream),
+                          ctypes.byref(h))
+        self._h = h
+        self.status = int(rc)
+        self.prec = int(prec)
+        self.bad_block = int(lib.dd_get_bad_block(h)) if h.value else -1
+        if rc != 0:
+            msg = lib.dd_last_error(h if h.value else None).decode()
+            if raise_on_error:
+                self.close()
+                raise DDError(rc, msg, self.bad_block)
+            self.error = msg
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DDError(rc, self._lib.dd_last_error(self._h).decode())
+
+    def apply(self, y, x, stream=None):
+        """x = B^-1 y (device tensors, float64, original numbering)."""
+        self._check(self._lib.dd_apply(self._h, _dev_ptr(y, self.n), _dev_ptr(x, self.n), _stream_handle(stream)))
+
+    def spmv(self, x, y, stream=None):
+        self._check(self._lib.dd_spmv(self._h, _dev_ptr(x, self.n), _dev_ptr(y, self.n), _stream_handle(stream)))
+
+    def gmres(self, b, x, tol=1e-8, restart=50, maxit=3000, history_cap=4096, stream=None):
+        """Right-preconditioned restarted FGMRES; returns a dict (status, iters, ...)."""
+        hist = np.zeros(history_cap)
+        info = dd_info()
+        info.history = hist.ctypes.data_as(ctypes.c_void_p).value
+        info.history_cap = history_cap
+        rc = self._lib.gmres_solve(self._h, _dev_ptr(b, self.n), _dev_ptr(x, self.n), float(tol), int(restart),
+                                   int(maxit), ctypes.byref(info), _stream_handle(stream))
+        if rc not in (0, 5, 6):
+            self._check(rc)
+        return dict(status=int(rc), iters=int(info.iters), restarts=int(info.restarts),
+                    relres=float(info.relres_true), solve_ms=float(info.solve_ms), setup_ms=float(info.setup_ms),
+                    history=hist[:min(info.iters, history_cap)].copy())
+
+    def stats(self):
+        s = dd_stats()
+        self._check(self._lib.dd_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in dd_stats._fields_}

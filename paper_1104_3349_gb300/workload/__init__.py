@@ -49,7 +49,7 @@ def _load():
                                          ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          i32p, i32p, f64p, f64p]
         lib.ddg_partition.restype = ctypes.c_int
-        lib.ddg_partition.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, i32p, i32p,
+        lib.ddg_partition.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, ctypes.c_int32, i32p, i32p,
                                       ctypes.POINTER(ctypes.c_int64)]
         lib.ddg_aggregates.restype = ctypes.c_int32
         lib.ddg_aggregates.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, i32p, ctypes.c_int32, i32p]
@@ -153,13 +153,16 @@ def mac_system(n: int, nu: float, stretch: float = 1.0, wind: int = WIND_POLY, w
     return CSR(N, rowptr, col[:nnz].copy(), val[:nnz].copy()), rhs
 
 
-def partition(A: CSR, m: int):
+IFACE_ASCENDING, IFACE_RCM = 0, 1
+
+
+def partition(A: CSR, m: int, iface_order: int = IFACE_ASCENDING):
     """Vertex-separator partition into m interiors + interface; returns (part, perm, moved)."""
     part = np.zeros(A.n, np.int32)
     perm = np.zeros(A.n, np.int32)
     stats = (ctypes.c_int64 * 2)()
     rc = _load().ddg_partition(A.n, _p(A.rowptr, ctypes.c_int32), _p(A.col, ctypes.c_int32),
-                               _p(A.val, ctypes.c_double), m, _p(part, ctypes.c_int32),
+                               _p(A.val, ctypes.c_double), m, iface_order, _p(part, ctypes.c_int32),
                                _p(perm, ctypes.c_int32), stats)
     if rc != 0:
         raise ValueError(f"ddg_partition failed (n={A.n}, m={m})")

@@ -700,12 +700,13 @@ static void rcm_order(const ddg_graph *g, const int32_t *label, int32_t lab, con
  *   part[i]  subdomain 0..m-1 of node i, or -1 for the interface
  *   perm[k]  original index of the k-th node of P^T C P: the interiors of
  *            subdomain 0 in RCM order, then subdomain 1, ..., then the
- *            interface in ascending original index
+ *            interface, in ascending original index (iface_order 0) or in
+ *            RCM order of the interface subgraph (iface_order 1)
  *   stats    [0] nodes moved by the enclosed-pressure repair
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int ddg_partition(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
-                  int32_t m, int32_t *part, int32_t *perm, int64_t *stats) {
+                  int32_t m, int32_t iface_order, int32_t *part, int32_t *perm, int64_t *stats) {
   if (n <= 0 || m <= 0 || (m & (m - 1))) return -1;
   ddg_graph g;
   if (graph_build(n, rowptr, col, &g)) return -1;
@@ -769,8 +770,14 @@ int ddg_partition(int32_t n, const int32_t *rowptr, const int32_t *col, const do
     rcm_order(&g, part, p, bucket + bstart[p], nv, &b, perm + bstart[p], seen, deg, order);
   }
   {
-    int32_t k = bstart[m];
+    int32_t k = bstart[m], k0 = bstart[m];
     for (int32_t i = 0; i < n; ++i) if (part[i] < 0) perm[k++] = i;
+    if (iface_order == 1 && k > k0) {
+      /* RCM of the interface subgraph: consecutive chunks become connected
+       * pieces of the separator */
+      for (int32_t q = k0; q < k; ++q) bucket[q - k0] = perm[q];
+      rcm_order(&g, part, -1, bucket, k - k0, &b, perm + k0, seen, deg, order);
+    }
   }
   rc = 0;
 done:
