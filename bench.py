@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-1e-8 residual & GMRES iters (learned/FP32 vs FP64 plain); apply GB/s"
 WORKLOAD = "oseen_mac_256x256_uniform_nu1e-3_fourier8_m64_msce_sz2048_fgmres50_tol1e-8"
 TOL, RESTART, MAXIT, SZ = 1e-8, 50, 3000, 2048
+# dram__bytes_read.sum + dram__bytes_write.sum of one band_solve_fwd_kernel
+# launch on this workload (ncu capture summarised in profiles/); None once the
+# kernel has changed since the capture
+TRAFFIC = {"fp32": None, "fp64": None}
 
 
 def _peaks():
@@ -130,6 +134,13 @@ def apply_bytes(st, elem):
             + 8 * 2 * n + elem * (4 * nI + 4 * nG))
 
 
+def sweep_bytes(st, elem):
+    """Algorithmic bytes of one interior solve (band_solve_fwd_kernel): the
+    in-band entries of L and U once, y gathered through perm, z1 written."""
+    nI = st["n_interior"]
+    return elem * st["factor_nonzeros"] + (8 + 4 + elem) * nI
+
+
 def run_ours(args):
     import torch
     from paper_1104_3349_gb300 import dd
@@ -160,6 +171,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(ws)
     iters, statuses, relres = [], [], []
+    launches = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -167,6 +179,7 @@ def run_ours(args):
         for _ in range(args.steps):
             P, r = step(prec)
             iters.append(r["iters"]); statuses.append(r["status"]); relres.append(r["relres"])
+            launches += P.stats()["launches"]
             P.close()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -209,6 +222,14 @@ def run_ours(args):
     apply_ms = g0.elapsed_time(g1) / reps
     elem = 4 if prec == dd.DD_FP32 else 8
     abytes = apply_bytes(st, elem)
+    # the dominant kernel alone: the interior solve z1 = D^-1 y1 (part 0)
+    g0.record(stream)
+    for _ in range(reps):
+        P.apply_part(0, y, xa)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = g0.elapsed_time(g1) / reps
+    sbytes = sweep_bytes(st, elem)
     P.close()
 
     # the plain FP64 method on the same input, for comparison
@@ -226,9 +247,11 @@ def run_ours(args):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = abytes / (apply_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "dd_apply (band sweeps + interface solve)",
-            "algorithmic_bytes": int(abytes), "launch_ms": round(apply_ms, 4),
+    s_ach = sbytes / (sweep_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(s_ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(s_ach / hbm, 4), "traffic": TRAFFIC.get(args.prec),
+            "kernel": "band_solve_fwd_kernel (interior forward+backward sweeps, all subdomains)",
+            "algorithmic_bytes": int(sbytes), "launch_ms": round(sweep_ms, 4),
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     cpu = None
@@ -253,7 +276,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(8 * w.A.n),
                     "d2h_bytes_per_step": int(8 * w.A.n),
                     "note": "C, partition and aggregates enter dd_setup as host arrays in both numbers"},
-            "roofline": roof, "clocks": clk.summary(), "gpu_launches": None,
+            "roofline": roof, "clocks": clk.summary(), "gpu_launches": int(launches),
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -301,6 +324,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def apply_only(args):
+    """One dd_setup on the bench workload, then args.apply_only dd_apply calls
+    (the command the kernel profiles in profiles/ are captured with)."""
+    import torch
+    from paper_1104_3349_gb300 import dd
+    dd.build()
+    w, agg = make_inputs()
+    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+    y = torch.from_numpy(w.b).cuda()
+    x = torch.empty_like(y)
+    for _ in range(args.apply_only):
+        P.apply(y, x)
+    torch.cuda.synchronize()
+    P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,7 +350,12 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--apply-only", type=int, default=0,
+                    help="profiling driver: one dd_setup, then this many dd_apply calls, no JSON line")
     args = ap.parse_args()
+    if args.apply_only:
+        apply_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

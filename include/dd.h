@@ -122,6 +122,7 @@ typedef struct {
   int64_t schur_bytes;       /* bytes of S_hat^-1 blocks read by one apply       */
   int64_t coupling_nnz;      /* nnz(E) + nnz(F)                                  */
   double setup_ms;           /* device time of the last dd_setup                 */
+  int64_t launches;          /* kernels this handle has launched so far          */
 } dd_stats;
 
 /*
@@ -159,6 +160,15 @@ dd_status dd_apply(void *handle, const double *y, double *x, void *stream);
  */
 dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int32_t restart,
                       int32_t maxit, dd_info *info, void *stream);
+
+/*
+ * One of the three kernels of dd_apply, for timing and profiling:
+ *   part 0: z1 = D^-1 y1 (both interior sweeps, all subdomains)
+ *   part 1: z2 = S_hat^-1 (y2 - F z1), x2 = z2 (needs part 0 first)
+ *   part 2: x1 = z1 - D^-1 (E z2) (needs parts 0 and 1 first)
+ * z1 and z2 live in the handle; y, x as in dd_apply.
+ */
+dd_status dd_apply_part(void *handle, int32_t part, const double *y, double *x, void *stream);
 
 /* y = C x with the handle's copy of C (device pointers, n doubles). */
 dd_status dd_spmv(void *handle, const double *x, double *y, void *stream);

@@ -34,6 +34,7 @@ struct DDHandle {
   int64_t n = 0, nnz = 0;
   int m = 0, nI = 0, nG = 0, nagg = 0, pmax = 0;
   int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0, sweep_threads = 256;
+  uint32_t stage_bytes = 0;
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   BandInfo *d_info = nullptr;
@@ -61,12 +62,17 @@ struct DDHandle {
 
 #define CK(call)                                                                     \
   do {                                                                               \
+    if (strncmp(#call, "launch_", 7) == 0) h->stats.launches += launch_cost(#call, h);  \
     cudaError_t e_ = (call);                                                         \
     if (e_ != cudaSuccess) {                                                         \
       h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
       return DD_ERR_CUDA;                                                            \
     }                                                                                \
   } while (0)
+
+// kernels behind one launcher call (the Gauss-Jordan inverse is 2 per pivot
+// step plus the final column exchange; the Hessenberg update is two)
+int64_t launch_cost(const char *call, const DDHandle *h);
 
 template <typename P>
 dd_status dalloc(DDHandle *h, P **p, size_t count) {
@@ -131,6 +137,7 @@ dd_status upload_T(DDHandle *h, T **p, const std::vector<double> &v) {
   TRY(upload(h, &tmp, v));
   TRY(dalloc(h, p, v.size()));
   if (!v.empty()) {
+    h->stats.launches += 1;
     convert_kernel<T><<<(unsigned)((v.size() + 255) / 256), 256, 0, h->stream>>>((int64_t)v.size(), tmp, *p);
     CK(cudaGetLastError());
   }
@@ -292,6 +299,12 @@ void extract_blocks(DDHandle *h, const dd_csr *csr, const dd_partition *pt, Host
   (void)m;
 }
 
+int64_t launch_cost(const char *call, const DDHandle *h) {
+  if (strstr(call, "launch_gj_inverse")) return 2LL * h->pmax + 1;
+  if (strstr(call, "launch_hess_solve_update")) return 2;
+  return 1;
+}
+
 }  // namespace
 
 namespace {
@@ -319,7 +332,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     b.piv_off = pivo; pivo += b.n;
     b.ltile_off = lto; lto += (int64_t)b.ntiles * bi_ltile_elems(b);
     b.utile_off = uto; uto += (int64_t)b.ntiles * bi_utile_elems(b);
-    b.src_off = srco; srco += (int64_t)b.ntiles * (DD_NB + b.kl);
+    b.src_off = srco; srco += (int64_t)b.ntiles * (((DD_NB + b.kl) + 3) & ~3);
+    h->stage_bytes = std::max(h->stage_bytes, band_stage_bytes(b.kl, b.ku, sizeof(T)));
     h->max_n = std::max(h->max_n, b.ntiles * DD_NB);
     h->max_kl = std::max(h->max_kl, b.kl);
     h->max_ku = std::max(h->max_ku, b.ku);
@@ -328,9 +342,9 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     // in-band entries of L (kl per column) and U (kl+ku+1 per row), clipped
     for (int i = 0; i < b.n; ++i) fac_nz += std::min(b.kl, b.n - 1 - i) + std::min(b.kl + b.ku, b.n - 1 - i) + 1;
     fac_bytes += (int64_t)b.ntiles * (bi_ltile_elems(b) + bi_utile_elems(b)) * sizeof(T) +
-                 (int64_t)b.ntiles * (DD_NB + b.kl) * sizeof(int32_t);
+                 (int64_t)b.ntiles * (((DD_NB + b.kl) + 3) & ~3) * sizeof(int32_t);
   }
-  if (band_sweep_smem_bytes(h->max_n, h->max_kl, h->max_ku2, h->sweep_threads, sizeof(T)) > 220 * 1024) {
+  if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->sweep_threads, sizeof(T), h->stage_bytes) < 2) {
     h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
     return DD_ERR_INVALID_ARG;
   }
@@ -359,6 +373,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(upload(h, &d_part, std::vector<int32_t>(pt->part, pt->part + h->n)));
   TRY(upload(h, &d_pos, hb.pos));
   TRY(upload(h, &h->d_perm, hb.perm));
+  h->stats.launches += 1;
   fill_band_kernel<T><<<(unsigned)((h->n + 255) / 256), 256, 0, s>>>(
       (int)h->n, h->c_rowptr, h->c_col, h->c_val, d_part, d_pos, h->d_info, B.band);
   CK(cudaGetLastError());
@@ -572,20 +587,24 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
 }
 
 template <typename T>
-dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s) {
+dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int part = -1) {
   PrecBufs<T> &B = bufs<T>(h);
-  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, B.ltile, B.utile,
-                              h->src, y, h->d_perm, B.z1, h->sweep_threads, s));
+  if (part == 0 || part < 0)
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+                              B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st,
+                              h->sweep_threads, s));
+  if (part == 1 || part < 0)
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, x, s));
-  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, B.ltile, B.utile,
-                              h->src, h->e_ptr, h->e_col, B.e_val, B.z2, B.z1, h->d_perm, x,
-                              h->sweep_threads, s));
+  if (part == 2 || part < 0)
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+                              B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, B.z2, B.z1,
+                              h->d_perm, x, h->st, h->sweep_threads, s));
   return DD_OK;
 }
 
-dd_status apply_any(DDHandle *h, const double *y, double *x, cudaStream_t s) {
-  return h->prec == DD_FP32 ? apply_T<float>(h, y, x, s) : apply_T<double>(h, y, x, s);
+dd_status apply_any(DDHandle *h, const double *y, double *x, cudaStream_t s, int part = -1) {
+  return h->prec == DD_FP32 ? apply_T<float>(h, y, x, s, part) : apply_T<double>(h, y, x, s, part);
 }
 
 }  // namespace
@@ -675,6 +694,15 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
     CK(launch_residual(n, h->c_rowptr, h->c_col, h->c_val, x, b, h->r, s));
     TRY(norm_sq(h, h->r, 3, s));
     TRY(read_scalars(h, h->nsq + 3, 1, s));
+    {
+      DevStatus dst{};
+      CK(cudaMemcpy(&dst, h->st, sizeof dst, cudaMemcpyDeviceToHost));
+      if (dst.code != 0) {
+        h->err = "device wait expired in an apply sweep";
+        rc = (dd_status)dst.code;
+        break;
+      }
+    }
     relres = sqrt(h->h_out[0]) / bnorm;
     if (!isfinite(relres)) { rc = DD_ERR_NONFINITE; break; }
     if (relres <= tol) { rc = DD_OK; break; }
@@ -783,6 +811,13 @@ dd_status dd_apply(void *handle, const double *y, double *x, void *stream) {
   if (!h || !y || !x) return DD_ERR_INVALID_ARG;
   if (h->bad_block >= 0) { h->err = "preconditioner failed in setup"; return DD_ERR_INVALID_ARG; }
   return apply_any(h, y, x, static_cast<cudaStream_t>(stream));
+}
+
+dd_status dd_apply_part(void *handle, int32_t part, const double *y, double *x, void *stream) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h || !y || !x || part < 0 || part > 2) return DD_ERR_INVALID_ARG;
+  if (h->bad_block >= 0) { h->err = "preconditioner failed in setup"; return DD_ERR_INVALID_ARG; }
+  return apply_any(h, y, x, static_cast<cudaStream_t>(stream), part);
 }
 
 dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int32_t restart,

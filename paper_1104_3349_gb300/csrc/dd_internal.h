@@ -49,7 +49,11 @@ struct Workspace;  // defined in dd_api.cu
 
 // ---- kernels exposed to dd_api.cu (implemented in k_band.cu / k_dense.cu /
 // ---- k_krylov.cu).  All return cudaGetLastError() of their launch.
-size_t band_sweep_smem_bytes(int max_n, int max_kl, int max_ku2, int threads, int elem_size);
+// Tile ring of the apply sweeps: bytes of one stage, and how many stages fit
+// next to the resident right-hand side (0: the subdomain is too large).
+uint32_t band_stage_bytes(int kl, int ku, int elem_size);
+int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
+                      uint32_t stage_bytes);
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *lm,
                            int32_t *piv, double pivtol, DevStatus *st, int threads, cudaStream_t s);
@@ -61,16 +65,18 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
 // numbering), z in the interior numbering.
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
-                                  const double *y, const int32_t *perm, T *z, int threads,
+                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
+                                  const T *utile, const int32_t *src, const double *y,
+                                  const int32_t *perm, T *z, DevStatus *st, int threads,
                                   cudaStream_t s);
 // x1 = z1 - A^-1 (E z2) per subdomain, scattered to x (original numbering).
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
-                                  const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
-                                  const T *z2, const T *z1, const int32_t *perm, double *x,
-                                  int threads, cudaStream_t s);
+                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
+                                  const T *utile, const int32_t *src, const int32_t *e_ptr,
+                                  const int32_t *e_col, const T *e_val, const T *z2, const T *z1,
+                                  const int32_t *perm, double *x, DevStatus *st, int threads,
+                                  cudaStream_t s);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>

@@ -11,18 +11,23 @@
 //   forward tile t, window rows c0 .. c0+NB+kl-1 (c0 = t*NB):
 //     src[q]   window position whose value moves to q once the tile's row
 //              exchanges are applied in order
-//     Linv     inverse of the tile's unit lower triangle (multipliers with the
-//              later exchanges of the same tile applied), column-major NB x NB
-//     L21      the kl rows below the tile, column-major (element (i,c) at c*kl+i)
+//     K        (NB+kl) x NB, column-major: rows 0..NB-1 hold Linv, the inverse
+//              of the tile's unit lower triangle L11 (multipliers with the
+//              later exchanges of the same tile applied); rows NB.. hold
+//              -L21 Linv.  The tile step is w <- [0; w_B] + K w_T on the
+//              exchanged window w.
 //   backward tile t, rows r0 .. r0+NB-1:
-//     Uinv     inverse of the NB x NB upper triangle, column-major
-//     U12      U(r0+i, r0+NB+q), stored [q*NB + i], q < kl+ku
+//     Kb       NB x (NB+kl+ku), row-major: [Uinv | -Uinv U12], Uinv the
+//              inverse of the tile's upper triangle U11 and U12 the band to
+//              its right, so x_T = Kb [b_T; x_next].
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "dd_internal.h"
 
 namespace {
+
+__host__ __device__ inline int src_stride(int kl) { return ((DD_NB + kl) + 3) & ~3; }
 
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
@@ -141,11 +146,11 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
   const int32_t *P = piv + b.piv_off;
   T *lt = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
   T *ut = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
-  int32_t *src = srcs + b.src_off + (int64_t)t * W;
+  int32_t *src = srcs + b.src_off + (int64_t)t * src_stride(kl);
   extern __shared__ unsigned char smraw[];
   T *L11 = reinterpret_cast<T *>(smraw);         // NB x NB, [row][col]
-  T *vbuf = L11 + DD_NB * DD_NB;                 // 32 columns x W
-  int32_t *idx = reinterpret_cast<int32_t *>(vbuf + (size_t)DD_NB * W);
+  T *vbuf = L11 + DD_NB * DD_NB;                 // 32 columns x W, then NB x NB
+  int32_t *idx = reinterpret_cast<int32_t *>(vbuf + (size_t)DD_NB * W + DD_NB * DD_NB);
 
   // (1) composite window permutation of the tile's row exchanges
   if (lane == 0) {
@@ -174,11 +179,11 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
       }
     }
     for (int q = 0; q < DD_NB; ++q) L11[q * DD_NB + lane] = (q == lane) ? T(1) : (q > lane ? v[q] : T(0));
-    T *L21 = lt + DD_NB * DD_NB;
-    for (int r = 0; r < kl; ++r) L21[(int64_t)lane * kl + r] = v[DD_NB + r];
   }
   __syncwarp();
-  // (3) Linv: column `lane` of the inverse of the unit lower triangle
+  // (3) Linv: column `lane` of the inverse of the unit lower triangle; then
+  //     K = [Linv; -L21 Linv], column-major (NB+kl) x NB
+  T *Lsm = vbuf + (size_t)DD_NB * W;  // NB x NB, [row][col], after the columns
   {
     T x[DD_NB];
 #pragma unroll
@@ -189,10 +194,22 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
       for (int r = lane; r < q; ++r) s += L11[q * DD_NB + r] * x[r];
       x[q] = -s;
     }
-    for (int q = 0; q < DD_NB; ++q) lt[lane * DD_NB + q] = x[q];
+    for (int q = 0; q < DD_NB; ++q) {
+      lt[(int64_t)lane * W + q] = x[q];
+      Lsm[q * DD_NB + lane] = x[q];
+    }
   }
   __syncwarp();
-  // (4) U11 (row-major in L11's buffer), Uinv, U12
+  {
+    // lane = column c of K: rows NB+r hold -sum_k L21(r,k) Linv(k,c)
+    for (int r = 0; r < kl; ++r) {
+      T s = T(0);
+      for (int k = 0; k < DD_NB; ++k) s += vbuf[(size_t)k * W + DD_NB + r] * Lsm[k * DD_NB + lane];
+      lt[(int64_t)lane * W + DD_NB + r] = -s;
+    }
+  }
+  __syncwarp();
+  // (4) U11 (row-major in L11's buffer) and its inverse; Kb = [Uinv | -Uinv U12]
   {
     const int r = c0 + lane;  // row of this lane
     for (int c = 0; c < DD_NB; ++c) {
@@ -205,16 +222,6 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
         v = T(1);
       }
       L11[lane * DD_NB + c] = v;
-    }
-    T *U12 = ut + DD_NB * DD_NB;
-    for (int q = 0; q < ku2; ++q) {
-      T v = T(0);
-      int col = c0 + DD_NB + q;
-      if (r < n && col < n) {
-        int off = col - r + kl;
-        if (off < wd) v = A[(int64_t)r * wd + off];
-      }
-      U12[(int64_t)q * DD_NB + lane] = v;
     }
   }
   __syncwarp();
@@ -229,114 +236,295 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
       for (int r = q + 1; r <= lane; ++r) s += L11[q * DD_NB + r] * x[r];
       x[q] = -s / L11[q * DD_NB + q];
     }
-    for (int q = 0; q < DD_NB; ++q) ut[lane * DD_NB + q] = x[q];
+    for (int q = 0; q < DD_NB; ++q) Lsm[q * DD_NB + lane] = x[q];  // Uinv(q, lane)
+  }
+  __syncwarp();
+  {
+    // lane = row i of Kb
+    const int KW = DD_NB + ku2;
+    T *kr = ut + (int64_t)lane * KW;
+    for (int c = 0; c < DD_NB; ++c) kr[c] = Lsm[lane * DD_NB + c];
+    for (int q = 0; q < ku2; ++q) {
+      const int col = c0 + DD_NB + q;
+      T s = T(0);
+      if (col < n)
+        for (int k = lane; k < DD_NB; ++k) {
+          const int rk = c0 + k;
+          if (rk >= n) break;
+          const int off = col - rk + kl;
+          if (off < wd) s += Lsm[lane * DD_NB + k] * A[(int64_t)rk * wd + off];
+        }
+      kr[DD_NB + q] = -s;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Single right-hand side sweeps over a vector resident in shared memory.
+// Single right-hand side sweeps (the apply).  One CTA per subdomain keeps the
+// right-hand side in shared memory; the tiles stream through a ring of
+// shared-memory stages filled by TMA bulk copies (cp.async.bulk, completion
+// on an mbarrier), forward tiles 0..T-1 then backward tiles T-1..0 as one job
+// sequence, so the copy of job q+S overlaps the arithmetic of job q.
+// Every wait on an mbarrier is bounded; on expiry the CTA records
+// DD_ERR_TIMEOUT, drains its own copies (bounded again) and returns.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+#define DD_WAIT_LIMIT (1u << 22)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < DD_WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Jobs of subdomain b: forward groups of gf consecutive tiles, then backward
+// groups of gb tiles taken from the end; one job = one bulk copy of
+// contiguous tile data (plus the forward window permutations), because a
+// copy's fixed cost is amortised only by copies of tens of kilobytes.
+struct Jobs {
+  int T, gf, gb, jf, jb;
+};
 template <typename T>
-__device__ void sweep_forward(const BandInfo &b, const T *__restrict__ ltile,
-                              const int32_t *__restrict__ srcs, T *vec, T *win, T *ysh) {
-  const int kl = b.kl, W = DD_NB + kl;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int t = 0; t < b.ntiles; ++t) {
-    const int c0 = t * DD_NB;
-    const int32_t *src = srcs + b.src_off + (int64_t)t * W;
-    const T *lt = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
-    for (int q = tid; q < W; q += nt) win[q] = vec[c0 + src[q]];
-    __syncthreads();
-    if (warp == 0) {
-      T y = T(0);
-#pragma unroll 8
-      for (int c = 0; c < DD_NB; ++c) y += lt[c * DD_NB + lane] * win[c];
-      ysh[lane] = y;
-      vec[c0 + lane] = y;
-    }
-    __syncthreads();
-    const T *L21 = lt + DD_NB * DD_NB;
-    for (int i = tid; i < kl; i += nt) {
-      T s = win[DD_NB + i];
-#pragma unroll 8
-      for (int c = 0; c < DD_NB; ++c) s -= L21[(int64_t)c * kl + i] * ysh[c];
-      vec[c0 + DD_NB + i] = s;
-    }
-    __syncthreads();
+__device__ __forceinline__ Jobs make_jobs(const BandInfo &b, uint32_t stage_bytes) {
+  Jobs J;
+  J.T = b.ntiles;
+  const uint32_t lb = (uint32_t)(bi_ltile_elems(b) * sizeof(T)) + (uint32_t)(src_stride(b.kl) * 4);
+  const uint32_t ub = (uint32_t)(bi_utile_elems(b) * sizeof(T));
+  J.gf = max(1, (int)(stage_bytes / lb));
+  J.gb = max(1, (int)(stage_bytes / ub));
+  J.jf = (J.T + J.gf - 1) / J.gf;
+  J.jb = (J.T + J.gb - 1) / J.gb;
+  return J;
+}
+// tile range [lo, hi) of job q
+__device__ __forceinline__ void job_range(const Jobs &J, int q, int &lo, int &hi) {
+  if (q < J.jf) {
+    lo = q * J.gf;
+    hi = min(J.T, lo + J.gf);
+  } else {
+    const int k = q - J.jf;
+    hi = J.T - k * J.gb;
+    lo = max(0, hi - J.gb);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void issue_job(const BandInfo &b, const Jobs &J, int q, const T *ltile,
+                                          const T *utile, const int32_t *srcs,
+                                          unsigned char *stage, uint64_t *bar) {
+  int lo, hi;
+  job_range(J, q, lo, hi);
+  const int nt = hi - lo;
+  if (q < J.jf) {
+    const uint32_t lb = (uint32_t)(bi_ltile_elems(b) * sizeof(T)) * nt;
+    const uint32_t sb = (uint32_t)(src_stride(b.kl) * sizeof(int32_t)) * nt;
+    mbar_expect_tx(bar, lb + sb);
+    bulk_g2s(stage, ltile + b.ltile_off + (int64_t)lo * bi_ltile_elems(b), lb, bar);
+    bulk_g2s(stage + lb, srcs + b.src_off + (int64_t)lo * src_stride(b.kl), sb, bar);
+  } else {
+    const uint32_t ub = (uint32_t)(bi_utile_elems(b) * sizeof(T)) * nt;
+    mbar_expect_tx(bar, ub);
+    bulk_g2s(stage, utile + b.utile_off + (int64_t)lo * bi_utile_elems(b), ub, bar);
   }
 }
 
+// Forward sweep in place over vec, backward sweep from vec into xout (both in
+// shared memory, length >= ntiles*NB + pad, xout zero beyond the tiles).
+// Returns false if a wait expired.
 template <typename T>
-__device__ void sweep_backward(const BandInfo &b, const T *__restrict__ utile, T *vec, T *part,
-                               T *ssh) {
-  const int ku2 = b.kl + b.ku;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int t = b.ntiles - 1; t >= 0; --t) {
-    const int r0 = t * DD_NB;
-    const T *ut = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
-    const T *U12 = ut + DD_NB * DD_NB;
-    T s = T(0);
-    for (int q = warp; q < ku2; q += nw) s += U12[(int64_t)q * DD_NB + lane] * vec[r0 + DD_NB + q];
-    part[warp * DD_NB + lane] = s;
-    __syncthreads();
-    if (warp == 0) {
-      T acc = vec[r0 + lane];
-      for (int w = 0; w < nw; ++w) acc -= part[w * DD_NB + lane];
-      ssh[lane] = acc;
-      __syncwarp();
-      T x = T(0);
-#pragma unroll 8
-      for (int c = 0; c < DD_NB; ++c) x += ut[c * DD_NB + lane] * ssh[c];
-      vec[r0 + lane] = x;
-    }
-    __syncthreads();
+__device__ bool sweep_pipelined(const BandInfo &b, const T *__restrict__ ltile,
+                                const T *__restrict__ utile, const int32_t *__restrict__ srcs,
+                                T *vec, T *xout, T *win, unsigned char *ring,
+                                uint32_t stage_bytes, int nstages, uint64_t *bars,
+                                DevStatus *st) {
+  const int kl = b.kl, ku2 = b.kl + b.ku, W = DD_NB + kl, KW = DD_NB + ku2;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const Jobs J = make_jobs<T>(b, stage_bytes);
+  const int nj = J.jf + J.jb;
+  if (tid == 0) {
+    for (int q = 0; q < nstages && q < nj; ++q)
+      issue_job<T>(b, J, q, ltile, utile, srcs, ring + (size_t)q * stage_bytes, &bars[q]);
   }
+  bool ok = true;
+  int q = 0;
+  for (; q < nj; ++q) {
+    const int sidx = q % nstages;
+    unsigned char *stage = ring + (size_t)sidx * stage_bytes;
+    // every thread waits (bounded); the verdict is made uniform at the
+    // first barrier of the job, so no thread can leave the loop alone
+    const bool got = mbar_wait_bounded(&bars[sidx], (uint32_t)((q / nstages) & 1));
+    int lo, hi;
+    job_range(J, q, lo, hi);
+    if (q < J.jf) {
+      const size_t lbytes = bi_ltile_elems(b) * sizeof(T);
+      const int32_t *src0 = reinterpret_cast<const int32_t *>(stage + lbytes * (hi - lo));
+      for (int t = lo; t < hi; ++t) {
+        // forward tile t: w <- [0; w_B] + K w_T on the exchanged window
+        const int c0 = t * DD_NB;
+        const T *K = reinterpret_cast<const T *>(stage + lbytes * (t - lo));
+        const int32_t *src = src0 + (size_t)src_stride(kl) * (t - lo);
+        if (got)
+          for (int e = tid; e < W; e += nt) win[e] = vec[c0 + src[e]];
+        if (!__syncthreads_and(got)) { ok = false; break; }
+        for (int r = tid; r < W; r += nt) {
+          // four independent partial sums shorten the dependent chain
+          T a0 = (r < DD_NB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+          for (int c = 0; c < DD_NB; c += 4) {
+            a0 += K[(c + 0) * W + r] * win[c + 0];
+            a1 += K[(c + 1) * W + r] * win[c + 1];
+            a2 += K[(c + 2) * W + r] * win[c + 2];
+            a3 += K[(c + 3) * W + r] * win[c + 3];
+          }
+          vec[c0 + r] = (a0 + a1) + (a2 + a3);
+        }
+        __syncthreads();
+      }
+      if (!ok) break;
+    } else {
+      const size_t ubytes = bi_utile_elems(b) * sizeof(T);
+      for (int t = hi - 1; t >= lo; --t) {
+        // backward tile t: x_T = Kb [b_T; x_next], one warp per output row;
+        // the outputs xout[r0..r0+NB) never overlap this tile's inputs
+        const int r0 = t * DD_NB;
+        const T *Kb = reinterpret_cast<const T *>(stage + ubytes * (t - lo));
+        // eight threads per output row (rows tid/8), strided over the row
+        for (int e = tid; e < DD_NB * 8; e += nt) {
+          const int i = e >> 3, h = e & 7;
+          const T *kr = Kb + i * KW;
+          T a0 = T(0), a1 = T(0);
+          if (got) {
+            int k = h;
+            for (; k < DD_NB; k += 16) {
+              a0 += kr[k] * vec[r0 + k];
+              if (k + 8 < DD_NB) a1 += kr[k + 8] * vec[r0 + k + 8];
+            }
+            for (k = DD_NB + h; k + 8 < KW; k += 16) {
+              a0 += kr[k] * xout[r0 + k];
+              a1 += kr[k + 8] * xout[r0 + k + 8];
+            }
+            if (k < KW) a0 += kr[k] * xout[r0 + k];
+          }
+          T acc = a0 + a1;
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+          if (h == 0) xout[r0 + i] = acc;
+        }
+        if (!__syncthreads_and(got)) { ok = false; break; }
+      }
+      if (!ok) break;
+    }
+    // the stage is free; vec / xout are current
+    if (tid == 0 && q + nstages < nj) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_job<T>(b, J, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
+    }
+  }
+  if (!ok) {
+    if (tid == 0) {
+      if (atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = blockIdx.x;
+    }
+    // drain the copies this CTA issued (jobs 0 .. q+nstages-1), bounded
+    const int last_issued = min(nj - 1, q + nstages - 1);
+    for (int s2 = 0; s2 < nstages; ++s2) {
+      int last = -1;
+      for (int j = s2; j <= last_issued; j += nstages) last = j;
+      if (last >= q) mbar_wait_bounded(&bars[s2], (uint32_t)((last / nstages) & 1));
+    }
+  }
+  return ok;
+}
+
+// shared-memory layout: [bars | vec | xout | win | ring]
+template <typename T>
+__device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, int max_kl,
+                                      uint64_t *&bars, T *&vec, T *&xout, T *&win,
+                                      unsigned char *&ring) {
+  bars = reinterpret_cast<uint64_t *>(smraw);
+  vec = reinterpret_cast<T *>(smraw + 64);
+  xout = vec + max_n + pad;
+  win = xout + max_n + pad;
+  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + DD_NB + max_kl);
+  used = (used + 127) & ~(size_t)127;
+  ring = smraw + used;
+}
+
+template <typename T>
+__device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstages; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 }
 
 // z = A_jj^-1 y_j with y gathered from the original numbering.
 template <typename T>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
-                                      int max_ku2, const T *__restrict__ ltile,
-                                      const T *__restrict__ utile, const int32_t *__restrict__ srcs,
-                                      const double *__restrict__ y, const int32_t *__restrict__ perm,
-                                      T *z) {
+                                      int max_ku2, int nstages, uint32_t stage_bytes,
+                                      const T *__restrict__ ltile, const T *__restrict__ utile,
+                                      const int32_t *__restrict__ srcs, const double *__restrict__ y,
+                                      const int32_t *__restrict__ perm, T *z, DevStatus *st) {
   const BandInfo b = info[blockIdx.x];
   if (b.n == 0) return;
-  extern __shared__ unsigned char smraw[];
-  T *vec = reinterpret_cast<T *>(smraw);
-  int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
-  T *win = vec + max_n + pad;
-  T *ysh = win + DD_NB + max_kl;
-  T *part = ysh + DD_NB;
-  T *ssh = part + (blockDim.x >> 5) * DD_NB;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
+  uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
+  carve<T>(smraw, max_n, pad, max_kl, bars, vec, xout, win, ring);
+  init_bars<T>(bars, nstages);
   const int ntot = b.ntiles * DD_NB + pad;
-  for (int i = threadIdx.x; i < ntot; i += blockDim.x)
+  for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
     vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
+    xout[i] = T(0);
+  }
   __syncthreads();
-  sweep_forward(b, ltile, srcs, vec, win, ysh);
-  sweep_backward(b, utile, vec, part, ssh);
-  for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = vec[i];
+  if (!sweep_pipelined<T>(b, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
+    return;
+  for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
 template <typename T>
 __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
-                                      int max_ku2, const T *__restrict__ ltile,
-                                      const T *__restrict__ utile, const int32_t *__restrict__ srcs,
+                                      int max_ku2, int nstages, uint32_t stage_bytes,
+                                      const T *__restrict__ ltile, const T *__restrict__ utile,
+                                      const int32_t *__restrict__ srcs,
                                       const int32_t *__restrict__ e_ptr,
                                       const int32_t *__restrict__ e_col,
                                       const T *__restrict__ e_val, const T *__restrict__ z2,
                                       const T *__restrict__ z1, const int32_t *__restrict__ perm,
-                                      double *x) {
+                                      double *x, DevStatus *st) {
   const BandInfo b = info[blockIdx.x];
   if (b.n == 0) return;
-  extern __shared__ unsigned char smraw[];
-  T *vec = reinterpret_cast<T *>(smraw);
-  int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
-  T *win = vec + max_n + pad;
-  T *ysh = win + DD_NB + max_kl;
-  T *part = ysh + DD_NB;
-  T *ssh = part + (blockDim.x >> 5) * DD_NB;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
+  uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
+  carve<T>(smraw, max_n, pad, max_kl, bars, vec, xout, win, ring);
+  init_bars<T>(bars, nstages);
   const int ntot = b.ntiles * DD_NB + pad;
   for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
     T v = T(0);
@@ -345,13 +533,14 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
       for (int k = e_ptr[r]; k < e_ptr[r + 1]; ++k) v += e_val[k] * z2[e_col[k]];
     }
     vec[i] = v;
+    xout[i] = T(0);
   }
   __syncthreads();
-  sweep_forward(b, ltile, srcs, vec, win, ysh);
-  sweep_backward(b, utile, vec, part, ssh);
+  if (!sweep_pipelined<T>(b, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
+    return;
   for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
     const int r = b.row0 + i;
-    x[perm[r]] = double(z1[r] - vec[i]);
+    x[perm[r]] = double(z1[r] - xout[i]);
   }
 }
 
@@ -375,42 +564,32 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
   T *X = Xall + x_off[blockIdx.x] + (int64_t)k0 * n;
   extern __shared__ unsigned char smraw[];
   T *win = reinterpret_cast<T *>(smraw);  // (NB + max(kl,ku2)) x NR, [row][r]
-  T *ysh = win + (size_t)(DD_NB + (kl > ku2 ? kl : ku2)) * NR;  // NB x NR
   const int tid = threadIdx.x, nt = blockDim.x;
-  // forward
+  const int KW = DD_NB + ku2;
+  // forward: X(window) <- [0; X_B] + K X_T on the exchanged window
   for (int t = 0; t < b.ntiles; ++t) {
     const int c0 = t * DD_NB;
-    const int32_t *src = srcs + b.src_off + (int64_t)t * W;
-    const T *lt = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
+    const int32_t *src = srcs + b.src_off + (int64_t)t * src_stride(kl);
+    const T *K = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
     for (int e = tid; e < W * NR; e += nt) {
       int q = e / NR, r = e % NR;
       int row = c0 + src[q];
       win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < DD_NB * NR; e += nt) {
+    for (int e = tid; e < W * NR; e += nt) {
       int i = e / NR, r = e % NR;
-      T y = T(0);
-      for (int c = 0; c < DD_NB; ++c) y += lt[c * DD_NB + i] * win[c * NR + r];
-      ysh[e] = y;
-      if (c0 + i < n && r < nr) X[(int64_t)r * n + c0 + i] = y;
-    }
-    __syncthreads();
-    const T *L21 = lt + DD_NB * DD_NB;
-    for (int e = tid; e < kl * NR; e += nt) {
-      int i = e / NR, r = e % NR;
-      T s = win[(DD_NB + i) * NR + r];
-      for (int c = 0; c < DD_NB; ++c) s -= L21[(int64_t)c * kl + i] * ysh[c * NR + r];
-      if (c0 + DD_NB + i < n && r < nr) X[(int64_t)r * n + c0 + DD_NB + i] = s;
+      T acc = (i < DD_NB) ? T(0) : win[e];
+      for (int c = 0; c < DD_NB; ++c) acc += K[c * W + i] * win[c * NR + r];
+      if (c0 + i < n && r < nr) X[(int64_t)r * n + c0 + i] = acc;
     }
     __syncthreads();
   }
-  // backward
+  // backward: X_T <- Kb [X_T; X_next]
   for (int t = b.ntiles - 1; t >= 0; --t) {
     const int r0 = t * DD_NB;
-    const T *ut = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
-    const T *U12 = ut + DD_NB * DD_NB;
-    for (int e = tid; e < (DD_NB + ku2) * NR; e += nt) {
+    const T *Kb = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
+    for (int e = tid; e < KW * NR; e += nt) {
       int q = e / NR, r = e % NR;
       int row = r0 + q;
       win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
@@ -418,16 +597,9 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
     __syncthreads();
     for (int e = tid; e < DD_NB * NR; e += nt) {
       int i = e / NR, r = e % NR;
-      T s = win[i * NR + r];
-      for (int q = 0; q < ku2; ++q) s -= U12[(int64_t)q * DD_NB + i] * win[(DD_NB + q) * NR + r];
-      ysh[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < DD_NB * NR; e += nt) {
-      int i = e / NR, r = e % NR;
-      T x = T(0);
-      for (int c = 0; c < DD_NB; ++c) x += ut[c * DD_NB + i] * ysh[c * NR + r];
-      if (r0 + i < n && r < nr) X[(int64_t)r * n + r0 + i] = x;
+      T acc = T(0);
+      for (int k = 0; k < KW; ++k) acc += Kb[i * KW + k] * win[k * NR + r];
+      if (r0 + i < n && r < nr) X[(int64_t)r * n + r0 + i] = acc;
     }
     __syncthreads();
   }
@@ -441,17 +613,41 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
 static size_t lu_smem(int max_kl, int max_ku, size_t es) { return es * (size_t)(2 * max_kl + max_ku + 2); }
 static size_t tiles_smem(int max_kl, size_t es) {
   int W = DD_NB + max_kl;
-  return es * (size_t)(DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
+  return es * (size_t)(2 * DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
 }
-static size_t sweep_smem(int max_n, int max_kl, int max_ku2, int threads, size_t es) {
+static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, int threads, size_t es) {
+  (void)threads;
   int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
-  size_t e = (size_t)max_n + pad + (DD_NB + max_kl) + DD_NB + (size_t)(threads / 32) * DD_NB + DD_NB;
-  return e * es;
+  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + DD_NB + max_kl);
+  return (used + 127) & ~(size_t)127;
+}
+#define DD_SMEM_LIMIT (227 * 1024)
+#define DD_MAX_STAGES 4
+// stages of the tile ring that fit next to the resident vector (0: does not fit)
+int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
+                      uint32_t stage_bytes) {
+  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, threads, (size_t)elem_size);
+  if (base + 2 * (size_t)stage_bytes > DD_SMEM_LIMIT) return 0;
+  int s = (int)((DD_SMEM_LIMIT - base) / stage_bytes);
+  return s > DD_MAX_STAGES ? DD_MAX_STAGES : s;
+}
+// bytes of one stage: whole tiles filling up to ~84 KiB (at least one forward
+// and one backward tile); the jobs of a subdomain then pack as many tiles
+// as fit, since a bulk copy's fixed cost is amortised only by large copies
+uint32_t band_stage_bytes(int kl, int ku, int elem_size) {
+  const size_t f = (size_t)DD_NB * (DD_NB + kl) * elem_size + (size_t)src_stride(kl) * 4;
+  const size_t b = (size_t)DD_NB * (DD_NB + kl + ku) * elem_size;
+  size_t S = 84 * 1024;
+  if (f > S) S = f;
+  if (b > S) S = b;
+  const size_t mf = (S / f) * f, mb = (S / b) * b;
+  const size_t m = mf > mb ? mf : mb;
+  return (uint32_t)((m + 127) & ~(size_t)127);
 }
 #define DD_MULTI_NR 16
 static size_t multi_smem(int max_kl, int max_ku2, size_t es) {
   int w = DD_NB + (max_kl > max_ku2 ? max_kl : max_ku2);
-  return es * (size_t)(w + DD_NB) * DD_MULTI_NR;
+  return es * (size_t)w * DD_MULTI_NR;
 }
 
 template <typename K>
@@ -460,9 +656,6 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-size_t band_sweep_smem_bytes(int max_n, int max_kl, int max_ku2, int threads, int elem_size) {
-  return sweep_smem(max_n, max_kl, max_ku2, threads, (size_t)elem_size);
-}
 
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *lm,
@@ -488,28 +681,35 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
 
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
-                                  const double *y, const int32_t *perm, T *z, int threads,
+                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
+                                  const T *utile, const int32_t *src, const double *y,
+                                  const int32_t *perm, T *z, DevStatus *st, int threads,
                                   cudaStream_t s) {
-  size_t smem = sweep_smem(max_n, max_kl, max_ku2, threads, sizeof(T));
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
+  if (ns < 2) return cudaErrorInvalidValue;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_fwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_fwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ltile, utile,
-                                                     src, y, perm, z);
+  band_solve_fwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ns, stage_bytes,
+                                                     ltile, utile, src, y, perm, z, st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, const T *ltile, const T *utile, const int32_t *src,
-                                  const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
-                                  const T *z2, const T *z1, const int32_t *perm, double *x,
-                                  int threads, cudaStream_t s) {
-  size_t smem = sweep_smem(max_n, max_kl, max_ku2, threads, sizeof(T));
+                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
+                                  const T *utile, const int32_t *src, const int32_t *e_ptr,
+                                  const int32_t *e_col, const T *e_val, const T *z2, const T *z1,
+                                  const int32_t *perm, double *x, DevStatus *st, int threads,
+                                  cudaStream_t s) {
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
+  if (ns < 2) return cudaErrorInvalidValue;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_bwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_bwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ltile, utile,
-                                                     src, e_ptr, e_col, e_val, z2, z1, perm, x);
+  band_solve_bwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ns, stage_bytes,
+                                                     ltile, utile, src, e_ptr, e_col, e_val, z2, z1,
+                                                     perm, x, st);
   return cudaGetLastError();
 }
 
@@ -534,13 +734,14 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
   template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const T *,          \
                                             const T *, const int32_t *, T *, T *, int32_t *,     \
                                             cudaStream_t);                                        \
-  template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int, const T *, \
-                                                const T *, const int32_t *, const double *,      \
-                                                const int32_t *, T *, int, cudaStream_t);         \
+  template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int, uint32_t,    \
+                                                const T *, const T *, const int32_t *,            \
+                                                const double *, const int32_t *, T *,             \
+                                                DevStatus *, int, cudaStream_t);                  \
   template cudaError_t launch_band_solve_bwd<T>(                                                 \
-      const BandInfo *, int, int, int, int, const T *, const T *, const int32_t *,               \
+      const BandInfo *, int, int, int, int, uint32_t, const T *, const T *, const int32_t *,     \
       const int32_t *, const int32_t *, const T *, const T *, const T *, const int32_t *,        \
-      double *, int, cudaStream_t);                                                              \
+      double *, DevStatus *, int, cudaStream_t);                                                 \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,        \
                                                   const int64_t *, int, int, int, const T *,     \
                                                   const T *, const int32_t *, T *, cudaStream_t);

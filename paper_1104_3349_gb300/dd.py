@@ -90,11 +90,12 @@ class dd_stats(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("m", ctypes.c_int32), ("n_agg", ctypes.c_int32),
                 ("max_agg", ctypes.c_int32), ("kl_max", ctypes.c_int32), ("ku_max", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("factor_bytes", ctypes.c_int64), ("factor_nonzeros", ctypes.c_int64),
-                ("schur_bytes", ctypes.c_int64), ("coupling_nnz", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+                ("schur_bytes", ctypes.c_int64), ("coupling_nnz", ctypes.c_int64), ("setup_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
-EXPORTS = ["dd_setup", "dd_apply", "gmres_solve", "dd_spmv", "dd_get_stats", "dd_get_bad_block",
-           "dd_destroy", "dd_last_error"]
+EXPORTS = ["dd_setup", "dd_apply", "dd_apply_part", "gmres_solve", "dd_spmv", "dd_get_stats",
+           "dd_get_bad_block", "dd_destroy", "dd_last_error"]
 
 _lib = None
 
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
     lib.gmres_solve.restype = ctypes.c_int
     lib.gmres_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.POINTER(dd_info), vp]
+    lib.dd_apply_part.restype = ctypes.c_int
+    lib.dd_apply_part.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
     lib.dd_spmv.restype = ctypes.c_int
     lib.dd_spmv.argtypes = [vp, vp, vp, vp]
     lib.dd_get_stats.restype = ctypes.c_int
@@ -205,6 +208,11 @@ class DD:
     def apply(self, y, x, stream=None):
         """x = B^-1 y (device tensors, float64, original numbering)."""
         self._check(self._lib.dd_apply(self._h, _dev_ptr(y, self.n), _dev_ptr(x, self.n), _stream_handle(stream)))
+
+    def apply_part(self, part, y, x, stream=None):
+        """One of the apply's three kernels (0: interior solve, 1: interface, 2: back-substitution)."""
+        self._check(self._lib.dd_apply_part(self._h, int(part), _dev_ptr(y, self.n), _dev_ptr(x, self.n),
+                                            _stream_handle(stream)))
 
     def spmv(self, x, y, stream=None):
         self._check(self._lib.dd_spmv(self._h, _dev_ptr(x, self.n), _dev_ptr(y, self.n), _stream_handle(stream)))
