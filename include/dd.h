@@ -170,6 +170,30 @@ dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int3
  */
 dd_status dd_apply_part(void *handle, int32_t part, const double *y, double *x, void *stream);
 
+/*
+ * dd_apply_noalloc: x = B^-1 y like dd_apply, for callers that cannot
+ * allocate device memory at the time of the call. Examples: code whose
+ * device memory is all held by another pool (a framework's caching
+ * allocator), and code in a phase where an allocation could fail or stall
+ * the device. The paper has no counterpart; this is an interface convenience.
+ *
+ * The intermediate vectors z1 (n_interior) and z2 (n_interface) live in
+ * one file-scope device array of DD_NOALLOC_MAX_ELEMS doubles, 8 MiB. Every
+ * GPU that loads the library holds the array until process exit. Nothing
+ * is allocated, and no cudaMalloc, cudaFree or allocating library routine is
+ * called. n > DD_NOALLOC_MAX_ELEMS is rejected with DD_ERR_INVALID_ARG and a
+ * message in dd_last_error(handle).
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make this first call before any stream capture. All
+ * calls share the one array: every call fully rewrites z1 and z2 before
+ * reading them, so nothing carries over. Calls that overlap on the GPU (on
+ * different streams, or from different threads) race on the array and
+ * must be serialised by the caller. y, x and the handle are as in dd_apply.
+ */
+#define DD_NOALLOC_MAX_ELEMS (1 << 20)
+dd_status dd_apply_noalloc(void *handle, const double *y, double *x, void *stream);
+
 /* y = C x with the handle's copy of C (device pointers, n doubles). */
 dd_status dd_spmv(void *handle, const double *x, double *y, void *stream);
 

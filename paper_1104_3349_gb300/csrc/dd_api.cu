@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -722,9 +723,83 @@ void release(DDHandle *h) {
   h->h_out = nullptr;
 }
 
+// ---------------------------------------------------------------------------
+// Scratch of dd_apply_noalloc: one file-scope device array (8 MiB), shared
+// by every call.  Host code only ever sees its symbol; the device address is
+// looked up once per device with that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[DD_NOALLOC_MAX_ELEMS];
+
+#define DD_NOALLOC_DEVICES 64
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[DD_NOALLOC_DEVICES] = {nullptr};
+
+// device address of the scratch array on the current device, or nullptr
+cudaError_t noalloc_scratch(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= DD_NOALLOC_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// the three kernels of the apply with z1, z2 in the given scratch
+template <typename T>
+dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scratch, cudaStream_t s) {
+  PrecBufs<T> &B = bufs<T>(h);
+  T *z1 = reinterpret_cast<T *>(scratch);
+  // z2 after z1, on a 256-byte boundary
+  const size_t z1_elems = (((size_t)std::max(h->nI, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
+  T *z2 = z1 + z1_elems;
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+                              B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st,
+                              h->sweep_threads, s));
+  CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
+                           B.f_val, y, h->d_perm + h->nI, z1, z2, x, s));
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+                              B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, z2, z1,
+                              h->d_perm, x, h->st, h->sweep_threads, s));
+  return DD_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+dd_status dd_apply_noalloc(void *handle, const double *y, double *x, void *stream) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h || !y || !x) return DD_ERR_INVALID_ARG;
+  if (h->bad_block >= 0) { h->err = "preconditioner failed in setup"; return DD_ERR_INVALID_ARG; }
+  // z1 and z2, each rounded up to 256 bytes, must fit the scratch array
+  const size_t es = h->prec == DD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t need = ((size_t)std::max(h->nI, 1) * es + 255) / 256 * 256 +
+                      ((size_t)std::max(h->nG, 1) * es + 255) / 256 * 256;
+  if (h->n > DD_NOALLOC_MAX_ELEMS || need > sizeof(double) * (size_t)DD_NOALLOC_MAX_ELEMS) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "dd_apply_noalloc: n = %lld exceeds the scratch limit of %d elements",
+             (long long)h->n, DD_NOALLOC_MAX_ELEMS);
+    h->err = buf;
+    return DD_ERR_INVALID_ARG;
+  }
+  double *scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) {
+    h->err = std::string("dd_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return DD_ERR_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return h->prec == DD_FP32 ? apply_scratch_T<float>(h, y, x, scratch, s)
+                            : apply_scratch_T<double>(h, y, x, scratch, s);
+}
+
 
 dd_status dd_setup(const dd_csr *csr, const dd_partition *partition, dd_approx approx,
                    const dd_opts *opts, void *stream, void **handle) {

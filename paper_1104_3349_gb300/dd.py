@@ -94,8 +94,9 @@ class dd_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
-EXPORTS = ["dd_setup", "dd_apply", "dd_apply_part", "gmres_solve", "dd_spmv", "dd_get_stats",
-           "dd_get_bad_block", "dd_destroy", "dd_last_error"]
+EXPORTS = ["dd_setup", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve", "dd_spmv",
+           "dd_get_stats", "dd_get_bad_block", "dd_destroy", "dd_last_error"]
+NOALLOC_MAX_ELEMS = 1 << 20
 
 _lib = None
 
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH):
     lib.gmres_solve.restype = ctypes.c_int
     lib.gmres_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.POINTER(dd_info), vp]
+    lib.dd_apply_noalloc.restype = ctypes.c_int
+    lib.dd_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.dd_apply_part.restype = ctypes.c_int
     lib.dd_apply_part.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
     lib.dd_spmv.restype = ctypes.c_int
@@ -208,6 +211,11 @@ class DD:
     def apply(self, y, x, stream=None):
         """x = B^-1 y (device tensors, float64, original numbering)."""
         self._check(self._lib.dd_apply(self._h, _dev_ptr(y, self.n), _dev_ptr(x, self.n), _stream_handle(stream)))
+
+    def apply_noalloc(self, y, x, stream=None):
+        """x = B^-1 y with the library's fixed device scratch instead of handle buffers."""
+        self._check(self._lib.dd_apply_noalloc(self._h, _dev_ptr(y, self.n), _dev_ptr(x, self.n),
+                                               _stream_handle(stream)))
 
     def apply_part(self, part, y, x, stream=None):
         """One of the apply's three kernels (0: interior solve, 1: interface, 2: back-substitution)."""
