@@ -27,6 +27,7 @@ struct PrecBufs {
   T *S = nullptr, *amax = nullptr, *X = nullptr;
   T *z1 = nullptr, *z2 = nullptr;
   T *Dm = nullptr, *Em = nullptr, *Fm = nullptr, *Tm = nullptr;
+  T *gj = nullptr;  // scratch of the blocked Gauss-Jordan inverses
 };
 
 struct DDHandle {
@@ -36,6 +37,7 @@ struct DDHandle {
   int m = 0, nI = 0, nG = 0, nagg = 0, pmax = 0;
   int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0, sweep_threads = 256;
   uint32_t stage_bytes = 0;
+  void *lu_scratch = nullptr;  // windows of the blocked LU (when not in shared memory)
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   BandInfo *d_info = nullptr;
@@ -301,7 +303,7 @@ void extract_blocks(DDHandle *h, const dd_csr *csr, const dd_partition *pt, Host
 }
 
 int64_t launch_cost(const char *call, const DDHandle *h) {
-  if (strstr(call, "launch_gj_inverse")) return 2LL * h->pmax + 1;
+  if (strstr(call, "launch_gj_inverse")) return 3LL * ((h->pmax + (h->prec == DD_FP32 ? 15 : 7)) / (h->prec == DD_FP32 ? 16 : 8)) + 1;
   if (strstr(call, "launch_hess_solve_update")) return 2;
   return 1;
 }
@@ -357,7 +359,13 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(upload(h, &h->d_info, info));
   TRY(dalloc(h, &B.band, band));
   CK(cudaMemsetAsync(B.band, 0, sizeof(T) * std::max<int64_t>(band, 1), s));
-  TRY(dalloc(h, &B.lm, lmo));
+  TRY(dalloc(h, &B.lm, lto));  // the blocked LU's multipliers, one tile block each
+  {
+    const size_t wb = band_lu_window_bytes(h->max_kl, h->max_ku, sizeof(T));
+    T *wscr = nullptr;
+    if (wb > 200 * 1024) TRY(dalloc(h, &wscr, (wb / sizeof(T)) * (size_t)m));
+    h->lu_scratch = wscr;
+  }
   TRY(dalloc(h, &h->piv, pivo));
   TRY(dalloc(h, &B.ltile, lto));
   TRY(dalloc(h, &B.utile, uto));
@@ -378,7 +386,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   fill_band_kernel<T><<<(unsigned)((h->n + 255) / 256), 256, 0, s>>>(
       (int)h->n, h->c_rowptr, h->c_col, h->c_val, d_part, d_pos, h->d_info, B.band);
   CK(cudaGetLastError());
-  CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv, pivtol, h->st, 256, s));
+  CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
+                       static_cast<T *>(h->lu_scratch), pivtol, h->st, 256, s));
   CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, B.band, B.lm, h->piv, B.ltile,
                           B.utile, h->src, s));
   // ---- couplings E (interior x interface) and F (interface x interior)
@@ -413,6 +422,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(dalloc(h, &B.S, soff[nagg]));
   CK(cudaMemsetAsync(B.S, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
   TRY(dalloc(h, &B.amax, nagg));
+  TRY(dalloc(h, &B.gj, gj_scratch_elems(nagg, poff[nagg], sizeof(T))));
   TRY(dalloc(h, &h->ipiv, poff[nagg]));
   TRY(dalloc(h, &h->failed, nagg));
   // G(R_a, R_a) into S
@@ -570,7 +580,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(launch_scatter_coo<T>((int64_t)fi.size(), d_i, d_v, B.Fm, s));
     CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.Dm, B.amax, s));
     CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.Dm, h->ipiv, h->poff, B.amax,
-                            h->failed, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
+                            h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
     if (h->kind == DD_MSCN) {
       CK(launch_block_gemm<T>(nagg, h->d_p, h->s_off, h->pmax, B.Dm, B.Em, B.Tm, T(1), T(0), s));
       CK(launch_block_gemm<T>(nagg, h->d_p, h->s_off, h->pmax, B.Fm, B.Tm, B.S, T(-1), T(1), s));
@@ -581,7 +591,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   // ---- explicit inverses of the S_hat blocks
   CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.S, B.amax, s));
   CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.S, h->ipiv, h->poff, B.amax,
-                          h->failed, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
+                          h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
   TRY(dalloc(h, &B.z1, std::max(nI, 1)));
   TRY(dalloc(h, &B.z2, std::max(nG, 1)));
   return DD_OK;

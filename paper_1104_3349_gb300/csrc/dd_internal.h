@@ -54,9 +54,14 @@ struct Workspace;  // defined in dd_api.cu
 uint32_t band_stage_bytes(int kl, int ku, int elem_size);
 int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
                       uint32_t stage_bytes);
+// Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
+// column-major, exchanged), wscratch holds the windows when they do not fit
+// in shared memory (band_lu_window_bytes per subdomain, else unused).
+size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size);
 template <typename T>
-cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *lm,
-                           int32_t *piv, double pivtol, DevStatus *st, int threads, cudaStream_t s);
+cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
+                           int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
+                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
                               const T *band, const T *lm, const int32_t *piv, T *ltile, T *utile,
@@ -92,10 +97,13 @@ cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off
 // In-place explicit inverses (Gauss-Jordan, partial pivoting); ipiv holds
 // p[b] entries per block at poff[b]; failing blocks are flagged and reported
 // through st with status_code.
+// scratch (elements of T) of launch_gj_inverse for nblk blocks of total size sum_p
+int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size);
 template <typename T>
 cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
                               int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
-                              double pivtol, DevStatus *st, int status_code, cudaStream_t s);
+                              T *scratch, double pivtol, DevStatus *st, int status_code,
+                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *val, T *dst,
                                cudaStream_t s);

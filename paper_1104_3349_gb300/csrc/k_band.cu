@@ -37,28 +37,37 @@ __device__ void set_status(DevStatus *st, int code, int block) {
 }
 
 // ---------------------------------------------------------------------------
-// Banded LU, one CTA per subdomain.  The active window (kl+1 rows by kl+ku+1
-// columns) stays in L2; the multipliers and the pivot row are staged in
-// shared memory for the rank-1 update.
+// Blocked banded LU with partial pivoting, one CTA per subdomain, panel =
+// sweep tile (DD_NB columns).  For panel t (columns c0 .. c0+NB-1) the window
+// rows c0 .. c0+NB+kl-1 by columns c0 .. c0+NB+kl+ku-1 is loaded (shared
+// memory, or global scratch when it does not fit), then
+//   - the panel columns are factored column by column (first largest
+//     magnitude as pivot, exchanges of whole window rows),
+//   - U12 = L11^-1 A12 and A22 -= L21 U12 (rank-NB update),
+//   - the window goes back to the band rows and the panel's multipliers, in
+//     the row order after the panel's exchanges, to ltraw (column-major
+//     (NB+kl) x NB per tile).
+// The pivots are those of the column-by-column algorithm; the exchanges of
+// later columns reach the multipliers of earlier columns of the same tile
+// only, which is the order the forward sweep applies them in.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lm, int32_t *piv,
+__global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
+                               T *wscratch, int64_t wscratch_stride, int smem_window,
                                double pivtol, DevStatus *st) {
   const BandInfo b = info[blockIdx.x];
   const int n = b.n, kl = b.kl, ku = b.ku, wd = 2 * kl + ku + 1;
   if (n == 0) return;
+  const int R = DD_NB + kl, Cw = DD_NB + kl + ku, ldw = Cw | 1;
   T *A = band + b.band_off;
-  T *L = lm + b.lm_off;
   int32_t *P = piv + b.piv_off;
-  extern __shared__ unsigned char smraw[];
-  T *lsh = reinterpret_cast<T *>(smraw);  // kl multipliers
-  T *ush = lsh + (kl + 1);                // kl+ku pivot-row entries
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *W = smem_window ? reinterpret_cast<T *>(smraw) : wscratch + (int64_t)blockIdx.x * wscratch_stride;
   __shared__ T red[32];
   __shared__ int32_t s_p;
   __shared__ int32_t s_fail;
   __shared__ T s_amax;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
-            nw = nt >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
   // largest magnitude of the block (the reference of the pivot test)
   T mx = T(0);
@@ -75,53 +84,103 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lm
   __syncthreads();
   const T thresh = T(pivtol) * s_amax;
 
-  for (int k = 0; k < n; ++k) {
-    const int last = min(n - 1, k + kl), jend = min(n - 1, k + kl + ku);
-    if (warp == 0) {
-      // first row holding the largest magnitude in column k
-      T best = T(-1);
-      int bi = n;
-      for (int i = k + lane; i <= last; i += 32) {
-        T v = tabs(A[(int64_t)i * wd + (k - i + kl)]);
-        if (v > best) { best = v; bi = i; }
+  for (int t = 0; t < b.ntiles; ++t) {
+    const int c0 = t * DD_NB;
+    const int nbe = min(DD_NB, n - c0);
+    // load the window
+    for (int e = tid; e < R * Cw; e += nt) {
+      const int r = e / Cw, c = e % Cw;
+      const int gr = c0 + r, gc = c0 + c, off = c - r + kl;
+      W[r * ldw + c] = (gr < n && gc < n && off >= 0 && off < wd) ? A[(int64_t)gr * wd + off] : T(0);
+    }
+    __syncthreads();
+    // panel: column by column
+    for (int c = 0; c < nbe; ++c) {
+      const int last = min(min(R - 1, c + kl), n - 1 - c0);
+      if (warp == 0) {
+        T best = T(-1);
+        int bi = R;
+        for (int r = c + lane; r <= last; r += 32) {
+          T v = tabs(W[r * ldw + c]);
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o; o >>= 1) {
+          T ov = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) {
+          s_p = bi;
+          P[c0 + c] = c0 + bi;
+          if (!(best > thresh)) { s_fail = 1; set_status(st, DD_ERR_SINGULAR_BLOCK, blockIdx.x); }
+        }
       }
-      for (int o = 16; o; o >>= 1) {
-        T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      __syncthreads();
+      if (s_fail) return;
+      const int pr = s_p;
+      if (pr != c)
+        for (int q = tid; q < Cw; q += nt) {
+          T tq = W[c * ldw + q]; W[c * ldw + q] = W[pr * ldw + q]; W[pr * ldw + q] = tq;
+        }
+      __syncthreads();
+      const T dkk = W[c * ldw + c];
+      for (int r = c + 1 + tid; r <= last; r += nt) {
+        const T l = W[r * ldw + c] / dkk;
+        W[r * ldw + c] = l;
+        for (int q = c + 1; q < DD_NB; ++q) W[r * ldw + q] -= l * W[c * ldw + q];
       }
-      if (lane == 0) {
-        s_p = bi;
-        P[k] = bi;
-        if (!(best > thresh)) { s_fail = 1; set_status(st, DD_ERR_SINGULAR_BLOCK, blockIdx.x); }
+      __syncthreads();
+    }
+    // U12 = L11^-1 A12 (rows 0..NB-1, columns NB..Cw-1)
+    for (int c = 0; c < nbe - 1; ++c) {
+      for (int e = tid; e < (DD_NB - 1 - c) * (Cw - DD_NB); e += nt) {
+        const int r = c + 1 + e / (Cw - DD_NB), q = DD_NB + e % (Cw - DD_NB);
+        W[r * ldw + q] -= W[r * ldw + c] * W[c * ldw + q];
+      }
+      __syncthreads();
+    }
+    // A22 -= L21 U12 (rows NB..R-1, columns NB..Cw-1), 4 x 4 outputs per thread
+    {
+      const int nr = kl, ncol = Cw - DD_NB;
+      const int tr = (nr + 3) / 4, tc = (ncol + 3) / 4;
+      for (int m = tid; m < tr * tc; m += nt) {
+        const int i0 = DD_NB + 4 * (m / tc), j0 = DD_NB + 4 * (m % tc);
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c2 = 0; c2 < 4; ++c2) acc[a][c2] = T(0);
+        for (int k = 0; k < nbe; ++k) {
+          T lv[4], uv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = (i0 + a < R) ? W[(i0 + a) * ldw + k] : T(0);
+#pragma unroll
+          for (int c2 = 0; c2 < 4; ++c2) uv[c2] = (j0 + c2 < Cw) ? W[k * ldw + j0 + c2] : T(0);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) acc[a][c2] += lv[a] * uv[c2];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c2 = 0; c2 < 4; ++c2)
+            if (i0 + a < R && j0 + c2 < Cw) W[(i0 + a) * ldw + j0 + c2] -= acc[a][c2];
       }
     }
     __syncthreads();
-    if (s_fail) return;
-    const int p = s_p;
-    if (p != k)
-      for (int c = k + tid; c <= jend; c += nt) {
-        T *a = &A[(int64_t)k * wd + (c - k + kl)];
-        T *bq = &A[(int64_t)p * wd + (c - p + kl)];
-        T t = *a; *a = *bq; *bq = t;
-      }
-    __syncthreads();
-    const T dkk = A[(int64_t)k * wd + kl];
-    for (int i = k + 1 + tid; i <= last; i += nt) {
-      T *a = &A[(int64_t)i * wd + (k - i + kl)];
-      T l = *a / dkk;
-      L[(int64_t)k * kl + (i - k - 1)] = l;
-      lsh[i - k - 1] = l;
-      *a = T(0);
+    // multipliers of the panel (strictly below the diagonal), then the window
+    // back to the band rows (multiplier positions zero)
+    T *lt = ltraw + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
+    for (int e = tid; e < R * DD_NB; e += nt) {
+      const int c = e / R, r = e % R;
+      lt[e] = (r > c && c < nbe) ? W[r * ldw + c] : T(0);
     }
-    for (int c = k + 1 + tid; c <= jend; c += nt) ush[c - k - 1] = A[(int64_t)k * wd + (c - k + kl)];
-    __syncthreads();
-    const int nr = last - k, nc = jend - k;
-    for (int r = warp; r < nr; r += nw) {
-      const T l = lsh[r];
-      const int i = k + 1 + r;
-      T *row = &A[(int64_t)i * wd + (k + 1 - i + kl)];
-      for (int c = lane; c < nc; c += 32) row[c] -= l * ush[c];
+    for (int e = tid; e < R * Cw; e += nt) {
+      const int r = e / Cw, c = e % Cw;
+      const int gr = c0 + r, gc = c0 + c, off = c - r + kl;
+      if (gr < n && gc < n && off >= 0 && off < wd)
+        A[(int64_t)gr * wd + off] = (c < DD_NB && r > c) ? T(0) : W[r * ldw + c];
     }
     __syncthreads();
   }
@@ -142,7 +201,6 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
   const int c0 = t * DD_NB;
   const int lane = threadIdx.x;
   const T *A = band + b.band_off;
-  const T *L = lm + b.lm_off;
   const int32_t *P = piv + b.piv_off;
   T *lt = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
   T *ut = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
@@ -163,21 +221,12 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
   __syncwarp();
   for (int q = lane; q < W; q += 32) src[q] = idx[q];
 
-  // (2) multipliers of column c0+lane with the later exchanges applied
+  // (2) multipliers of column c0+lane, already in the row order after the
+  //     tile's exchanges (written so by the blocked LU)
   {
     T *v = vbuf + (size_t)lane * W;
-    for (int q = 0; q < W; ++q) v[q] = T(0);
-    const int c = c0 + lane;
-    if (c < n) {
-      for (int r = 0; r < kl; ++r) {
-        int row = c + 1 + r;
-        if (row < n) v[row - c0] = L[(int64_t)c * kl + r];
-      }
-      for (int c2 = c + 1; c2 < c0 + DD_NB && c2 < n; ++c2) {
-        int a = c2 - c0, bq = P[c2] - c0;
-        T tmp = v[a]; v[a] = v[bq]; v[bq] = tmp;
-      }
-    }
+    const T *lr = lm + b.ltile_off + (int64_t)t * bi_ltile_elems(b) + (int64_t)lane * W;
+    for (int q = 0; q < W; ++q) v[q] = lr[q];
     for (int q = 0; q < DD_NB; ++q) L11[q * DD_NB + lane] = (q == lane) ? T(1) : (q > lane ? v[q] : T(0));
   }
   __syncwarp();
@@ -610,7 +659,6 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static size_t lu_smem(int max_kl, int max_ku, size_t es) { return es * (size_t)(2 * max_kl + max_ku + 2); }
 static size_t tiles_smem(int max_kl, size_t es) {
   int W = DD_NB + max_kl;
   return es * (size_t)(2 * DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
@@ -657,13 +705,23 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
 }
 
 
+// shared memory of the blocked LU window (0: it goes to global scratch)
+size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
+  const int R = DD_NB + max_kl, Cw = DD_NB + max_kl + max_ku;
+  return (size_t)R * (size_t)(Cw | 1) * elem_size;
+}
+
 template <typename T>
-cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *lm,
-                           int32_t *piv, double pivtol, DevStatus *st, int threads, cudaStream_t s) {
-  size_t smem = lu_smem(max_kl, max_ku, sizeof(T));
+cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
+                           int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
+                           cudaStream_t s) {
+  const size_t wb = band_lu_window_bytes(max_kl, max_ku, sizeof(T));
+  const bool in_smem = wb <= 200 * 1024;
+  const size_t smem = in_smem ? wb : 0;
   cudaError_t e = ensure_smem(band_lu_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_lu_kernel<T><<<m, threads, smem, s>>>(d_info, band, lm, piv, pivtol, st);
+  band_lu_kernel<T><<<m, threads, smem, s>>>(d_info, band, ltraw, piv, wscratch,
+                                             (int64_t)(wb / sizeof(T)), in_smem ? 1 : 0, pivtol, st);
   return cudaGetLastError();
 }
 
@@ -730,7 +788,7 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
 
 #define DD_INST_BAND(T)                                                                          \
   template cudaError_t launch_band_lu<T>(const BandInfo *, int, int, int, T *, T *, int32_t *,   \
-                                         double, DevStatus *, int, cudaStream_t);                 \
+                                         T *, double, DevStatus *, int, cudaStream_t);            \
   template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const T *,          \
                                             const T *, const int32_t *, T *, T *, int32_t *,     \
                                             cudaStream_t);                                        \

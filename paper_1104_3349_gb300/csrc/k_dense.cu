@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "dd_internal.h"
 
 namespace {
@@ -137,6 +139,214 @@ __global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_
         a[(int64_t)r * p + q] = t;
       }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inverse.  For each panel of NB columns k0..k0+NB-1:
+//  (1) panel kernel (one CTA per block): LU with partial pivoting of the
+//      panel rows k0..p-1 on a copy in shared memory (or global scratch when
+//      the panel does not fit), the row exchanges applied to whole rows of A,
+//      and A11^-1 = U11^-1 L11^-1 of the pivot block;
+//  (2) row-block kernel: Rnew = A11^-1 A(R, :) and a copy Pcol = A(:, panel);
+//  (3) update kernel (tiled, many CTAs per block):
+//        A(R, panel) = A11^-1,  A(R, j) = Rnew(:, j),
+//        A(i, panel) = -Pcol(i, :) A11^-1,  A(i, j) -= Pcol(i, :) Rnew(:, j).
+// The pivots are those of LU with partial pivoting (first largest magnitude),
+// so the inverse is the one Gauss-Jordan computes column by column, with the
+// rank-1 passes grouped into rank-NB updates.  The row exchanges are undone
+// as column exchanges at the end.
+// Scratch per block b at soff2[b] = 3*NB*poff[b] + NB*NB*b elements:
+//   [panel p x NB | Pcol p x NB | Rnew NB x p | A11inv NB x NB]
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                 T *A, T *scratch, const int64_t *__restrict__ poff,
+                                 int32_t *ipiv, const T *__restrict__ amax, double pivtol,
+                                 int32_t *failed, DevStatus *st, int code, int smem_rows) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbe = min(NB, p - k0), rows = p - k0;
+  T *a = A + off[b];
+  T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *W = (rows <= smem_rows) ? reinterpret_cast<T *>(smraw) : scr;  // rows x NB
+  T *a11inv = scr + 3 * (int64_t)NB * p;
+  __shared__ T bv[32];
+  __shared__ int bi[32];
+  __shared__ int s_piv;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  if (tid == 0) s_fail = 0;
+  for (int e = tid; e < rows * NB; e += nt) {
+    const int r = e / NB, c = e % NB;
+    W[e] = (c < nbe) ? a[(int64_t)(k0 + r) * p + k0 + c] : T(0);
+  }
+  __syncthreads();
+  const T thresh = T(pivtol) * amax[b];
+  for (int c = 0; c < nbe; ++c) {
+    T best = T(-1);
+    int besti = rows;
+    for (int r = c + tid; r < rows; r += nt) {
+      T v = tabs(W[r * NB + c]);
+      if (v > best) { best = v; besti = r; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+      if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
+    }
+    if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
+    __syncthreads();
+    if (tid == 0) {
+      T bb = bv[0];
+      int ii = bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
+      if (!(bb > thresh)) {
+        s_fail = 1;
+        failed[b] = 1;
+        set_status2(st, code, b);
+      }
+      s_piv = ii;
+      ipiv[poff[b] + k0 + c] = k0 + ii;
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const int pr = s_piv;
+    if (pr != c && tid < NB) {
+      T t = W[c * NB + tid]; W[c * NB + tid] = W[pr * NB + tid]; W[pr * NB + tid] = t;
+    }
+    __syncthreads();
+    const T piv = W[c * NB + c];
+    for (int r = c + 1 + tid; r < rows; r += nt) {
+      const T l = W[r * NB + c] / piv;
+      W[r * NB + c] = l;
+      for (int q = c + 1; q < nbe; ++q) W[r * NB + q] -= l * W[c * NB + q];
+    }
+    __syncthreads();
+  }
+  // row exchanges on whole rows of A, in order
+  for (int c = 0; c < nbe; ++c) {
+    const int q = ipiv[poff[b] + k0 + c];
+    if (q != k0 + c)
+      for (int j = tid; j < p; j += nt) {
+        T t = a[(int64_t)(k0 + c) * p + j];
+        a[(int64_t)(k0 + c) * p + j] = a[(int64_t)q * p + j];
+        a[(int64_t)q * p + j] = t;
+      }
+    __syncthreads();
+  }
+  // A11^-1 = U11^-1 L11^-1, one column per thread of warp 0
+  if (tid < nbe) {
+    const int j = tid;
+    T x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) x[i] = T(0);
+    x[j] = T(1);
+    for (int i = j + 1; i < nbe; ++i) {  // L11 y = e_j (unit lower)
+      T s2 = T(0);
+      for (int q = j; q < i; ++q) s2 += W[i * NB + q] * x[q];
+      x[i] = -s2;
+    }
+    for (int i = nbe - 1; i >= 0; --i) {  // U11 x = y
+      T s2 = x[i];
+      for (int q = i + 1; q < nbe; ++q) s2 -= W[i * NB + q] * x[q];
+      x[i] = s2 / W[i * NB + i];
+    }
+    for (int i = 0; i < NB; ++i) a11inv[i * NB + j] = (i < nbe) ? x[i] : T(0);
+  } else if (tid < NB) {
+    for (int i = 0; i < NB; ++i) a11inv[i * NB + tid] = T(0);
+  }
+}
+
+template <typename T, int NB>
+__global__ void bgj_rowblock_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                    const T *__restrict__ A, T *scratch, const int64_t *__restrict__ poff,
+                                    const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbe = min(NB, p - k0);
+  const T *a = A + off[b];
+  T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
+  T *Pcol = scr + (int64_t)NB * p;
+  T *Rnew = scr + 2 * (int64_t)NB * p;
+  const T *a11inv = scr + 3 * (int64_t)NB * p;
+  __shared__ T ai[NB * NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) ai[e] = a11inv[e];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
+  // Rnew(:, j) = A11^-1 A(R, j);  Pcol(j, :) = A(j, panel)
+  T col[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) col[c] = (c < nbe) ? a[(int64_t)(k0 + c) * p + j] : T(0);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    T s2 = T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) s2 += ai[r * NB + c] * col[c];
+    Rnew[(int64_t)r * p + j] = s2;
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c) Pcol[(int64_t)j * NB + c] = (c < nbe) ? a[(int64_t)j * p + k0 + c] : T(0);
+}
+
+#define DD_BGJ_TILE 64
+template <typename T, int NB>
+__global__ void bgj_update_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                  T *A, const T *__restrict__ scratch, const int64_t *__restrict__ poff,
+                                  const int32_t *__restrict__ failed) {
+  const int b = blockIdx.z;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int i0 = blockIdx.y * DD_BGJ_TILE, j0 = blockIdx.x * DD_BGJ_TILE;
+  if (i0 >= p || j0 >= p) return;
+  const int nbe = min(NB, p - k0);
+  T *a = A + off[b];
+  const T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
+  const T *Pcol = scr + (int64_t)NB * p;
+  const T *Rnew = scr + 2 * (int64_t)NB * p;
+  const T *a11inv = scr + 3 * (int64_t)NB * p;
+  __shared__ T Ps[DD_BGJ_TILE][NB + 1];
+  __shared__ T Rs[NB][DD_BGJ_TILE + 1];
+  const int tid = threadIdx.x;  // 256 threads: 16 x 16, each 4 x 4 outputs
+  for (int e = tid; e < DD_BGJ_TILE * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    const int i = i0 + r;
+    Ps[r][c] = (i < p) ? Pcol[(int64_t)i * NB + c] : T(0);
+  }
+  for (int e = tid; e < NB * DD_BGJ_TILE; e += blockDim.x) {
+    const int c = e / DD_BGJ_TILE, q = e % DD_BGJ_TILE;
+    const int j = j0 + q;
+    T v = T(0);
+    if (j < p) v = (j >= k0 && j < k0 + nbe) ? a11inv[c * NB + (j - k0)] : Rnew[(int64_t)c * p + j];
+    Rs[c][q] = v;
+  }
+  __syncthreads();
+  const int tr = tid / 16, tc = tid % 16;
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii) {
+    const int r = tr + 16 * ii, i = i0 + r;
+    if (i >= p) continue;
+    const bool pivot_row = (i >= k0 && i < k0 + nbe);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int q = tc + 16 * jj, j = j0 + q;
+      if (j >= p) continue;
+      const bool panel_col = (j >= k0 && j < k0 + nbe);
+      T *o = &a[(int64_t)i * p + j];
+      if (pivot_row) {
+        *o = Rs[i - k0][q];
+      } else {
+        T s2 = T(0);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) s2 += Ps[r][c] * Rs[c][q];
+        *o = panel_col ? -s2 : *o - s2;
+      }
+    }
   }
 }
 
@@ -294,21 +504,41 @@ cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off
   return cudaGetLastError();
 }
 
-// Explicit inverse of every block (in place); blocks that fail the pivot test
-// are flagged and reported through st with the given status code.
+template <typename T>
+struct BgjNB { static const int value = 16; };
+template <>
+struct BgjNB<double> { static const int value = 8; };
+
+int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size) {
+  const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
+  return 3 * (int64_t)nb * sum_p + (int64_t)nb * nb * nblk;
+}
+
+// Explicit inverse of every block (in place), blocked Gauss-Jordan; blocks
+// that fail the pivot test are flagged and reported through st.
 template <typename T>
 cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
                               int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
-                              double pivtol, DevStatus *st, int status_code, cudaStream_t s) {
+                              T *scratch, double pivtol, DevStatus *st, int status_code,
+                              cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
+  constexpr int NB = BgjNB<T>::value;
   cudaError_t e = cudaMemsetAsync(failed, 0, sizeof(int32_t) * nblk, s);
   if (e != cudaSuccess) return e;
-  const int rows_per_cta = 8;
-  dim3 ug((pmax + rows_per_cta - 1) / rows_per_cta, nblk);
-  for (int k = 0; k < pmax; ++k) {
-    gj_pivot_kernel<T><<<nblk, 256, 0, s>>>(k, d_p, d_off, A, ipiv, d_poff, amax, pivtol, failed,
-                                            st, status_code);
-    gj_update_kernel<T><<<ug, 32 * rows_per_cta, 0, s>>>(k, d_p, d_off, A, failed);
+  const size_t smem_cap = 200 * 1024;
+  const int smem_rows = (int)(smem_cap / (NB * sizeof(T)));
+  const size_t smem = (size_t)std::min(pmax, smem_rows) * NB * sizeof(T);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(bgj_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 rg((pmax + 255) / 256, nblk);
+  const dim3 ug((pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, (pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, nblk);
+  for (int k0 = 0; k0 < pmax; k0 += NB) {
+    bgj_panel_kernel<T, NB><<<nblk, 256, smem, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, amax,
+                                                   pivtol, failed, st, status_code, smem_rows);
+    bgj_rowblock_kernel<T, NB><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    bgj_update_kernel<T, NB><<<ug, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
   }
   gj_unscramble_kernel<T><<<nblk, 256, 0, s>>>(d_p, d_off, A, ipiv, d_poff, failed);
   return cudaGetLastError();
@@ -383,7 +613,7 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
   template cudaError_t launch_block_amax<T>(int, const int32_t *, const int64_t *, const T *, T *, \
                                             cudaStream_t);                                         \
   template cudaError_t launch_gj_inverse<T>(int, const int32_t *, const int64_t *, int, T *,      \
-                                            int32_t *, const int64_t *, const T *, int32_t *,     \
+                                            int32_t *, const int64_t *, const T *, int32_t *, T *, \
                                             double, DevStatus *, int, cudaStream_t);              \
   template cudaError_t launch_scatter_coo<T>(int64_t, const int64_t *, const double *, T *,       \
                                              cudaStream_t);                                        \
