@@ -94,7 +94,7 @@ typedef struct {
                          Arnoldi step; 0: plain launches                       */
   int32_t max_restart;/* largest restart length gmres_solve will be called
                          with (its Krylov workspace is allocated by dd_setup);
-                         <= 0 selects 50                                       */
+                         <= 0 selects 50, at most 120                          */
   int32_t reserved[4];
 } dd_opts;
 
@@ -177,16 +177,17 @@ dd_status dd_apply_part(void *handle, int32_t part, const double *y, double *x, 
  * allocator), and code in a phase where an allocation could fail or stall
  * the device. The paper has no counterpart; this is an interface convenience.
  *
- * The intermediate vectors z1 (n_interior) and z2 (n_interface) live in
- * one file-scope device array of DD_NOALLOC_MAX_ELEMS doubles, 8 MiB. Every
- * GPU that loads the library holds the array until process exit. Nothing
- * is allocated, and no cudaMalloc, cudaFree or allocating library routine is
- * called. n > DD_NOALLOC_MAX_ELEMS is rejected with DD_ERR_INVALID_ARG and a
+ * The intermediate vectors z1 (n_interior) and z2, t (n_interface each)
+ * live in one file-scope device array of DD_NOALLOC_MAX_ELEMS doubles,
+ * 8 MiB. Every GPU that loads the library holds the array until process
+ * exit. Nothing is allocated, and no cudaMalloc, cudaFree or allocating
+ * library routine is called. Systems whose vectors do not fit (always
+ * n > DD_NOALLOC_MAX_ELEMS) are rejected with DD_ERR_INVALID_ARG and a
  * message in dd_last_error(handle).
  *
  * The first call on a device looks up the array's device address with that
  * device current; make this first call before any stream capture. All
- * calls share the one array: every call fully rewrites z1 and z2 before
+ * calls share the one array: every call fully rewrites z1, z2 and t before
  * reading them, so nothing carries over. Calls that overlap on the GPU (on
  * different streams, or from different threads) race on the array and
  * must be serialised by the caller. y, x and the handle are as in dd_apply.

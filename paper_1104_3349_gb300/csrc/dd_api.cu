@@ -25,7 +25,7 @@ struct PrecBufs {
   T *band = nullptr, *lm = nullptr, *ltile = nullptr, *utile = nullptr;
   T *e_val = nullptr, *f_val = nullptr, *fsub_val = nullptr;
   T *S = nullptr, *amax = nullptr, *X = nullptr;
-  T *z1 = nullptr, *z2 = nullptr;
+  T *z1 = nullptr, *z2 = nullptr, *t = nullptr;
   T *Dm = nullptr, *Em = nullptr, *Fm = nullptr, *Tm = nullptr;
   T *gj = nullptr;  // scratch of the blocked Gauss-Jordan inverses
 };
@@ -52,7 +52,7 @@ struct DDHandle {
   PrecBufs<double> pd;
   PrecBufs<float> pf;
   // FGMRES workspace
-  int Rmax = 0, nblocks = 304;
+  int Rmax = 0, nblocks = 304, cgs_blocks = 0;
   int64_t ldv = 0;
   double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
          *y = nullptr, *hc1 = nullptr, *hc2 = nullptr, *nsq = nullptr, *out = nullptr,
@@ -305,6 +305,7 @@ void extract_blocks(DDHandle *h, const dd_csr *csr, const dd_partition *pt, Host
 int64_t launch_cost(const char *call, const DDHandle *h) {
   if (strstr(call, "launch_gj_inverse")) return 3LL * ((h->pmax + (h->prec == DD_FP32 ? 15 : 7)) / (h->prec == DD_FP32 ? 16 : 8)) + 1;
   if (strstr(call, "launch_hess_solve_update")) return 2;
+  if (strstr(call, "launch_schur_apply")) return 2;
   return 1;
 }
 
@@ -594,6 +595,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
                           h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
   TRY(dalloc(h, &B.z1, std::max(nI, 1)));
   TRY(dalloc(h, &B.z2, std::max(nG, 1)));
+  TRY(dalloc(h, &B.t, std::max(nG, 1)));
   return DD_OK;
 }
 
@@ -606,7 +608,7 @@ dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int p
                               h->sweep_threads, s));
   if (part == 1 || part < 0)
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
-                           B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, x, s));
+                           B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, B.t, h->nG, x, s));
   if (part == 2 || part < 0)
   CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
                               B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, B.z2, B.z1,
@@ -632,11 +634,13 @@ dd_status alloc_krylov(DDHandle *h, int R) {
   TRY(dalloc(h, &h->sn, R));
   TRY(dalloc(h, &h->g, R + 1));
   TRY(dalloc(h, &h->y, R + 1));
-  TRY(dalloc(h, &h->hc1, R + 1));
-  TRY(dalloc(h, &h->hc2, R + 1));
+  TRY(dalloc(h, &h->hc1, R + 2));
+  TRY(dalloc(h, &h->hc2, R + 2));
   TRY(dalloc(h, &h->nsq, 4));
   TRY(dalloc(h, &h->out, 4));
-  TRY(dalloc(h, &h->partial, (size_t)h->nblocks * (R + 1)));
+  h->cgs_blocks = cgs2_blocks(304);
+  if (h->cgs_blocks <= 0) { h->err = "no resident blocks for the cooperative CGS2 kernel"; return DD_ERR_CUDA; }
+  TRY(dalloc(h, &h->partial, 3 * (size_t)std::max(h->nblocks, h->cgs_blocks) * (R + 2)));
   TRY(dalloc(h, &h->r, h->ldv));
   cudaError_t e = cudaMallocHost(&h->h_out, 8 * sizeof(double));
   if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return DD_ERR_OOM; }
@@ -682,16 +686,8 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
       double *w = h->V + (int64_t)(j + 1) * h->ldv;
       TRY(apply_any(h, vj, zj, s));
       CK(launch_spmv(n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
-      TRY(norm_sq(h, w, 1, s));
-      CK(launch_multidot(n, j + 1, h->V, h->ldv, w, h->partial, h->nblocks, s));
-      CK(launch_reduce_cols(h->nblocks, j + 1, h->partial, h->hc1, 0, s));
-      CK(launch_gemv_sub(n, j + 1, h->V, h->ldv, h->hc1, w, s));
-      CK(launch_multidot(n, j + 1, h->V, h->ldv, w, h->partial, h->nblocks, s));
-      CK(launch_reduce_cols(h->nblocks, j + 1, h->partial, h->hc2, 0, s));
-      CK(launch_gemv_sub(n, j + 1, h->V, h->ldv, h->hc2, w, s));
-      TRY(norm_sq(h, w, 0, s));
-      CK(launch_givens2(j, R, h->H, h->hc1, h->hc2, h->nsq, h->cs, h->sn, h->g, bnorm, h->out, s));
-      CK(launch_scale_by(n, h->out, w, s));
+      CK(launch_cgs2(n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
+                     h->sn, h->g, bnorm, h->out, h->cgs_blocks, s));
       TRY(read_scalars(h, h->out, 3, s));
       ++iters;
       const double est = h->h_out[2];
@@ -768,12 +764,13 @@ dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scrat
   T *z1 = reinterpret_cast<T *>(scratch);
   // z2 after z1, on a 256-byte boundary
   const size_t z1_elems = (((size_t)std::max(h->nI, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
+  const size_t z2_elems = (((size_t)std::max(h->nG, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   T *z2 = z1 + z1_elems;
   CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
                               B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st,
                               h->sweep_threads, s));
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
-                           B.f_val, y, h->d_perm + h->nI, z1, z2, x, s));
+                           B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, s));
   CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
                               B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, z2, z1,
                               h->d_perm, x, h->st, h->sweep_threads, s));
@@ -791,7 +788,7 @@ dd_status dd_apply_noalloc(void *handle, const double *y, double *x, void *strea
   // z1 and z2, each rounded up to 256 bytes, must fit the scratch array
   const size_t es = h->prec == DD_FP32 ? sizeof(float) : sizeof(double);
   const size_t need = ((size_t)std::max(h->nI, 1) * es + 255) / 256 * 256 +
-                      ((size_t)std::max(h->nG, 1) * es + 255) / 256 * 256;
+                      2 * (((size_t)std::max(h->nG, 1) * es + 255) / 256 * 256);
   if (h->n > DD_NOALLOC_MAX_ELEMS || need > sizeof(double) * (size_t)DD_NOALLOC_MAX_ELEMS) {
     char buf[160];
     snprintf(buf, sizeof buf, "dd_apply_noalloc: n = %lld exceeds the scratch limit of %d elements",
@@ -829,6 +826,7 @@ dd_status dd_setup(const dd_csr *csr, const dd_partition *partition, dd_approx a
   h->kind = approx;
   const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
   const int R = o.max_restart > 0 ? o.max_restart : 50;
+  if (R > 120) { g_setup_error = "max_restart must be <= 120"; delete h; return DD_ERR_INVALID_ARG; }
   HostBlocks hb;
   dd_status rc = validate_and_order(h, csr, partition, hb);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

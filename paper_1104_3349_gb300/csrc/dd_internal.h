@@ -123,11 +123,12 @@ cudaError_t launch_mscnr_diag(int nblk, const int32_t *d_p, const int64_t *d_off
                               const T *Dinv, const T *E, const T *F, T *S, cudaStream_t s);
 // z2 = S_hat^-1 (y2 - F z1) with explicit inverses; also writes x2 = z2 to x
 // (original numbering).
+// (two kernels: t = y2 - F z1 into t, then the block GEMV)
 template <typename T>
 cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
                                const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
                                const T *f_val, const double *y, const int32_t *perm_iface,
-                               const T *z1, T *z2, double *x, cudaStream_t s);
+                               const T *z1, T *z2, T *t, int ng, double *x, cudaStream_t s);
 
 // Krylov (k_krylov.cu), FP64
 cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
@@ -151,3 +152,9 @@ cudaError_t launch_hess_solve_update(int n, int jlast, int R, const double *H, c
                                      cudaStream_t s);
 cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
+// One Arnoldi orthogonalisation step (CGS2 + Givens + normalisation) as a
+// single cooperative kernel; partial holds nblocks * pk doubles, pk >= R + 2.
+int cgs2_blocks(int cap);
+cudaError_t launch_cgs2(int n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
+                        int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
+                        double bnorm, double *scal, int nblocks, cudaStream_t s);

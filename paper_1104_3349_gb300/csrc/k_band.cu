@@ -744,7 +744,8 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
                                   const int32_t *perm, T *z, DevStatus *st, int threads,
                                   cudaStream_t s) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
-  if (ns < 2) return cudaErrorInvalidValue;
+  // the backward tile step maps exactly 8 threads to each of the 32 rows
+  if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
   size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_fwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
@@ -761,7 +762,7 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
                                   const int32_t *perm, double *x, DevStatus *st, int threads,
                                   cudaStream_t s) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
-  if (ns < 2) return cudaErrorInvalidValue;
+  if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
   size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_bwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;

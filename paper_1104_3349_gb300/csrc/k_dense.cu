@@ -455,37 +455,55 @@ __global__ void mscnr_diag_kernel(const int32_t *__restrict__ P, const int64_t *
   }
 }
 
-// z2 = S_hat^-1 (y2 - F z1): each CTA rebuilds t for its aggregate in shared
-// memory, then computes DD_SROWS rows of the block product (warp per row).
-#define DD_SROWS 32
+// t = y2 - F z1 (one thread per interface row)
 template <typename T>
-__global__ void schur_apply_kernel(const int32_t *__restrict__ agg_off,
-                                   const int64_t *__restrict__ s_off, const T *__restrict__ Sinv,
-                                   const int32_t *__restrict__ f_ptr, const int32_t *__restrict__ f_col,
-                                   const T *__restrict__ f_val, const double *__restrict__ y,
-                                   const int32_t *__restrict__ perm_iface, const T *__restrict__ z1,
-                                   T *z2, double *x) {
+__global__ void schur_rhs_kernel(int ng, const int32_t *__restrict__ f_ptr, const int32_t *__restrict__ f_col,
+                                 const T *__restrict__ f_val, const double *__restrict__ y,
+                                 const int32_t *__restrict__ perm_iface, const T *__restrict__ z1, T *t) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  T s = T(y[perm_iface[g]]);
+  for (int k = f_ptr[g]; k < f_ptr[g + 1]; ++k) s -= f_val[k] * z1[f_col[k]];
+  t[g] = s;
+}
+
+// z2 = S_hat^-1 t per aggregate: t of the aggregate in shared memory, one warp
+// per row of S_hat^-1 with 16-byte loads; x2 = z2 written to x
+#define DD_SROWS 64
+template <typename T>
+__global__ void schur_gemv_kernel(const int32_t *__restrict__ agg_off, const int64_t *__restrict__ s_off,
+                                  const T *__restrict__ Sinv, const T *__restrict__ t,
+                                  const int32_t *__restrict__ perm_iface, T *z2, double *x) {
   const int a = blockIdx.y;
   const int g0 = agg_off[a], p = agg_off[a + 1] - g0;
   const int rbase = blockIdx.x * DD_SROWS;
   if (rbase >= p) return;
-  extern __shared__ unsigned char smraw[];
-  T *t = reinterpret_cast<T *>(smraw);
-  for (int r = threadIdx.x; r < p; r += blockDim.x) {
-    const int g = g0 + r;
-    T s = T(y[perm_iface[g]]);
-    for (int k = f_ptr[g]; k < f_ptr[g + 1]; ++k) s -= f_val[k] * z1[f_col[k]];
-    t[r] = s;
-  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *ts = reinterpret_cast<T *>(smraw);
+  for (int r = threadIdx.x; r < p; r += blockDim.x) ts[r] = t[g0 + r];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T *Sa = Sinv + s_off[a];
+  constexpr int V = 16 / sizeof(T);
   for (int rr = warp; rr < DD_SROWS; rr += nw) {
     const int r = rbase + rr;
     if (r >= p) break;
     const T *row = Sa + (int64_t)r * p;
     T acc = T(0);
-    for (int c = lane; c < p; c += 32) acc += row[c] * t[c];
+    // rows start on a 16-byte boundary only when p is a multiple of V
+    if ((p % V) == 0 && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
+      for (int c = lane * V; c < p; c += 32 * V) {
+        if (V == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + c);
+          acc += T(v.x) * ts[c] + T(v.y) * ts[c + 1] + T(v.z) * ts[c + 2] + T(v.w) * ts[c + 3];
+        } else {
+          const double2 v = *reinterpret_cast<const double2 *>(row + c);
+          acc += T(v.x) * ts[c] + T(v.y) * ts[c + 1];
+        }
+      }
+    } else {
+      for (int c = lane; c < p; c += 32) acc += row[c] * ts[c];
+    }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       z2[g0 + r] = acc;
@@ -595,17 +613,17 @@ template <typename T>
 cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
                                const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
                                const T *f_val, const double *y, const int32_t *perm_iface,
-                               const T *z1, T *z2, double *x, cudaStream_t s) {
+                               const T *z1, T *z2, T *t, int ng, double *x, cudaStream_t s) {
   if (nagg <= 0) return cudaSuccess;
+  schur_rhs_kernel<T><<<(ng + 255) / 256, 256, 0, s>>>(ng, f_ptr, f_col, f_val, y, perm_iface, z1, t);
   size_t smem = sizeof(T) * (size_t)pmax;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(schur_apply_kernel<T>,
+    cudaError_t e = cudaFuncSetAttribute(schur_gemv_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((pmax + DD_SROWS - 1) / DD_SROWS, nagg);
-  schur_apply_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, f_ptr, f_col, f_val, y,
-                                                perm_iface, z1, z2, x);
+  schur_gemv_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, t, perm_iface, z2, x);
   return cudaGetLastError();
 }
 
@@ -627,8 +645,8 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                             const T *, const T *, T *, cudaStream_t);              \
   template cudaError_t launch_schur_apply<T>(int, const int32_t *, const int64_t *, int, const T *, \
                                              const int32_t *, const int32_t *, const T *,          \
-                                             const double *, const int32_t *, const T *, T *,      \
-                                             double *, cudaStream_t);
+                                             const double *, const int32_t *, const T *, T *, T *, \
+                                             int, double *, cudaStream_t);
 
 DD_INST_DENSE(double)
 DD_INST_DENSE(float)

@@ -7,7 +7,11 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include "dd_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -160,6 +164,221 @@ __global__ void zero_kernel(double *p, int64_t n) {
   if (i < n) p[i] = 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// One Arnoldi orthogonalisation step as a single cooperative kernel: classical
+// Gram-Schmidt applied twice to w = V_{j+1} against V_0..V_j, the norms, the
+// Givens rotation of the new Hessenberg column and the normalisation of w.
+// Every CTA owns a contiguous chunk of rows.  Three grid-wide barriers:
+//   A  partial dots V^T w, w^T w                          -> bufA
+//   B  every CTA sums bufA (h1), w -= V h1, dots V^T w    -> bufB
+//   C  every CTA sums bufB (h2), w -= V h2, partial w^T w -> bufC
+//   D  every CTA sums bufC (||w||), w /= ||w|| unless breakdown;
+//      CTA 0 also forms the Hessenberg column and applies the rotations.
+// Each sum runs over the CTAs in the same fixed order in every CTA, so all
+// CTAs hold bit-identical coefficients and results do not depend on
+// scheduling.  scal: [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}|/||b||
+// ---------------------------------------------------------------------------
+#define DD_CGS_THREADS 256
+#define DD_CGS_MAXK 128  // restart lengths up to DD_CGS_MAXK - 2
+
+// Sum of 16 per-lane values over a warp with 16 FP64 additions per lane:
+// each butterfly step hands half of the remaining values to the partner lane
+// and keeps the other half.  On return lane l holds the warp sum of value
+// v(l) = 8*bit4 + 4*bit3 + 2*bit2 + bit1 of l (lanes l and l^1 agree).
+__device__ __forceinline__ double warp_sum16(const double (&a)[16]) {
+  const int lane = threadIdx.x & 31;
+  double b[8], c[4], d[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int s2 = 0; s2 < 8; ++s2) {
+    const double give = h16 ? a[s2] : a[s2 + 8], keep = h16 ? a[s2 + 8] : a[s2];
+    b[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < 4; ++s2) {
+    const double give = h8 ? b[s2] : b[s2 + 4], keep = h8 ? b[s2 + 4] : b[s2];
+    c[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    const double give = h4 ? c[s2] : c[s2 + 2], keep = h4 ? c[s2 + 2] : c[s2];
+    d[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+  }
+  const double give = h2 ? d[0] : d[1], keep = h2 ? d[1] : d[0];
+  double e = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+  return e + __shfl_xor_sync(0xffffffffu, e, 1);
+}
+
+// partial dots of 16 columns at a time: 16 independent accumulators per
+// thread over its rows, a butterfly per warp, then the warps through shared
+// memory (fixed order)
+__device__ void block_dots(int i0, int i1, int k, const double *__restrict__ V, int64_t ldv,
+                           const double *__restrict__ w, bool self, double *out, double *red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ktot = k + (self ? 1 : 0);
+  for (int q0 = 0; q0 < ktot; q0 += 16) {
+    double a[16];
+#pragma unroll
+    for (int s2 = 0; s2 < 16; ++s2) a[s2] = 0.0;
+    for (int i = i0 + tid; i < i1; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int s2 = 0; s2 < 16; ++s2) {
+        const int q = q0 + s2;
+        if (q < k) a[s2] += V[(int64_t)q * ldv + i] * wi;
+        else if (q == k && self) a[s2] += wi * wi;
+      }
+    }
+    const double ws = warp_sum16(a);
+    if ((lane & 1) == 0) {
+      const int v = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+      red[warp * 16 + v] = ws;
+    }
+    __syncthreads();
+    if (tid < 16 && q0 + tid < ktot) {
+      double t = 0.0;
+      for (int ww = 0; ww < nw; ++ww) t += red[ww * 16 + tid];
+      out[q0 + tid] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// CTA c sums columns q = c, c + nctas, ... of the partials over all CTAs in a
+// fixed order into dst[q]
+__device__ void column_sums(int ncols, int nb, int pk, const double *__restrict__ partial, double *dst,
+                            double *red, int cta, int nctas) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int q = cta; q < ncols; q += nctas) {
+    double t = 0.0;
+    for (int b = tid; b < nb; b += blockDim.x) t += partial[(int64_t)b * pk + q];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double u = 0.0;
+      for (int ww = 0; ww < nw; ++ww) u += red[ww];
+      dst[q] = u;
+    }
+    __syncthreads();
+  }
+}
+
+// w_i - sum_q h_q V_q[i], eight loads in flight per thread
+__device__ __forceinline__ double row_update(int i, int k, const double *__restrict__ V, int64_t ldv,
+                                             const double *hs, double wi) {
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int q = 0;
+  for (; q + 8 <= k; q += 8) {
+#pragma unroll
+    for (int s2 = 0; s2 < 8; ++s2) a[s2] += hs[q + s2] * V[(int64_t)(q + s2) * ldv + i];
+  }
+  for (; q < k; ++q) a[0] += hs[q] * V[(int64_t)q * ldv + i];
+  return wi - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+}
+
+// ---------------------------------------------------------------------------
+// One Arnoldi orthogonalisation step as a single cooperative kernel: classical
+// Gram-Schmidt applied twice to w = V_{j+1} against V_0..V_j, the norms, the
+// Givens rotation of the new Hessenberg column and the normalisation of w.
+// Every CTA owns a contiguous chunk of rows; grid-wide barriers separate
+//   1 partial dots V^T w, w^T w            2 column sums (CTA q: column q) -> h1
+//   3 w -= V h1, partial dots V^T w        4 column sums -> h2
+//   5 w -= V h2, partial w^T w             6 CTA 0: norm, Hessenberg column
+//                                            and rotations in shared memory
+//   7 w /= h_{j+1,j} unless breakdown
+// The FP64 pipe bounds this kernel on GB300, so reductions are kept to one
+// pass over the partials per column.  Sums run in a fixed order.
+// scal: [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}| / ||b||
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
+    int n, int j, int R, const double *__restrict__ V, int64_t ldv, double *w, double *partial,
+    int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g, double bnorm,
+    double *scal) {
+  cg::grid_group grid = cg::this_grid();
+  const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int chunk = (n + nb - 1) / nb;
+  const int i0 = min(n, b * chunk), i1 = min(n, i0 + chunk);
+  const int k = j + 1;
+  __shared__ double red[8 * 16];
+  __shared__ double hs[DD_CGS_MAXK + 8];
+  // 1
+  block_dots(i0, i1, k, V, ldv, w, true, partial + (int64_t)b * pk, red);
+  grid.sync();
+  // 2: hc1[0..k-1] and hc1[k] = ||w||^2 before orthogonalisation
+  column_sums(k + 1, nb, pk, partial, hc1, red, b, nb);
+  grid.sync();
+  // 3
+  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc1[q];
+  __syncthreads();
+  for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] = row_update(i, k, V, ldv, hs, w[i]);
+  __syncthreads();
+  block_dots(i0, i1, k, V, ldv, w, false, partial + (int64_t)b * pk, red);
+  grid.sync();
+  // 4
+  column_sums(k, nb, pk, partial, hc2, red, b, nb);
+  grid.sync();
+  // 5
+  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc2[q];
+  __syncthreads();
+  {
+    double nn = 0.0;
+    for (int i = i0 + tid; i < i1; i += blockDim.x) {
+      const double s2 = row_update(i, k, V, ldv, hs, w[i]);
+      w[i] = s2;
+      nn += s2 * s2;
+    }
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) red[warp] = nn;
+    __syncthreads();
+    if (tid == 0) {
+      double u = 0.0;
+      for (int ww = 0; ww < nw; ++ww) u += red[ww];
+      partial[(int64_t)b * pk] = u;
+    }
+  }
+  grid.sync();
+  // 6
+  if (b == 0) {
+    column_sums(1, nb, pk, partial, hs + DD_CGS_MAXK, red, 0, 1);  // ||w||^2 after
+    // column j of H (passes 1 + 2) and the rotations, in shared memory
+    for (int q = tid; q <= j; q += blockDim.x) hs[q] = hc1[q] + hc2[q];
+    __syncthreads();
+    if (tid == 0) {
+      const double hn = sqrt(hs[DD_CGS_MAXK]);
+      const double w0 = sqrt(hc1[k]);
+      const bool breakdown = !(hn > 1e-14 * w0);
+      hs[j + 1] = hn;
+      for (int q = 0; q < j; ++q) {
+        const double a = hs[q], c2 = hs[q + 1], c = cs[q], sv = sn[q];
+        hs[q] = c * a + sv * c2;
+        hs[q + 1] = -sv * a + c * c2;
+      }
+      const double a = hs[j], c2 = hs[j + 1];
+      const double r = hypot(a, c2);
+      cs[j] = a / r;
+      sn[j] = c2 / r;
+      hs[j] = r;
+      hs[j + 1] = 0.0;
+      const double gj = g[j];
+      g[j + 1] = -sn[j] * gj;
+      g[j] = cs[j] * gj;
+      scal[0] = hn;
+      scal[1] = breakdown ? 1.0 : 0.0;
+      scal[2] = fabs(g[j + 1]) / bnorm;
+    }
+    __syncthreads();
+    for (int q = tid; q <= j + 1; q += blockDim.x) H[(int64_t)q * R + j] = hs[q];
+  }
+  grid.sync();
+  // 7
+  if (scal[1] == 0.0) {
+    const double hn = scal[0];
+    for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] /= hn;
+  }
+}
+
 }  // namespace
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -225,6 +444,26 @@ cudaError_t launch_hess_solve_update(int n, int jlast, int R, const double *H, c
 cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s) {
   init_g_kernel<<<1, 64, 0, s>>>(g, R, nsq);
   return cudaGetLastError();
+}
+
+// blocks of the cooperative CGS2 kernel that can be resident at once (capped)
+int cgs2_blocks(int cap) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgs2_kernel, DD_CGS_THREADS, 0) != cudaSuccess)
+    return 0;
+  int nb = sms * (per < 2 ? per : 2);
+  return nb < cap ? nb : cap;
+}
+
+cudaError_t launch_cgs2(int n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
+                        int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
+                        double bnorm, double *scal, int nblocks, cudaStream_t s) {
+  void *args[] = {&n, &j, &R, (void *)&V, &ldv, &w, &partial, &pk, &hc1, &hc2, &H, &cs, &sn, &g,
+                  &bnorm, &scal};
+  return cudaLaunchCooperativeKernel((const void *)cgs2_kernel, dim3(nblocks), dim3(DD_CGS_THREADS),
+                                     args, 0, s);
 }
 
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s) {
