@@ -38,6 +38,8 @@ struct DDHandle {
   int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0, sweep_threads = 256;
   uint32_t stage_bytes = 0;
   void *lu_scratch = nullptr;  // windows of the blocked LU (when not in shared memory)
+  TileMeta *tm = nullptr;      // packed sweep tiles
+  SweepJob *jobs = nullptr;    // jobs of the sweep ring
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   BandInfo *d_info = nullptr;
@@ -321,7 +323,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   cudaStream_t s = h->stream;
   // ---- interior factors: geometry
   std::vector<BandInfo> info(m);
-  int64_t band = 0, lmo = 0, pivo = 0, lto = 0, uto = 0, srco = 0, fac_nz = 0, fac_bytes = 0;
+  int64_t band = 0, lraw = 0, pivo = 0, fac_nz = 0;
+  int32_t tiles = 0;
   h->max_n = h->max_kl = h->max_ku = h->max_ku2 = h->max_tiles = 0;
   for (int j = 0; j < m; ++j) {
     BandInfo &b = info[j];
@@ -332,12 +335,9 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     b.ntiles = (b.n + DD_NB - 1) / DD_NB;
     b.row0 = hb.off[j];
     b.band_off = band; band += (int64_t)b.n * bi_wd(b);
-    b.lm_off = lmo; lmo += (int64_t)b.n * b.kl;
+    b.lraw_off = lraw; lraw += (int64_t)b.ntiles * bi_lraw_elems(b);
     b.piv_off = pivo; pivo += b.n;
-    b.ltile_off = lto; lto += (int64_t)b.ntiles * bi_ltile_elems(b);
-    b.utile_off = uto; uto += (int64_t)b.ntiles * bi_utile_elems(b);
-    b.src_off = srco; srco += (int64_t)b.ntiles * (((DD_NB + b.kl) + 3) & ~3);
-    h->stage_bytes = std::max(h->stage_bytes, band_stage_bytes(b.kl, b.ku, sizeof(T)));
+    b.tile0 = tiles; tiles += b.ntiles;
     h->max_n = std::max(h->max_n, b.ntiles * DD_NB);
     h->max_kl = std::max(h->max_kl, b.kl);
     h->max_ku = std::max(h->max_ku, b.ku);
@@ -345,14 +345,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     h->max_tiles = std::max(h->max_tiles, b.ntiles);
     // in-band entries of L (kl per column) and U (kl+ku+1 per row), clipped
     for (int i = 0; i < b.n; ++i) fac_nz += std::min(b.kl, b.n - 1 - i) + std::min(b.kl + b.ku, b.n - 1 - i) + 1;
-    fac_bytes += (int64_t)b.ntiles * (bi_ltile_elems(b) + bi_utile_elems(b)) * sizeof(T) +
-                 (int64_t)b.ntiles * (((DD_NB + b.kl) + 3) & ~3) * sizeof(int32_t);
   }
-  if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->sweep_threads, sizeof(T), h->stage_bytes) < 2) {
-    h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
-    return DD_ERR_INVALID_ARG;
-  }
-  h->stats.factor_bytes = fac_bytes;
   h->stats.factor_nonzeros = fac_nz;
   h->stats.kl_max = h->max_kl;
   h->stats.ku_max = h->max_ku;
@@ -360,7 +353,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(upload(h, &h->d_info, info));
   TRY(dalloc(h, &B.band, band));
   CK(cudaMemsetAsync(B.band, 0, sizeof(T) * std::max<int64_t>(band, 1), s));
-  TRY(dalloc(h, &B.lm, lto));  // the blocked LU's multipliers, one tile block each
+  TRY(dalloc(h, &B.lm, lraw));  // the blocked LU's multipliers, one block per tile
   {
     const size_t wb = band_lu_window_bytes(h->max_kl, h->max_ku, sizeof(T));
     T *wscr = nullptr;
@@ -368,9 +361,6 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     h->lu_scratch = wscr;
   }
   TRY(dalloc(h, &h->piv, pivo));
-  TRY(dalloc(h, &B.ltile, lto));
-  TRY(dalloc(h, &B.utile, uto));
-  TRY(dalloc(h, &h->src, srco));
   // ---- C itself (FP64, original numbering) for the SpMV
   {
     std::vector<int32_t> rp(csr->rowptr, csr->rowptr + h->n + 1), cc(csr->col, csr->col + h->nnz);
@@ -389,8 +379,82 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   CK(cudaGetLastError());
   CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
                        static_cast<T *>(h->lu_scratch), pivtol, h->st, 256, s));
-  CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, B.band, B.lm, h->piv, B.ltile,
-                          B.utile, h->src, s));
+  // ---- packed sweep tiles: widths from the factors, offsets and jobs here
+  {
+    int32_t *d_wl = nullptr, *d_wu = nullptr;
+    TRY(dalloc(h, &d_wl, tiles));
+    TRY(dalloc(h, &d_wu, tiles));
+    CK(launch_tile_widths<T>(h->d_info, m, h->max_tiles, B.band, B.lm, h->piv, d_wl, d_wu, s));
+    std::vector<int32_t> wl(tiles), wu(tiles);
+    if (tiles) {
+      CK(cudaMemcpyAsync(wl.data(), d_wl, sizeof(int32_t) * tiles, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(wu.data(), d_wu, sizeof(int32_t) * tiles, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    std::vector<TileMeta> tm(tiles);
+    int64_t lofs = 0, uofs = 0, sofs = 0;
+    size_t max_tile = 0;
+    for (int t = 0; t < tiles; ++t) {
+      tm[t].lofs = lofs; tm[t].uofs = uofs; tm[t].sofs = sofs;
+      tm[t].wl = wl[t]; tm[t].wu = wu[t];
+      lofs += (int64_t)wl[t] * DD_NB;
+      uofs += (int64_t)DD_NB * wu[t];
+      sofs += round4(wl[t]);
+      max_tile = std::max(max_tile, std::max((size_t)wl[t] * DD_NB * sizeof(T) + (size_t)round4(wl[t]) * 4,
+                                             (size_t)DD_NB * wu[t] * sizeof(T)));
+    }
+    // stage: ~84 KiB, or one whole tile when a tile is larger
+    size_t stage = std::max<size_t>(84 * 1024, max_tile);
+    stage = (stage + 127) & ~(size_t)127;
+    h->stage_bytes = (uint32_t)stage;
+    std::vector<SweepJob> jobs;
+    for (int j = 0; j < m; ++j) {
+      BandInfo &b = info[j];
+      b.jf0 = (int32_t)jobs.size();
+      for (int lo = 0; lo < b.ntiles;) {
+        size_t bytes = 0;
+        int hi = lo;
+        while (hi < b.ntiles) {
+          const TileMeta &q = tm[b.tile0 + hi];
+          const size_t tb = (size_t)q.wl * DD_NB * sizeof(T) + (size_t)round4(q.wl) * 4;
+          if (hi > lo && bytes + tb > stage) break;
+          bytes += tb;
+          ++hi;
+        }
+        jobs.push_back(SweepJob{lo, hi});
+        lo = hi;
+      }
+      b.njf = (int32_t)jobs.size() - b.jf0;
+      b.jb0 = (int32_t)jobs.size();
+      for (int hi = b.ntiles; hi > 0;) {
+        size_t bytes = 0;
+        int lo = hi;
+        while (lo > 0) {
+          const TileMeta &q = tm[b.tile0 + lo - 1];
+          const size_t tb = (size_t)DD_NB * q.wu * sizeof(T);
+          if (lo < hi && bytes + tb > stage) break;
+          bytes += tb;
+          --lo;
+        }
+        jobs.push_back(SweepJob{lo, hi});
+        hi = lo;
+      }
+      b.njb = (int32_t)jobs.size() - b.jb0;
+    }
+    CK(cudaMemcpyAsync(h->d_info, info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, s));
+    TRY(upload(h, &h->tm, tm));
+    TRY(upload(h, &h->jobs, jobs));
+    TRY(dalloc(h, &B.ltile, lofs));
+    TRY(dalloc(h, &B.utile, uofs));
+    TRY(dalloc(h, &h->src, sofs));
+    h->stats.factor_bytes = (lofs + uofs) * (int64_t)sizeof(T) + sofs * (int64_t)sizeof(int32_t);
+    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->sweep_threads, sizeof(T), h->stage_bytes) < 2) {
+      h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
+      return DD_ERR_INVALID_ARG;
+    }
+    CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tm, B.band, B.lm, h->piv,
+                            B.ltile, B.utile, h->src, s));
+  }
   // ---- couplings E (interior x interface) and F (interface x interior)
   TRY(upload(h, &h->e_ptr, hb.e_ptr));
   TRY(upload(h, &h->e_col, hb.e_col));
@@ -519,7 +583,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(launch_scatter_coo<T>((int64_t)xidx.size(), d_xidx, d_xval, B.X, s));
     // X_j = A_jj^-1 E(I_j, gam_j)
     CK(launch_band_solve_multi<T>(h->d_info, m, d_ncols, d_xoff, max_gam, h->max_kl, h->max_ku2,
-                                  B.ltile, B.utile, h->src, B.X, s));
+                                  h->tm, B.ltile, B.utile, h->src, B.X, s));
     // S(R_a,R_a) -= F(R_a, I_j) X_j
     CK(launch_schur_accumulate<T>(m, d_fr_ptr, d_fr_row, d_fr_agg, d_fs_ptr, d_fs_col, B.fsub_val,
                                   d_gam_ptr, d_gam_idx, d_gam_agg, d_xoff, h->d_info, B.X,
@@ -604,15 +668,15 @@ dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int p
   PrecBufs<T> &B = bufs<T>(h);
   if (part == 0 || part < 0)
   CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st,
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st,
                               h->sweep_threads, s));
   if (part == 1 || part < 0)
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, B.t, h->nG, x, s));
   if (part == 2 || part < 0)
   CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, B.z2, B.z1,
-                              h->d_perm, x, h->st, h->sweep_threads, s));
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
+                              B.z2, B.z1, h->d_perm, x, h->st, h->sweep_threads, s));
   return DD_OK;
 }
 
@@ -767,13 +831,13 @@ dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scrat
   const size_t z2_elems = (((size_t)std::max(h->nG, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   T *z2 = z1 + z1_elems;
   CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st,
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st,
                               h->sweep_threads, s));
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, s));
   CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val, z2, z1,
-                              h->d_perm, x, h->st, h->sweep_threads, s));
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
+                              z2, z1, h->d_perm, x, h->st, h->sweep_threads, s));
   return DD_OK;
 }
 

@@ -17,27 +17,36 @@ struct BandInfo {
   int32_t n;        // rows of A_jj
   int32_t kl, ku;   // lower / upper bandwidth of A_jj in its local order
   int32_t ntiles;   // ceil(n / DD_NB)
-  int64_t band_off; // offset of the band rows (elements): row i at band_off + i*wd
-  int64_t lm_off;   // offset of the unpermuted multipliers, n*kl entries
-  int64_t piv_off;  // offset into the pivot array (n entries)
-  int64_t ltile_off;// offset of the forward tiles (elements)
-  int64_t utile_off;// offset of the backward tiles (elements)
-  int64_t src_off;  // offset of the forward window permutations (int32)
+  int64_t band_off; // band rows (elements): row i at band_off + i*wd
+  int64_t lraw_off; // the LU's per-tile multipliers, (NB+kl) x NB column-major each
+  int64_t piv_off;  // pivots (n entries)
   int32_t row0;     // first row in the permuted interior numbering
-  int32_t pad;
+  int32_t tile0;    // index of the first tile in the packed tile tables
+  int32_t jf0, njf; // forward jobs [jf0, jf0 + njf) of the sweep ring
+  int32_t jb0, njb; // backward jobs
 };
 
 __host__ __device__ inline int bi_wd(const BandInfo &b) { return 2 * b.kl + b.ku + 1; }
 __host__ __device__ inline int bi_ku2(const BandInfo &b) { return b.kl + b.ku; }
-// window length of a forward tile and its element count:
-//   Linv (NB x NB, column-major) + L21 (kl x NB, column-major)
-__host__ __device__ inline int64_t bi_ltile_elems(const BandInfo &b) {
-  return (int64_t)DD_NB * DD_NB + (int64_t)b.kl * DD_NB;
+__host__ __device__ inline int64_t bi_lraw_elems(const BandInfo &b) {
+  return (int64_t)(DD_NB + b.kl) * DD_NB;
 }
-//   Uinv (NB x NB, column-major) + U12 (ku2 x NB, stored [q][i])
-__host__ __device__ inline int64_t bi_utile_elems(const BandInfo &b) {
-  return (int64_t)DD_NB * DD_NB + (int64_t)bi_ku2(b) * DD_NB;
-}
+
+// One packed sweep tile (offsets in elements of T / int32 for src):
+//   forward  K  wl x NB, row-major with 16-byte chunks swizzled by row
+//            (chunk c of row r stored at chunk c ^ (r & 7)); src wl entries
+//   backward Kb NB x wu, row-major
+struct TileMeta {
+  int64_t lofs, uofs, sofs;
+  int32_t wl, wu;
+};
+
+// a job of the sweep ring: tiles [lo, hi) of one subdomain, one bulk copy
+struct SweepJob {
+  int32_t lo, hi;
+};
+
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
 // Device-side error word: first failure wins.
 struct DevStatus {
@@ -49,9 +58,8 @@ struct Workspace;  // defined in dd_api.cu
 
 // ---- kernels exposed to dd_api.cu (implemented in k_band.cu / k_dense.cu /
 // ---- k_krylov.cu).  All return cudaGetLastError() of their launch.
-// Tile ring of the apply sweeps: bytes of one stage, and how many stages fit
-// next to the resident right-hand side (0: the subdomain is too large).
-uint32_t band_stage_bytes(int kl, int ku, int elem_size);
+// Tile ring of the apply sweeps: how many stages of stage_bytes fit next to
+// the resident right-hand side (0: the subdomain is too large).
 int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
                       uint32_t stage_bytes);
 // Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
@@ -62,33 +70,39 @@ template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
                            int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
                            cudaStream_t s);
+// Widths of every tile (forward rows wl and backward columns wu that hold
+// nonzeros after the factorisation), written to wl/wu at tile0 + t.
+template <typename T>
+cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_tiles, const T *band,
+                               const T *lraw, const int32_t *piv, int32_t *wl, int32_t *wu,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
-                              const T *band, const T *lm, const int32_t *piv, T *ltile, T *utile,
-                              int32_t *src, cudaStream_t s);
+                              const TileMeta *tm, const T *band, const T *lraw, const int32_t *piv,
+                              T *ltile, T *utile, int32_t *src, cudaStream_t s);
 // z = A_jj^-1 y_j per subdomain; y gathered through perm (original
 // numbering), z in the interior numbering.
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
-                                  const T *utile, const int32_t *src, const double *y,
-                                  const int32_t *perm, T *z, DevStatus *st, int threads,
-                                  cudaStream_t s);
+                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  const SweepJob *jobs, const T *ltile, const T *utile,
+                                  const int32_t *src, const double *y, const int32_t *perm, T *z,
+                                  DevStatus *st, int threads, cudaStream_t s);
 // x1 = z1 - A^-1 (E z2) per subdomain, scattered to x (original numbering).
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
-                                  const T *utile, const int32_t *src, const int32_t *e_ptr,
-                                  const int32_t *e_col, const T *e_val, const T *z2, const T *z1,
-                                  const int32_t *perm, double *x, DevStatus *st, int threads,
-                                  cudaStream_t s);
+                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  const SweepJob *jobs, const T *ltile, const T *utile,
+                                  const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
+                                  const T *e_val, const T *z2, const T *z1, const int32_t *perm,
+                                  double *x, DevStatus *st, int threads, cudaStream_t s);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>
 cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t *ncols,
                                     const int64_t *x_off, int max_cols, int max_kl, int max_ku2,
-                                    const T *ltile, const T *utile, const int32_t *src, T *X,
-                                    cudaStream_t s);
+                                    const TileMeta *tm, const T *ltile, const T *utile,
+                                    const int32_t *src, T *X, cudaStream_t s);
 
 // Dense blocks (k_dense.cu): block b of size p[b] at offset off[b], row-major.
 template <typename T>

@@ -1,25 +1,24 @@
-// Interior blocks A_jj: banded LU with partial pivoting, conversion of the
-// factors into sweep tiles, and the blocked forward/backward sweeps
+// Interior blocks A_jj: blocked banded LU with partial pivoting, packing of
+// the factors into sweep tiles, and the blocked forward/backward sweeps
 // (Section 4: exact triangular factors of every D_ii, all subdomains in one
 // launch; Algorithm 2: z1 = A^-1 y1 and x1 = z1 - A^-1 (E x2)).
 //
 // Storage (per subdomain j, rows in the local RCM order):
 //   band   row i holds columns i-kl .. i+kl+ku at offsets 0 .. 2kl+ku
-//   lm     multipliers of step k (rows k+1..k+kl in the row order of step k)
+//   lraw   per tile of DD_NB = 32 columns, the multipliers in the row order
+//          after the tile's exchanges, (NB+kl) x NB column-major
 //   piv    row exchanged with k at step k
-// Sweep tiles (DD_NB = 32 columns each):
-//   forward tile t, window rows c0 .. c0+NB+kl-1 (c0 = t*NB):
+// Packed sweep tiles (TileMeta), trimmed to the rows / columns that hold
+// nonzeros after the factorisation:
+//   forward tile t, window rows c0 .. c0+wl-1 (c0 = t*NB):
 //     src[q]   window position whose value moves to q once the tile's row
 //              exchanges are applied in order
-//     K        (NB+kl) x NB, column-major: rows 0..NB-1 hold Linv, the inverse
-//              of the tile's unit lower triangle L11 (multipliers with the
-//              later exchanges of the same tile applied); rows NB.. hold
-//              -L21 Linv.  The tile step is w <- [0; w_B] + K w_T on the
-//              exchanged window w.
+//     K        wl x NB: rows 0..NB-1 hold Linv, the inverse of the tile's
+//              unit lower triangle L11; rows NB.. hold -L21 Linv.  The tile
+//              step is w <- [0; w_B] + K w_T on the exchanged window w.
 //   backward tile t, rows r0 .. r0+NB-1:
-//     Kb       NB x (NB+kl+ku), row-major: [Uinv | -Uinv U12], Uinv the
-//              inverse of the tile's upper triangle U11 and U12 the band to
-//              its right, so x_T = Kb [b_T; x_next].
+//     Kb       NB x wu: [Uinv | -Uinv U12], Uinv the inverse of the tile's
+//              upper triangle, so x_T = Kb [b_T; x_next].
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,13 +26,25 @@
 
 namespace {
 
-__host__ __device__ inline int src_stride(int kl) { return ((DD_NB + kl) + 3) & ~3; }
+__host__ __device__ inline int src_stride_w(int w) { return round4(w); }
+// zero padding beyond the tiles of the resident vectors: room for the
+// widest window or row of a tile, a multiple of 32 elements
+__host__ __device__ inline int sweep_pad_hd(int max_kl, int max_ku2) {
+  return ((max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB + 31) & ~31;
+}
 
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
 
 __device__ void set_status(DevStatus *st, int code, int block) {
   if (atomicCAS(&st->code, 0, code) == 0) st->block = block;
+}
+
+// element (r, c) of a forward tile K (row-major, 16-byte chunks swizzled by row)
+template <typename T>
+__host__ __device__ __forceinline__ int kidx(int r, int c) {
+  constexpr int CH = 16 / sizeof(T);
+  return r * DD_NB + (((c / CH) ^ (r & 7)) * CH) + (c % CH);
 }
 
 // ---------------------------------------------------------------------------
@@ -45,8 +56,7 @@ __device__ void set_status(DevStatus *st, int code, int block) {
 //     magnitude as pivot, exchanges of whole window rows),
 //   - U12 = L11^-1 A12 and A22 -= L21 U12 (rank-NB update),
 //   - the window goes back to the band rows and the panel's multipliers, in
-//     the row order after the panel's exchanges, to ltraw (column-major
-//     (NB+kl) x NB per tile).
+//     the row order after the panel's exchanges, to lraw.
 // The pivots are those of the column-by-column algorithm; the exchanges of
 // later columns reach the multipliers of earlier columns of the same tile
 // only, which is the order the forward sweep applies them in.
@@ -171,7 +181,7 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
     __syncthreads();
     // multipliers of the panel (strictly below the diagonal), then the window
     // back to the band rows (multiplier positions zero)
-    T *lt = ltraw + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
+    T *lt = ltraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b);
     for (int e = tid; e < R * DD_NB; e += nt) {
       const int c = e / R, r = e % R;
       lt[e] = (r > c && c < nbe) ? W[r * ldw + c] : T(0);
@@ -187,28 +197,69 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
 }
 
 // ---------------------------------------------------------------------------
-// Sweep tiles: one warp per (subdomain, tile); lane = tile column / row.
+// Tile widths, one warp per (subdomain, tile):
+//   wl = rows of the forward window that the tile touches: the last nonzero
+//        multiplier row of any of its columns, and every pivot row, at
+//        least NB, rounded up to 4;
+//   wu = NB + the columns right of the tile that its U rows reach, rounded
+//        up to 4.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__restrict__ band,
-                                  const T *__restrict__ lm, const int32_t *__restrict__ piv,
-                                  T *ltile, T *utile, int32_t *srcs) {
+__global__ void tile_widths_kernel(const BandInfo *__restrict__ info, const T *__restrict__ band,
+                                   const T *__restrict__ lraw, const int32_t *__restrict__ piv,
+                                   int32_t *wl, int32_t *wu) {
   const BandInfo b = info[blockIdx.x];
   const int t = blockIdx.y;
   if (t >= b.ntiles) return;
+  const int n = b.n, kl = b.kl, wd = 2 * b.kl + b.ku + 1, W = DD_NB + kl;
+  const int c0 = t * DD_NB, lane = threadIdx.x;
+  int el = DD_NB - 1, eu = -1;
+  const int c = c0 + lane;
+  if (c < n) {
+    const T *col = lraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b) + (int64_t)lane * W;
+    for (int q = W - 1; q > lane; --q)
+      if (col[q] != T(0)) { el = max(el, q); break; }
+    el = max(el, piv[b.piv_off + c] - c0);
+    const T *row = band + b.band_off + (int64_t)c * wd;
+    for (int off = wd - 1; off >= kl; --off)
+      if (row[off] != T(0)) { eu = (c + off - kl) - (c0 + DD_NB); break; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    el = max(el, __shfl_xor_sync(0xffffffffu, el, o));
+    eu = max(eu, __shfl_xor_sync(0xffffffffu, eu, o));
+  }
+  if (lane == 0) {
+    wl[b.tile0 + t] = round4(el + 1);
+    wu[b.tile0 + t] = round4(DD_NB + max(eu + 1, 0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Packed sweep tiles: one warp per (subdomain, tile); lane = tile column / row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const TileMeta *__restrict__ tm,
+                                  const T *__restrict__ band, const T *__restrict__ lraw,
+                                  const int32_t *__restrict__ piv, T *ltile, T *utile,
+                                  int32_t *srcs) {
+  const BandInfo b = info[blockIdx.x];
+  const int t = blockIdx.y;
+  if (t >= b.ntiles) return;
+  const TileMeta mt = tm[b.tile0 + t];
   const int n = b.n, kl = b.kl, ku2 = b.kl + b.ku, wd = 2 * b.kl + b.ku + 1;
-  const int W = DD_NB + kl;
+  const int W = DD_NB + kl, WL = mt.wl, WU = mt.wu;
   const int c0 = t * DD_NB;
   const int lane = threadIdx.x;
-  const T *A = band + b.band_off;
   const int32_t *P = piv + b.piv_off;
-  T *lt = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
-  T *ut = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
-  int32_t *src = srcs + b.src_off + (int64_t)t * src_stride(kl);
-  extern __shared__ unsigned char smraw[];
-  T *L11 = reinterpret_cast<T *>(smraw);         // NB x NB, [row][col]
-  T *vbuf = L11 + DD_NB * DD_NB;                 // 32 columns x W, then NB x NB
-  int32_t *idx = reinterpret_cast<int32_t *>(vbuf + (size_t)DD_NB * W + DD_NB * DD_NB);
+  const T *A = band + b.band_off;
+  T *K = ltile + mt.lofs;
+  T *Kb = utile + mt.uofs;
+  int32_t *src = srcs + mt.sofs;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *L11 = reinterpret_cast<T *>(smraw);  // NB x NB, [row][col]
+  T *vbuf = L11 + DD_NB * DD_NB;          // 32 columns x W
+  T *Lsm = vbuf + (size_t)DD_NB * W;      // NB x NB
+  int32_t *idx = reinterpret_cast<int32_t *>(Lsm + DD_NB * DD_NB);
 
   // (1) composite window permutation of the tile's row exchanges
   if (lane == 0) {
@@ -219,20 +270,17 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
     }
   }
   __syncwarp();
-  for (int q = lane; q < W; q += 32) src[q] = idx[q];
+  for (int q = lane; q < src_stride_w(WL); q += 32) src[q] = (q < W) ? idx[q] : q;
 
-  // (2) multipliers of column c0+lane, already in the row order after the
-  //     tile's exchanges (written so by the blocked LU)
+  // (2) multipliers of column c0+lane (already in the exchanged row order)
   {
     T *v = vbuf + (size_t)lane * W;
-    const T *lr = lm + b.ltile_off + (int64_t)t * bi_ltile_elems(b) + (int64_t)lane * W;
+    const T *lr = lraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b) + (int64_t)lane * W;
     for (int q = 0; q < W; ++q) v[q] = lr[q];
     for (int q = 0; q < DD_NB; ++q) L11[q * DD_NB + lane] = (q == lane) ? T(1) : (q > lane ? v[q] : T(0));
   }
   __syncwarp();
-  // (3) Linv: column `lane` of the inverse of the unit lower triangle; then
-  //     K = [Linv; -L21 Linv], column-major (NB+kl) x NB
-  T *Lsm = vbuf + (size_t)DD_NB * W;  // NB x NB, [row][col], after the columns
+  // (3) Linv (column `lane`), then K = [Linv; -L21 Linv] for rows < WL
   {
     T x[DD_NB];
 #pragma unroll
@@ -244,18 +292,16 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
       x[q] = -s;
     }
     for (int q = 0; q < DD_NB; ++q) {
-      lt[(int64_t)lane * W + q] = x[q];
+      K[kidx<T>(q, lane)] = x[q];
       Lsm[q * DD_NB + lane] = x[q];
     }
   }
   __syncwarp();
-  {
-    // lane = column c of K: rows NB+r hold -sum_k L21(r,k) Linv(k,c)
-    for (int r = 0; r < kl; ++r) {
-      T s = T(0);
-      for (int k = 0; k < DD_NB; ++k) s += vbuf[(size_t)k * W + DD_NB + r] * Lsm[k * DD_NB + lane];
-      lt[(int64_t)lane * W + DD_NB + r] = -s;
-    }
+  for (int r = DD_NB; r < WL; ++r) {
+    T s = T(0);
+    if (r < W)
+      for (int k = 0; k < DD_NB; ++k) s += vbuf[(size_t)k * W + r] * Lsm[k * DD_NB + lane];
+    K[kidx<T>(r, lane)] = -s;
   }
   __syncwarp();
   // (4) U11 (row-major in L11's buffer) and its inverse; Kb = [Uinv | -Uinv U12]
@@ -275,7 +321,6 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
   }
   __syncwarp();
   {
-    // column `lane` of U11^-1: x[lane] = 1/U(lane,lane), back substitution up
     T x[DD_NB];
 #pragma unroll
     for (int q = 0; q < DD_NB; ++q) x[q] = T(0);
@@ -289,14 +334,12 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
   }
   __syncwarp();
   {
-    // lane = row i of Kb
-    const int KW = DD_NB + ku2;
-    T *kr = ut + (int64_t)lane * KW;
+    T *kr = Kb + (int64_t)lane * WU;
     for (int c = 0; c < DD_NB; ++c) kr[c] = Lsm[lane * DD_NB + c];
-    for (int q = 0; q < ku2; ++q) {
+    for (int q = 0; q < WU - DD_NB; ++q) {
       const int col = c0 + DD_NB + q;
       T s = T(0);
-      if (col < n)
+      if (col < n && q < ku2)
         for (int k = lane; k < DD_NB; ++k) {
           const int rk = c0 + k;
           if (rk >= n) break;
@@ -312,10 +355,12 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const T *__
 // Single right-hand side sweeps (the apply).  One CTA per subdomain keeps the
 // right-hand side in shared memory; the tiles stream through a ring of
 // shared-memory stages filled by TMA bulk copies (cp.async.bulk, completion
-// on an mbarrier), forward tiles 0..T-1 then backward tiles T-1..0 as one job
-// sequence, so the copy of job q+S overlaps the arithmetic of job q.
-// Every wait on an mbarrier is bounded; on expiry the CTA records
-// DD_ERR_TIMEOUT, drains its own copies (bounded again) and returns.
+// on an mbarrier).  A job is a run of consecutive tiles of one sweep packed
+// into one copy (a copy's fixed cost is amortised only by copies of tens of
+// kilobytes); forward jobs, then backward jobs, form one sequence, so the
+// copy of job q+S overlaps the arithmetic of job q.  Every wait on an
+// mbarrier is bounded; on expiry the CTA records DD_ERR_TIMEOUT, drains its
+// own copies (bounded again) and returns.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -350,72 +395,76 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
-// Jobs of subdomain b: forward groups of gf consecutive tiles, then backward
-// groups of gb tiles taken from the end; one job = one bulk copy of
-// contiguous tile data (plus the forward window permutations), because a
-// copy's fixed cost is amortised only by copies of tens of kilobytes.
-struct Jobs {
-  int T, gf, gb, jf, jb;
-};
-template <typename T>
-__device__ __forceinline__ Jobs make_jobs(const BandInfo &b, uint32_t stage_bytes) {
-  Jobs J;
-  J.T = b.ntiles;
-  const uint32_t lb = (uint32_t)(bi_ltile_elems(b) * sizeof(T)) + (uint32_t)(src_stride(b.kl) * 4);
-  const uint32_t ub = (uint32_t)(bi_utile_elems(b) * sizeof(T));
-  J.gf = max(1, (int)(stage_bytes / lb));
-  J.gb = max(1, (int)(stage_bytes / ub));
-  J.jf = (J.T + J.gf - 1) / J.gf;
-  J.jb = (J.T + J.gb - 1) / J.gb;
-  return J;
+// job q of subdomain b (forward jobs first), tiles [lo, hi)
+__device__ __forceinline__ SweepJob get_job(const BandInfo &b, const SweepJob *jobs, int q, bool &fwd) {
+  fwd = q < b.njf;
+  return jobs[fwd ? b.jf0 + q : b.jb0 + (q - b.njf)];
 }
-// tile range [lo, hi) of job q
-__device__ __forceinline__ void job_range(const Jobs &J, int q, int &lo, int &hi) {
-  if (q < J.jf) {
-    lo = q * J.gf;
-    hi = min(J.T, lo + J.gf);
-  } else {
-    const int k = q - J.jf;
-    hi = J.T - k * J.gb;
-    lo = max(0, hi - J.gb);
-  }
-}
+
 template <typename T>
-__device__ __forceinline__ void issue_job(const BandInfo &b, const Jobs &J, int q, const T *ltile,
-                                          const T *utile, const int32_t *srcs,
+__device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
+                                          int q, const T *ltile, const T *utile, const int32_t *srcs,
                                           unsigned char *stage, uint64_t *bar) {
-  int lo, hi;
-  job_range(J, q, lo, hi);
-  const int nt = hi - lo;
-  if (q < J.jf) {
-    const uint32_t lb = (uint32_t)(bi_ltile_elems(b) * sizeof(T)) * nt;
-    const uint32_t sb = (uint32_t)(src_stride(b.kl) * sizeof(int32_t)) * nt;
+  bool fwd;
+  const SweepJob jb = get_job(b, jobs, q, fwd);
+  const TileMeta &a = tm[b.tile0 + jb.lo];
+  if (fwd) {
+    const TileMeta &z = tm[b.tile0 + jb.hi - 1];
+    const uint32_t lb = (uint32_t)((z.lofs + (int64_t)z.wl * DD_NB - a.lofs) * sizeof(T));
+    const uint32_t sb = (uint32_t)((z.sofs + src_stride_w(z.wl) - a.sofs) * sizeof(int32_t));
     mbar_expect_tx(bar, lb + sb);
-    bulk_g2s(stage, ltile + b.ltile_off + (int64_t)lo * bi_ltile_elems(b), lb, bar);
-    bulk_g2s(stage + lb, srcs + b.src_off + (int64_t)lo * src_stride(b.kl), sb, bar);
+    bulk_g2s(stage, ltile + a.lofs, lb, bar);
+    bulk_g2s(stage + lb, srcs + a.sofs, sb, bar);
   } else {
-    const uint32_t ub = (uint32_t)(bi_utile_elems(b) * sizeof(T)) * nt;
+    const TileMeta &z = tm[b.tile0 + jb.hi - 1];
+    const uint32_t ub = (uint32_t)((z.uofs + (int64_t)DD_NB * z.wu - a.uofs) * sizeof(T));
     mbar_expect_tx(bar, ub);
-    bulk_g2s(stage, utile + b.utile_off + (int64_t)lo * bi_utile_elems(b), ub, bar);
+    bulk_g2s(stage, utile + a.uofs, ub, bar);
   }
 }
+
+// 16-byte chunk of T values
+template <typename T>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  // acc + a . b as a chain of fused multiply-adds
+  __device__ static float fmadd(const float4 &a, const float4 &b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+  }
+};
+template <>
+struct Chunk<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static double fmadd(const double2 &a, const double2 &b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+  }
+};
 
 // Forward sweep in place over vec, backward sweep from vec into xout (both in
 // shared memory, length >= ntiles*NB + pad, xout zero beyond the tiles).
 // Returns false if a wait expired.
 template <typename T>
-__device__ bool sweep_pipelined(const BandInfo &b, const T *__restrict__ ltile,
+__device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ tm,
+                                const SweepJob *__restrict__ jobs, const T *__restrict__ ltile,
                                 const T *__restrict__ utile, const int32_t *__restrict__ srcs,
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
                                 DevStatus *st) {
-  const int kl = b.kl, ku2 = b.kl + b.ku, W = DD_NB + kl, KW = DD_NB + ku2;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const Jobs J = make_jobs<T>(b, stage_bytes);
-  const int nj = J.jf + J.jb;
+  using CV = typename Chunk<T>::V;
+  constexpr int CN = Chunk<T>::N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nj = b.njf + b.njb;
   if (tid == 0) {
     for (int q = 0; q < nstages && q < nj; ++q)
-      issue_job<T>(b, J, q, ltile, utile, srcs, ring + (size_t)q * stage_bytes, &bars[q]);
+      issue_job<T>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)q * stage_bytes, &bars[q]);
   }
   bool ok = true;
   int q = 0;
@@ -425,64 +474,62 @@ __device__ bool sweep_pipelined(const BandInfo &b, const T *__restrict__ ltile,
     // every thread waits (bounded); the verdict is made uniform at the
     // first barrier of the job, so no thread can leave the loop alone
     const bool got = mbar_wait_bounded(&bars[sidx], (uint32_t)((q / nstages) & 1));
-    int lo, hi;
-    job_range(J, q, lo, hi);
-    if (q < J.jf) {
-      const size_t lbytes = bi_ltile_elems(b) * sizeof(T);
-      const int32_t *src0 = reinterpret_cast<const int32_t *>(stage + lbytes * (hi - lo));
-      for (int t = lo; t < hi; ++t) {
+    bool fwd;
+    const SweepJob jb = get_job(b, jobs, q, fwd);
+    const TileMeta &a = tm[b.tile0 + jb.lo];
+    if (fwd) {
+      const TileMeta &z = tm[b.tile0 + jb.hi - 1];
+      const size_t kbytes = (size_t)(z.lofs + (int64_t)z.wl * DD_NB - a.lofs) * sizeof(T);
+      for (int t = jb.lo; t < jb.hi; ++t) {
         // forward tile t: w <- [0; w_B] + K w_T on the exchanged window
-        const int c0 = t * DD_NB;
-        const T *K = reinterpret_cast<const T *>(stage + lbytes * (t - lo));
-        const int32_t *src = src0 + (size_t)src_stride(kl) * (t - lo);
+        const TileMeta &mt = tm[b.tile0 + t];
+        const int c0 = t * DD_NB, WL = mt.wl;
+        const T *K = reinterpret_cast<const T *>(stage + (mt.lofs - a.lofs) * sizeof(T));
+        const int32_t *src = reinterpret_cast<const int32_t *>(stage + kbytes) + (mt.sofs - a.sofs);
         if (got)
-          for (int e = tid; e < W; e += nt) win[e] = vec[c0 + src[e]];
+          for (int e = tid; e < WL; e += nt) win[e] = vec[c0 + src[e]];
         if (!__syncthreads_and(got)) { ok = false; break; }
-        for (int r = tid; r < W; r += nt) {
-          // four independent partial sums shorten the dependent chain
-          T a0 = (r < DD_NB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
+        for (int r = tid; r < WL; r += nt) {
+          const CV *kr = reinterpret_cast<const CV *>(K + r * DD_NB);
+          const CV *wv = reinterpret_cast<const CV *>(win);
+          T a0 = (r < DD_NB) ? T(0) : win[r], a1 = T(0);
 #pragma unroll
-          for (int c = 0; c < DD_NB; c += 4) {
-            a0 += K[(c + 0) * W + r] * win[c + 0];
-            a1 += K[(c + 1) * W + r] * win[c + 1];
-            a2 += K[(c + 2) * W + r] * win[c + 2];
-            a3 += K[(c + 3) * W + r] * win[c + 3];
+          for (int ch = 0; ch < DD_NB / CN; ch += 2) {
+            a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
+            a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
           }
-          vec[c0 + r] = (a0 + a1) + (a2 + a3);
+          vec[c0 + r] = a0 + a1;
         }
         __syncthreads();
       }
       if (!ok) break;
     } else {
-      const size_t ubytes = bi_utile_elems(b) * sizeof(T);
-      for (int t = hi - 1; t >= lo; --t) {
-        // backward tile t: x_T = Kb [b_T; x_next], one warp per output row;
+      for (int t = jb.hi - 1; t >= jb.lo; --t) {
+        // backward tile t: x_T = Kb [b_T; x_next]; 8 threads per output row;
         // the outputs xout[r0..r0+NB) never overlap this tile's inputs
-        const int r0 = t * DD_NB;
-        const T *Kb = reinterpret_cast<const T *>(stage + ubytes * (t - lo));
-        // eight threads per output row (rows tid/8), strided over the row
-        for (int e = tid; e < DD_NB * 8; e += nt) {
-          const int i = e >> 3, h = e & 7;
-          const T *kr = Kb + i * KW;
+        const TileMeta &mt = tm[b.tile0 + t];
+        const int r0 = t * DD_NB, WU = mt.wu, nch = WU / CN;
+        const T *Kb = reinterpret_cast<const T *>(stage + (mt.uofs - a.uofs) * sizeof(T));
+        const int i = tid >> 3, h = tid & 7;
+        T acc = T(0);
+        if (got) {
+          const CV *kr = reinterpret_cast<const CV *>(Kb + (int64_t)i * WU);
+          const CV *bv = reinterpret_cast<const CV *>(vec + r0);
+          const CV *xv = reinterpret_cast<const CV *>(xout + r0);
           T a0 = T(0), a1 = T(0);
-          if (got) {
-            int k = h;
-            for (; k < DD_NB; k += 16) {
-              a0 += kr[k] * vec[r0 + k];
-              if (k + 8 < DD_NB) a1 += kr[k + 8] * vec[r0 + k + 8];
-            }
-            for (k = DD_NB + h; k + 8 < KW; k += 16) {
-              a0 += kr[k] * xout[r0 + k];
-              a1 += kr[k + 8] * xout[r0 + k + 8];
-            }
-            if (k < KW) a0 += kr[k] * xout[r0 + k];
+          int ch = h;
+          for (; ch < DD_NB / CN; ch += 8) a0 = Chunk<T>::fmadd(kr[ch], bv[ch], a0);
+          for (; ch + 8 < nch; ch += 16) {
+            a0 = Chunk<T>::fmadd(kr[ch], xv[ch], a0);
+            a1 = Chunk<T>::fmadd(kr[ch + 8], xv[ch + 8], a1);
           }
-          T acc = a0 + a1;
-          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-          if (h == 0) xout[r0 + i] = acc;
+          if (ch < nch) a0 = Chunk<T>::fmadd(kr[ch], xv[ch], a0);
+          acc = a0 + a1;
         }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (h == 0) xout[r0 + i] = acc;
         if (!__syncthreads_and(got)) { ok = false; break; }
       }
       if (!ok) break;
@@ -490,7 +537,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const T *__restrict__ ltile,
     // the stage is free; vec / xout are current
     if (tid == 0 && q + nstages < nj) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_job<T>(b, J, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
+      issue_job<T>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
     }
   }
   if (!ok) {
@@ -508,21 +555,40 @@ __device__ bool sweep_pipelined(const BandInfo &b, const T *__restrict__ ltile,
   return ok;
 }
 
-// shared-memory layout: [bars | vec | xout | win | ring]
+// shared-memory layout: [bars | vec | xout | win | tile table | job table | ring]
 template <typename T>
 __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, int max_kl,
-                                      uint64_t *&bars, T *&vec, T *&xout, T *&win,
+                                      int max_tiles, int max_jobs, uint64_t *&bars, T *&vec,
+                                      T *&xout, T *&win, TileMeta *&tms, SweepJob *&jbs,
                                       unsigned char *&ring) {
   bars = reinterpret_cast<uint64_t *>(smraw);
   vec = reinterpret_cast<T *>(smraw + 64);
   xout = vec + max_n + pad;
   win = xout + max_n + pad;
-  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + DD_NB + max_kl);
+  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + DD_NB + max_kl + 8);
+  used = (used + 15) & ~(size_t)15;
+  tms = reinterpret_cast<TileMeta *>(smraw + used);
+  used += sizeof(TileMeta) * (size_t)max_tiles;
+  jbs = reinterpret_cast<SweepJob *>(smraw + used);
+  used += sizeof(SweepJob) * (size_t)max_jobs;
   used = (used + 127) & ~(size_t)127;
   ring = smraw + used;
 }
 
-template <typename T>
+// this subdomain's tile and job tables into shared memory; returns the
+// BandInfo with tile0 / jf0 / jb0 rebased onto the local tables
+__device__ __forceinline__ BandInfo stage_tables(BandInfo b, const TileMeta *__restrict__ tm,
+                                                 const SweepJob *__restrict__ jobs, TileMeta *tms,
+                                                 SweepJob *jbs) {
+  for (int t = threadIdx.x; t < b.ntiles; t += blockDim.x) tms[t] = tm[b.tile0 + t];
+  for (int q = threadIdx.x; q < b.njf; q += blockDim.x) jbs[q] = jobs[b.jf0 + q];
+  for (int q = threadIdx.x; q < b.njb; q += blockDim.x) jbs[b.njf + q] = jobs[b.jb0 + q];
+  b.tile0 = 0;
+  b.jf0 = 0;
+  b.jb0 = b.njf;
+  return b;
+}
+
 __device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) mbar_init(&bars[s], 1);
@@ -534,24 +600,28 @@ __device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
 // z = A_jj^-1 y_j with y gathered from the original numbering.
 template <typename T>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
-                                      int max_ku2, int nstages, uint32_t stage_bytes,
+                                      int max_ku2, int max_tiles, int max_jobs, int nstages,
+                                      uint32_t stage_bytes,
+                                      const TileMeta *__restrict__ tm, const SweepJob *__restrict__ jobs,
                                       const T *__restrict__ ltile, const T *__restrict__ utile,
                                       const int32_t *__restrict__ srcs, const double *__restrict__ y,
                                       const int32_t *__restrict__ perm, T *z, DevStatus *st) {
-  const BandInfo b = info[blockIdx.x];
-  if (b.n == 0) return;
+  const BandInfo bg = info[blockIdx.x];
+  if (bg.n == 0) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  const int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
+  const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
-  carve<T>(smraw, max_n, pad, max_kl, bars, vec, xout, win, ring);
-  init_bars<T>(bars, nstages);
+  TileMeta *tms; SweepJob *jbs;
+  carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+  init_bars(bars, nstages);
   const int ntot = b.ntiles * DD_NB + pad;
   for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
     vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
     xout[i] = T(0);
   }
   __syncthreads();
-  if (!sweep_pipelined<T>(b, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
+  if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
     return;
   for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
 }
@@ -559,7 +629,9 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
 template <typename T>
 __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
-                                      int max_ku2, int nstages, uint32_t stage_bytes,
+                                      int max_ku2, int max_tiles, int max_jobs, int nstages,
+                                      uint32_t stage_bytes,
+                                      const TileMeta *__restrict__ tm, const SweepJob *__restrict__ jobs,
                                       const T *__restrict__ ltile, const T *__restrict__ utile,
                                       const int32_t *__restrict__ srcs,
                                       const int32_t *__restrict__ e_ptr,
@@ -567,13 +639,15 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       const T *__restrict__ e_val, const T *__restrict__ z2,
                                       const T *__restrict__ z1, const int32_t *__restrict__ perm,
                                       double *x, DevStatus *st) {
-  const BandInfo b = info[blockIdx.x];
-  if (b.n == 0) return;
+  const BandInfo bg = info[blockIdx.x];
+  if (bg.n == 0) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  const int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
+  const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
-  carve<T>(smraw, max_n, pad, max_kl, bars, vec, xout, win, ring);
-  init_bars<T>(bars, nstages);
+  TileMeta *tms; SweepJob *jbs;
+  carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+  init_bars(bars, nstages);
   const int ntot = b.ntiles * DD_NB + pad;
   for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
     T v = T(0);
@@ -585,7 +659,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     xout[i] = T(0);
   }
   __syncthreads();
-  if (!sweep_pipelined<T>(b, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
+  if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
     return;
   for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
     const int r = b.row0 + i;
@@ -602,6 +676,7 @@ template <typename T, int NR>
 __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
                                         const int32_t *__restrict__ ncols,
                                         const int64_t *__restrict__ x_off,
+                                        const TileMeta *__restrict__ tm,
                                         const T *__restrict__ ltile, const T *__restrict__ utile,
                                         const int32_t *__restrict__ srcs, T *Xall) {
   const BandInfo b = info[blockIdx.x];
@@ -609,36 +684,37 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
   const int k0 = blockIdx.y * NR;
   if (b.n == 0 || k0 >= nc) return;
   const int nr = min(NR, nc - k0);
-  const int n = b.n, kl = b.kl, ku2 = b.kl + b.ku, W = DD_NB + kl;
+  const int n = b.n;
   T *X = Xall + x_off[blockIdx.x] + (int64_t)k0 * n;
-  extern __shared__ unsigned char smraw[];
-  T *win = reinterpret_cast<T *>(smraw);  // (NB + max(kl,ku2)) x NR, [row][r]
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *win = reinterpret_cast<T *>(smraw);  // max(wl, wu) x NR, [row][r]
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int KW = DD_NB + ku2;
   // forward: X(window) <- [0; X_B] + K X_T on the exchanged window
   for (int t = 0; t < b.ntiles; ++t) {
-    const int c0 = t * DD_NB;
-    const int32_t *src = srcs + b.src_off + (int64_t)t * src_stride(kl);
-    const T *K = ltile + b.ltile_off + (int64_t)t * bi_ltile_elems(b);
-    for (int e = tid; e < W * NR; e += nt) {
+    const TileMeta mt = tm[b.tile0 + t];
+    const int c0 = t * DD_NB, WL = mt.wl;
+    const int32_t *src = srcs + mt.sofs;
+    const T *K = ltile + mt.lofs;
+    for (int e = tid; e < WL * NR; e += nt) {
       int q = e / NR, r = e % NR;
       int row = c0 + src[q];
       win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < W * NR; e += nt) {
+    for (int e = tid; e < WL * NR; e += nt) {
       int i = e / NR, r = e % NR;
       T acc = (i < DD_NB) ? T(0) : win[e];
-      for (int c = 0; c < DD_NB; ++c) acc += K[c * W + i] * win[c * NR + r];
+      for (int c = 0; c < DD_NB; ++c) acc += K[kidx<T>(i, c)] * win[c * NR + r];
       if (c0 + i < n && r < nr) X[(int64_t)r * n + c0 + i] = acc;
     }
     __syncthreads();
   }
   // backward: X_T <- Kb [X_T; X_next]
   for (int t = b.ntiles - 1; t >= 0; --t) {
-    const int r0 = t * DD_NB;
-    const T *Kb = utile + b.utile_off + (int64_t)t * bi_utile_elems(b);
-    for (int e = tid; e < KW * NR; e += nt) {
+    const TileMeta mt = tm[b.tile0 + t];
+    const int r0 = t * DD_NB, WU = mt.wu;
+    const T *Kb = utile + mt.uofs;
+    for (int e = tid; e < WU * NR; e += nt) {
       int q = e / NR, r = e % NR;
       int row = r0 + q;
       win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
@@ -647,7 +723,7 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
     for (int e = tid; e < DD_NB * NR; e += nt) {
       int i = e / NR, r = e % NR;
       T acc = T(0);
-      for (int k = 0; k < KW; ++k) acc += Kb[i * KW + k] * win[k * NR + r];
+      for (int k = 0; k < WU; ++k) acc += Kb[(int64_t)i * WU + k] * win[k * NR + r];
       if (r0 + i < n && r < nr) X[(int64_t)r * n + r0 + i] = acc;
     }
     __syncthreads();
@@ -659,53 +735,33 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static size_t tiles_smem(int max_kl, size_t es) {
-  int W = DD_NB + max_kl;
-  return es * (size_t)(2 * DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
-}
-static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, int threads, size_t es) {
-  (void)threads;
-  int pad = (max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB;
-  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + DD_NB + max_kl);
-  return (used + 127) & ~(size_t)127;
-}
-#define DD_SMEM_LIMIT (227 * 1024)
-#define DD_MAX_STAGES 4
-// stages of the tile ring that fit next to the resident vector (0: does not fit)
-int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
-                      uint32_t stage_bytes) {
-  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, threads, (size_t)elem_size);
-  if (base + 2 * (size_t)stage_bytes > DD_SMEM_LIMIT) return 0;
-  int s = (int)((DD_SMEM_LIMIT - base) / stage_bytes);
-  return s > DD_MAX_STAGES ? DD_MAX_STAGES : s;
-}
-// bytes of one stage: whole tiles filling up to ~84 KiB (at least one forward
-// and one backward tile); the jobs of a subdomain then pack as many tiles
-// as fit, since a bulk copy's fixed cost is amortised only by large copies
-uint32_t band_stage_bytes(int kl, int ku, int elem_size) {
-  const size_t f = (size_t)DD_NB * (DD_NB + kl) * elem_size + (size_t)src_stride(kl) * 4;
-  const size_t b = (size_t)DD_NB * (DD_NB + kl + ku) * elem_size;
-  size_t S = 84 * 1024;
-  if (f > S) S = f;
-  if (b > S) S = b;
-  const size_t mf = (S / f) * f, mb = (S / b) * b;
-  const size_t m = mf > mb ? mf : mb;
-  return (uint32_t)((m + 127) & ~(size_t)127);
-}
-#define DD_MULTI_NR 16
-static size_t multi_smem(int max_kl, int max_ku2, size_t es) {
-  int w = DD_NB + (max_kl > max_ku2 ? max_kl : max_ku2);
-  return es * (size_t)w * DD_MULTI_NR;
-}
-
 template <typename K>
 static cudaError_t ensure_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, int max_tiles,
+                               int max_jobs) {
+  const int pad = sweep_pad_hd(max_kl, max_ku2);
+  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + DD_NB + max_kl + 8);
+  used = (used + 15) & ~(size_t)15;
+  used += sizeof(TileMeta) * (size_t)max_tiles + sizeof(SweepJob) * (size_t)max_jobs;
+  return (used + 127) & ~(size_t)127;
+}
+#define DD_SMEM_LIMIT (227 * 1024)
+#define DD_MAX_STAGES 4
+int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
+                      uint32_t stage_bytes) {
+  (void)threads;
+  // tables: at most max_n / NB tiles and twice as many jobs
+  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, max_n / DD_NB,
+                                 2 * (max_n / DD_NB));
+  if (stage_bytes == 0 || base + 2 * (size_t)stage_bytes > DD_SMEM_LIMIT) return 0;
+  int s = (int)((DD_SMEM_LIMIT - base) / stage_bytes);
+  return s > DD_MAX_STAGES ? DD_MAX_STAGES : s;
+}
 
-// shared memory of the blocked LU window (0: it goes to global scratch)
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
   const int R = DD_NB + max_kl, Cw = DD_NB + max_kl + max_ku;
   return (size_t)R * (size_t)(Cw | 1) * elem_size;
@@ -726,84 +782,103 @@ cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku
 }
 
 template <typename T>
+cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_tiles, const T *band,
+                               const T *lraw, const int32_t *piv, int32_t *wl, int32_t *wu,
+                               cudaStream_t s) {
+  if (m <= 0 || max_tiles <= 0) return cudaSuccess;
+  tile_widths_kernel<T><<<dim3(m, max_tiles), 32, 0, s>>>(d_info, band, lraw, piv, wl, wu);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
-                              const T *band, const T *lm, const int32_t *piv, T *ltile, T *utile,
-                              int32_t *src, cudaStream_t s) {
-  size_t smem = tiles_smem(max_kl, sizeof(T));
+                              const TileMeta *tm, const T *band, const T *lraw, const int32_t *piv,
+                              T *ltile, T *utile, int32_t *src, cudaStream_t s) {
+  if (m <= 0 || max_tiles <= 0) return cudaSuccess;
+  const int W = DD_NB + max_kl;
+  const size_t smem = sizeof(T) * (size_t)(2 * DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
   cudaError_t e = ensure_smem(band_tiles_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(m, max_tiles);
-  band_tiles_kernel<T><<<grid, 32, smem, s>>>(d_info, band, lm, piv, ltile, utile, src);
+  band_tiles_kernel<T><<<dim3(m, max_tiles), 32, smem, s>>>(d_info, tm, band, lraw, piv, ltile, utile, src);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
-                                  const T *utile, const int32_t *src, const double *y,
-                                  const int32_t *perm, T *z, DevStatus *st, int threads,
-                                  cudaStream_t s) {
+                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  const SweepJob *jobs, const T *ltile, const T *utile,
+                                  const int32_t *src, const double *y, const int32_t *perm, T *z,
+                                  DevStatus *st, int threads, cudaStream_t s) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
   // the backward tile step maps exactly 8 threads to each of the 32 rows
   if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
+  const int mt = max_n / DD_NB, mj = 2 * mt;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_fwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_fwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ns, stage_bytes,
-                                                     ltile, utile, src, y, perm, z, st);
+  band_solve_fwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                     stage_bytes, tm, jobs, ltile, utile, src, y,
+                                                     perm, z, st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const T *ltile,
-                                  const T *utile, const int32_t *src, const int32_t *e_ptr,
-                                  const int32_t *e_col, const T *e_val, const T *z2, const T *z1,
-                                  const int32_t *perm, double *x, DevStatus *st, int threads,
-                                  cudaStream_t s) {
+                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  const SweepJob *jobs, const T *ltile, const T *utile,
+                                  const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
+                                  const T *e_val, const T *z2, const T *z1, const int32_t *perm,
+                                  double *x, DevStatus *st, int threads, cudaStream_t s) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
   if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, threads, sizeof(T)) + (size_t)ns * stage_bytes;
+  const int mt = max_n / DD_NB, mj = 2 * mt;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
   cudaError_t e = ensure_smem(band_solve_bwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_bwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, ns, stage_bytes,
-                                                     ltile, utile, src, e_ptr, e_col, e_val, z2, z1,
-                                                     perm, x, st);
+  band_solve_bwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                     stage_bytes, tm, jobs, ltile, utile, src, e_ptr,
+                                                     e_col, e_val, z2, z1, perm, x, st);
   return cudaGetLastError();
 }
 
+#define DD_MULTI_NR 16
 template <typename T>
 cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t *ncols,
                                     const int64_t *x_off, int max_cols, int max_kl, int max_ku2,
-                                    const T *ltile, const T *utile, const int32_t *src, T *X,
-                                    cudaStream_t s) {
+                                    const TileMeta *tm, const T *ltile, const T *utile,
+                                    const int32_t *src, T *X, cudaStream_t s) {
   if (max_cols <= 0) return cudaSuccess;
-  size_t smem = multi_smem(max_kl, max_ku2, sizeof(T));
+  const int w = round4(DD_NB + (max_kl > max_ku2 ? max_kl : max_ku2));
+  size_t smem = sizeof(T) * (size_t)w * DD_MULTI_NR;
   cudaError_t e = ensure_smem(band_solve_multi_kernel<T, DD_MULTI_NR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m, (max_cols + DD_MULTI_NR - 1) / DD_MULTI_NR);
-  band_solve_multi_kernel<T, DD_MULTI_NR><<<grid, 256, smem, s>>>(d_info, ncols, x_off, ltile,
+  band_solve_multi_kernel<T, DD_MULTI_NR><<<grid, 256, smem, s>>>(d_info, ncols, x_off, tm, ltile,
                                                                   utile, src, X);
   return cudaGetLastError();
 }
 
-#define DD_INST_BAND(T)                                                                          \
-  template cudaError_t launch_band_lu<T>(const BandInfo *, int, int, int, T *, T *, int32_t *,   \
-                                         T *, double, DevStatus *, int, cudaStream_t);            \
-  template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const T *,          \
-                                            const T *, const int32_t *, T *, T *, int32_t *,     \
-                                            cudaStream_t);                                        \
+#define DD_INST_BAND(T)                                                                            \
+  template cudaError_t launch_band_lu<T>(const BandInfo *, int, int, int, T *, T *, int32_t *,     \
+                                         T *, double, DevStatus *, int, cudaStream_t);              \
+  template cudaError_t launch_tile_widths<T>(const BandInfo *, int, int, const T *, const T *,     \
+                                             const int32_t *, int32_t *, int32_t *, cudaStream_t); \
+  template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const TileMeta *,     \
+                                            const T *, const T *, const int32_t *, T *, T *,       \
+                                            int32_t *, cudaStream_t);                               \
   template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int, uint32_t,    \
-                                                const T *, const T *, const int32_t *,            \
-                                                const double *, const int32_t *, T *,             \
-                                                DevStatus *, int, cudaStream_t);                  \
-  template cudaError_t launch_band_solve_bwd<T>(                                                 \
-      const BandInfo *, int, int, int, int, uint32_t, const T *, const T *, const int32_t *,     \
-      const int32_t *, const int32_t *, const T *, const T *, const T *, const int32_t *,        \
-      double *, DevStatus *, int, cudaStream_t);                                                 \
-  template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,        \
-                                                  const int64_t *, int, int, int, const T *,     \
-                                                  const T *, const int32_t *, T *, cudaStream_t);
+                                                const TileMeta *, const SweepJob *, const T *,      \
+                                                const T *, const int32_t *, const double *,         \
+                                                const int32_t *, T *, DevStatus *, int,             \
+                                                cudaStream_t);                                      \
+  template cudaError_t launch_band_solve_bwd<T>(                                                   \
+      const BandInfo *, int, int, int, int, uint32_t, const TileMeta *, const SweepJob *,          \
+      const T *, const T *, const int32_t *, const int32_t *, const int32_t *, const T *,          \
+      const T *, const T *, const int32_t *, double *, DevStatus *, int, cudaStream_t);            \
+  template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \
+                                                  const int64_t *, int, int, int,                  \
+                                                  const TileMeta *, const T *, const T *,          \
+                                                  const int32_t *, T *, cudaStream_t);
 
 DD_INST_BAND(double)
 DD_INST_BAND(float)
