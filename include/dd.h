@@ -95,14 +95,17 @@ typedef struct {
   int32_t max_restart;/* largest restart length gmres_solve will be called
                          with (its Krylov workspace is allocated by dd_setup);
                          <= 0 selects 50, at most 120                          */
-  int32_t reserved[4];
+  int32_t autotune;   /* 1: dd_setup times the apply's sweep kernels for each
+                         candidate ring-stage size (and with it CTAs per SM)
+                         and keeps the fastest; 0: the fixed default           */
+  int32_t reserved[3];
 } dd_opts;
 
 typedef struct {
   int32_t iters;        /* Arnoldi steps over all restarts                    */
   int32_t restarts;
   int32_t bad_block;    /* index of the failing block for SINGULAR_* statuses */
-  int32_t pad;
+  int32_t status;       /* this solve's dd_status (per system in a batch)     */
   double relres_true;   /* ||b - C x|| / ||b|| at return                      */
   double setup_ms;      /* device time of dd_setup (set by dd_setup's handle) */
   double solve_ms;      /* device time of gmres_solve                         */
@@ -123,6 +126,13 @@ typedef struct {
   int64_t coupling_nnz;      /* nnz(E) + nnz(F)                                  */
   double setup_ms;           /* device time of the last dd_setup                 */
   int64_t launches;          /* kernels this handle has launched so far          */
+  int32_t stage_bytes;       /* ring stage of the apply's sweep kernels          */
+  int32_t sweep_grid;        /* CTAs of one sweep launch                         */
+  int32_t sweep_slots;       /* sweep CTAs resident on the device at once        */
+  int32_t tuned;             /* stage sizes the autotuner timed (0: not run)     */
+  double tuned_us;           /* fastest forward + backward sweep it measured     */
+  int32_t batch;             /* independent systems behind the handle (>= 1)     */
+  int32_t graphs;            /* CUDA graphs instantiated so far                  */
 } dd_stats;
 
 /*
@@ -160,6 +170,38 @@ dd_status dd_apply(void *handle, const double *y, double *x, void *stream);
  */
 dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int32_t restart,
                       int32_t maxit, dd_info *info, void *stream);
+
+/*
+ * A batch of `count` independent systems behind one handle.  The batch is
+ * set up as one block-diagonal system: the systems' rows one after the
+ * other, the subdomains of every system renumbered after those of the
+ * previous ones, and the aggregates (Section 3.2) taken per system, so that
+ * B is block diagonal with one block B_q per system and every kernel of the
+ * setup and the apply covers all systems in one launch (persistent,
+ * longest-first task lists when the subdomains outnumber resident CTAs).
+ *   csrs[q], partitions[q]: host, copied, as for dd_setup (each system in
+ *   its own numbering).  approx: DD_EXACT (one Schur block per system),
+ *   DD_MSCE_INF or DD_LUM; DD_MSCN / DD_MSCNR pair interface and interior
+ *   index ranges of one system and return DD_ERR_INVALID_ARG.  Errors as
+ *   dd_setup; dd_apply on the handle applies every B_q to the concatenated
+ *   vector.
+ */
+dd_status dd_setup_batched(int32_t count, const dd_csr *csrs, const dd_partition *partitions,
+                           dd_approx approx, const dd_opts *opts, void *stream, void **handle);
+
+/*
+ * Independent FGMRES solves C_q x_q = b_q of every system of a batched
+ * handle, with gmres_solve's algorithm and tests per system.  The systems
+ * step in lock step (one set of launches per Arnoldi step for all systems
+ * still iterating); a system that meets its own test stops stepping, so each
+ * takes the steps a solve of it alone would take.
+ *   b[q], x[q]: device pointers, n_q doubles each.  infos: host array of
+ *   count entries (may be NULL); infos[q].status is system q's dd_status.
+ *   Returns DD_OK when every system converged, else the first failing
+ *   system's status (DD_ERR_TIMEOUT / DD_ERR_CUDA for the batch as a whole).
+ */
+dd_status gmres_solve_batched(void *handle, const double *const *b, double *const *x, double tol,
+                              int32_t restart, int32_t maxit, dd_info *infos, void *stream);
 
 /*
  * One of the three kernels of dd_apply, for timing and profiling:

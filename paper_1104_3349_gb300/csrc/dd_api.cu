@@ -35,8 +35,13 @@ struct DDHandle {
   dd_approx kind = DD_MSCE_INF;
   int64_t n = 0, nnz = 0;
   int m = 0, nI = 0, nG = 0, nagg = 0, pmax = 0;
-  int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0, sweep_threads = 256;
-  uint32_t stage_bytes = 0;
+  int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0;
+  SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
+  std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
+  std::vector<TileMeta> h_tm;
+  size_t max_tile = 0;           // bytes of the largest packed tile
+  int32_t *sweep_sched = nullptr, *sweep_off = nullptr;
+  int sweep_sched_cap = 0;
   void *lu_scratch = nullptr;  // windows of the blocked LU (when not in shared memory)
   TileMeta *tm = nullptr;      // packed sweep tiles
   SweepJob *jobs = nullptr;    // jobs of the sweep ring
@@ -53,13 +58,26 @@ struct DDHandle {
   DevStatus *st = nullptr;
   PrecBufs<double> pd;
   PrecBufs<float> pf;
-  // FGMRES workspace
+  // FGMRES workspace; per-system arrays hold nseg systems (strides from Rmax)
   int Rmax = 0, nblocks = 304, cgs_blocks = 0;
   int64_t ldv = 0;
   double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
          *y = nullptr, *hc1 = nullptr, *hc2 = nullptr, *nsq = nullptr, *out = nullptr,
          *partial = nullptr, *r = nullptr;
-  double *h_out = nullptr;  // pinned host scalars
+  double *h_out = nullptr;  // pinned host scalars (4 per system)
+  // batch of independent systems (nseg > 1): rows, CTAs and state per system
+  int nseg = 1, seg_ctas = 0;
+  std::vector<int64_t> seg_row0_h;
+  int32_t *cta_seg = nullptr, *seg_cta0 = nullptr, *d_act = nullptr, *d_jl = nullptr;
+  int64_t *seg_row0 = nullptr;
+  int32_t *h_act = nullptr;  // pinned: act then jl, nseg each
+  double *bcat = nullptr, *xcat = nullptr, *bn2 = nullptr, *rn2 = nullptr;
+  // CUDA graphs of the Arnoldi steps (use_graph), one per step index
+  int use_graph = 0, graph_key = -1;
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<int64_t> glaunch;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
   std::string err;
   int bad_block = -1;
   dd_stats stats{};
@@ -236,7 +254,7 @@ dd_status build_aggregates(DDHandle *h, const dd_partition *pt, dd_approx kind, 
   const int nG = h->nG;
   hb.agg.clear();
   if (nG == 0) { hb.agg.push_back(0); return DD_OK; }
-  if (kind == DD_EXACT) {
+  if (kind == DD_EXACT && !(h->nseg > 1 && pt->agg_offsets)) {  // a batch: one block per system
     hb.agg = {0, nG};
   } else if (pt->agg_offsets) {
     if (pt->n_agg <= 0) { h->err = "n_agg must be positive"; return DD_ERR_INVALID_ARG; }
@@ -308,12 +326,143 @@ int64_t launch_cost(const char *call, const DDHandle *h) {
   if (strstr(call, "launch_gj_inverse")) return 3LL * ((h->pmax + (h->prec == DD_FP32 ? 15 : 7)) / (h->prec == DD_FP32 ? 16 : 8)) + 1;
   if (strstr(call, "launch_hess_solve_update")) return 2;
   if (strstr(call, "launch_schur_apply")) return 2;
+  if (strstr(call, "launch_seg_norms")) return 2;
+  if (strstr(call, "launch_seg_hess_update")) return 2;
   return 1;
 }
 
 }  // namespace
 
 namespace {
+
+// Jobs of the sweep ring for one stage size: runs of consecutive tiles of
+// one subdomain whose packed bytes fit a stage (a larger tile is a job of
+// its own); forward jobs ascend, backward jobs descend.
+void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, size_t stage, size_t es,
+                std::vector<SweepJob> &jobs) {
+  jobs.clear();
+  for (BandInfo &b : info) {
+    b.jf0 = (int32_t)jobs.size();
+    for (int lo = 0; lo < b.ntiles;) {
+      size_t bytes = 0;
+      int hi = lo;
+      while (hi < b.ntiles) {
+        const TileMeta &q = tm[b.tile0 + hi];
+        const size_t tb = (size_t)q.wl * DD_NB * es + (size_t)round4(q.wl) * 4;
+        if (hi > lo && bytes + tb > stage) break;
+        bytes += tb;
+        ++hi;
+      }
+      jobs.push_back(SweepJob{lo, hi});
+      lo = hi;
+    }
+    b.njf = (int32_t)jobs.size() - b.jf0;
+    b.jb0 = (int32_t)jobs.size();
+    for (int hi = b.ntiles; hi > 0;) {
+      size_t bytes = 0;
+      int lo = hi;
+      while (lo > 0) {
+        const TileMeta &q = tm[b.tile0 + lo - 1];
+        const size_t tb = (size_t)DD_NB * q.wu * es;
+        if (lo < hi && bytes + tb > stage) break;
+        bytes += tb;
+        --lo;
+      }
+      jobs.push_back(SweepJob{lo, hi});
+      hi = lo;
+    }
+    b.njb = (int32_t)jobs.size() - b.jb0;
+  }
+}
+
+// Longest processing time first: tasks in order of decreasing cost (ties by
+// index), each to the least loaded of `slots` CTAs (ties by CTA index); CTA
+// c's tasks are sched[off[c] .. off[c+1]), longest first.
+void lpt_schedule(const std::vector<double> &cost, int slots, std::vector<int32_t> &sched,
+                  std::vector<int32_t> &off) {
+  const int m = (int)cost.size();
+  std::vector<int32_t> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<double> load(slots, 0.0);
+  std::vector<std::vector<int32_t>> lists(slots);
+  for (int32_t t : order) {
+    int best = 0;
+    for (int c = 1; c < slots; ++c)
+      if (load[c] < load[best]) best = c;
+    load[best] += cost[t];
+    lists[best].push_back(t);
+  }
+  sched.clear();
+  off.assign(slots + 1, 0);
+  for (int c = 0; c < slots; ++c) {
+    sched.insert(sched.end(), lists[c].begin(), lists[c].end());
+    off[c + 1] = (int32_t)sched.size();
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+// The sweep plan for one stage size: the job table, and a persistent LPT
+// schedule when the subdomains outnumber the CTAs that fit on the device.
+template <typename T>
+dd_status set_sweep_plan(DDHandle *h, size_t stage) {
+  std::vector<SweepJob> jobs;
+  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), jobs);
+  const int m = h->m;
+  if (!h->jobs) TRY(dalloc(h, &h->jobs, 2 * std::max<size_t>(h->h_tm.size(), 1)));
+  if (!jobs.empty())
+    CK(cudaMemcpyAsync(h->jobs, jobs.data(), sizeof(SweepJob) * jobs.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_info, h->h_info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, h->stream));
+  h->plan.stage_bytes = (uint32_t)stage;
+  h->plan.threads = 8 * DD_NB;
+  const int occ = band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, h->plan.threads, h->plan.stage_bytes);
+  if (occ <= 0) {
+    h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
+    return DD_ERR_INVALID_ARG;
+  }
+  const int slots = occ * sm_count();
+  h->stats.sweep_slots = slots;
+  h->stats.stage_bytes = (int32_t)stage;
+  if (m > slots) {
+    std::vector<double> cost(m);
+    for (int j = 0; j < m; ++j) {
+      const BandInfo &b = h->h_info[j];
+      double bytes = 0;
+      for (int t = 0; t < b.ntiles; ++t) {
+        const TileMeta &q = h->h_tm[b.tile0 + t];
+        bytes += (double)(q.wl + q.wu) * DD_NB * sizeof(T);
+      }
+      cost[j] = 2.0 * b.ntiles + bytes / 32768.0;  // dependent tile steps + streamed bytes
+    }
+    std::vector<int32_t> sched, off;
+    lpt_schedule(cost, slots, sched, off);
+    if (!h->sweep_sched) TRY(dalloc(h, &h->sweep_sched, std::max(m, 1)));
+    if (h->sweep_sched_cap < slots + 1) {
+      TRY(dalloc(h, &h->sweep_off, slots + 1));
+      h->sweep_sched_cap = slots + 1;
+    }
+    CK(cudaMemcpyAsync(h->sweep_sched, sched.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->sweep_off, off.data(), sizeof(int32_t) * (slots + 1), cudaMemcpyHostToDevice, h->stream));
+    // pageable sources: make the copies complete before the vectors go
+    CK(cudaStreamSynchronize(h->stream));
+    h->plan.grid = slots;
+    h->plan.sched = h->sweep_sched;
+    h->plan.sched_off = h->sweep_off;
+  } else {
+    CK(cudaStreamSynchronize(h->stream));
+    h->plan.grid = m;
+    h->plan.sched = nullptr;
+    h->plan.sched_off = nullptr;
+  }
+  h->stats.sweep_grid = h->plan.grid;
+  return DD_OK;
+}
 
 template <typename T>
 dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb,
@@ -377,8 +526,24 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   fill_band_kernel<T><<<(unsigned)((h->n + 255) / 256), 256, 0, s>>>(
       (int)h->n, h->c_rowptr, h->c_col, h->c_val, d_part, d_pos, h->d_info, B.band);
   CK(cudaGetLastError());
-  CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
-                       static_cast<T *>(h->lu_scratch), pivtol, h->st, 256, s));
+  {
+    // persistent LPT task lists when the subdomains outnumber resident CTAs
+    const int occ = band_lu_occupancy<T>(h->max_kl, h->max_ku, 256);
+    if (occ <= 0) { h->err = "band LU: no resident CTA fits"; return DD_ERR_CUDA; }
+    const int slots = occ * sm_count();
+    int32_t *d_sched = nullptr, *d_off = nullptr;
+    if (m > slots) {
+      std::vector<double> cost(m);
+      for (int j = 0; j < m; ++j)
+        cost[j] = (double)info[j].n * (info[j].kl + 1) * (info[j].kl + info[j].ku + 1);
+      std::vector<int32_t> sched, off;
+      lpt_schedule(cost, slots, sched, off);
+      TRY(upload(h, &d_sched, sched));
+      TRY(upload(h, &d_off, off));
+    }
+    CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
+                         static_cast<T *>(h->lu_scratch), pivtol, h->st, 256, slots, d_sched, d_off, s));
+  }
   // ---- packed sweep tiles: widths from the factors, offsets and jobs here
   {
     int32_t *d_wl = nullptr, *d_wu = nullptr;
@@ -406,52 +571,16 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     // stage: ~84 KiB, or one whole tile when a tile is larger
     size_t stage = std::max<size_t>(84 * 1024, max_tile);
     stage = (stage + 127) & ~(size_t)127;
-    h->stage_bytes = (uint32_t)stage;
-    std::vector<SweepJob> jobs;
-    for (int j = 0; j < m; ++j) {
-      BandInfo &b = info[j];
-      b.jf0 = (int32_t)jobs.size();
-      for (int lo = 0; lo < b.ntiles;) {
-        size_t bytes = 0;
-        int hi = lo;
-        while (hi < b.ntiles) {
-          const TileMeta &q = tm[b.tile0 + hi];
-          const size_t tb = (size_t)q.wl * DD_NB * sizeof(T) + (size_t)round4(q.wl) * 4;
-          if (hi > lo && bytes + tb > stage) break;
-          bytes += tb;
-          ++hi;
-        }
-        jobs.push_back(SweepJob{lo, hi});
-        lo = hi;
-      }
-      b.njf = (int32_t)jobs.size() - b.jf0;
-      b.jb0 = (int32_t)jobs.size();
-      for (int hi = b.ntiles; hi > 0;) {
-        size_t bytes = 0;
-        int lo = hi;
-        while (lo > 0) {
-          const TileMeta &q = tm[b.tile0 + lo - 1];
-          const size_t tb = (size_t)DD_NB * q.wu * sizeof(T);
-          if (lo < hi && bytes + tb > stage) break;
-          bytes += tb;
-          --lo;
-        }
-        jobs.push_back(SweepJob{lo, hi});
-        hi = lo;
-      }
-      b.njb = (int32_t)jobs.size() - b.jb0;
-    }
-    CK(cudaMemcpyAsync(h->d_info, info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, s));
+    h->max_tile = max_tile;
+    h->h_info = info;
+    h->h_tm = tm;
     TRY(upload(h, &h->tm, tm));
-    TRY(upload(h, &h->jobs, jobs));
+    TRY(set_sweep_plan<T>(h, stage));
+    info = h->h_info;
     TRY(dalloc(h, &B.ltile, lofs));
     TRY(dalloc(h, &B.utile, uofs));
     TRY(dalloc(h, &h->src, sofs));
     h->stats.factor_bytes = (lofs + uofs) * (int64_t)sizeof(T) + sofs * (int64_t)sizeof(int32_t);
-    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->sweep_threads, sizeof(T), h->stage_bytes) < 2) {
-      h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
-      return DD_ERR_INVALID_ARG;
-    }
     CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tm, B.band, B.lm, h->piv,
                             B.ltile, B.utile, h->src, s));
   }
@@ -667,16 +796,15 @@ template <typename T>
 dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int part = -1) {
   PrecBufs<T> &B = bufs<T>(h);
   if (part == 0 || part < 0)
-  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st,
-                              h->sweep_threads, s));
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st, s));
   if (part == 1 || part < 0)
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, B.t, h->nG, x, s));
   if (part == 2 || part < 0)
-  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
-                              B.z2, B.z1, h->d_perm, x, h->st, h->sweep_threads, s));
+                              B.z2, B.z1, h->d_perm, x, h->st, s));
   return DD_OK;
 }
 
@@ -689,26 +817,93 @@ dd_status apply_any(DDHandle *h, const double *y, double *x, cudaStream_t s, int
 namespace {
 
 dd_status alloc_krylov(DDHandle *h, int R) {
+  const int S = h->nseg;
   h->Rmax = R;
   h->ldv = ((h->n + 31) / 32) * 32;
   TRY(dalloc(h, &h->V, (size_t)h->ldv * (R + 1)));
   TRY(dalloc(h, &h->Z, (size_t)h->ldv * R));
-  TRY(dalloc(h, &h->H, (size_t)(R + 1) * R));
-  TRY(dalloc(h, &h->cs, R));
-  TRY(dalloc(h, &h->sn, R));
-  TRY(dalloc(h, &h->g, R + 1));
-  TRY(dalloc(h, &h->y, R + 1));
-  TRY(dalloc(h, &h->hc1, R + 2));
-  TRY(dalloc(h, &h->hc2, R + 2));
+  // the batched apply reads every system's vectors, stepping or not
+  CK(cudaMemsetAsync(h->V, 0, sizeof(double) * (size_t)h->ldv * (R + 1), h->stream));
+  CK(cudaMemsetAsync(h->Z, 0, sizeof(double) * (size_t)h->ldv * R, h->stream));
+  TRY(dalloc(h, &h->H, (size_t)S * (R + 1) * R));
+  TRY(dalloc(h, &h->cs, (size_t)S * R));
+  TRY(dalloc(h, &h->sn, (size_t)S * R));
+  TRY(dalloc(h, &h->g, (size_t)S * (R + 1)));
+  TRY(dalloc(h, &h->y, (size_t)S * (R + 1)));
+  TRY(dalloc(h, &h->hc1, (size_t)S * (R + 2)));
+  TRY(dalloc(h, &h->hc2, (size_t)S * (R + 2)));
   TRY(dalloc(h, &h->nsq, 4));
-  TRY(dalloc(h, &h->out, 4));
+  TRY(dalloc(h, &h->out, (size_t)S * 4));
   h->cgs_blocks = cgs2_blocks(304);
   if (h->cgs_blocks <= 0) { h->err = "no resident blocks for the cooperative CGS2 kernel"; return DD_ERR_CUDA; }
   TRY(dalloc(h, &h->partial, 3 * (size_t)std::max(h->nblocks, h->cgs_blocks) * (R + 2)));
   TRY(dalloc(h, &h->r, h->ldv));
-  cudaError_t e = cudaMallocHost(&h->h_out, 8 * sizeof(double));
+  cudaError_t e = cudaMallocHost(&h->h_out, sizeof(double) * std::max(8, 4 * S));
   if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return DD_ERR_OOM; }
+  if (S > 1) {
+    // CTAs of the batched Krylov kernels: proportional to the rows, at least one each
+    const int nb = h->cgs_blocks;
+    if (S > nb) { h->err = "more systems in the batch than resident CTAs of the CGS2 kernel"; return DD_ERR_INVALID_ARG; }
+    const int64_t N = h->seg_row0_h[S];
+    std::vector<int32_t> cnt(S);
+    int tot = 0;
+    for (int q = 0; q < S; ++q) {
+      const int64_t ns = h->seg_row0_h[q + 1] - h->seg_row0_h[q];
+      cnt[q] = (int32_t)std::max<int64_t>(1, (ns * nb) / std::max<int64_t>(N, 1));
+      tot += cnt[q];
+    }
+    while (tot > nb) {  // trim the system with the most CTAs
+      int q = (int)(std::max_element(cnt.begin(), cnt.end()) - cnt.begin());
+      --cnt[q];
+      --tot;
+    }
+    while (tot < nb) {  // add to the system with the most rows per CTA
+      int best = 0;
+      double worst = -1.0;
+      for (int q = 0; q < S; ++q) {
+        const double per = (double)(h->seg_row0_h[q + 1] - h->seg_row0_h[q]) / cnt[q];
+        if (per > worst) { worst = per; best = q; }
+      }
+      ++cnt[best];
+      ++tot;
+    }
+    std::vector<int32_t> c0(S + 1, 0), cseg;
+    for (int q = 0; q < S; ++q) {
+      c0[q + 1] = c0[q] + cnt[q];
+      for (int c = 0; c < cnt[q]; ++c) cseg.push_back(q);
+    }
+    h->seg_ctas = c0[S];
+    TRY(upload(h, &h->seg_cta0, c0));
+    TRY(upload(h, &h->cta_seg, cseg));
+    TRY(upload(h, &h->seg_row0, h->seg_row0_h));
+    TRY(dalloc(h, &h->d_act, S));
+    TRY(dalloc(h, &h->d_jl, S));
+    TRY(dalloc(h, &h->bcat, (size_t)h->n));
+    TRY(dalloc(h, &h->xcat, (size_t)h->n));
+    TRY(dalloc(h, &h->bn2, S));
+    TRY(dalloc(h, &h->rn2, S));
+    e = cudaMallocHost(&h->h_act, sizeof(int32_t) * 2 * S);
+    if (e != cudaSuccess) { h->err = "cudaMallocHost failed"; return DD_ERR_OOM; }
+  }
   return DD_OK;
+}
+
+SegMap single_map(const DDHandle *h) {
+  SegMap sm;
+  sm.nseg = 1;
+  sm.rmax = h->Rmax;
+  return sm;
+}
+
+SegMap batch_map(const DDHandle *h) {
+  SegMap sm;
+  sm.nseg = h->nseg;
+  sm.rmax = h->Rmax;
+  sm.cta_seg = h->cta_seg;
+  sm.seg_cta0 = h->seg_cta0;
+  sm.seg_row0 = h->seg_row0;
+  sm.act = h->d_act;
+  return sm;
 }
 
 // nsq[slot] = ||v||^2
@@ -724,12 +919,83 @@ dd_status read_scalars(DDHandle *h, const double *d, int count, cudaStream_t s) 
   return DD_OK;
 }
 
+// The launches of Arnoldi step j: z_j = B^-1 v_j, w = C z_j, CGS2 with the
+// Givens update, and the step's scalars (4 per system) to pinned host memory.
+dd_status arnoldi_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, const double *bn2,
+                       cudaStream_t s) {
+  double *vj = h->V + (int64_t)j * h->ldv, *zj = h->Z + (int64_t)j * h->ldv;
+  double *w = h->V + (int64_t)(j + 1) * h->ldv;
+  TRY(apply_any(h, vj, zj, s));
+  CK(launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
+  CK(launch_cgs2(h->n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
+                 h->sn, h->g, bn2, h->out, sm, ncta, s));
+  CK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 4 * sm.nseg, cudaMemcpyDeviceToHost, s));
+  return DD_OK;
+}
+
+void drop_graphs(DDHandle *h) {
+  for (cudaGraphExec_t &e : h->gexec)
+    if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  h->graph_key = -1;
+}
+
+// Step j as one CUDA graph, captured on first use (per restart length and
+// mode) and replayed afterwards; without use_graph, plain launches.
+dd_status run_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, const double *bn2,
+                   cudaStream_t s) {
+  if (!h->use_graph) return arnoldi_step(h, j, R, sm, ncta, bn2, s);
+  const int key = 2 * R + (sm.nseg > 1 ? 1 : 0);
+  if (h->graph_key != key) {
+    drop_graphs(h);
+    h->graph_key = key;
+    h->gexec.assign(h->Rmax, nullptr);
+    h->glaunch.assign(h->Rmax, 0);
+  }
+  if (!h->gexec[j]) {
+    const int64_t l0 = h->stats.launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const dd_status rc = arnoldi_step(h, j, R, sm, ncta, bn2, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (rc != DD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ec != cudaSuccess) { h->err = std::string("graph capture: ") + cudaGetErrorString(ec); return DD_ERR_CUDA; }
+    const cudaError_t ei = cudaGraphInstantiate(&h->gexec[j], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->gexec[j] = nullptr;
+      h->err = std::string("graph instantiate: ") + cudaGetErrorString(ei);
+      return DD_ERR_CUDA;
+    }
+    h->glaunch[j] = h->stats.launches - l0;  // counted while capturing, charged per replay
+    h->stats.launches = l0;
+    h->stats.graphs += 1;
+  }
+  h->stats.launches += h->glaunch[j];
+  CK(cudaGraphLaunch(h->gexec[j], s));
+  return DD_OK;
+}
+
+dd_status device_status(DDHandle *h, cudaStream_t s) {
+  DevStatus dst{};
+  CK(cudaMemcpyAsync(&dst, h->st, sizeof dst, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (dst.code != 0) {
+    h->err = "device wait expired in an apply sweep";
+    return (dd_status)dst.code;
+  }
+  return DD_OK;
+}
+
 dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int maxit,
                  dd_info *info, cudaStream_t s) {
   const int n = (int)h->n;
   int iters = 0, restarts = 0;
   double relres = 0.0;
   dd_status rc = DD_ERR_NOT_CONVERGED;
+  const SegMap sm = single_map(h);
   CK(launch_zero(x, n, s));
   TRY(norm_sq(h, b, 2, s));
   TRY(read_scalars(h, h->nsq + 2, 1, s));
@@ -746,13 +1012,8 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
     CK(launch_copy_scaled(n, h->r, h->nsq, h->V, s));
     int jlast = -1;
     for (int j = 0; j < R; ++j) {
-      double *vj = h->V + (int64_t)j * h->ldv, *zj = h->Z + (int64_t)j * h->ldv;
-      double *w = h->V + (int64_t)(j + 1) * h->ldv;
-      TRY(apply_any(h, vj, zj, s));
-      CK(launch_spmv(n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
-      CK(launch_cgs2(n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
-                     h->sn, h->g, bnorm, h->out, h->cgs_blocks, s));
-      TRY(read_scalars(h, h->out, 3, s));
+      TRY(run_step(h, j, R, sm, h->cgs_blocks, h->nsq + 2, s));
+      CK(cudaStreamSynchronize(s));
       ++iters;
       const double est = h->h_out[2];
       const bool breakdown = h->h_out[1] != 0.0;
@@ -766,13 +1027,8 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
     TRY(norm_sq(h, h->r, 3, s));
     TRY(read_scalars(h, h->nsq + 3, 1, s));
     {
-      DevStatus dst{};
-      CK(cudaMemcpy(&dst, h->st, sizeof dst, cudaMemcpyDeviceToHost));
-      if (dst.code != 0) {
-        h->err = "device wait expired in an apply sweep";
-        rc = (dd_status)dst.code;
-        break;
-      }
+      const dd_status ds = device_status(h, s);
+      if (ds != DD_OK) { rc = ds; break; }
     }
     relres = sqrt(h->h_out[0]) / bnorm;
     if (!isfinite(relres)) { rc = DD_ERR_NONFINITE; break; }
@@ -785,12 +1041,124 @@ done:
   return rc;
 }
 
+// Independent FGMRES solves of every system of a batched handle, in lock
+// step: each Arnoldi step is one set of launches over all systems still
+// stepping.  A system leaves the cycle when its own test says so and the
+// others go on; cycles end together, then every system that stepped forms
+// its x and is tested on its true residual.  Each system so takes exactly
+// the steps a solve of it alone would take.
+dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, double tol, int R,
+                         int maxit, dd_info *infos, cudaStream_t s) {
+  const int S = h->nseg, nc = h->seg_ctas;
+  const int64_t n = h->n;
+  const SegMap sm = batch_map(h);
+  SegMap all = sm;
+  all.act = nullptr;
+  for (int q = 0; q < S; ++q) {
+    const int64_t r0 = h->seg_row0_h[q], ns = h->seg_row0_h[q + 1] - r0;
+    if (ns > 0)
+      CK(cudaMemcpyAsync(h->bcat + r0, b[q], sizeof(double) * ns, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(launch_zero(h->xcat, n, s));
+  CK(launch_seg_norms(n, h->bcat, h->partial, h->bn2, all, nc, s));
+  CK(cudaMemcpyAsync(h->h_out, h->bn2, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> bnorm(S), relres(S, 0.0);
+  std::vector<int> iters(S, 0), restarts(S, 0), done(S, 0);
+  std::vector<dd_status> st(S, DD_ERR_NOT_CONVERGED);
+  int32_t *act = h->h_act, *jl = h->h_act + S;
+  for (int q = 0; q < S; ++q) {
+    bnorm[q] = sqrt(h->h_out[q]);
+    if (!isfinite(bnorm[q])) { st[q] = DD_ERR_NONFINITE; done[q] = 1; }
+    else if (bnorm[q] == 0.0) { st[q] = DD_OK; done[q] = 1; }
+  }
+  CK(cudaMemcpyAsync(h->r, h->bcat, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  dd_status rc_dev = DD_OK;
+  for (;;) {
+    int nact = 0;
+    for (int q = 0; q < S; ++q) {
+      act[q] = done[q] ? 0 : 1;
+      jl[q] = -1;
+      nact += act[q];
+    }
+    if (nact == 0) break;
+    CK(cudaMemcpyAsync(h->d_act, act, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+    CK(launch_seg_norms(n, h->r, h->partial, h->rn2, all, nc, s));
+    CK(launch_seg_start(n, h->r, h->rn2, h->V, h->g, sm, nc, s));
+    for (int j = 0; j < R && nact > 0; ++j) {
+      TRY(run_step(h, j, R, sm, nc, h->bn2, s));
+      CK(cudaStreamSynchronize(s));
+      bool changed = false;
+      for (int q = 0; q < S; ++q) {
+        if (!act[q]) continue;
+        ++iters[q];
+        const double est = h->h_out[4 * q + 2];
+        const bool breakdown = h->h_out[4 * q + 1] != 0.0;
+        dd_info *inf = infos ? &infos[q] : nullptr;
+        if (inf && inf->history && iters[q] - 1 < inf->history_cap) inf->history[iters[q] - 1] = est;
+        jl[q] = j;
+        if (!isfinite(est)) {
+          st[q] = DD_ERR_NONFINITE;
+          done[q] = 1;
+          jl[q] = -1;  // no update of x from a non-finite cycle
+        }
+        if (done[q] || est <= tol || breakdown || iters[q] >= maxit) {
+          act[q] = 0;
+          changed = true;
+          --nact;
+        }
+      }
+      // copies from pinned memory read it when they run: wait before the next change
+      if (changed && nact > 0) {
+        CK(cudaMemcpyAsync(h->d_act, act, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+      }
+    }
+    CK(cudaMemcpyAsync(h->d_jl, jl, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+    CK(launch_seg_hess_update(n, R, h->d_jl, h->H, h->g, h->y, h->Z, h->ldv, h->xcat, all, nc, s));
+    CK(launch_residual((int)n, h->c_rowptr, h->c_col, h->c_val, h->xcat, h->bcat, h->r, s));
+    CK(launch_seg_norms(n, h->r, h->partial, h->rn2, all, nc, s));
+    CK(cudaMemcpyAsync(h->h_out, h->rn2, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+    rc_dev = device_status(h, s);
+    if (rc_dev != DD_OK) break;
+    for (int q = 0; q < S; ++q) {
+      if (done[q] || jl[q] < 0) continue;
+      relres[q] = sqrt(h->h_out[q]) / bnorm[q];
+      if (!isfinite(relres[q])) { st[q] = DD_ERR_NONFINITE; done[q] = 1; }
+      else if (relres[q] <= tol) { st[q] = DD_OK; done[q] = 1; }
+      else if (iters[q] >= maxit) { st[q] = DD_ERR_NOT_CONVERGED; done[q] = 1; }
+      else ++restarts[q];
+    }
+  }
+  for (int q = 0; q < S; ++q) {
+    const int64_t r0 = h->seg_row0_h[q], ns = h->seg_row0_h[q + 1] - r0;
+    if (ns > 0) CK(cudaMemcpyAsync(x[q], h->xcat + r0, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s));
+    if (infos) {
+      infos[q].iters = iters[q];
+      infos[q].restarts = restarts[q];
+      infos[q].relres_true = relres[q];
+      infos[q].status = rc_dev != DD_OK ? rc_dev : st[q];
+    }
+  }
+  if (rc_dev != DD_OK) return rc_dev;
+  dd_status rc = DD_OK;
+  for (int q = 0; q < S; ++q)
+    if (st[q] != DD_OK && rc == DD_OK) rc = st[q];
+  return rc;
+}
+
 void release(DDHandle *h) {
+  drop_graphs(h);
+  if (h->gstream) { cudaStreamSynchronize(h->gstream); cudaStreamDestroy(h->gstream); h->gstream = nullptr; }
+  for (cudaEvent_t &e : h->gev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
   for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
   cudaStreamSynchronize(h->stream);
   if (h->h_out) cudaFreeHost(h->h_out);
   h->h_out = nullptr;
+  if (h->h_act) cudaFreeHost(h->h_act);
+  h->h_act = nullptr;
 }
 
 // ---------------------------------------------------------------------------
@@ -830,15 +1198,294 @@ dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scrat
   const size_t z1_elems = (((size_t)std::max(h->nI, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   const size_t z2_elems = (((size_t)std::max(h->nG, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   T *z2 = z1 + z1_elems;
-  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
-                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st,
-                              h->sweep_threads, s));
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+                              h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st, s));
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, s));
-  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->stage_bytes,
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
-                              z2, z1, h->d_perm, x, h->st, h->sweep_threads, s));
+                              z2, z1, h->d_perm, x, h->st, s));
   return DD_OK;
+}
+
+// Autotuner of the apply's sweep kernels: each candidate ring-stage size
+// (which fixes the stages, the CTAs per SM and so the persistent schedule)
+// is timed on the handle's own factors, forward plus backward sweep, best
+// of three after a warm-up; the fastest stays.  y and x are scratch vectors.
+template <typename T>
+dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
+  PrecBufs<T> &B = bufs<T>(h);
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(y, 0, sizeof(double) * h->n, s));
+  CK(cudaMemsetAsync(B.z2, 0, sizeof(T) * std::max(h->nG, 1), s));
+  std::vector<size_t> cand;
+  const size_t base = (h->max_tile + 127) & ~(size_t)127;
+  for (size_t kb : {24, 32, 48, 64, 84, 112, 144}) cand.push_back(std::max(base, kb * 1024));
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  size_t best = 0;
+  float best_ms = 1e30f;
+  int tried = 0;
+  for (size_t st : cand) {
+    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, 8 * DD_NB, sizeof(T), (uint32_t)st) < 2) continue;
+    if (band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, 8 * DD_NB, (uint32_t)st) <= 0) continue;
+    dd_status rc = set_sweep_plan<T>(h, st);
+    if (rc != DD_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      TRY(apply_T<T>(h, y, x, s, 0));
+      TRY(apply_T<T>(h, y, x, s, 2));
+      cudaEventRecord(e1, s);
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    ++tried;
+    if (tmin < best_ms) { best_ms = tmin; best = st; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tried == 0) { h->err = "autotune: no stage size fits"; return DD_ERR_INVALID_ARG; }
+  TRY(set_sweep_plan<T>(h, best));
+  h->stats.tuned = tried;
+  h->stats.tuned_us = 1000.0 * best_ms;
+  return DD_OK;
+}
+
+// Validation, extraction and device setup of a new handle (stream, nseg and
+// seg_row0_h already set); times itself with events on the handle's stream.
+dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *partition, dd_approx approx,
+                       const dd_opts *opts) {
+  if ((int)approx < DD_EXACT || (int)approx > DD_LUM) { h->err = "unknown approximation"; return DD_ERR_INVALID_ARG; }
+  dd_opts o{};
+  o.prec = DD_FP64;
+  if (opts) o = *opts;
+  if (o.prec != DD_FP64 && o.prec != DD_FP32) { h->err = "unknown precision"; return DD_ERR_INVALID_ARG; }
+  h->prec = o.prec;
+  h->kind = approx;
+  h->use_graph = o.use_graph != 0;
+  const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
+  const int R = o.max_restart > 0 ? o.max_restart : 50;
+  if (R > 120) { h->err = "max_restart must be <= 120"; return DD_ERR_INVALID_ARG; }
+  HostBlocks hb;
+  dd_status rc = validate_and_order(h, csr, partition, hb);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == DD_OK) {
+    h->n = csr->n;
+    h->nnz = csr->nnz;
+    h->m = partition->m;
+    h->nI = hb.off[h->m];
+    h->nG = (int)(h->n - h->nI);
+    rc = build_aggregates(h, partition, approx, hb);
+  }
+  if (rc == DD_OK) {
+    extract_blocks(h, csr, partition, hb);
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      h->err = "cudaEventCreate failed";
+      rc = DD_ERR_CUDA;
+    }
+  }
+  if (rc == DD_OK) {
+    cudaEventRecord(e0, h->stream);
+    rc = dalloc(h, &h->st, 1);
+    if (rc == DD_OK && cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream) != cudaSuccess) rc = DD_ERR_CUDA;
+    if (rc == DD_OK) rc = (h->prec == DD_FP32) ? setup_device<float>(h, csr, partition, hb, pivtol)
+                                               : setup_device<double>(h, csr, partition, hb, pivtol);
+    if (rc == DD_OK) rc = alloc_krylov(h, R);
+    if (rc == DD_OK && o.autotune)
+      rc = (h->prec == DD_FP32) ? autotune_sweeps<float>(h, h->V, h->V + h->ldv)
+                                : autotune_sweeps<double>(h, h->V, h->V + h->ldv);
+    if (rc == DD_OK && h->use_graph) {
+      if (cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+        h->err = "graph stream or event creation failed";
+        rc = DD_ERR_CUDA;
+      }
+    }
+    cudaEventRecord(e1, h->stream);
+    cudaError_t se = cudaStreamSynchronize(h->stream);
+    if (rc == DD_OK && se != cudaSuccess) { h->err = cudaGetErrorString(se); rc = DD_ERR_CUDA; }
+    if (rc == DD_OK) {
+      DevStatus st{};
+      if (cudaMemcpy(&st, h->st, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = DD_ERR_CUDA; }
+      else if (st.code != 0) {
+        rc = (dd_status)st.code;
+        h->bad_block = st.block;
+        char buf[128];
+        snprintf(buf, sizeof buf, "%s in block %d",
+                 st.code == DD_ERR_SINGULAR_BLOCK ? "singular interior block" : "singular Schur block", st.block);
+        h->err = buf;
+      }
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->stats.setup_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->stats.n = h->n;
+  h->stats.n_interior = h->nI;
+  h->stats.n_interface = h->nG;
+  h->stats.nnz = h->nnz;
+  h->stats.m = h->m;
+  h->stats.batch = h->nseg;
+  return rc;
+}
+
+// hands the handle out (also on SINGULAR_*, for dd_get_bad_block) or frees it
+dd_status finish_setup(DDHandle *h, dd_status rc, void **handle) {
+  g_setup_error = h->err;
+  if (rc == DD_OK || rc == DD_ERR_SINGULAR_BLOCK || rc == DD_ERR_SINGULAR_SCHUR) {
+    *handle = h;
+    return rc;
+  }
+  release(h);
+  delete h;
+  return rc;
+}
+
+// The batch as one block-diagonal system: rows of system q follow those of
+// q-1; interiors renumbered after the previous systems' subdomains, the
+// interface of every system after all interiors, aggregates per system.
+struct BatchInput {
+  std::vector<int32_t> rowptr, col, partv, perm, agg;
+  std::vector<double> val;
+  std::vector<int64_t> row0;
+  dd_csr csr{};
+  dd_partition pt{};
+};
+
+dd_status concat_batch(int count, const dd_csr *csrs, const dd_partition *pts, dd_approx approx, BatchInput &bi) {
+  int64_t N = 0, NNZ = 0;
+  bi.row0.assign(count + 1, 0);
+  for (int q = 0; q < count; ++q) {
+    const dd_csr &c = csrs[q];
+    if (c.n <= 0 || !c.rowptr || !c.col || !c.val || !pts[q].part || pts[q].m <= 0) {
+      g_setup_error = "batch member " + std::to_string(q) + ": invalid CSR or partition";
+      return DD_ERR_INVALID_ARG;
+    }
+    N += c.n;
+    NNZ += c.nnz;
+    bi.row0[q + 1] = N;
+  }
+  if (N > INT32_MAX - 1 || NNZ > INT32_MAX) { g_setup_error = "batch too large for 32-bit indices"; return DD_ERR_INVALID_ARG; }
+  bi.rowptr.assign(N + 1, 0);
+  bi.col.resize(NNZ);
+  bi.val.resize(NNZ);
+  bi.partv.resize(N);
+  std::vector<int32_t> inter, iface;  // concatenated interior order, then interface order
+  std::vector<int32_t> gsz;           // interface size per system
+  int64_t k = 0;
+  int32_t moff = 0;
+  for (int q = 0; q < count; ++q) {
+    const dd_csr &c = csrs[q];
+    const dd_partition &p = pts[q];
+    const int64_t r0 = bi.row0[q];
+    if (c.rowptr[0] != 0 || c.rowptr[c.n] != c.nnz) {
+      g_setup_error = "batch member " + std::to_string(q) + ": rowptr[0] must be 0 and rowptr[n] == nnz";
+      return DD_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < c.n; ++i) {
+      for (int64_t e = c.rowptr[i]; e < c.rowptr[i + 1]; ++e) {
+        const int32_t cc = c.col[e];
+        bi.col[k] = (cc >= 0 && cc < c.n) ? (int32_t)(cc + r0) : -1;  // -1 fails validation
+        bi.val[k++] = c.val[e];
+      }
+      bi.rowptr[r0 + i + 1] = (int32_t)k;
+      const int32_t pv = p.part[i];
+      bi.partv[r0 + i] = (pv >= 0 && pv < p.m) ? pv + moff : (pv == -1 ? -1 : INT32_MIN);
+    }
+    // this system's order: its perm, or interiors by subdomain then interface, ascending
+    std::vector<int32_t> order;
+    int64_t nI = 0;
+    for (int64_t i = 0; i < c.n; ++i) nI += (p.part[i] >= 0);
+    if (p.perm) {
+      order.assign(p.perm, p.perm + c.n);
+    } else {
+      std::vector<int32_t> cnt(p.m + 1, 0);
+      for (int64_t i = 0; i < c.n; ++i) if (p.part[i] >= 0 && p.part[i] < p.m) cnt[p.part[i] + 1]++;
+      for (int j = 0; j < p.m; ++j) cnt[j + 1] += cnt[j];
+      order.assign(c.n, 0);
+      int64_t g = nI;
+      for (int64_t i = 0; i < c.n; ++i) {
+        if (p.part[i] >= 0 && p.part[i] < p.m) order[cnt[p.part[i]]++] = (int32_t)i;
+        else if (g < c.n) order[g++] = (int32_t)i;
+      }
+    }
+    for (int64_t i = 0; i < c.n; ++i) {
+      const int32_t o = order[i];
+      if (o < 0 || o >= c.n) { g_setup_error = "batch member " + std::to_string(q) + ": perm out of range"; return DD_ERR_INVALID_PARTITION; }
+      (i < nI ? inter : iface).push_back((int32_t)(o + r0));
+    }
+    // aggregates of this system in its own interface numbering
+    const int32_t nG = (int32_t)(c.n - nI);
+    gsz.push_back(nG);
+    const int32_t g0 = bi.agg.empty() ? 0 : bi.agg.back();
+    if (bi.agg.empty()) bi.agg.push_back(0);
+    if (nG > 0) {
+      if (approx == DD_EXACT) {
+        bi.agg.push_back(g0 + nG);
+      } else if (p.agg_offsets) {
+        if (p.n_agg <= 0 || p.agg_offsets[0] != 0 || p.agg_offsets[p.n_agg] != nG) {
+          g_setup_error = "batch member " + std::to_string(q) + ": aggregate offsets must run from 0 to n_G";
+          return DD_ERR_INVALID_ARG;
+        }
+        for (int a = 1; a <= p.n_agg; ++a) bi.agg.push_back(g0 + p.agg_offsets[a]);
+      } else {
+        if (p.sz <= 0) { g_setup_error = "aggregate size sz must be positive"; return DD_ERR_INVALID_ARG; }
+        for (int32_t a = p.sz; a < nG; a += p.sz) bi.agg.push_back(g0 + a);
+        bi.agg.push_back(g0 + nG);
+      }
+    }
+    moff += p.m;
+  }
+  bi.perm = inter;
+  bi.perm.insert(bi.perm.end(), iface.begin(), iface.end());
+  bi.csr.n = N;
+  bi.csr.nnz = NNZ;
+  bi.csr.rowptr = bi.rowptr.data();
+  bi.csr.col = bi.col.data();
+  bi.csr.val = bi.val.data();
+  bi.pt.m = moff;
+  bi.pt.part = bi.partv.data();
+  bi.pt.perm = bi.perm.data();
+  bi.pt.sz = 0;
+  bi.pt.agg_offsets = bi.agg.data();
+  bi.pt.n_agg = (int32_t)bi.agg.size() - 1;
+  return DD_OK;
+}
+
+// Runs a solve on the caller's stream, or, with graphs, on the handle's
+// capture stream ordered after and before the caller's work.
+template <typename F>
+dd_status timed_solve(DDHandle *h, cudaStream_t s, F &&solve, float &ms) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  dd_status rc;
+  if (h->use_graph) {
+    cudaEventRecord(h->gev[0], s);
+    cudaStreamWaitEvent(h->gstream, h->gev[0], 0);
+    rc = solve(h->gstream);
+    cudaEventRecord(h->gev[1], h->gstream);
+    cudaStreamWaitEvent(s, h->gev[1], 0);
+  } else {
+    rc = solve(s);
+  }
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 }  // namespace
@@ -878,79 +1525,35 @@ dd_status dd_setup(const dd_csr *csr, const dd_partition *partition, dd_approx a
   *handle = nullptr;
   g_setup_error.clear();
   if (!csr || !partition) { g_setup_error = "csr and partition are required"; return DD_ERR_INVALID_ARG; }
-  if ((int)approx < DD_EXACT || (int)approx > DD_LUM) { g_setup_error = "unknown approximation"; return DD_ERR_INVALID_ARG; }
-  dd_opts o{};
-  o.prec = DD_FP64;
-  if (opts) o = *opts;
-  if (o.prec != DD_FP64 && o.prec != DD_FP32) { g_setup_error = "unknown precision"; return DD_ERR_INVALID_ARG; }
   DDHandle *h = new (std::nothrow) DDHandle();
   if (!h) return DD_ERR_OOM;
   h->stream = static_cast<cudaStream_t>(stream);
-  h->prec = o.prec;
-  h->kind = approx;
-  const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
-  const int R = o.max_restart > 0 ? o.max_restart : 50;
-  if (R > 120) { g_setup_error = "max_restart must be <= 120"; delete h; return DD_ERR_INVALID_ARG; }
-  HostBlocks hb;
-  dd_status rc = validate_and_order(h, csr, partition, hb);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (rc == DD_OK) {
-    h->n = csr->n;
-    h->nnz = csr->nnz;
-    h->m = partition->m;
-    h->nI = hb.off[h->m];
-    h->nG = (int)(h->n - h->nI);
-    rc = build_aggregates(h, partition, approx, hb);
+  h->nseg = 1;
+  h->seg_row0_h = {0, csr->n};
+  const dd_status rc = setup_handle(h, csr, partition, approx, opts);
+  return finish_setup(h, rc, handle);
+}
+
+dd_status dd_setup_batched(int32_t count, const dd_csr *csrs, const dd_partition *partitions,
+                           dd_approx approx, const dd_opts *opts, void *stream, void **handle) {
+  if (!handle) return DD_ERR_INVALID_ARG;
+  *handle = nullptr;
+  g_setup_error.clear();
+  if (count <= 0 || !csrs || !partitions) { g_setup_error = "count >= 1, csrs and partitions are required"; return DD_ERR_INVALID_ARG; }
+  if (approx == DD_MSCN || approx == DD_MSCNR) {
+    g_setup_error = "MSCN and MSCNR pair interface and interior index ranges of one system; not available in a batch";
+    return DD_ERR_INVALID_ARG;
   }
-  if (rc == DD_OK) {
-    extract_blocks(h, csr, partition, hb);
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-      h->err = "cudaEventCreate failed";
-      rc = DD_ERR_CUDA;
-    }
-  }
-  if (rc == DD_OK) {
-    cudaEventRecord(e0, h->stream);
-    rc = dalloc(h, &h->st, 1);
-    if (rc == DD_OK && cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream) != cudaSuccess) rc = DD_ERR_CUDA;
-    if (rc == DD_OK) rc = (h->prec == DD_FP32) ? setup_device<float>(h, csr, partition, hb, pivtol)
-                                               : setup_device<double>(h, csr, partition, hb, pivtol);
-    if (rc == DD_OK) rc = alloc_krylov(h, R);
-    cudaEventRecord(e1, h->stream);
-    cudaError_t se = cudaStreamSynchronize(h->stream);
-    if (rc == DD_OK && se != cudaSuccess) { h->err = cudaGetErrorString(se); rc = DD_ERR_CUDA; }
-    if (rc == DD_OK) {
-      DevStatus st{};
-      if (cudaMemcpy(&st, h->st, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = DD_ERR_CUDA; }
-      else if (st.code != 0) {
-        rc = (dd_status)st.code;
-        h->bad_block = st.block;
-        char buf[128];
-        snprintf(buf, sizeof buf, "%s in block %d",
-                 st.code == DD_ERR_SINGULAR_BLOCK ? "singular interior block" : "singular Schur block", st.block);
-        h->err = buf;
-      }
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    h->stats.setup_ms = ms;
-  }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  h->stats.n = h->n;
-  h->stats.n_interior = h->nI;
-  h->stats.n_interface = h->nG;
-  h->stats.nnz = h->nnz;
-  h->stats.m = h->m;
-  if (rc == DD_OK || rc == DD_ERR_SINGULAR_BLOCK || rc == DD_ERR_SINGULAR_SCHUR) {
-    *handle = h;
-    g_setup_error = h->err;
-    return rc;
-  }
-  g_setup_error = h->err;
-  release(h);
-  delete h;
-  return rc;
+  BatchInput bi;
+  const dd_status rc0 = concat_batch(count, csrs, partitions, approx, bi);
+  if (rc0 != DD_OK) return rc0;
+  DDHandle *h = new (std::nothrow) DDHandle();
+  if (!h) return DD_ERR_OOM;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->nseg = count;
+  h->seg_row0_h = bi.row0;
+  const dd_status rc = setup_handle(h, &bi.csr, &bi.pt, approx, opts);
+  return finish_setup(h, rc, handle);
 }
 
 dd_status dd_apply(void *handle, const double *y, double *x, void *stream) {
@@ -975,19 +1578,40 @@ dd_status gmres_solve(void *handle, const double *b, double *x, double tol, int3
     return DD_ERR_INVALID_ARG;
   }
   if (h->bad_block >= 0) { h->err = "preconditioner failed in setup"; return DD_ERR_INVALID_ARG; }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  dd_status rc = fgmres(h, b, x, tol, restart, maxit, info, s);
-  cudaEventRecord(e1, s);
-  cudaEventSynchronize(e1);
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (info) { info->solve_ms = ms; info->setup_ms = h->stats.setup_ms; info->bad_block = h->bad_block; }
+  const dd_status rc = timed_solve(
+      h, static_cast<cudaStream_t>(stream),
+      [&](cudaStream_t s2) { return fgmres(h, b, x, tol, restart, maxit, info, s2); }, ms);
+  if (info) {
+    info->solve_ms = ms;
+    info->setup_ms = h->stats.setup_ms;
+    info->bad_block = h->bad_block;
+    info->status = rc;
+  }
+  return rc;
+}
+
+dd_status gmres_solve_batched(void *handle, const double *const *b, double *const *x, double tol,
+                              int32_t restart, int32_t maxit, dd_info *infos, void *stream) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h || !b || !x || restart <= 0 || restart > h->Rmax || maxit <= 0 || !(tol > 0)) {
+    if (h) h->err = "invalid gmres_solve_batched arguments (restart must be <= max_restart of dd_setup)";
+    return DD_ERR_INVALID_ARG;
+  }
+  if (h->nseg < 2) { h->err = "gmres_solve_batched needs a handle from dd_setup_batched with >= 2 systems"; return DD_ERR_INVALID_ARG; }
+  for (int q = 0; q < h->nseg; ++q)
+    if (!b[q] || !x[q]) { h->err = "null right-hand side or solution pointer"; return DD_ERR_INVALID_ARG; }
+  if (h->bad_block >= 0) { h->err = "preconditioner failed in setup"; return DD_ERR_INVALID_ARG; }
+  float ms = 0.f;
+  const dd_status rc = timed_solve(
+      h, static_cast<cudaStream_t>(stream),
+      [&](cudaStream_t s2) { return fgmres_batched(h, b, x, tol, restart, maxit, infos, s2); }, ms);
+  if (infos)
+    for (int q = 0; q < h->nseg; ++q) {
+      infos[q].solve_ms = ms;
+      infos[q].setup_ms = h->stats.setup_ms;
+      infos[q].bad_block = h->bad_block;
+    }
   return rc;
 }
 

@@ -48,6 +48,35 @@ struct SweepJob {
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
+// Launch plan of the sweep kernels: ring stage size, threads per CTA, and,
+// when there are more subdomains than resident CTAs, a persistent grid whose
+// CTA c takes the tasks sched[sched_off[c] .. sched_off[c+1]) (longest
+// first, balanced on the host); sched_off == nullptr means one CTA per
+// subdomain.
+// Rows and CTAs of the systems a Krylov kernel works on.  nseg == 1: the
+// whole vector, every CTA, one set of per-system state (the other pointers
+// may be null).  nseg > 1: system s owns rows [seg_row0[s], seg_row0[s+1])
+// and CTAs [seg_cta0[s], seg_cta0[s+1]); cta_seg maps a CTA to its system;
+// act[s] != 0 while system s takes Arnoldi steps (null: all).  rmax sets the
+// strides of the per-system state arrays.
+struct SegMap {
+  int nseg = 1;
+  int rmax = 0;
+  int nctas = 0;  // set on the device from the grid
+  const int32_t *cta_seg = nullptr;
+  const int32_t *seg_cta0 = nullptr;
+  const int64_t *seg_row0 = nullptr;
+  const int32_t *act = nullptr;
+};
+
+struct SweepPlan {
+  uint32_t stage_bytes = 0;
+  int threads = 256;
+  int grid = 0;
+  const int32_t *sched = nullptr;
+  const int32_t *sched_off = nullptr;
+};
+
 // Device-side error word: first failure wins.
 struct DevStatus {
   int32_t code;   // 0 ok, else a dd_status
@@ -65,11 +94,16 @@ int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_
 // Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
 // column-major, exchanged), wscratch holds the windows when they do not fit
 // in shared memory (band_lu_window_bytes per subdomain, else unused).
+// sched / sched_off: optional persistent task lists of `grid` CTAs (as in
+// SweepPlan).
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size);
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
                            int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
-                           cudaStream_t s);
+                           int grid, const int32_t *sched, const int32_t *sched_off, cudaStream_t s);
+// resident CTAs per SM of the band LU (0 on error)
+template <typename T>
+int band_lu_occupancy(int max_kl, int max_ku, int threads);
 // Widths of every tile (forward rows wl and backward columns wu that hold
 // nonzeros after the factorisation), written to wl/wu at tile0 + t.
 template <typename T>
@@ -84,18 +118,21 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
 // numbering), z in the interior numbering.
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  int max_ku2, const SweepPlan &pl, const TileMeta *tm,
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const double *y, const int32_t *perm, T *z,
-                                  DevStatus *st, int threads, cudaStream_t s);
+                                  DevStatus *st, cudaStream_t s);
 // x1 = z1 - A^-1 (E z2) per subdomain, scattered to x (original numbering).
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  int max_ku2, const SweepPlan &pl, const TileMeta *tm,
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
-                                  double *x, DevStatus *st, int threads, cudaStream_t s);
+                                  double *x, DevStatus *st, cudaStream_t s);
+// resident CTAs per SM of the sweep kernels at this stage size (0: does not fit)
+template <typename T>
+int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32_t stage_bytes);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>
@@ -169,6 +206,16 @@ cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
 // One Arnoldi orthogonalisation step (CGS2 + Givens + normalisation) as a
 // single cooperative kernel; partial holds nblocks * pk doubles, pk >= R + 2.
 int cgs2_blocks(int cap);
-cudaError_t launch_cgs2(int n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
+cudaError_t launch_cgs2(int64_t n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
                         int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
-                        double bnorm, double *scal, int nblocks, cudaStream_t s);
+                        const double *bn2, double *scal, const SegMap &sm, int nblocks, cudaStream_t s);
+// Batched FGMRES over a SegMap (nseg >= 2, nblocks = seg_cta0[nseg] CTAs):
+// out[s] = ||v_s||^2; v0 = r / ||r_s|| and g_s = ||r_s|| e_0 for active
+// systems; y_s = H_s^-1 g_s and x_s += Z y_s for systems with jl[s] >= 0.
+cudaError_t launch_seg_norms(int64_t n, const double *v, double *partial, double *out, const SegMap &sm,
+                             int nblocks, cudaStream_t s);
+cudaError_t launch_seg_start(int64_t n, const double *r, const double *nsq, double *v0, double *g,
+                             const SegMap &sm, int nblocks, cudaStream_t s);
+cudaError_t launch_seg_hess_update(int64_t n, int R, const int32_t *jl, const double *H, const double *g,
+                                   double *y, const double *Z, int64_t ldz, double *x, const SegMap &sm,
+                                   int nblocks, cudaStream_t s);

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "dd_internal.h"
 
 namespace {
@@ -62,17 +64,12 @@ __host__ __device__ __forceinline__ int kidx(int r, int c) {
 // only, which is the order the forward sweep applies them in.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
-                               T *wscratch, int64_t wscratch_stride, int smem_window,
-                               double pivtol, DevStatus *st) {
-  const BandInfo b = info[blockIdx.x];
+__device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int32_t *piv, T *W,
+                             double pivtol, DevStatus *st) {
   const int n = b.n, kl = b.kl, ku = b.ku, wd = 2 * kl + ku + 1;
-  if (n == 0) return;
   const int R = DD_NB + kl, Cw = DD_NB + kl + ku, ldw = Cw | 1;
   T *A = band + b.band_off;
   int32_t *P = piv + b.piv_off;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *W = smem_window ? reinterpret_cast<T *>(smraw) : wscratch + (int64_t)blockIdx.x * wscratch_stride;
   __shared__ T red[32];
   __shared__ int32_t s_p;
   __shared__ int32_t s_fail;
@@ -122,7 +119,7 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
         if (lane == 0) {
           s_p = bi;
           P[c0 + c] = c0 + bi;
-          if (!(best > thresh)) { s_fail = 1; set_status(st, DD_ERR_SINGULAR_BLOCK, blockIdx.x); }
+          if (!(best > thresh)) { s_fail = 1; set_status(st, DD_ERR_SINGULAR_BLOCK, task); }
         }
       }
       __syncthreads();
@@ -196,6 +193,28 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
   }
 }
 
+// Every subdomain of the CTA's task list (or subdomain blockIdx.x); the
+// window sits in shared memory when it fits the launch's smem_bytes, else in
+// wscratch (wscratch_stride elements per subdomain).
+template <typename T>
+__global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
+                               T *wscratch, int64_t wscratch_stride, int smem_bytes, double pivtol,
+                               const int32_t *__restrict__ sched, const int32_t *__restrict__ sched_off,
+                               DevStatus *st) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int t0 = sched_off ? sched_off[blockIdx.x] : (int)blockIdx.x;
+  const int t1 = sched_off ? sched_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+  for (int it = t0; it < t1; ++it) {
+    const int task = sched ? sched[it] : it;
+    const BandInfo b = info[task];
+    if (b.n == 0) continue;
+    const int64_t wb = (int64_t)(DD_NB + b.kl) * ((DD_NB + b.kl + b.ku) | 1) * (int64_t)sizeof(T);
+    T *W = (wb <= smem_bytes) ? reinterpret_cast<T *>(smraw) : wscratch + (int64_t)task * wscratch_stride;
+    __syncthreads();  // the previous task is done with the window and the shared scalars
+    band_lu_task<T>(b, task, band, ltraw, piv, W, pivtol, st);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Tile widths, one warp per (subdomain, tile):
 //   wl = rows of the forward window that the tile touches: the last nonzero
@@ -255,7 +274,7 @@ __global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const TileM
   T *K = ltile + mt.lofs;
   T *Kb = utile + mt.uofs;
   int32_t *src = srcs + mt.sofs;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T *L11 = reinterpret_cast<T *>(smraw);  // NB x NB, [row][col]
   T *vbuf = L11 + DD_NB * DD_NB;          // 32 columns x W
   T *Lsm = vbuf + (size_t)DD_NB * W;      // NB x NB
@@ -457,23 +476,29 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
                                 const T *__restrict__ utile, const int32_t *__restrict__ srcs,
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
-                                DevStatus *st) {
+                                uint32_t &jbase, int task, DevStatus *st) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nj = b.njf + b.njb;
+  // job q of this task is job jbase + q of the CTA: its stage and phase
   if (tid == 0) {
-    for (int q = 0; q < nstages && q < nj; ++q)
-      issue_job<T>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)q * stage_bytes, &bars[q]);
+    // the stages were last read by generic loads of the previous task
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int q = 0; q < nstages && q < nj; ++q) {
+      const int sq = (int)((jbase + q) % nstages);
+      issue_job<T>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq]);
+    }
   }
   bool ok = true;
   int q = 0;
   for (; q < nj; ++q) {
-    const int sidx = q % nstages;
+    const uint32_t gq = jbase + q;
+    const int sidx = (int)(gq % nstages);
     unsigned char *stage = ring + (size_t)sidx * stage_bytes;
     // every thread waits (bounded); the verdict is made uniform at the
     // first barrier of the job, so no thread can leave the loop alone
-    const bool got = mbar_wait_bounded(&bars[sidx], (uint32_t)((q / nstages) & 1));
+    const bool got = mbar_wait_bounded(&bars[sidx], (gq / nstages) & 1u);
     bool fwd;
     const SweepJob jb = get_job(b, jobs, q, fwd);
     const TileMeta &a = tm[b.tile0 + jb.lo];
@@ -542,16 +567,17 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
   }
   if (!ok) {
     if (tid == 0) {
-      if (atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = blockIdx.x;
+      if (atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = task;
     }
-    // drain the copies this CTA issued (jobs 0 .. q+nstages-1), bounded
+    // drain the copies still in flight (jobs q .. q+nstages-1, one per
+    // stage), bounded
     const int last_issued = min(nj - 1, q + nstages - 1);
-    for (int s2 = 0; s2 < nstages; ++s2) {
-      int last = -1;
-      for (int j = s2; j <= last_issued; j += nstages) last = j;
-      if (last >= q) mbar_wait_bounded(&bars[s2], (uint32_t)((last / nstages) & 1));
+    for (int j = q; j <= last_issued; ++j) {
+      const uint32_t gj = jbase + j;
+      mbar_wait_bounded(&bars[gj % nstages], (gj / nstages) & 1u);
     }
   }
+  jbase += nj;
   return ok;
 }
 
@@ -597,6 +623,13 @@ __device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
   __syncthreads();
 }
 
+// Tasks of CTA c: sched[sched_off[c] .. sched_off[c+1]) when a schedule is
+// given (more subdomains than resident CTAs), else the one task c.
+__device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, int &t1) {
+  t0 = sched_off ? sched_off[blockIdx.x] : (int)blockIdx.x;
+  t1 = sched_off ? sched_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+}
+
 // z = A_jj^-1 y_j with y gathered from the original numbering.
 template <typename T>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
@@ -605,25 +638,35 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
                                       const TileMeta *__restrict__ tm, const SweepJob *__restrict__ jobs,
                                       const T *__restrict__ ltile, const T *__restrict__ utile,
                                       const int32_t *__restrict__ srcs, const double *__restrict__ y,
-                                      const int32_t *__restrict__ perm, T *z, DevStatus *st) {
-  const BandInfo bg = info[blockIdx.x];
-  if (bg.n == 0) return;
+                                      const int32_t *__restrict__ perm, T *z,
+                                      const int32_t *__restrict__ sched,
+                                      const int32_t *__restrict__ sched_off, DevStatus *st) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
   carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
-  const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
   init_bars(bars, nstages);
-  const int ntot = b.ntiles * DD_NB + pad;
-  for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
-    vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
-    xout[i] = T(0);
+  int t0, t1;
+  task_range(sched_off, t0, t1);
+  uint32_t jbase = 0;
+  for (int it = t0; it < t1; ++it) {
+    const int task = sched ? sched[it] : it;
+    const BandInfo bg = info[task];
+    if (bg.n == 0) continue;
+    __syncthreads();  // the previous task's reads of the tables and vectors are done
+    const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+    const int ntot = b.ntiles * DD_NB + pad;
+    for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
+      vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
+      xout[i] = T(0);
+    }
+    __syncthreads();
+    if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
+                            nstages, bars, jbase, task, st))
+      return;
+    for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
   }
-  __syncthreads();
-  if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
-    return;
-  for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
@@ -638,32 +681,41 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       const int32_t *__restrict__ e_col,
                                       const T *__restrict__ e_val, const T *__restrict__ z2,
                                       const T *__restrict__ z1, const int32_t *__restrict__ perm,
-                                      double *x, DevStatus *st) {
-  const BandInfo bg = info[blockIdx.x];
-  if (bg.n == 0) return;
+                                      double *x, const int32_t *__restrict__ sched,
+                                      const int32_t *__restrict__ sched_off, DevStatus *st) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
   carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
-  const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
   init_bars(bars, nstages);
-  const int ntot = b.ntiles * DD_NB + pad;
-  for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
-    T v = T(0);
-    if (i < b.n) {
-      const int r = b.row0 + i;
-      for (int k = e_ptr[r]; k < e_ptr[r + 1]; ++k) v += e_val[k] * z2[e_col[k]];
+  int t0, t1;
+  task_range(sched_off, t0, t1);
+  uint32_t jbase = 0;
+  for (int it = t0; it < t1; ++it) {
+    const int task = sched ? sched[it] : it;
+    const BandInfo bg = info[task];
+    if (bg.n == 0) continue;
+    __syncthreads();
+    const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+    const int ntot = b.ntiles * DD_NB + pad;
+    for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
+      T v = T(0);
+      if (i < b.n) {
+        const int r = b.row0 + i;
+        for (int k = e_ptr[r]; k < e_ptr[r + 1]; ++k) v += e_val[k] * z2[e_col[k]];
+      }
+      vec[i] = v;
+      xout[i] = T(0);
     }
-    vec[i] = v;
-    xout[i] = T(0);
-  }
-  __syncthreads();
-  if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages, bars, st))
-    return;
-  for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
-    const int r = b.row0 + i;
-    x[perm[r]] = double(z1[r] - xout[i]);
+    __syncthreads();
+    if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
+                            nstages, bars, jbase, task, st))
+      return;
+    for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
+      const int r = b.row0 + i;
+      x[perm[r]] = double(z1[r] - xout[i]);
+    }
   }
 }
 
@@ -686,7 +738,7 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
   const int nr = min(NR, nc - k0);
   const int n = b.n;
   T *X = Xall + x_off[blockIdx.x] + (int64_t)k0 * n;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T *win = reinterpret_cast<T *>(smraw);  // max(wl, wu) x NR, [row][r]
   const int tid = threadIdx.x, nt = blockDim.x;
   // forward: X(window) <- [0; X_B] + K X_T on the exchanged window
@@ -762,6 +814,7 @@ int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_
   return s > DD_MAX_STAGES ? DD_MAX_STAGES : s;
 }
 
+#define DD_LU_SMEM (200 * 1024)
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
   const int R = DD_NB + max_kl, Cw = DD_NB + max_kl + max_ku;
   return (size_t)R * (size_t)(Cw | 1) * elem_size;
@@ -770,15 +823,26 @@ size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
                            int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
-                           cudaStream_t s) {
+                           int grid, const int32_t *sched, const int32_t *sched_off, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
   const size_t wb = band_lu_window_bytes(max_kl, max_ku, sizeof(T));
-  const bool in_smem = wb <= 200 * 1024;
-  const size_t smem = in_smem ? wb : 0;
+  const size_t smem = std::min(wb, (size_t)DD_LU_SMEM);
   cudaError_t e = ensure_smem(band_lu_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_lu_kernel<T><<<m, threads, smem, s>>>(d_info, band, ltraw, piv, wscratch,
-                                             (int64_t)(wb / sizeof(T)), in_smem ? 1 : 0, pivtol, st);
+  band_lu_kernel<T><<<sched_off ? grid : m, threads, smem, s>>>(d_info, band, ltraw, piv, wscratch,
+                                                                (int64_t)(wb / sizeof(T)), (int)smem,
+                                                                pivtol, sched, sched_off, st);
   return cudaGetLastError();
+}
+
+// resident CTAs per SM of the band LU
+template <typename T>
+int band_lu_occupancy(int max_kl, int max_ku, int threads) {
+  const size_t smem = std::min(band_lu_window_bytes(max_kl, max_ku, sizeof(T)), (size_t)DD_LU_SMEM);
+  if (ensure_smem(band_lu_kernel<T>, smem) != cudaSuccess) return 0;
+  int a = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_lu_kernel<T>, threads, smem) != cudaSuccess) return 0;
+  return a;
 }
 
 template <typename T>
@@ -805,40 +869,63 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
 
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  int max_ku2, const SweepPlan &pl, const TileMeta *tm,
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const double *y, const int32_t *perm, T *z,
-                                  DevStatus *st, int threads, cudaStream_t s) {
-  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
+                                  DevStatus *st, cudaStream_t s) {
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
   // the backward tile step maps exactly 8 threads to each of the 32 rows
-  if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
+  if (ns < 2 || pl.threads != 8 * DD_NB) return cudaErrorInvalidValue;
   const int mt = max_n / DD_NB, mj = 2 * mt;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
+  const int grid = pl.sched_off ? pl.grid : m;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * pl.stage_bytes;
   cudaError_t e = ensure_smem(band_solve_fwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_fwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                     stage_bytes, tm, jobs, ltile, utile, src, y,
-                                                     perm, z, st);
+  if (grid <= 0) return cudaSuccess;
+  band_solve_fwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                          pl.stage_bytes, tm, jobs, ltile, utile, src,
+                                                          y, perm, z, pl.sched, pl.sched_off, st);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int max_kl,
-                                  int max_ku2, uint32_t stage_bytes, const TileMeta *tm,
+                                  int max_ku2, const SweepPlan &pl, const TileMeta *tm,
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
-                                  double *x, DevStatus *st, int threads, cudaStream_t s) {
-  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
-  if (ns < 2 || threads != 8 * DD_NB) return cudaErrorInvalidValue;
+                                  double *x, DevStatus *st, cudaStream_t s) {
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
+  if (ns < 2 || pl.threads != 8 * DD_NB) return cudaErrorInvalidValue;
   const int mt = max_n / DD_NB, mj = 2 * mt;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
+  const int grid = pl.sched_off ? pl.grid : m;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * pl.stage_bytes;
   cudaError_t e = ensure_smem(band_solve_bwd_kernel<T>, smem);
   if (e != cudaSuccess) return e;
-  band_solve_bwd_kernel<T><<<m, threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                     stage_bytes, tm, jobs, ltile, utile, src, e_ptr,
-                                                     e_col, e_val, z2, z1, perm, x, st);
+  if (grid <= 0) return cudaSuccess;
+  band_solve_bwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                          pl.stage_bytes, tm, jobs, ltile, utile, src,
+                                                          e_ptr, e_col, e_val, z2, z1, perm, x,
+                                                          pl.sched, pl.sched_off, st);
   return cudaGetLastError();
+}
+
+// resident CTAs per SM of the two sweep kernels at this shared-memory size
+// (the smaller of the two), 0 on error
+template <typename T>
+int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32_t stage_bytes) {
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
+  if (ns < 2) return 0;
+  const int mt = max_n / DD_NB, mj = 2 * mt;
+  const size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
+  if (ensure_smem(band_solve_fwd_kernel<T>, smem) != cudaSuccess) return 0;
+  if (ensure_smem(band_solve_bwd_kernel<T>, smem) != cudaSuccess) return 0;
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T>, threads, smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T>, threads, smem) != cudaSuccess)
+    return 0;
+  return a < b ? a : b;
 }
 
 #define DD_MULTI_NR 16
@@ -860,21 +947,24 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
 
 #define DD_INST_BAND(T)                                                                            \
   template cudaError_t launch_band_lu<T>(const BandInfo *, int, int, int, T *, T *, int32_t *,     \
-                                         T *, double, DevStatus *, int, cudaStream_t);              \
+                                         T *, double, DevStatus *, int, int, const int32_t *,       \
+                                         const int32_t *, cudaStream_t);                            \
+  template int band_lu_occupancy<T>(int, int, int);                                                \
   template cudaError_t launch_tile_widths<T>(const BandInfo *, int, int, const T *, const T *,     \
                                              const int32_t *, int32_t *, int32_t *, cudaStream_t); \
   template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const TileMeta *,     \
                                             const T *, const T *, const int32_t *, T *, T *,       \
                                             int32_t *, cudaStream_t);                               \
-  template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int, uint32_t,    \
-                                                const TileMeta *, const SweepJob *, const T *,      \
-                                                const T *, const int32_t *, const double *,         \
-                                                const int32_t *, T *, DevStatus *, int,             \
-                                                cudaStream_t);                                      \
+  template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int,             \
+                                                const SweepPlan &, const TileMeta *,                \
+                                                const SweepJob *, const T *, const T *,             \
+                                                const int32_t *, const double *, const int32_t *,   \
+                                                T *, DevStatus *, cudaStream_t);                    \
   template cudaError_t launch_band_solve_bwd<T>(                                                   \
-      const BandInfo *, int, int, int, int, uint32_t, const TileMeta *, const SweepJob *,          \
-      const T *, const T *, const int32_t *, const int32_t *, const int32_t *, const T *,          \
-      const T *, const T *, const int32_t *, double *, DevStatus *, int, cudaStream_t);            \
+      const BandInfo *, int, int, int, int, const SweepPlan &, const TileMeta *,                   \
+      const SweepJob *, const T *, const T *, const int32_t *, const int32_t *, const int32_t *,    \
+      const T *, const T *, const T *, const int32_t *, double *, DevStatus *, cudaStream_t);      \
+  template int band_sweep_occupancy<T>(int, int, int, int, uint32_t);                              \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \
                                                   const int64_t *, int, int, int,                  \
                                                   const TileMeta *, const T *, const T *,          \

@@ -156,8 +156,8 @@ __global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_
 // so the inverse is the one Gauss-Jordan computes column by column, with the
 // rank-1 passes grouped into rank-NB updates.  The row exchanges are undone
 // as column exchanges at the end.
-// Scratch per block b at soff2[b] = 3*NB*poff[b] + NB*NB*b elements:
-//   [panel p x NB | Pcol p x NB | Rnew NB x p | A11inv NB x NB]
+// Scratch per block b at 4*NB*poff[b] + NB*NB*b elements:
+//   [panel p x (NB+1) within 2*NB*p | Pcol p x NB | Rnew NB x p | A11inv NB x NB]
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
 __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
@@ -169,10 +169,12 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
   if (k0 >= p || failed[b]) return;
   const int nbe = min(NB, p - k0), rows = p - k0;
   T *a = A + off[b];
-  T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *W = (rows <= smem_rows) ? reinterpret_cast<T *>(smraw) : scr;  // rows x NB
-  T *a11inv = scr + 3 * (int64_t)NB * p;
+  T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // rows x NB with row stride NB+1 (conflict-free for row- and column-wise access)
+  constexpr int LD = NB + 1;
+  T *W = (rows <= smem_rows) ? reinterpret_cast<T *>(smraw) : scr;
+  T *a11inv = scr + 4 * (int64_t)NB * p;
   __shared__ T bv[32];
   __shared__ int bi[32];
   __shared__ int s_piv;
@@ -181,7 +183,7 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
   if (tid == 0) s_fail = 0;
   for (int e = tid; e < rows * NB; e += nt) {
     const int r = e / NB, c = e % NB;
-    W[e] = (c < nbe) ? a[(int64_t)(k0 + r) * p + k0 + c] : T(0);
+    W[r * LD + c] = (c < nbe) ? a[(int64_t)(k0 + r) * p + k0 + c] : T(0);
   }
   __syncthreads();
   const T thresh = T(pivtol) * amax[b];
@@ -189,7 +191,7 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
     T best = T(-1);
     int besti = rows;
     for (int r = c + tid; r < rows; r += nt) {
-      T v = tabs(W[r * NB + c]);
+      T v = tabs(W[r * LD + c]);
       if (v > best) { best = v; besti = r; }
     }
     for (int o = 16; o; o >>= 1) {
@@ -216,14 +218,14 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
     if (s_fail) return;
     const int pr = s_piv;
     if (pr != c && tid < NB) {
-      T t = W[c * NB + tid]; W[c * NB + tid] = W[pr * NB + tid]; W[pr * NB + tid] = t;
+      T t = W[c * LD + tid]; W[c * LD + tid] = W[pr * LD + tid]; W[pr * LD + tid] = t;
     }
     __syncthreads();
-    const T piv = W[c * NB + c];
+    const T piv = W[c * LD + c];
     for (int r = c + 1 + tid; r < rows; r += nt) {
-      const T l = W[r * NB + c] / piv;
-      W[r * NB + c] = l;
-      for (int q = c + 1; q < nbe; ++q) W[r * NB + q] -= l * W[c * NB + q];
+      const T l = W[r * LD + c] / piv;
+      W[r * LD + c] = l;
+      for (int q = c + 1; q < nbe; ++q) W[r * LD + q] -= l * W[c * LD + q];
     }
     __syncthreads();
   }
@@ -247,13 +249,13 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
     x[j] = T(1);
     for (int i = j + 1; i < nbe; ++i) {  // L11 y = e_j (unit lower)
       T s2 = T(0);
-      for (int q = j; q < i; ++q) s2 += W[i * NB + q] * x[q];
+      for (int q = j; q < i; ++q) s2 += W[i * LD + q] * x[q];
       x[i] = -s2;
     }
     for (int i = nbe - 1; i >= 0; --i) {  // U11 x = y
       T s2 = x[i];
-      for (int q = i + 1; q < nbe; ++q) s2 -= W[i * NB + q] * x[q];
-      x[i] = s2 / W[i * NB + i];
+      for (int q = i + 1; q < nbe; ++q) s2 -= W[i * LD + q] * x[q];
+      x[i] = s2 / W[i * LD + i];
     }
     for (int i = 0; i < NB; ++i) a11inv[i * NB + j] = (i < nbe) ? x[i] : T(0);
   } else if (tid < NB) {
@@ -270,10 +272,10 @@ __global__ void bgj_rowblock_kernel(int k0, const int32_t *__restrict__ P, const
   if (k0 >= p || failed[b]) return;
   const int nbe = min(NB, p - k0);
   const T *a = A + off[b];
-  T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
-  T *Pcol = scr + (int64_t)NB * p;
-  T *Rnew = scr + 2 * (int64_t)NB * p;
-  const T *a11inv = scr + 3 * (int64_t)NB * p;
+  T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
+  T *Pcol = scr + 2 * (int64_t)NB * p;
+  T *Rnew = scr + 3 * (int64_t)NB * p;
+  const T *a11inv = scr + 4 * (int64_t)NB * p;
   __shared__ T ai[NB * NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) ai[e] = a11inv[e];
   __syncthreads();
@@ -306,10 +308,10 @@ __global__ void bgj_update_kernel(int k0, const int32_t *__restrict__ P, const i
   if (i0 >= p || j0 >= p) return;
   const int nbe = min(NB, p - k0);
   T *a = A + off[b];
-  const T *scr = scratch + 3 * NB * poff[b] + (int64_t)NB * NB * b;
-  const T *Pcol = scr + (int64_t)NB * p;
-  const T *Rnew = scr + 2 * (int64_t)NB * p;
-  const T *a11inv = scr + 3 * (int64_t)NB * p;
+  const T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
+  const T *Pcol = scr + 2 * (int64_t)NB * p;
+  const T *Rnew = scr + 3 * (int64_t)NB * p;
+  const T *a11inv = scr + 4 * (int64_t)NB * p;
   __shared__ T Ps[DD_BGJ_TILE][NB + 1];
   __shared__ T Rs[NB][DD_BGJ_TILE + 1];
   const int tid = threadIdx.x;  // 256 threads: 16 x 16, each 4 x 4 outputs
@@ -431,7 +433,7 @@ __global__ void mscnr_diag_kernel(const int32_t *__restrict__ P, const int64_t *
                                   const T *__restrict__ F, T *S) {
   const int b = blockIdx.x;
   const int p = P[b];
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T *v = reinterpret_cast<T *>(smraw);
   T *w = v + p;
   const T *e = E + off[b], *d = Dinv + off[b], *f = F + off[b];
@@ -478,7 +480,7 @@ __global__ void schur_gemv_kernel(const int32_t *__restrict__ agg_off, const int
   const int g0 = agg_off[a], p = agg_off[a + 1] - g0;
   const int rbase = blockIdx.x * DD_SROWS;
   if (rbase >= p) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T *ts = reinterpret_cast<T *>(smraw);
   for (int r = threadIdx.x; r < p; r += blockDim.x) ts[r] = t[g0 + r];
   __syncthreads();
@@ -529,7 +531,7 @@ struct BgjNB<double> { static const int value = 8; };
 
 int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size) {
   const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
-  return 3 * (int64_t)nb * sum_p + (int64_t)nb * nb * nblk;
+  return 4 * (int64_t)nb * sum_p + (int64_t)nb * nb * nblk;
 }
 
 // Explicit inverse of every block (in place), blocked Gauss-Jordan; blocks
@@ -544,8 +546,8 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   cudaError_t e = cudaMemsetAsync(failed, 0, sizeof(int32_t) * nblk, s);
   if (e != cudaSuccess) return e;
   const size_t smem_cap = 200 * 1024;
-  const int smem_rows = (int)(smem_cap / (NB * sizeof(T)));
-  const size_t smem = (size_t)std::min(pmax, smem_rows) * NB * sizeof(T);
+  const int smem_rows = (int)(smem_cap / ((NB + 1) * sizeof(T)));
+  const size_t smem = (size_t)std::min(pmax, smem_rows) * (NB + 1) * sizeof(T);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(bgj_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -244,26 +244,6 @@ __device__ void block_dots(int i0, int i1, int k, const double *__restrict__ V, 
   }
 }
 
-// CTA c sums columns q = c, c + nctas, ... of the partials over all CTAs in a
-// fixed order into dst[q]
-__device__ void column_sums(int ncols, int nb, int pk, const double *__restrict__ partial, double *dst,
-                            double *red, int cta, int nctas) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int q = cta; q < ncols; q += nctas) {
-    double t = 0.0;
-    for (int b = tid; b < nb; b += blockDim.x) t += partial[(int64_t)b * pk + q];
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[warp] = t;
-    __syncthreads();
-    if (tid == 0) {
-      double u = 0.0;
-      for (int ww = 0; ww < nw; ++ww) u += red[ww];
-      dst[q] = u;
-    }
-    __syncthreads();
-  }
-}
-
 // w_i - sum_q h_q V_q[i], eight loads in flight per thread
 __device__ __forceinline__ double row_update(int i, int k, const double *__restrict__ V, int64_t ldv,
                                              const double *hs, double wi) {
@@ -277,49 +257,108 @@ __device__ __forceinline__ double row_update(int i, int k, const double *__restr
   return wi - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
 }
 
+// The rows, CTAs and per-system state a CTA works on.  With one system the
+// CTA owns chunk b of [0, n) and the state arrays hold one system; with
+// several, CTA b belongs to system cta_seg[b] and owns a chunk of its rows.
+struct SegCta {
+  int s, c0, nc;   // system, its first CTA, its CTA count
+  int64_t i0, i1;  // this CTA's rows
+  bool act;        // the system takes this step
+};
+__device__ __forceinline__ SegCta seg_cta(const SegMap &sm, int b, int nb, int64_t n) {
+  SegCta c;
+  int64_t r0 = 0, r1 = n;
+  if (sm.nseg == 1) {
+    c.s = 0; c.c0 = 0; c.nc = nb;
+  } else {
+    c.s = sm.cta_seg[b];
+    c.c0 = sm.seg_cta0[c.s];
+    c.nc = sm.seg_cta0[c.s + 1] - c.c0;
+    r0 = sm.seg_row0[c.s];
+    r1 = sm.seg_row0[c.s + 1];
+  }
+  const int64_t ns = r1 - r0, chunk = (ns + c.nc - 1) / c.nc;
+  c.i0 = r0 + min(ns, (int64_t)(b - c.c0) * chunk);
+  c.i1 = min(r1, c.i0 + chunk);
+  c.act = sm.act ? sm.act[c.s] != 0 : true;
+  if (!c.act) c.i1 = c.i0;
+  return c;
+}
+
+// Sums over the CTAs of each system, of `ncols` columns of the partials, in
+// a fixed order: pair p = s * ncols + q goes to CTA p mod nctas, which
+// writes dst[s * dstride + q].  Inactive systems are skipped.
+__device__ void seg_column_sums(const SegMap &sm, int ncols, int pk, const double *__restrict__ partial,
+                                double *dst, int dstride, double *red, int cta, int nctas) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int total = sm.nseg * ncols;
+  for (int p = cta; p < total; p += nctas) {
+    const int sys = p / ncols, q = p % ncols;
+    if (sm.act && !sm.act[sys]) continue;
+    const int b0 = sm.nseg == 1 ? 0 : sm.seg_cta0[sys];
+    const int b1 = sm.nseg == 1 ? sm.nctas : sm.seg_cta0[sys + 1];
+    double t = 0.0;
+    for (int b = b0 + tid; b < b1; b += blockDim.x) t += partial[(int64_t)b * pk + q];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double u = 0.0;
+      for (int ww = 0; ww < nw; ++ww) u += red[ww];
+      dst[(int64_t)sys * dstride + q] = u;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One Arnoldi orthogonalisation step as a single cooperative kernel: classical
 // Gram-Schmidt applied twice to w = V_{j+1} against V_0..V_j, the norms, the
-// Givens rotation of the new Hessenberg column and the normalisation of w.
-// Every CTA owns a contiguous chunk of rows; grid-wide barriers separate
-//   1 partial dots V^T w, w^T w            2 column sums (CTA q: column q) -> h1
+// Givens rotation of the new Hessenberg column and the normalisation of w,
+// for one system or for every active system of a batch at once (each system
+// its own rows, CTAs, sums and Hessenberg matrix).  Grid-wide barriers
+// separate
+//   1 partial dots V^T w, w^T w            2 column sums per system -> h1
 //   3 w -= V h1, partial dots V^T w        4 column sums -> h2
-//   5 w -= V h2, partial w^T w             6 CTA 0: norm, Hessenberg column
-//                                            and rotations in shared memory
+//   5 w -= V h2, partial w^T w             6 CTA s: norm, Hessenberg column
+//                                            and rotations of system s
 //   7 w /= h_{j+1,j} unless breakdown
 // The FP64 pipe bounds this kernel on GB300, so reductions are kept to one
 // pass over the partials per column.  Sums run in a fixed order.
-// scal: [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}| / ||b||
+// Per-system state (strides from sm.rmax): hc1/hc2 rmax+2, H (rmax+1)*rmax
+// with row stride R, cs/sn rmax, g rmax+1, bn2 (||b||^2) 1, scal 4:
+// [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}| / ||b||.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
-    int n, int j, int R, const double *__restrict__ V, int64_t ldv, double *w, double *partial,
-    int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g, double bnorm,
-    double *scal) {
+    int64_t n, int j, int R, const double *__restrict__ V, int64_t ldv, double *w, double *partial,
+    int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
+    const double *__restrict__ bn2, double *scal, SegMap sm) {
   cg::grid_group grid = cg::this_grid();
   const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  const int chunk = (n + nb - 1) / nb;
-  const int i0 = min(n, b * chunk), i1 = min(n, i0 + chunk);
-  const int k = j + 1;
+  sm.nctas = nb;
+  const SegCta me = seg_cta(sm, b, nb, n);
+  const int i0 = (int)me.i0, i1 = (int)me.i1;
+  const int k = j + 1, hst = sm.rmax + 2;
   __shared__ double red[8 * 16];
   __shared__ double hs[DD_CGS_MAXK + 8];
   // 1
   block_dots(i0, i1, k, V, ldv, w, true, partial + (int64_t)b * pk, red);
   grid.sync();
   // 2: hc1[0..k-1] and hc1[k] = ||w||^2 before orthogonalisation
-  column_sums(k + 1, nb, pk, partial, hc1, red, b, nb);
+  seg_column_sums(sm, k + 1, pk, partial, hc1, hst, red, b, nb);
   grid.sync();
   // 3
-  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc1[q];
+  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc1[(int64_t)me.s * hst + q];
   __syncthreads();
   for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] = row_update(i, k, V, ldv, hs, w[i]);
   __syncthreads();
   block_dots(i0, i1, k, V, ldv, w, false, partial + (int64_t)b * pk, red);
   grid.sync();
   // 4
-  column_sums(k, nb, pk, partial, hc2, red, b, nb);
+  seg_column_sums(sm, k, pk, partial, hc2, hst, red, b, nb);
   grid.sync();
   // 5
-  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc2[q];
+  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc2[(int64_t)me.s * hst + q];
   __syncthreads();
   {
     double nn = 0.0;
@@ -339,43 +378,154 @@ __global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
     }
   }
   grid.sync();
-  // 6
-  if (b == 0) {
-    column_sums(1, nb, pk, partial, hs + DD_CGS_MAXK, red, 0, 1);  // ||w||^2 after
+  // 6: CTA b takes systems b, b + nb, ...
+  for (int sys = b; sys < sm.nseg; sys += nb) {
+    if (sm.act && !sm.act[sys]) continue;
+    const double *h1 = hc1 + (int64_t)sys * hst, *h2 = hc2 + (int64_t)sys * hst;
+    double *Hs = H + (int64_t)sys * (sm.rmax + 1) * sm.rmax;
+    double *css = cs + (int64_t)sys * sm.rmax, *sns = sn + (int64_t)sys * sm.rmax;
+    double *gs = g + (int64_t)sys * (sm.rmax + 1), *scs = scal + (int64_t)sys * 4;
+    {
+      // ||w||^2 after, summed over the system's CTAs in order
+      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+      const int b0 = sm.nseg == 1 ? 0 : sm.seg_cta0[sys];
+      const int b1 = sm.nseg == 1 ? nb : sm.seg_cta0[sys + 1];
+      double t = 0.0;
+      for (int c = b0 + tid; c < b1; c += blockDim.x) t += partial[(int64_t)c * pk];
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[warp] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double u = 0.0;
+        for (int ww = 0; ww < nw; ++ww) u += red[ww];
+        hs[DD_CGS_MAXK] = u;
+      }
+      __syncthreads();
+    }
     // column j of H (passes 1 + 2) and the rotations, in shared memory
-    for (int q = tid; q <= j; q += blockDim.x) hs[q] = hc1[q] + hc2[q];
+    for (int q = tid; q <= j; q += blockDim.x) hs[q] = h1[q] + h2[q];
     __syncthreads();
     if (tid == 0) {
       const double hn = sqrt(hs[DD_CGS_MAXK]);
-      const double w0 = sqrt(hc1[k]);
+      const double w0 = sqrt(h1[k]);
       const bool breakdown = !(hn > 1e-14 * w0);
       hs[j + 1] = hn;
       for (int q = 0; q < j; ++q) {
-        const double a = hs[q], c2 = hs[q + 1], c = cs[q], sv = sn[q];
+        const double a = hs[q], c2 = hs[q + 1], c = css[q], sv = sns[q];
         hs[q] = c * a + sv * c2;
         hs[q + 1] = -sv * a + c * c2;
       }
       const double a = hs[j], c2 = hs[j + 1];
       const double r = hypot(a, c2);
-      cs[j] = a / r;
-      sn[j] = c2 / r;
+      css[j] = a / r;
+      sns[j] = c2 / r;
       hs[j] = r;
       hs[j + 1] = 0.0;
-      const double gj = g[j];
-      g[j + 1] = -sn[j] * gj;
-      g[j] = cs[j] * gj;
-      scal[0] = hn;
-      scal[1] = breakdown ? 1.0 : 0.0;
-      scal[2] = fabs(g[j + 1]) / bnorm;
+      const double gj = gs[j];
+      gs[j + 1] = -sns[j] * gj;
+      gs[j] = css[j] * gj;
+      scs[0] = hn;
+      scs[1] = breakdown ? 1.0 : 0.0;
+      scs[2] = fabs(gs[j + 1]) / sqrt(bn2[sys]);
     }
     __syncthreads();
-    for (int q = tid; q <= j + 1; q += blockDim.x) H[(int64_t)q * R + j] = hs[q];
+    for (int q = tid; q <= j + 1; q += blockDim.x) Hs[(int64_t)q * R + j] = hs[q];
+    __syncthreads();
   }
   grid.sync();
   // 7
-  if (scal[1] == 0.0) {
-    const double hn = scal[0];
+  if (me.act && scal[(int64_t)me.s * 4 + 1] == 0.0) {
+    const double hn = scal[(int64_t)me.s * 4];
     for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] /= hn;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched helpers: the same per-system quantities as the single-system
+// kernels above, over a SegMap.
+// ---------------------------------------------------------------------------
+// partial[b] = sum of v[i]^2 over CTA b's rows (every system, active or not)
+__global__ void seg_sumsq_kernel(int64_t n, const double *__restrict__ v, double *partial, SegMap sm) {
+  sm.act = nullptr;
+  sm.nctas = gridDim.x;
+  const SegCta me = seg_cta(sm, blockIdx.x, gridDim.x, n);
+  __shared__ double red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double t = 0.0;
+  for (int64_t i = me.i0 + tid; i < me.i1; i += blockDim.x) t += v[i] * v[i];
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) red[warp] = t;
+  __syncthreads();
+  if (tid == 0) {
+    double u = 0.0;
+    for (int ww = 0; ww < nw; ++ww) u += red[ww];
+    partial[blockIdx.x] = u;
+  }
+}
+
+// out[s] = sum of partial over system s's CTAs, in order (one CTA per system)
+__global__ void seg_reduce_kernel(const double *__restrict__ partial, double *out, SegMap sm) {
+  const int sys = blockIdx.x;
+  const int b0 = sm.seg_cta0[sys], b1 = sm.seg_cta0[sys + 1];
+  __shared__ double red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double t = 0.0;
+  for (int b = b0 + tid; b < b1; b += blockDim.x) t += partial[b];
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) red[warp] = t;
+  __syncthreads();
+  if (tid == 0) {
+    double u = 0.0;
+    for (int ww = 0; ww < nw; ++ww) u += red[ww];
+    out[sys] = u;
+  }
+}
+
+// start of a cycle for the active systems: v0 = r / ||r||, g = ||r|| e_0
+__global__ void seg_start_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__ nsq,
+                                 double *v0, double *g, SegMap sm) {
+  sm.nctas = gridDim.x;
+  const SegCta me = seg_cta(sm, blockIdx.x, gridDim.x, n);
+  if (me.act) {
+    const double nr = sqrt(nsq[me.s]);
+    for (int64_t i = me.i0 + threadIdx.x; i < me.i1; i += blockDim.x) v0[i] = r[i] / nr;
+  }
+  if (blockIdx.x == me.c0 && me.act)
+    for (int q = threadIdx.x; q <= sm.rmax; q += blockDim.x)
+      g[(int64_t)me.s * (sm.rmax + 1) + q] = (q == 0) ? sqrt(nsq[me.s]) : 0.0;
+}
+
+// y_s = H_s(0:jl,0:jl)^-1 g_s(0:jl) for every system with jl[s] >= 0
+__global__ void seg_hess_solve_kernel(int R, const int32_t *__restrict__ jl, const double *__restrict__ H,
+                                      const double *__restrict__ g, double *y, SegMap sm) {
+  const int sys = blockIdx.x;
+  const int jlast = jl[sys];
+  if (threadIdx.x != 0 || jlast < 0) return;
+  const double *Hs = H + (int64_t)sys * (sm.rmax + 1) * sm.rmax;
+  const double *gs = g + (int64_t)sys * (sm.rmax + 1);
+  double *ys = y + (int64_t)sys * (sm.rmax + 1);
+  for (int q = jlast; q >= 0; --q) {
+    double t = gs[q];
+    for (int c = q + 1; c <= jlast; ++c) t -= Hs[(int64_t)q * R + c] * ys[c];
+    ys[q] = t / Hs[(int64_t)q * R + q];
+  }
+}
+
+// x += Z y_s over the rows of every system with jl[s] >= 0
+__global__ void seg_update_x_kernel(int64_t n, const int32_t *__restrict__ jl, const double *__restrict__ y,
+                                    const double *__restrict__ Z, int64_t ldz, double *x, SegMap sm) {
+  sm.act = nullptr;
+  sm.nctas = gridDim.x;
+  const SegCta me = seg_cta(sm, blockIdx.x, gridDim.x, n);
+  const int k = jl[me.s] + 1;
+  if (k <= 0) return;
+  __shared__ double ys[DD_CGS_MAXK];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[(int64_t)me.s * (sm.rmax + 1) + q];
+  __syncthreads();
+  for (int64_t i = me.i0 + threadIdx.x; i < me.i1; i += blockDim.x) {
+    double t = x[i];
+    for (int q = 0; q < k; ++q) t += ys[q] * Z[(int64_t)q * ldz + i];
+    x[i] = t;
   }
 }
 
@@ -457,13 +607,35 @@ int cgs2_blocks(int cap) {
   return nb < cap ? nb : cap;
 }
 
-cudaError_t launch_cgs2(int n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
+cudaError_t launch_cgs2(int64_t n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
                         int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
-                        double bnorm, double *scal, int nblocks, cudaStream_t s) {
+                        const double *bn2, double *scal, const SegMap &sm, int nblocks, cudaStream_t s) {
+  SegMap m2 = sm;
   void *args[] = {&n, &j, &R, (void *)&V, &ldv, &w, &partial, &pk, &hc1, &hc2, &H, &cs, &sn, &g,
-                  &bnorm, &scal};
+                  (void *)&bn2, &scal, &m2};
   return cudaLaunchCooperativeKernel((const void *)cgs2_kernel, dim3(nblocks), dim3(DD_CGS_THREADS),
                                      args, 0, s);
+}
+
+cudaError_t launch_seg_norms(int64_t n, const double *v, double *partial, double *out, const SegMap &sm,
+                             int nblocks, cudaStream_t s) {
+  seg_sumsq_kernel<<<nblocks, 256, 0, s>>>(n, v, partial, sm);
+  seg_reduce_kernel<<<sm.nseg, 256, 0, s>>>(partial, out, sm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_start(int64_t n, const double *r, const double *nsq, double *v0, double *g,
+                             const SegMap &sm, int nblocks, cudaStream_t s) {
+  seg_start_kernel<<<nblocks, 256, 0, s>>>(n, r, nsq, v0, g, sm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_hess_update(int64_t n, int R, const int32_t *jl, const double *H, const double *g,
+                                   double *y, const double *Z, int64_t ldz, double *x, const SegMap &sm,
+                                   int nblocks, cudaStream_t s) {
+  seg_hess_solve_kernel<<<sm.nseg, 32, 0, s>>>(R, jl, H, g, y, sm);
+  seg_update_x_kernel<<<nblocks, 256, 0, s>>>(n, jl, y, Z, ldz, x, sm);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s) {

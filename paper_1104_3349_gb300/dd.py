@@ -75,12 +75,12 @@ class dd_partition(ctypes.Structure):
 
 class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("max_restart", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class dd_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("bad_block", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("relres_true", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("relres_true", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int32),
                 ("pad2", ctypes.c_int32)]
 
@@ -91,10 +91,13 @@ class dd_stats(ctypes.Structure):
                 ("max_agg", ctypes.c_int32), ("kl_max", ctypes.c_int32), ("ku_max", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("factor_bytes", ctypes.c_int64), ("factor_nonzeros", ctypes.c_int64),
                 ("schur_bytes", ctypes.c_int64), ("coupling_nnz", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("stage_bytes", ctypes.c_int32), ("sweep_grid", ctypes.c_int32),
+                ("sweep_slots", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tuned_us", ctypes.c_double),
+                ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
-EXPORTS = ["dd_setup", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve", "dd_spmv",
+EXPORTS = ["dd_setup", "dd_setup_batched", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve",
+           "gmres_solve_batched", "dd_spmv",
            "dd_get_stats", "dd_get_bad_block", "dd_destroy", "dd_last_error"]
 NOALLOC_MAX_ELEMS = 1 << 20
 
@@ -113,6 +116,12 @@ def load(path: str = LIB_PATH):
     lib.dd_setup.restype = ctypes.c_int
     lib.dd_setup.argtypes = [ctypes.POINTER(dd_csr), ctypes.POINTER(dd_partition), ctypes.c_int,
                              ctypes.POINTER(dd_opts), vp, ctypes.POINTER(vp)]
+    lib.dd_setup_batched.restype = ctypes.c_int
+    lib.dd_setup_batched.argtypes = [ctypes.c_int32, ctypes.POINTER(dd_csr), ctypes.POINTER(dd_partition),
+                                     ctypes.c_int, ctypes.POINTER(dd_opts), vp, ctypes.POINTER(vp)]
+    lib.gmres_solve_batched.restype = ctypes.c_int
+    lib.gmres_solve_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_double,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(dd_info), vp]
     lib.dd_apply.restype = ctypes.c_int
     lib.dd_apply.argtypes = [vp, vp, vp, vp]
     lib.gmres_solve.restype = ctypes.c_int
@@ -166,7 +175,8 @@ class DD:
     """One preconditioner B built by dd_setup; owns the library handle."""
 
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
-                 pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True):
+                 pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
+                 autotune=False):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -177,7 +187,7 @@ class DD:
         rp, col, val, pa, pe, ag = self._arrs
         csr = dd_csr(self.n, int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
         pt = dd_partition(int(m), _ptr(pa), _ptr(pe), int(sz), _ptr(ag), 0 if ag is None else len(ag) - 1)
-        o = dd_opts(int(prec), float(pivot_tol), 0, int(max_restart))
+        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)))
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
         h = ctypes.c_void_p()
         rc = lib.dd_setup(ctypes.byref(csr), ctypes.byref(pt), k, ctypes.byref(o), _stream_handle(stream),
@@ -242,4 +252,83 @@ class DD:
     def stats(self):
         s = dd_stats()
         self._check(self._lib.dd_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in dd_stats._fields_}
+
+
+class DDBatch:
+    """A batch of independent systems behind one handle (dd_setup_batched)."""
+
+    def __init__(self, systems, kind="msce_inf", prec=DD_FP64, pivot_tol=0.0, max_restart=50, stream=None,
+                 use_graph=False, autotune=False):
+        """systems: list of (A, part, m, perm, agg_offsets) with A a CSR (perm, agg_offsets may be None)."""
+        lib = load()
+        self._lib = lib
+        self.count = len(systems)
+        self.sizes = [int(sy[0].n) for sy in systems]
+        self._arrs = []
+        csrs = (dd_csr * self.count)()
+        pts = (dd_partition * self.count)()
+        for q, (A, part, m, perm, agg) in enumerate(systems):
+            arrs = [np.ascontiguousarray(A.rowptr, np.int32), np.ascontiguousarray(A.col, np.int32),
+                    np.ascontiguousarray(A.val, np.float64), np.ascontiguousarray(part, np.int32),
+                    None if perm is None else np.ascontiguousarray(perm, np.int32),
+                    None if agg is None else np.ascontiguousarray(agg, np.int32)]
+            self._arrs.append(arrs)
+            rp, col, val, pa, pe, ag = arrs
+            csrs[q] = dd_csr(int(A.n), int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
+            pts[q] = dd_partition(int(m), _ptr(pa), _ptr(pe), 64, _ptr(ag), 0 if ag is None else len(ag) - 1)
+        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)))
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        h = ctypes.c_void_p()
+        rc = lib.dd_setup_batched(self.count, csrs, pts, k, ctypes.byref(o), _stream_handle(stream), ctypes.byref(h))
+        self._h = h
+        self.n = sum(self.sizes)
+        if rc != 0:
+            msg = lib.dd_last_error(h if h.value else None).decode()
+            bad = int(lib.dd_get_bad_block(h)) if h.value else -1
+            self.close()
+            raise DDError(rc, msg, bad)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, y, x, stream=None):
+        """x = B^-1 y on the concatenated vector (every system's block)."""
+        rc = self._lib.dd_apply(self._h, _dev_ptr(y, self.n), _dev_ptr(x, self.n), _stream_handle(stream))
+        if rc != 0:
+            raise DDError(rc, self._lib.dd_last_error(self._h).decode())
+
+    def gmres(self, bs, xs, tol=1e-8, restart=30, maxit=3000, history_cap=4096, stream=None):
+        """Independent FGMRES solves; bs, xs: lists of device tensors. Returns (status, [per-system dicts])."""
+        if len(bs) != self.count or len(xs) != self.count:
+            raise ValueError("one right-hand side and one solution per system")
+        bp = (ctypes.c_void_p * self.count)(*[_dev_ptr(b, n).value for b, n in zip(bs, self.sizes)])
+        xp = (ctypes.c_void_p * self.count)(*[_dev_ptr(x, n).value for x, n in zip(xs, self.sizes)])
+        infos = (dd_info * self.count)()
+        hists = [np.zeros(history_cap) for _ in range(self.count)]
+        for q in range(self.count):
+            infos[q].history = hists[q].ctypes.data_as(ctypes.c_void_p).value
+            infos[q].history_cap = history_cap
+        rc = self._lib.gmres_solve_batched(self._h, bp, xp, float(tol), int(restart), int(maxit), infos,
+                                           _stream_handle(stream))
+        if rc not in (0, 5, 6):
+            raise DDError(rc, self._lib.dd_last_error(self._h).decode())
+        out = [dict(status=int(i.status), iters=int(i.iters), restarts=int(i.restarts), relres=float(i.relres_true),
+                    solve_ms=float(i.solve_ms), setup_ms=float(i.setup_ms),
+                    history=h[:min(i.iters, history_cap)].copy()) for i, h in zip(infos, hists)]
+        return int(rc), out
+
+    def stats(self):
+        s = dd_stats()
+        rc = self._lib.dd_get_stats(self._h, ctypes.byref(s))
+        if rc != 0:
+            raise DDError(rc, "dd_get_stats")
         return {f: getattr(s, f) for f, _ in dd_stats._fields_}

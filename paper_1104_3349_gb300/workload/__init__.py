@@ -242,6 +242,28 @@ def batch64_specs(count: int = 64, seed: int = 4000):
     return out
 
 
+def batch_workloads(specs, sz: int = 64, rhs_seed: int = 0):
+    """One uniform-grid Fourier-wind Oseen workload per spec (grid, nu, m, wind_seed)."""
+    return [make_workload(f"oseen_mac_{s['grid']}x{s['grid']}_nu{s['nu']:.2e}_m{s['m']}", s["grid"], s["nu"], 1.0,
+                          WIND_FOURIER, s["wind_seed"], s["m"], rhs_seed=rhs_seed, sz=sz) for s in specs]
+
+
+def batch64(sz: int = 2048):
+    """The 64-system batch: sides in {64,...,256}, nu log-uniform in [1e-3, 1e-2], 16-64 subdomains each."""
+    return batch_workloads(batch64_specs(), sz=sz)
+
+
+def batch_small(count: int = 48, seed: int = 4100):
+    """A small batch with many tiny subdomains: 16x16-32x32 grids split into 16-64 subdomains each."""
+    u = uniform(seed, 2 * count, 0.0, 1.0).reshape(count, 2)
+    out = []
+    for i in range(count):
+        grid = [16, 24, 32][min(int(u[i, 0] * 3), 2)]
+        m = [16, 32, 64][min(int(u[i, 1] * 3), 2)] if i else 64
+        out.append(dict(grid=grid, nu=10.0 ** (-3.0 + u[i, 1]), m=m, wind_seed=seed + i))
+    return batch_workloads(out, sz=64)
+
+
 def stretched1024() -> Workload:
     """1024x1024 MAC Oseen with wall stretching of max aspect 100, nu=1e-3, 1024 subdomains."""
     r = 100.0 ** (1.0 / 511.0)
