@@ -71,6 +71,9 @@ struct DDHandle {
   int32_t *cta_seg = nullptr, *seg_cta0 = nullptr, *d_act = nullptr, *d_jl = nullptr;
   int64_t *seg_row0 = nullptr;
   int32_t *h_act = nullptr;  // pinned: act then jl, nseg each
+  std::vector<int32_t> sub_sys_h, agg_sys_h;  // system of every subdomain / aggregate
+  int32_t *sub_sys = nullptr, *agg_sys = nullptr;
+  bool masked = false;       // the apply skips systems that have stopped stepping
   double *bcat = nullptr, *xcat = nullptr, *bn2 = nullptr, *rn2 = nullptr;
   // CUDA graphs of the Arnoldi steps (use_graph), one per step index
   int use_graph = 0, graph_key = -1;
@@ -568,9 +571,12 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
       max_tile = std::max(max_tile, std::max((size_t)wl[t] * DD_NB * sizeof(T) + (size_t)round4(wl[t]) * 4,
                                              (size_t)DD_NB * wu[t] * sizeof(T)));
     }
-    // stage: ~84 KiB, or one whole tile when a tile is larger
+    // stage: ~84 KiB, or one whole tile when a tile is larger; smaller when
+    // two such stages do not fit beside the resident vectors
     size_t stage = std::max<size_t>(84 * 1024, max_tile);
     stage = (stage + 127) & ~(size_t)127;
+    const size_t smax = band_sweep_max_stage(h->max_n, h->max_kl, h->max_ku2, sizeof(T));
+    if (stage > smax) stage = std::max((max_tile + 127) & ~(size_t)127, smax);
     h->max_tile = max_tile;
     h->h_info = info;
     h->h_tm = tm;
@@ -795,14 +801,22 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
 template <typename T>
 dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int part = -1) {
   PrecBufs<T> &B = bufs<T>(h);
+  SweepPlan pl = h->plan;
+  const int32_t *agg_sys = nullptr, *act = nullptr;
+  if (h->masked) {
+    pl.task_sys = h->sub_sys;
+    pl.act = h->d_act;
+    agg_sys = h->agg_sys;
+    act = h->d_act;
+  }
   if (part == 0 || part < 0)
-  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, pl,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, B.z1, h->st, s));
   if (part == 1 || part < 0)
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
-                           B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, B.t, h->nG, x, s));
+                           B.f_val, y, h->d_perm + h->nI, B.z1, B.z2, B.t, h->nG, x, agg_sys, act, s));
   if (part == 2 || part < 0)
-  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, pl,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
                               B.z2, B.z1, h->d_perm, x, h->st, s));
   return DD_OK;
@@ -878,6 +892,12 @@ dd_status alloc_krylov(DDHandle *h, int R) {
     TRY(upload(h, &h->seg_row0, h->seg_row0_h));
     TRY(dalloc(h, &h->d_act, S));
     TRY(dalloc(h, &h->d_jl, S));
+    TRY(upload(h, &h->sub_sys, h->sub_sys_h));
+    TRY(upload(h, &h->agg_sys, h->agg_sys_h));
+    if ((int)h->agg_sys_h.size() != h->nagg || (int)h->sub_sys_h.size() != h->m) {
+      h->err = "batch maps do not match the subdomains and aggregates";
+      return DD_ERR_INVALID_ARG;
+    }
     TRY(dalloc(h, &h->bcat, (size_t)h->n));
     TRY(dalloc(h, &h->xcat, (size_t)h->n));
     TRY(dalloc(h, &h->bn2, S));
@@ -1052,6 +1072,12 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
   const int S = h->nseg, nc = h->seg_ctas;
   const int64_t n = h->n;
   const SegMap sm = batch_map(h);
+  // the apply skips the subdomains and aggregates of systems not stepping
+  struct Mask {
+    DDHandle *h;
+    explicit Mask(DDHandle *hh) : h(hh) { h->masked = true; }
+    ~Mask() { h->masked = false; }
+  } mask(h);
   SegMap all = sm;
   all.act = nullptr;
   for (int q = 0; q < S; ++q) {
@@ -1201,7 +1227,8 @@ dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scrat
   CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st, s));
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
-                           B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, s));
+                           B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, nullptr,
+                           nullptr, s));
   CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
                               z2, z1, h->d_perm, x, h->st, s));
@@ -1354,7 +1381,7 @@ dd_status finish_setup(DDHandle *h, dd_status rc, void **handle) {
 // q-1; interiors renumbered after the previous systems' subdomains, the
 // interface of every system after all interiors, aggregates per system.
 struct BatchInput {
-  std::vector<int32_t> rowptr, col, partv, perm, agg;
+  std::vector<int32_t> rowptr, col, partv, perm, agg, sub_sys, agg_sys;
   std::vector<double> val;
   std::vector<int64_t> row0;
   dd_csr csr{};
@@ -1444,6 +1471,8 @@ dd_status concat_batch(int count, const dd_csr *csrs, const dd_partition *pts, d
       }
     }
     moff += p.m;
+    for (int j = 0; j < p.m; ++j) bi.sub_sys.push_back(q);
+    while ((int)bi.agg_sys.size() < (int)bi.agg.size() - 1) bi.agg_sys.push_back(q);
   }
   bi.perm = inter;
   bi.perm.insert(bi.perm.end(), iface.begin(), iface.end());
@@ -1552,6 +1581,8 @@ dd_status dd_setup_batched(int32_t count, const dd_csr *csrs, const dd_partition
   h->stream = static_cast<cudaStream_t>(stream);
   h->nseg = count;
   h->seg_row0_h = bi.row0;
+  h->sub_sys_h = bi.sub_sys;
+  h->agg_sys_h = bi.agg_sys;
   const dd_status rc = setup_handle(h, &bi.csr, &bi.pt, approx, opts);
   return finish_setup(h, rc, handle);
 }

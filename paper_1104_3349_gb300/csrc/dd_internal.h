@@ -75,6 +75,10 @@ struct SweepPlan {
   int grid = 0;
   const int32_t *sched = nullptr;
   const int32_t *sched_off = nullptr;
+  // batched solves: subdomain j is skipped while act[task_sys[j]] == 0 (its
+  // system has stopped stepping); null: every subdomain
+  const int32_t *task_sys = nullptr;
+  const int32_t *act = nullptr;
 };
 
 // Device-side error word: first failure wins.
@@ -91,6 +95,8 @@ struct Workspace;  // defined in dd_api.cu
 // the resident right-hand side (0: the subdomain is too large).
 int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
                       uint32_t stage_bytes);
+// largest stage size that leaves room for two stages (0: the vectors alone do not fit)
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size);
 // Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
 // column-major, exchanged), wscratch holds the windows when they do not fit
 // in shared memory (band_lu_window_bytes per subdomain, else unused).
@@ -179,7 +185,8 @@ template <typename T>
 cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
                                const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
                                const T *f_val, const double *y, const int32_t *perm_iface,
-                               const T *z1, T *z2, T *t, int ng, double *x, cudaStream_t s);
+                               const T *z1, T *z2, T *t, int ng, double *x, const int32_t *agg_sys,
+                               const int32_t *act, cudaStream_t s);
 
 // Krylov (k_krylov.cu), FP64
 cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,

@@ -640,7 +640,9 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
                                       const int32_t *__restrict__ srcs, const double *__restrict__ y,
                                       const int32_t *__restrict__ perm, T *z,
                                       const int32_t *__restrict__ sched,
-                                      const int32_t *__restrict__ sched_off, DevStatus *st) {
+                                      const int32_t *__restrict__ sched_off,
+                                      const int32_t *__restrict__ task_sys,
+                                      const int32_t *__restrict__ act, DevStatus *st) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -653,7 +655,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
   for (int it = t0; it < t1; ++it) {
     const int task = sched ? sched[it] : it;
     const BandInfo bg = info[task];
-    if (bg.n == 0) continue;
+    if (bg.n == 0 || (act && !act[task_sys[task]])) continue;  // empty, or its system is done
     __syncthreads();  // the previous task's reads of the tables and vectors are done
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     const int ntot = b.ntiles * DD_NB + pad;
@@ -682,7 +684,9 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       const T *__restrict__ e_val, const T *__restrict__ z2,
                                       const T *__restrict__ z1, const int32_t *__restrict__ perm,
                                       double *x, const int32_t *__restrict__ sched,
-                                      const int32_t *__restrict__ sched_off, DevStatus *st) {
+                                      const int32_t *__restrict__ sched_off,
+                                      const int32_t *__restrict__ task_sys,
+                                      const int32_t *__restrict__ act, DevStatus *st) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -695,7 +699,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
   for (int it = t0; it < t1; ++it) {
     const int task = sched ? sched[it] : it;
     const BandInfo bg = info[task];
-    if (bg.n == 0) continue;
+    if (bg.n == 0 || (act && !act[task_sys[task]])) continue;
     __syncthreads();
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     const int ntot = b.ntiles * DD_NB + pad;
@@ -815,6 +819,15 @@ int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_
 }
 
 #define DD_LU_SMEM (200 * 1024)
+// largest ring stage (multiple of 128 bytes) that still leaves room for two
+// stages next to the resident vectors and tables; 0 if none does
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size) {
+  const size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, max_n / DD_NB,
+                                       2 * (max_n / DD_NB));
+  if (base >= DD_SMEM_LIMIT) return 0;
+  return ((DD_SMEM_LIMIT - base) / 2) & ~(size_t)127;
+}
+
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
   const int R = DD_NB + max_kl, Cw = DD_NB + max_kl + max_ku;
   return (size_t)R * (size_t)(Cw | 1) * elem_size;
@@ -884,7 +897,8 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
   if (grid <= 0) return cudaSuccess;
   band_solve_fwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
                                                           pl.stage_bytes, tm, jobs, ltile, utile, src,
-                                                          y, perm, z, pl.sched, pl.sched_off, st);
+                                                          y, perm, z, pl.sched, pl.sched_off,
+                                                          pl.task_sys, pl.act, st);
   return cudaGetLastError();
 }
 
@@ -906,7 +920,8 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
   band_solve_bwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
                                                           pl.stage_bytes, tm, jobs, ltile, utile, src,
                                                           e_ptr, e_col, e_val, z2, z1, perm, x,
-                                                          pl.sched, pl.sched_off, st);
+                                                          pl.sched, pl.sched_off, pl.task_sys, pl.act,
+                                                          st);
   return cudaGetLastError();
 }
 

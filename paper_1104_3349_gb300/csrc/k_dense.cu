@@ -475,8 +475,10 @@ __global__ void schur_rhs_kernel(int ng, const int32_t *__restrict__ f_ptr, cons
 template <typename T>
 __global__ void schur_gemv_kernel(const int32_t *__restrict__ agg_off, const int64_t *__restrict__ s_off,
                                   const T *__restrict__ Sinv, const T *__restrict__ t,
-                                  const int32_t *__restrict__ perm_iface, T *z2, double *x) {
+                                  const int32_t *__restrict__ perm_iface, T *z2, double *x,
+                                  const int32_t *__restrict__ agg_sys, const int32_t *__restrict__ act) {
   const int a = blockIdx.y;
+  if (act && !act[agg_sys[a]]) return;  // a batched system that has stopped stepping
   const int g0 = agg_off[a], p = agg_off[a + 1] - g0;
   const int rbase = blockIdx.x * DD_SROWS;
   if (rbase >= p) return;
@@ -615,7 +617,8 @@ template <typename T>
 cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *s_off, int pmax,
                                const T *Sinv, const int32_t *f_ptr, const int32_t *f_col,
                                const T *f_val, const double *y, const int32_t *perm_iface,
-                               const T *z1, T *z2, T *t, int ng, double *x, cudaStream_t s) {
+                               const T *z1, T *z2, T *t, int ng, double *x, const int32_t *agg_sys,
+                               const int32_t *act, cudaStream_t s) {
   if (nagg <= 0) return cudaSuccess;
   schur_rhs_kernel<T><<<(ng + 255) / 256, 256, 0, s>>>(ng, f_ptr, f_col, f_val, y, perm_iface, z1, t);
   size_t smem = sizeof(T) * (size_t)pmax;
@@ -625,7 +628,7 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
     if (e != cudaSuccess) return e;
   }
   dim3 grid((pmax + DD_SROWS - 1) / DD_SROWS, nagg);
-  schur_gemv_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, t, perm_iface, z2, x);
+  schur_gemv_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, t, perm_iface, z2, x, agg_sys, act);
   return cudaGetLastError();
 }
 
@@ -648,7 +651,8 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
   template cudaError_t launch_schur_apply<T>(int, const int32_t *, const int64_t *, int, const T *, \
                                              const int32_t *, const int32_t *, const T *,          \
                                              const double *, const int32_t *, const T *, T *, T *, \
-                                             int, double *, cudaStream_t);
+                                             int, double *, const int32_t *, const int32_t *,      \
+                                             cudaStream_t);
 
 DD_INST_DENSE(double)
 DD_INST_DENSE(float)
