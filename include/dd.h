@@ -54,7 +54,11 @@ typedef enum {
   DD_MSCN = 2,     /* G_ii - F_ii D_ii^-1 E_ii, principal blocks with the same
                       local index range (Algorithm 1, MSCN)                    */
   DD_MSCNR = 3,    /* G_ii - diag(F_ii D_ii^-1 E_ii 1) (Algorithm 1, MSCNR)     */
-  DD_LUM = 4       /* G_ii (Definition of LUM)                                  */
+  DD_LUM = 4,      /* G_ii (Definition of LUM)                                  */
+  DD_LEARNED = 5   /* G_ii + a learned correction on the pattern of G_ii and of
+                      (F E)(R_i, R_i); an aggregate whose learned block fails
+                      the pivot test takes its MSCE_INF block instead.  Not in
+                      the paper: an extension of LUM (see dd_mlp_*)           */
 } dd_approx;
 
 typedef enum {
@@ -99,6 +103,8 @@ typedef struct {
                          candidate ring-stage size (and with it CTAs per SM)
                          and keeps the fastest; 0: the fixed default           */
   int32_t reserved[3];
+  const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
+                              (format under dd_mlp_*); ignored otherwise       */
 } dd_opts;
 
 typedef struct {
@@ -133,6 +139,9 @@ typedef struct {
   double tuned_us;           /* fastest forward + backward sweep it measured     */
   int32_t batch;             /* independent systems behind the handle (>= 1)     */
   int32_t graphs;            /* CUDA graphs instantiated so far                  */
+  int64_t learned_entries;   /* DD_LEARNED: entries of the learned patterns      */
+  int32_t learned_fallback;  /* DD_LEARNED: aggregates that took MSCE_INF         */
+  int32_t pad3;
 } dd_stats;
 
 /*
@@ -252,6 +261,69 @@ dd_status dd_destroy(void *handle);
 
 /* One-line description of the last error (handle NULL: last dd_setup). */
 const char *dd_last_error(void *handle);
+
+/* ------------------------------------------------------------------------
+ * The learned Schur correction (DD_LEARNED).  Not in the paper.
+ *
+ * For an aggregate R_i (Section 3.2) the learned block is
+ *   S_L(R_i, R_i) = G(R_i, R_i) + Delta,
+ * where Delta is nonzero only on P_i = {(r, c) in R_i x R_i : G(r, c) != 0,
+ * or F(r, k) E(k, c) != 0 for some interior k, or r == c}.  On each entry,
+ * Delta(r, c) = out_scale * MLP((x(r, c) - mean) / std).  The MLP is
+ * 14 -> 64 (ReLU) -> 1; its inputs and weights are rounded to BF16 and it
+ * accumulates in FP32.  The 14 features of (r, c), with d_k = D(k, k) and
+ * Dinv_k = 1 / d_k where d_k != 0 (else 0):
+ *   G(r,c), G(c,r), (F E)(r,c), (F Dinv E)(r,c), [r==c], [G(r,r)==0],
+ *   [G(c,c)==0], G(r,r), G(c,c), sum_k |F(r,k)|, sum_k |E(k,c)|,
+ *   #{k: F(r,k)!=0}/8, #{k: E(k,c)!=0}/8, (F Dinv E)(r,r).
+ * The network is trained to the MSCE_INF correction S_ii - G_ii on P_i.
+ * Parameters: DD_MLP_NPARAM floats, W1 (64 x 14, row-major), b1 (64),
+ * w2 (64), b2.
+ *
+ * Weight file (little-endian): "DDMLPW01" | u32 version 1 | u32 14 | u32 64 |
+ * f32 out_scale | f32 mean[14] | f32 std[14] | f32 params[1025] |
+ * f32 adam_m[1025] | f32 adam_v[1025] | i64 step | u64 FNV-1a of all the
+ * bytes before it.  dd_setup rejects a file with a wrong header or hash
+ * (DD_ERR_INVALID_ARG).
+ *
+ * Training runs on the device, on a data set held by a training handle.
+ * Row e of the data set is x_e (DD_MLP_IN normalised features, stored as
+ * BF16) with target y_e (FP32, already divided by out_scale).  The loss is
+ * the mean of (MLP(x_e) - y_e)^2 over a row range.  Its gradient is summed
+ * in a fixed order, so a training run is reproducible bit for bit.
+ * ---------------------------------------------------------------------- */
+#define DD_MLP_IN 14
+#define DD_MLP_HIDDEN 64
+#define DD_MLP_NPARAM (DD_MLP_HIDDEN * DD_MLP_IN + 2 * DD_MLP_HIDDEN + 1)
+
+/* New training handle holding a copy of params (host, DD_MLP_NPARAM FP32
+ * master weights); Adam state zero. */
+dd_status dd_mlp_create(const float *params, void **mlp);
+/* Upload the data set: X host, n x DD_MLP_IN (row-major, normalised), y host,
+ * n targets.  Replaces any previous data set. */
+dd_status dd_mlp_set_data(void *mlp, const float *X, const float *y, int64_t n, void *stream);
+/* Mean loss over rows [lo, hi) at the current weights and, if grad is not
+ * NULL, its gradient (host, DD_MLP_NPARAM).  Synchronises the stream. */
+dd_status dd_mlp_loss_grad(void *mlp, int64_t lo, int64_t hi, double *loss, float *grad, void *stream);
+/* One Adam step (bias-corrected) on the gradient of rows [lo, hi); the
+ * device keeps FP32 master weights and their BF16 copy.  Asynchronous. */
+dd_status dd_mlp_adam_step(void *mlp, int64_t lo, int64_t hi, float lr, float beta1, float beta2,
+                           float eps, void *stream);
+/* MLP outputs of rows [lo, hi) into out (host, hi - lo floats). */
+dd_status dd_mlp_predict(void *mlp, int64_t lo, int64_t hi, float *out, void *stream);
+/* Master weights, Adam moments and step count (host arrays may be NULL). */
+dd_status dd_mlp_get(void *mlp, float *params, float *adam_m, float *adam_v, int64_t *step);
+/* Resume: set the Adam moments and step count (host). */
+dd_status dd_mlp_set_adam(void *mlp, const float *adam_m, const float *adam_v, int64_t step);
+dd_status dd_mlp_destroy(void *mlp);
+
+/* The raw features of a DD_LEARNED handle's entries, in order of aggregate,
+ * then local row, then local column: ents (host, 3 per entry: aggregate,
+ * r, c), feats (host, DD_MLP_IN doubles per entry), delta (host, the Delta
+ * value added per entry); each array may be NULL; at most cap entries are
+ * written; *count receives the number of entries. */
+dd_status dd_learned_entries(void *handle, int32_t *ents, double *feats, float *delta, int64_t cap,
+                             int64_t *count);
 
 #ifdef __cplusplus
 }

@@ -62,6 +62,8 @@ def _load():
         lib.orc_bandwidths.argtypes = [vp, i32p]
         lib.orc_schur_block.restype = ctypes.c_int
         lib.orc_schur_block.argtypes = [vp, ctypes.c_int32, f64p]
+        lib.orc_replace_block.restype = ctypes.c_int
+        lib.orc_replace_block.argtypes = [vp, ctypes.c_int32, f64p, ctypes.c_double]
         lib.orc_bad_block.restype = ctypes.c_int32
         lib.orc_bad_block.argtypes = [vp]
         lib.orc_dense_lu.restype = ctypes.c_int
@@ -193,6 +195,14 @@ class OracleDD:
         if self._lib.orc_schur_block(self._h, i, _p(o, ctypes.c_double)) != 0:
             raise IndexError(i)
         return o
+
+    def replace_block(self, i, blk, pivtol=1e-14):
+        """Use blk as S_hat block i if its LU passes the pivot test; returns whether it did."""
+        blk = np.ascontiguousarray(blk, np.float64)
+        rc = self._lib.orc_replace_block(self._h, int(i), _p(blk, ctypes.c_double), float(pivtol))
+        if rc not in (0, 4):
+            raise OracleError(rc)
+        return rc == 0
 
     def apply(self, y):
         y = np.ascontiguousarray(y, np.float64)

@@ -613,6 +613,25 @@ void orc_bandwidths(const orc *h, int32_t *o) {
   for (int32_t j = 0; j < h->m; ++j) { o[2 * j] = h->A[j].kl; o[2 * j + 1] = h->A[j].ku; }
 }
 
+/* Replace S_hat block i by blk (row-major, p x p) when blk passes the pivot
+ * test of its LU; otherwise keep the block it had (the fallback of the
+ * learned approximation) and return ORC_SINGULAR_SCHUR. */
+int orc_replace_block(orc *h, int32_t i, const double *blk, double pivtol) {
+  if (!h->S || i < 0 || i >= h->nagg || !h->S[i] || h->kind == -2) return ORC_INVALID_ARG;
+  int32_t p = h->agg[i + 1] - h->agg[i];
+  double *lu = (double *)malloc(sizeof(double) * (size_t)p * p);
+  int32_t *piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)p);
+  if (!lu || !piv) { free(lu); free(piv); return ORC_OOM; }
+  memcpy(lu, blk, sizeof(double) * (size_t)p * p);
+  if (orc_dense_lu(p, lu, piv, pivtol)) { free(lu); free(piv); return ORC_SINGULAR_SCHUR; }
+  memcpy(h->S[i], blk, sizeof(double) * (size_t)p * p);
+  free(h->Slu[i]);
+  free(h->Spiv[i]);
+  h->Slu[i] = lu;
+  h->Spiv[i] = piv;
+  return ORC_OK;
+}
+
 /* copy S_hat block i (row-major, unfactored) */
 int orc_schur_block(const orc *h, int32_t i, double *o) {
   if (!h->S || i < 0 || i >= h->nagg || !h->S[i]) return -1;

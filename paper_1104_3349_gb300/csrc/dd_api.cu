@@ -74,6 +74,12 @@ struct DDHandle {
   std::vector<int32_t> sub_sys_h, agg_sys_h;  // system of every subdomain / aggregate
   int32_t *sub_sys = nullptr, *agg_sys = nullptr;
   bool masked = false;       // the apply skips systems that have stopped stepping
+  // DD_LEARNED: the network and its entries
+  std::string mlp_path;
+  std::vector<int32_t> l_ents;  // 3 per entry
+  double *l_feat = nullptr;
+  float *l_delta = nullptr;
+  DevStatus *st_probe = nullptr;  // status word of the first (learned) inversion
   double *bcat = nullptr, *xcat = nullptr, *bn2 = nullptr, *rn2 = nullptr;
   // CUDA graphs of the Arnoldi steps (use_graph), one per step index
   int use_graph = 0, graph_key = -1;
@@ -467,6 +473,213 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage) {
   return DD_OK;
 }
 
+// The network's weight file (format in dd.h): header, FNV-1a hash, then
+// out_scale, the feature normalisation and the FP32 master parameters.
+struct MlpFile {
+  float out_scale = 1.f;
+  float mean[DD_MLP_IN], stdv[DD_MLP_IN];
+  std::vector<float> params;
+};
+
+bool read_mlp_file(const std::string &path, MlpFile &w, std::string &err) {
+  FILE *f = fopen(path.c_str(), "rb");
+  if (!f) { err = "cannot open the weight file " + path; return false; }
+  std::vector<unsigned char> raw;
+  unsigned char buf[65536];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) raw.insert(raw.end(), buf, buf + k);
+  fclose(f);
+  const size_t want = 8 + 12 + 4 + 8 * DD_MLP_IN + 12 * (size_t)DD_MLP_NPARAM + 8 + 8;
+  if (raw.size() != want) { err = "weight file has the wrong size"; return false; }
+  uint64_t hsh = 0xCBF29CE484222325ull;
+  for (size_t i = 0; i + 8 < raw.size(); ++i) { hsh ^= raw[i]; hsh *= 0x100000001B3ull; }
+  uint64_t stored = 0;
+  for (int i = 7; i >= 0; --i) stored = (stored << 8) | raw[raw.size() - 8 + i];
+  if (stored != hsh) { err = "weight file checksum mismatch"; return false; }
+  if (memcmp(raw.data(), "DDMLPW01", 8) != 0) { err = "not a weight file"; return false; }
+  auto u32 = [&](size_t o) { uint32_t v; memcpy(&v, raw.data() + o, 4); return v; };
+  if (u32(8) != 1 || u32(12) != DD_MLP_IN || u32(16) != DD_MLP_HIDDEN) {
+    err = "unsupported weight file version or shape";
+    return false;
+  }
+  size_t o = 20;
+  memcpy(&w.out_scale, raw.data() + o, 4); o += 4;
+  memcpy(w.mean, raw.data() + o, 4 * DD_MLP_IN); o += 4 * DD_MLP_IN;
+  memcpy(w.stdv, raw.data() + o, 4 * DD_MLP_IN); o += 4 * DD_MLP_IN;
+  w.params.resize(DD_MLP_NPARAM);
+  memcpy(w.params.data(), raw.data() + o, 4 * (size_t)DD_MLP_NPARAM);
+  for (int i = 0; i < DD_MLP_IN; ++i)
+    if (!(w.stdv[i] > 0.f) || !isfinite(w.mean[i])) { err = "weight file: invalid normalisation"; return false; }
+  for (float v : w.params)
+    if (!isfinite(v)) { err = "weight file: non-finite parameter"; return false; }
+  return true;
+}
+
+// BF16 value of v (round to nearest even), as a float
+float bf16_round(float v) {
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return v;  // inf / nan kept
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+// DD_LEARNED blocks: G_ii + Delta on the patterns, inverted; a block whose
+// inversion fails the pivot test takes its MSCE_INF block (built and
+// inverted only when some block fails).
+template <typename T, typename Msce>
+dd_status learned_blocks(DDHandle *h, const dd_csr *csr, HostBlocks &hb, const std::vector<int32_t> &agg_of,
+                         const std::vector<int32_t> &p, const std::vector<int64_t> &soff,
+                         const std::vector<int64_t> &poff, double pivtol, Msce &msce_into,
+                         const int64_t *d_gidx, const double *d_gval, int64_t gcount) {
+  PrecBufs<T> &B = bufs<T>(h);
+  cudaStream_t s = h->stream;
+  const int nI = h->nI, nG = h->nG, nagg = h->nagg;
+  MlpFile w;
+  std::string err;
+  if (!read_mlp_file(h->mlp_path, w, err)) { h->err = err; return DD_ERR_INVALID_ARG; }
+  // the patterns P_a: G entries, the structure of F E, and the diagonal
+  std::vector<int32_t> ents;
+  {
+    std::vector<int32_t> cols;
+    for (int a = 0; a < nagg; ++a) {
+      const int g0 = hb.agg[a], g1 = hb.agg[a + 1];
+      for (int r = g0; r < g1; ++r) {
+        cols.clear();
+        cols.push_back(r);
+        const int o = hb.perm[nI + r];
+        for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
+          const int c = hb.pos[csr->col[k]] - nI;
+          if (c >= g0 && c < g1 && csr->val[k] != 0.0) cols.push_back(c);
+        }
+        for (int q = hb.f_ptr[r]; q < hb.f_ptr[r + 1]; ++q) {
+          if (hb.f_val[q] == 0.0) continue;
+          const int kk = hb.f_col[q];
+          for (int e = hb.e_ptr[kk]; e < hb.e_ptr[kk + 1]; ++e) {
+            const int c = hb.e_col[e];
+            if (c >= g0 && c < g1 && hb.e_val[e] != 0.0) cols.push_back(c);
+          }
+        }
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        for (int c : cols) { ents.push_back(a); ents.push_back(r - g0); ents.push_back(c - g0); }
+      }
+    }
+  }
+  const int64_t ne = (int64_t)ents.size() / 3;
+  h->l_ents = ents;
+  h->stats.learned_entries = ne;
+  // E^T (values per interface column), 1 / diag(D)
+  std::vector<int32_t> et_ptr(nG + 1, 0);
+  for (int k = 0; k < nI; ++k)
+    for (int e = hb.e_ptr[k]; e < hb.e_ptr[k + 1]; ++e) et_ptr[hb.e_col[e] + 1]++;
+  for (int g = 0; g < nG; ++g) et_ptr[g + 1] += et_ptr[g];
+  std::vector<double> et_val(et_ptr[nG]);
+  {
+    std::vector<int32_t> fill(et_ptr.begin(), et_ptr.end() - 1);
+    for (int k = 0; k < nI; ++k)
+      for (int e = hb.e_ptr[k]; e < hb.e_ptr[k + 1]; ++e) et_val[fill[hb.e_col[e]]++] = hb.e_val[e];
+  }
+  std::vector<double> dinv(std::max(nI, 1), 0.0);
+  for (int k = 0; k < nI; ++k) {
+    const int o = hb.perm[k];
+    double d = 0.0;
+    for (int64_t q = csr->rowptr[o]; q < csr->rowptr[o + 1]; ++q)
+      if (csr->col[q] == o) d = csr->val[q];
+    dinv[k] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+  std::vector<float> wbf(DD_MLP_NPARAM);
+  for (int q = 0; q < DD_MLP_NPARAM; ++q) wbf[q] = bf16_round(w.params[q]);
+  std::vector<float> mean(w.mean, w.mean + DD_MLP_IN), stdv(w.stdv, w.stdv + DD_MLP_IN);
+  LearnedArgs la;
+  int32_t *d_ent, *d_et_ptr, *d_fp, *d_fc, *d_ep, *d_ec;
+  double *d_etv, *d_dinv, *d_fv, *d_ev;
+  float *d_w, *d_mean, *d_std;
+  TRY(upload(h, &d_ent, ents));
+  TRY(upload(h, &d_et_ptr, et_ptr));
+  TRY(upload(h, &d_etv, et_val));
+  TRY(upload(h, &d_dinv, dinv));
+  TRY(upload(h, &d_fp, hb.f_ptr));
+  TRY(upload(h, &d_fc, hb.f_col));
+  TRY(upload(h, &d_fv, hb.f_val));
+  TRY(upload(h, &d_ep, hb.e_ptr));
+  TRY(upload(h, &d_ec, hb.e_col));
+  TRY(upload(h, &d_ev, hb.e_val));
+  TRY(upload(h, &d_w, wbf));
+  TRY(upload(h, &d_mean, mean));
+  TRY(upload(h, &d_std, stdv));
+  TRY(dalloc(h, &h->l_feat, (size_t)std::max<int64_t>(ne, 1) * DD_MLP_IN));
+  TRY(dalloc(h, &h->l_delta, (size_t)std::max<int64_t>(ne, 1)));
+  la.n_ent = ne;
+  la.ent = d_ent;
+  la.agg_off = h->agg_off;
+  la.s_off = h->s_off;
+  la.perm_iface = h->d_perm + nI;
+  la.c_rowptr = h->c_rowptr;
+  la.c_col = h->c_col;
+  la.c_val = h->c_val;
+  la.f_ptr = d_fp; la.f_col = d_fc; la.f_val = d_fv;
+  la.e_ptr = d_ep; la.e_col = d_ec; la.e_val = d_ev;
+  la.et_ptr = d_et_ptr; la.et_val = d_etv;
+  la.dinv = d_dinv;
+  la.wbf = d_w;
+  la.mean = d_mean;
+  la.stdv = d_std;
+  la.out_scale = w.out_scale;
+  la.feat = h->l_feat;
+  la.delta = h->l_delta;
+  h->stats.launches += 1;
+  CK(launch_learned_delta<T>(la, B.S, s));
+  // invert; failures go to a scratch status word and the failed flags
+  TRY(dalloc(h, &h->st_probe, 1));
+  CK(cudaMemsetAsync(h->st_probe, 0, sizeof(DevStatus), s));
+  CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.S, B.amax, s));
+  CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.S, h->ipiv, h->poff, B.amax, h->failed, B.gj,
+                          pivtol, h->st_probe, DD_ERR_SINGULAR_SCHUR, s));
+  std::vector<int32_t> failed(nagg, 0);
+  if (nagg) CK(cudaMemcpyAsync(failed.data(), h->failed, sizeof(int32_t) * nagg, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int32_t> fb;
+  for (int a = 0; a < nagg; ++a)
+    if (failed[a]) fb.push_back(a);
+  h->stats.learned_fallback = (int32_t)fb.size();
+  if (fb.empty()) return DD_OK;
+  // fallback: MSCE_INF blocks into a second buffer, the failed ones inverted and copied over
+  T *S2 = nullptr;
+  TRY(dalloc(h, &S2, soff[nagg]));
+  CK(cudaMemsetAsync(S2, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
+  CK(launch_scatter_coo<T>(gcount, d_gidx, d_gval, S2, s));
+  TRY(msce_into(S2));
+  std::vector<int32_t> fp;
+  std::vector<int64_t> fo, fpo(1, 0);
+  int fpmax = 0;
+  for (int a : fb) {
+    fp.push_back(p[a]);
+    fo.push_back(soff[a]);
+    fpo.push_back(fpo.back() + p[a]);
+    fpmax = std::max(fpmax, p[a]);
+  }
+  int32_t *d_fpp, *d_ff;
+  int64_t *d_fo, *d_fpo;
+  T *famax;
+  TRY(upload(h, &d_fpp, fp));
+  TRY(upload(h, &d_fo, fo));
+  TRY(upload(h, &d_fpo, fpo));
+  TRY(dalloc(h, &d_ff, fb.size()));
+  TRY(dalloc(h, &famax, fb.size()));
+  CK(launch_block_amax<T>((int)fb.size(), d_fpp, d_fo, S2, famax, s));
+  CK(launch_gj_inverse<T>((int)fb.size(), d_fpp, d_fo, fpmax, S2, h->ipiv, d_fpo, famax, d_ff, B.gj, pivtol,
+                          h->st, DD_ERR_SINGULAR_SCHUR, s));
+  for (size_t q = 0; q < fb.size(); ++q)
+    CK(cudaMemcpyAsync(B.S + soff[fb[q]], S2 + soff[fb[q]], sizeof(T) * (size_t)p[fb[q]] * p[fb[q]],
+                       cudaMemcpyDeviceToDevice, s));
+  (void)poff;
+  (void)agg_of;
+  return DD_OK;
+}
+
 template <typename T>
 dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb,
                        double pivtol) {
@@ -626,6 +839,9 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(dalloc(h, &h->ipiv, poff[nagg]));
   TRY(dalloc(h, &h->failed, nagg));
   // G(R_a, R_a) into S
+  int64_t *d_gidx = nullptr;
+  double *d_gval = nullptr;
+  size_t gcount = 0;
   {
     std::vector<int64_t> idx;
     std::vector<double> val;
@@ -639,13 +855,13 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
         val.push_back(csr->val[k]);
       }
     }
-    int64_t *d_idx = nullptr;
-    double *d_val = nullptr;
-    TRY(upload(h, &d_idx, idx));
-    TRY(upload(h, &d_val, val));
-    CK(launch_scatter_coo<T>((int64_t)idx.size(), d_idx, d_val, B.S, s));
+    TRY(upload(h, &d_gidx, idx));
+    TRY(upload(h, &d_gval, val));
+    gcount = idx.size();
+    CK(launch_scatter_coo<T>((int64_t)idx.size(), d_gidx, d_gval, B.S, s));
   }
-  if (h->kind == DD_MSCE_INF || h->kind == DD_EXACT) {
+  // S_dst(R_a, R_a) -= sum_j F(R_a, I_j) A_jj^-1 E(I_j, R_a) (MSCE_INF / EXACT)
+  auto msce_into = [&](T *Sdst) -> dd_status {
     // per subdomain: interface columns of E (gam) and interface rows of F (fr)
     std::vector<int32_t> gam_ptr(m + 1, 0), gam_idx, gam_agg, fr_ptr(m + 1, 0), fr_row, fr_agg;
     std::vector<int32_t> fs_ptr(1, 0), fs_col;
@@ -722,7 +938,18 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     // S(R_a,R_a) -= F(R_a, I_j) X_j
     CK(launch_schur_accumulate<T>(m, d_fr_ptr, d_fr_row, d_fr_agg, d_fs_ptr, d_fs_col, B.fsub_val,
                                   d_gam_ptr, d_gam_idx, d_gam_agg, d_xoff, h->d_info, B.X,
-                                  h->agg_off, h->s_off, B.S, max_fr, max_gam, s));
+                                  h->agg_off, h->s_off, Sdst, max_fr, max_gam, s));
+    return DD_OK;
+  };
+  if (h->kind == DD_MSCE_INF || h->kind == DD_EXACT) {
+    TRY(msce_into(B.S));
+  } else if (h->kind == DD_LEARNED) {
+    TRY(learned_blocks<T>(h, csr, hb, agg_of, p, soff, poff, pivtol, msce_into, d_gidx, d_gval,
+                          (int64_t)gcount));
+    TRY(dalloc(h, &B.z1, std::max(nI, 1)));
+    TRY(dalloc(h, &B.z2, std::max(nG, 1)));
+    TRY(dalloc(h, &B.t, std::max(nG, 1)));
+    return DD_OK;  // the blocks are inverted (with their fallbacks)
   } else if (h->kind == DD_MSCN || h->kind == DD_MSCNR) {
     // principal blocks with the same local index range (Algorithm 1)
     std::vector<int64_t> di, ei, fi;
@@ -1288,10 +1515,14 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
 // seg_row0_h already set); times itself with events on the handle's stream.
 dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *partition, dd_approx approx,
                        const dd_opts *opts) {
-  if ((int)approx < DD_EXACT || (int)approx > DD_LUM) { h->err = "unknown approximation"; return DD_ERR_INVALID_ARG; }
+  if ((int)approx < DD_EXACT || (int)approx > DD_LEARNED) { h->err = "unknown approximation"; return DD_ERR_INVALID_ARG; }
   dd_opts o{};
   o.prec = DD_FP64;
   if (opts) o = *opts;
+  if (approx == DD_LEARNED) {
+    if (!o.mlp_weights) { h->err = "DD_LEARNED needs opts.mlp_weights"; return DD_ERR_INVALID_ARG; }
+    h->mlp_path = o.mlp_weights;
+  }
   if (o.prec != DD_FP64 && o.prec != DD_FP32) { h->err = "unknown precision"; return DD_ERR_INVALID_ARG; }
   h->prec = o.prec;
   h->kind = approx;
@@ -1651,6 +1882,23 @@ dd_status dd_spmv(void *handle, const double *x, double *y, void *stream) {
   if (!h || !x || !y) return DD_ERR_INVALID_ARG;
   cudaError_t e = launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, x, y, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) { h->err = cudaGetErrorString(e); return DD_ERR_CUDA; }
+  return DD_OK;
+}
+
+dd_status dd_learned_entries(void *handle, int32_t *ents, double *feats, float *delta, int64_t cap,
+                             int64_t *count) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h || !count || cap < 0) return DD_ERR_INVALID_ARG;
+  if (h->kind != DD_LEARNED) { h->err = "not a DD_LEARNED handle"; return DD_ERR_INVALID_ARG; }
+  const int64_t ne = (int64_t)h->l_ents.size() / 3;
+  *count = ne;
+  const int64_t k = std::min(ne, cap);
+  if (k <= 0) return DD_OK;
+  if (ents) memcpy(ents, h->l_ents.data(), sizeof(int32_t) * 3 * (size_t)k);
+  if (feats && cudaMemcpy(feats, h->l_feat, sizeof(double) * DD_MLP_IN * (size_t)k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DD_ERR_CUDA;
+  if (delta && cudaMemcpy(delta, h->l_delta, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DD_ERR_CUDA;
   return DD_OK;
 }
 

@@ -226,3 +226,32 @@ cudaError_t launch_seg_start(int64_t n, const double *r, const double *nsq, doub
 cudaError_t launch_seg_hess_update(int64_t n, int R, const int32_t *jl, const double *H, const double *g,
                                    double *y, const double *Z, int64_t ldz, double *x, const SegMap &sm,
                                    int nblocks, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// DD_LEARNED setup: per-entry features, the network and Delta added to S.
+// Index arrays in the permuted numbering (interface rows local to the
+// interface); values FP64.
+// ---------------------------------------------------------------------------
+struct LearnedArgs {
+  int64_t n_ent = 0;
+  const int32_t *ent = nullptr;         // 3 per entry: aggregate, local row, local column
+  const int32_t *agg_off = nullptr;     // nagg + 1
+  const int64_t *s_off = nullptr;       // block offsets in S
+  const int32_t *perm_iface = nullptr;  // interface index -> original index
+  const int32_t *c_rowptr = nullptr, *c_col = nullptr;  // C, original numbering
+  const double *c_val = nullptr;
+  const int32_t *f_ptr = nullptr, *f_col = nullptr;    // F: interface rows -> interior
+  const double *f_val = nullptr;
+  const int32_t *e_ptr = nullptr, *e_col = nullptr;    // E: interior rows -> interface
+  const double *e_val = nullptr;
+  const int32_t *et_ptr = nullptr;                     // E^T values per interface row
+  const double *et_val = nullptr;
+  const double *dinv = nullptr;                        // 1 / D(k, k), 0 where D(k, k) = 0
+  const float *wbf = nullptr;                          // BF16-rounded parameters (DD_MLP_NPARAM)
+  const float *mean = nullptr, *stdv = nullptr;        // feature normalisation
+  float out_scale = 1.f;
+  double *feat = nullptr;                              // optional: raw features out
+  float *delta = nullptr;                              // optional: Delta per entry out
+};
+template <typename T>
+cudaError_t launch_learned_delta(const LearnedArgs &a, T *S, cudaStream_t s);

@@ -19,7 +19,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_ROOT, "_build")
 LIB_PATH = os.path.join(_PKG, "libdd.so")
-SOURCES = ["dd_api.cu", "k_band.cu", "k_dense.cu", "k_krylov.cu"]
+SOURCES = ["dd_api.cu", "k_band.cu", "k_dense.cu", "k_krylov.cu", "k_mlp.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
@@ -28,7 +28,11 @@ DD_FP64, DD_FP32 = 0, 1
 STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_INVALID_ARG", 2: "DD_ERR_INVALID_PARTITION",
                 3: "DD_ERR_SINGULAR_BLOCK", 4: "DD_ERR_SINGULAR_SCHUR", 5: "DD_ERR_NOT_CONVERGED",
                 6: "DD_ERR_NONFINITE", 7: "DD_ERR_TIMEOUT", 8: "DD_ERR_OOM", 9: "DD_ERR_CUDA"}
-KINDS = {"exact": DD_EXACT, "msce_inf": DD_MSCE_INF, "mscn": DD_MSCN, "mscnr": DD_MSCNR, "lum": DD_LUM}
+DD_LEARNED = 5
+KINDS = {"exact": DD_EXACT, "msce_inf": DD_MSCE_INF, "mscn": DD_MSCN, "mscnr": DD_MSCNR, "lum": DD_LUM,
+         "learned": DD_LEARNED}
+MLP_IN, MLP_HIDDEN = 14, 64
+MLP_NPARAM = MLP_HIDDEN * MLP_IN + 2 * MLP_HIDDEN + 1
 
 
 def _nvcc():
@@ -75,7 +79,8 @@ class dd_partition(ctypes.Structure):
 
 class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("mlp_weights", ctypes.c_char_p)]
 
 
 class dd_info(ctypes.Structure):
@@ -93,12 +98,14 @@ class dd_stats(ctypes.Structure):
                 ("schur_bytes", ctypes.c_int64), ("coupling_nnz", ctypes.c_int64), ("setup_ms", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("stage_bytes", ctypes.c_int32), ("sweep_grid", ctypes.c_int32),
                 ("sweep_slots", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tuned_us", ctypes.c_double),
-                ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32), ("learned_entries", ctypes.c_int64),
+                ("learned_fallback", ctypes.c_int32), ("pad3", ctypes.c_int32)]
 
 
 EXPORTS = ["dd_setup", "dd_setup_batched", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve",
-           "gmres_solve_batched", "dd_spmv",
-           "dd_get_stats", "dd_get_bad_block", "dd_destroy", "dd_last_error"]
+           "gmres_solve_batched", "dd_spmv", "dd_get_stats", "dd_get_bad_block", "dd_destroy", "dd_last_error",
+           "dd_learned_entries", "dd_mlp_create", "dd_mlp_set_data", "dd_mlp_loss_grad", "dd_mlp_adam_step",
+           "dd_mlp_predict", "dd_mlp_get", "dd_mlp_set_adam", "dd_mlp_destroy"]
 NOALLOC_MAX_ELEMS = 1 << 20
 
 _lib = None
@@ -141,6 +148,25 @@ def load(path: str = LIB_PATH):
     lib.dd_destroy.argtypes = [vp]
     lib.dd_last_error.restype = ctypes.c_char_p
     lib.dd_last_error.argtypes = [vp]
+    i64, f32p = ctypes.c_int64, ctypes.POINTER(ctypes.c_float)
+    lib.dd_learned_entries.restype = ctypes.c_int
+    lib.dd_learned_entries.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.dd_mlp_create.restype = ctypes.c_int
+    lib.dd_mlp_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.dd_mlp_set_data.restype = ctypes.c_int
+    lib.dd_mlp_set_data.argtypes = [vp, vp, vp, i64, vp]
+    lib.dd_mlp_loss_grad.restype = ctypes.c_int
+    lib.dd_mlp_loss_grad.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_double), vp, vp]
+    lib.dd_mlp_adam_step.restype = ctypes.c_int
+    lib.dd_mlp_adam_step.argtypes = [vp, i64, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+    lib.dd_mlp_predict.restype = ctypes.c_int
+    lib.dd_mlp_predict.argtypes = [vp, i64, i64, vp, vp]
+    lib.dd_mlp_get.restype = ctypes.c_int
+    lib.dd_mlp_get.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64)]
+    lib.dd_mlp_set_adam.restype = ctypes.c_int
+    lib.dd_mlp_set_adam.argtypes = [vp, vp, vp, i64]
+    lib.dd_mlp_destroy.restype = ctypes.c_int
+    lib.dd_mlp_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -176,7 +202,7 @@ class DD:
 
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
-                 autotune=False):
+                 autotune=False, mlp_weights=None):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -188,6 +214,8 @@ class DD:
         csr = dd_csr(self.n, int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
         pt = dd_partition(int(m), _ptr(pa), _ptr(pe), int(sz), _ptr(ag), 0 if ag is None else len(ag) - 1)
         o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)))
+        self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
+        o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
         h = ctypes.c_void_p()
         rc = lib.dd_setup(ctypes.byref(csr), ctypes.byref(pt), k, ctypes.byref(o), _stream_handle(stream),
@@ -253,6 +281,17 @@ class DD:
         s = dd_stats()
         self._check(self._lib.dd_get_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in dd_stats._fields_}
+
+    def learned_entries(self):
+        """(entries [n x 3] aggregate/row/col, raw features [n x 14] FP64, Delta [n]) of a DD_LEARNED handle."""
+        cnt = ctypes.c_int64()
+        self._check(self._lib.dd_learned_entries(self._h, None, None, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        ents = np.zeros((n, 3), np.int32)
+        feats = np.zeros((n, MLP_IN), np.float64)
+        delta = np.zeros(n, np.float32)
+        self._check(self._lib.dd_learned_entries(self._h, _ptr(ents), _ptr(feats), _ptr(delta), n, ctypes.byref(cnt)))
+        return ents, feats, delta
 
 
 class DDBatch:
@@ -332,3 +371,72 @@ class DDBatch:
         if rc != 0:
             raise DDError(rc, "dd_get_stats")
         return {f: getattr(s, f) for f, _ in dd_stats._fields_}
+
+
+class MLP:
+    """Training handle of the learned Schur correction's network (dd_mlp_*)."""
+
+    def __init__(self, params):
+        lib = load()
+        self._lib = lib
+        p = np.ascontiguousarray(params, np.float32)
+        if p.shape != (MLP_NPARAM,):
+            raise ValueError(f"expected {MLP_NPARAM} parameters")
+        h = ctypes.c_void_p()
+        rc = lib.dd_mlp_create(_ptr(p), ctypes.byref(h))
+        if rc != 0:
+            raise DDError(rc, "dd_mlp_create")
+        self._h = h
+        self.n = 0
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise DDError(rc, what)
+
+    def set_data(self, X, y, stream=None):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        if X.ndim != 2 or X.shape[1] != MLP_IN or len(y) != len(X):
+            raise ValueError("X must be n x 14 and y n long")
+        self._check(self._lib.dd_mlp_set_data(self._h, _ptr(X), _ptr(y), len(y), _stream_handle(stream)), "set_data")
+        self.n = len(y)
+
+    def loss_grad(self, lo=0, hi=None, stream=None):
+        hi = self.n if hi is None else hi
+        loss = ctypes.c_double()
+        g = np.zeros(MLP_NPARAM, np.float32)
+        self._check(self._lib.dd_mlp_loss_grad(self._h, lo, hi, ctypes.byref(loss), _ptr(g), _stream_handle(stream)),
+                    "loss_grad")
+        return loss.value, g
+
+    def adam_step(self, lo, hi, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(self._lib.dd_mlp_adam_step(self._h, lo, hi, lr, beta1, beta2, eps, _stream_handle(stream)),
+                    "adam_step")
+
+    def predict(self, lo=0, hi=None, stream=None):
+        hi = self.n if hi is None else hi
+        out = np.zeros(hi - lo, np.float32)
+        self._check(self._lib.dd_mlp_predict(self._h, lo, hi, _ptr(out), _stream_handle(stream)), "predict")
+        return out
+
+    def get(self):
+        p, m, v = (np.zeros(MLP_NPARAM, np.float32) for _ in range(3))
+        st = ctypes.c_int64()
+        self._check(self._lib.dd_mlp_get(self._h, _ptr(p), _ptr(m), _ptr(v), ctypes.byref(st)), "get")
+        return p, m, v, st.value
+
+    def set_adam(self, m, v, step):
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        self._check(self._lib.dd_mlp_set_adam(self._h, _ptr(m), _ptr(v), int(step)), "set_adam")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dd_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

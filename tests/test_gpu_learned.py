@@ -1,0 +1,175 @@
+"""The learned Schur correction on the GPU against the oracle.
+
+- The network's gradient (dd_mlp_loss_grad) is checked against the oracle's
+  FP64 backprop at the same BF16-rounded weights and inputs.  The GPU sums in
+  FP32, so the bar is 1e-4 of the gradient's norm.  The oracle's backprop is
+  itself pinned by finite differences.
+- Training is deterministic: two runs of the same steps give the same bits.
+- Training lowers the loss of a regression that the network can fit.
+- DD_LEARNED setup: the GPU features equal the oracle's (FP64, 1e-12).  Its
+  Delta equals the oracle's FP64 network on the same BF16 inputs to FP32
+  accuracy.  Its apply equals the oracle's learned preconditioner to 1e-4,
+  which is the effect of FP32 Delta through the block inverses.
+- Fallback: with out_scale = 0 the learned block is G_ii.  With one-node
+  aggregates every interface pressure node then has a zero block, so those
+  aggregates take the MSCE_INF block.  The apply then matches the oracle's
+  fallback bit-for-bit in meaning, to 1e-10.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import learned as L
+from paper_1104_3349_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1104_3349_gb300",
+                       "weights", "schur_mlp.bin")
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1104_3349_gb300 import dd
+    dd.build()
+    dd.load()
+    return torch, dd, torch.device("cuda:0")
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (n, L.N_IN)).astype(np.float32)
+    p = rng.normal(0, 0.3, L.NPARAM).astype(np.float32)
+    y = rng.normal(0, 1, n).astype(np.float32)
+    return X, y, p
+
+
+def test_gradient_matches_oracle_backprop(env):
+    torch, dd, dev = env
+    X, y, p = _data(1, 3000)
+    M = dd.MLP(p)
+    M.set_data(X, y)
+    loss, g = M.loss_grad()
+    lo, go = L.loss_grad(L.bf16(p), L.bf16(X), y.astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    # a sub-range, not a multiple of the tile
+    loss2, g2 = M.loss_grad(100, 1133)
+    lo2, go2 = L.loss_grad(L.bf16(p), L.bf16(X[100:1133]), y[100:1133].astype(np.float64))
+    assert np.linalg.norm(g2 - go2) <= 1e-4 * np.linalg.norm(go2)
+    out = M.predict(0, 50)
+    ref, _ = L.forward(L.bf16(p), L.bf16(X[:50]))
+    np.testing.assert_allclose(out, ref, rtol=1e-5, atol=1e-5)
+    M.close()
+
+
+def test_training_is_deterministic_and_learns(env):
+    torch, dd, dev = env
+    rng = np.random.default_rng(2)
+    X = rng.normal(0, 1, (20000, L.N_IN)).astype(np.float32)
+    y = (np.maximum(X[:, 0], 0) - 0.5 * X[:, 3] + 0.25 * X[:, 5] * (X[:, 7] > 0)).astype(np.float32)
+    from paper_1104_3349_gb300 import train_mlp as T
+    runs = []
+    for _ in range(2):
+        M = dd.MLP(T.init_params(0))
+        M.set_data(X, y)
+        l0, _ = M.loss_grad()
+        for ep in range(20):
+            for q in range(0, 20000, 2048):
+                M.adam_step(q, min(20000, q + 2048), 3e-3)
+        l1, _ = M.loss_grad()
+        runs.append((l0, l1, M.get()[0]))
+        M.close()
+    assert runs[0][1] < 0.05 * runs[0][0]
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
+def _trained_or_skip():
+    if not os.path.exists(WEIGHTS):
+        pytest.skip("no trained weight file")
+    return L.read_weights(WEIGHTS)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_learned_setup_matches_oracle(env, prec):
+    torch, dd, dev = env
+    wts = _trained_or_skip()
+    w = W.cavity32()
+    P = dd.DD(w.A, w.part, w.m, "learned", perm=w.perm, agg_offsets=w.agg, prec=prec, mlp_weights=WEIGHTS)
+    ents, feats, delta = P.learned_entries()
+    R, ents_o, delta_o, fell = L.learned_oracle(w.A, w.part, w.m, w.perm, w.agg, wts)
+    _, X_o = L.features(w.A, w.part, w.perm, w.agg)
+    np.testing.assert_array_equal(ents, ents_o)
+    np.testing.assert_allclose(feats, X_o, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(delta, delta_o, rtol=1e-4, atol=1e-5 * np.abs(delta_o).max())
+    st = P.stats()
+    assert st["learned_entries"] == len(ents) and st["learned_fallback"] == len(fell)
+    y = W.uniform(1, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    torch.cuda.synchronize()
+    xr = R.apply(y)
+    err = np.linalg.norm(xd.cpu().numpy() - xr) / np.linalg.norm(xr)
+    assert err <= 1e-4, err
+    b = torch.from_numpy(w.b).to(dev)
+    x = torch.zeros_like(b)
+    r = P.gmres(b, x, tol=1e-8, restart=50)
+    ro = R.fgmres(w.b, tol=1e-8, restart=50)
+    assert r["status"] == 0 and ro["status"] == 0
+    assert abs(r["iters"] - ro["iters"]) <= 1, (r["iters"], ro["iters"])
+    P.close()
+    R.close()
+
+
+def test_learned_fallback_takes_msce_blocks(env, tmp_path):
+    torch, dd, dev = env
+    from paper_1104_3349_gb300 import train_mlp as T
+    f = tmp_path / "zero.bin"
+    T.write_weights(str(f), 0.0, np.zeros(14), np.ones(14), T.init_params(1))
+    wts = L.read_weights(str(f))
+    w = W.cavity32()
+    nG = int((w.part < 0).sum())
+    # one node per aggregate, merged with the next where even the MSCE_INF
+    # block is singular (a pressure node without interior neighbours)
+    agg = list(range(nG + 1))
+    for _ in range(nG):
+        Rt = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=np.asarray(agg, np.int32),
+                        raise_on_error=False)
+        st, bad = Rt.status, Rt.bad_block
+        Rt.close()
+        if st == 0:
+            break
+        assert st == 4 and 0 <= bad < len(agg) - 2
+        del agg[bad + 1]
+    agg = np.asarray(agg, np.int32)
+    P = dd.DD(w.A, w.part, w.m, "learned", perm=w.perm, agg_offsets=agg, mlp_weights=str(f))
+    R, _, _, fell = L.learned_oracle(w.A, w.part, w.m, w.perm, agg, wts)
+    assert len(fell) > 0
+    assert P.stats()["learned_fallback"] == len(fell)
+    y = W.uniform(1, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    torch.cuda.synchronize()
+    xr = R.apply(y)
+    assert np.linalg.norm(xd.cpu().numpy() - xr) <= 1e-10 * np.linalg.norm(xr)
+    P.close()
+    R.close()
+
+
+def test_learned_rejects_a_corrupt_weight_file(env, tmp_path):
+    torch, dd, dev = env
+    from paper_1104_3349_gb300 import train_mlp as T
+    f = tmp_path / "bad.bin"
+    T.write_weights(str(f), 1.0, np.zeros(14), np.ones(14), T.init_params(1))
+    raw = bytearray(f.read_bytes())
+    raw[40] ^= 4
+    f.write_bytes(bytes(raw))
+    w = W.cavity32()
+    with pytest.raises(dd.DDError) as ei:
+        dd.DD(w.A, w.part, w.m, "learned", perm=w.perm, agg_offsets=w.agg, mlp_weights=str(f))
+    assert ei.value.status == 1
