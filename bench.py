@@ -369,6 +369,61 @@ def run_variants(args, dev):
         "one_by_one_ms": round(e0.elapsed_time(e1), 1), "sweep_grid": int(st["sweep_grid"]),
         "stage_bytes": int(st["stage_bytes"]), "autotune_candidates": int(st["tuned"]),
         "graphs": int(st["graphs"]), "launches": int(st["launches"])}
+    out["learned"] = run_learned(args, dev)
+    return out
+
+
+WEIGHTS = os.path.join(ROOT, "paper_1104_3349_gb300", "weights", "schur_mlp.bin")
+
+
+def run_learned(args, dev):
+    """The learned correction (DD_LEARNED) against the method without it (LUM)
+    and the MSCE_INF blocks it is trained on.  Two workloads: held-out 64x64
+    problems like the training set's (seeds outside it), and the 1024x1024
+    stretched grid (aspect 100, 1024 subdomains) at an iteration cap."""
+    import math
+    import torch
+    from paper_1104_3349_gb300 import dd, workload as W
+
+    def solve(A, part, m, perm, agg, b, kind, prec, maxit):
+        try:
+            P = dd.DD(A, part, m, kind, perm=perm, agg_offsets=agg, prec=prec,
+                      mlp_weights=WEIGHTS if kind == "learned" else None)
+        except dd.DDError as e:
+            return {"setup_error": str(e)[:120]}
+        bd = torch.from_numpy(b).to(dev)
+        x = torch.zeros_like(bd)
+        r = P.gmres(bd, x, tol=TOL, restart=RESTART, maxit=maxit)
+        st = P.stats()
+        P.close()
+        return {"iters": r["iters"], "status": r["status"], "relres": r["relres"], "setup_ms": round(r["setup_ms"], 2),
+                "solve_ms": round(r["solve_ms"], 2), "fallback": int(st["learned_fallback"])}
+
+    kinds = ("lum", "learned", "msce_inf")
+    small = {k: [] for k in kinds}
+    for seed in range(9000, 9008):
+        u = W.uniform(seed, 2, 0.0, 1.0)
+        nu = math.exp(math.log(1e-3) + (math.log(1e-2) - math.log(1e-3)) * float(u[0]))
+        A, _ = W.mac_system(64, nu, 1.0 + 0.03 * float(u[1]), W.WIND_FOURIER, seed)
+        part, perm, _ = W.partition(A, 4)
+        agg = W.aggregates(A, part, perm, 64)
+        b = W.uniform(0, A.n)
+        for k in kinds:
+            small[k].append(solve(A, part, 4, perm, agg, b, k, dd.DD_FP32, MAXIT))
+    summ = {k: {"iters": [r.get("iters") for r in v], "setup_ms_mean": round(float(np.mean([r["setup_ms"] for r in v])), 2),
+                "all_converged": all(r.get("status") == 0 for r in v)} for k, v in small.items()}
+    out = {"heldout64": {"workload": "8 held-out 64x64 MAC Oseen problems (nu log-uniform [1e-3,1e-2], stretch [1,1.03], "
+                                     "seeds 9000-9007), 4 subdomains, aggregates sz 64, FP32 preconditioner, FGMRES(50)",
+                         **summ}}
+    if not args.skip_cfg5:
+        w = W.stretched1024()
+        agg = W.aggregates(w.A, w.part, w.perm, 64)
+        big = {}
+        for prec, name in ((dd.DD_FP64, "fp64"), (dd.DD_FP32, "fp32")):
+            for k in kinds:
+                big[f"{k}_{name}"] = solve(w.A, w.part, w.m, w.perm, agg, w.b, k, prec, args.c5_maxit)
+        out["stretched1024"] = {"workload": "oseen_mac_1024x1024_aspect100_nu1e-3_fourier8_m1024_sz64_fgmres50",
+                                "n": int(w.A.n), "maxit": args.c5_maxit, **big}
     return out
 
 
@@ -441,6 +496,9 @@ def main():
                     help="leave out the stretched 512x512 and 64-system batch measurements")
     ap.add_argument("--c3-maxit", type=int, default=300,
                     help="FGMRES iteration cap of the stretched 512x512 measurement")
+    ap.add_argument("--c5-maxit", type=int, default=200,
+                    help="FGMRES iteration cap of the stretched 1024x1024 learned measurement")
+    ap.add_argument("--skip-cfg5", action="store_true", help="leave out the 1024x1024 learned measurement")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling driver: one dd_setup, then this many dd_apply calls, no JSON line")
     args = ap.parse_args()

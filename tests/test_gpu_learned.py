@@ -173,3 +173,27 @@ def test_learned_rejects_a_corrupt_weight_file(env, tmp_path):
     with pytest.raises(dd.DDError) as ei:
         dd.DD(w.A, w.part, w.m, "learned", perm=w.perm, agg_offsets=w.agg, mlp_weights=str(f))
     assert ei.value.status == 1
+
+
+def test_learned_apply_matches_oracle_128(env):
+    # a larger system (16 subdomains, ~190 aggregates): the same parity bar
+    torch, dd, dev = env
+    wts = _trained_or_skip()
+    A, _ = W.mac_system(128, 3e-3, 1.02, W.WIND_FOURIER, 4321)
+    part, perm, _ = W.partition(A, 16)
+    agg = W.aggregates(A, part, perm, 64)
+    P = dd.DD(A, part, 16, "learned", perm=perm, agg_offsets=agg, mlp_weights=WEIGHTS)
+    R, ents_o, delta_o, fell = L.learned_oracle(A, part, 16, perm, agg, wts)
+    ents, feats, delta = P.learned_entries()
+    np.testing.assert_array_equal(ents, ents_o)
+    np.testing.assert_allclose(delta, delta_o, rtol=1e-4, atol=1e-5 * np.abs(delta_o).max())
+    assert P.stats()["learned_fallback"] == len(fell)
+    y = W.uniform(1, A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    torch.cuda.synchronize()
+    xr = R.apply(y)
+    assert np.linalg.norm(xd.cpu().numpy() - xr) <= 1e-4 * np.linalg.norm(xr)
+    P.close()
+    R.close()
