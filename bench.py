@@ -483,6 +483,22 @@ def apply_only(args):
     P.close()
 
 
+def solve_only(args):
+    """One dd_setup on the bench workload, then one FGMRES solve capped at
+    args.solve_only iterations, no JSON line (the CGS2 kernel's profiles)."""
+    import torch
+    from paper_1104_3349_gb300 import dd
+    dd.build()
+    w, agg = make_inputs()
+    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+    b = torch.from_numpy(w.b).cuda()
+    x = torch.empty_like(b)
+    P.gmres(b, x, tol=TOL, restart=RESTART, maxit=args.solve_only)
+    torch.cuda.synchronize()
+    P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,9 +517,14 @@ def main():
     ap.add_argument("--skip-cfg5", action="store_true", help="leave out the 1024x1024 learned measurement")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling driver: one dd_setup, then this many dd_apply calls, no JSON line")
+    ap.add_argument("--solve-only", type=int, default=0,
+                    help="profiling driver: one dd_setup, then one solve capped at this many iterations")
     args = ap.parse_args()
     if args.apply_only:
         apply_only(args)
+        return
+    if args.solve_only:
+        solve_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -138,20 +138,29 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       }
       __syncthreads();
     }
-    // U12 = L11^-1 A12 (rows 0..NB-1, columns NB..Cw-1)
-    for (int c = 0; c < nbe - 1; ++c) {
-      for (int e = tid; e < (DD_NB - 1 - c) * (Cw - DD_NB); e += nt) {
-        const int r = c + 1 + e / (Cw - DD_NB), q = DD_NB + e % (Cw - DD_NB);
-        W[r * ldw + q] -= W[r * ldw + c] * W[c * ldw + q];
-      }
-      __syncthreads();
+    // U12 = L11^-1 A12 (rows 0..NB-1, columns NB..Cw-1): one thread per
+    // column, forward substitution with the unit lower L11 in registers
+    for (int q = DD_NB + tid; q < Cw; q += nt) {
+      T x[DD_NB];
+#pragma unroll
+      for (int r = 0; r < DD_NB; ++r) x[r] = W[r * ldw + q];
+#pragma unroll
+      for (int c = 0; c < DD_NB - 1; ++c)
+#pragma unroll
+        for (int r = c + 1; r < DD_NB; ++r)
+          if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
+#pragma unroll
+      for (int r = 1; r < DD_NB; ++r) W[r * ldw + q] = x[r];
     }
-    // A22 -= L21 U12 (rows NB..R-1, columns NB..Cw-1), 4 x 4 outputs per thread
+    __syncthreads();
+    // A22 -= L21 U12 (rows NB..R-1, columns NB..Cw-1): each thread 4 rows by
+    // 4 columns a quarter of the width apart, so neighbouring threads read
+    // neighbouring columns
     {
       const int nr = kl, ncol = Cw - DD_NB;
-      const int tr = (nr + 3) / 4, tc = (ncol + 3) / 4;
-      for (int m = tid; m < tr * tc; m += nt) {
-        const int i0 = DD_NB + 4 * (m / tc), j0 = DD_NB + 4 * (m % tc);
+      const int tr = (nr + 3) / 4, qw = (ncol + 3) / 4;
+      for (int m = tid; m < tr * qw; m += nt) {
+        const int i0 = DD_NB + 4 * (m / qw), jc = DD_NB + (m % qw);
         T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -162,7 +171,10 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 #pragma unroll
           for (int a = 0; a < 4; ++a) lv[a] = (i0 + a < R) ? W[(i0 + a) * ldw + k] : T(0);
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2) uv[c2] = (j0 + c2 < Cw) ? W[k * ldw + j0 + c2] : T(0);
+          for (int c2 = 0; c2 < 4; ++c2) {
+            const int j = jc + c2 * qw;
+            uv[c2] = (j < Cw) ? W[k * ldw + j] : T(0);
+          }
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -171,8 +183,10 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2)
-            if (i0 + a < R && j0 + c2 < Cw) W[(i0 + a) * ldw + j0 + c2] -= acc[a][c2];
+          for (int c2 = 0; c2 < 4; ++c2) {
+            const int j = jc + c2 * qw;
+            if (i0 + a < R && j < Cw) W[(i0 + a) * ldw + j] -= acc[a][c2];
+          }
       }
     }
     __syncthreads();
@@ -496,7 +510,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     const uint32_t gq = jbase + q;
     const int sidx = (int)(gq % nstages);
     unsigned char *stage = ring + (size_t)sidx * stage_bytes;
-    // every thread waits (bounded); the verdict is made uniform at the
+    // every thread waits (bounded); the outcome is made uniform at the
     // first barrier of the job, so no thread can leave the loop alone
     const bool got = mbar_wait_bounded(&bars[sidx], (gq / nstages) & 1u);
     bool fwd;

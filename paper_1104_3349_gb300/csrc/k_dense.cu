@@ -229,17 +229,21 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
     }
     __syncthreads();
   }
-  // row exchanges on whole rows of A, in order
-  for (int c = 0; c < nbe; ++c) {
-    const int q = ipiv[poff[b] + k0 + c];
-    if (q != k0 + c)
-      for (int j = tid; j < p; j += nt) {
+  // row exchanges on whole rows of A, in order; every thread applies all of
+  // them to its own columns, so no barrier is needed between exchanges
+  __shared__ int s_q[NB];
+  if (tid < nbe) s_q[tid] = ipiv[poff[b] + k0 + tid];
+  __syncthreads();
+  for (int j = tid; j < p; j += nt)
+    for (int c = 0; c < nbe; ++c) {
+      const int q = s_q[c];
+      if (q != k0 + c) {
         T t = a[(int64_t)(k0 + c) * p + j];
         a[(int64_t)(k0 + c) * p + j] = a[(int64_t)q * p + j];
         a[(int64_t)q * p + j] = t;
       }
-    __syncthreads();
-  }
+    }
+  __syncthreads();
   // A11^-1 = U11^-1 L11^-1, one column per thread of warp 0
   if (tid < nbe) {
     const int j = tid;
@@ -297,10 +301,15 @@ __global__ void bgj_rowblock_kernel(int k0, const int32_t *__restrict__ P, const
 }
 
 #define DD_BGJ_TILE 64
+// Rank-NB update of one 64 x 64 tile: each of the 256 threads owns 4
+// consecutive rows by 4 consecutive columns and accumulates the outer
+// products of a transposed P column chunk and an R row chunk in registers.
 template <typename T, int NB>
-__global__ void bgj_update_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                  T *A, const T *__restrict__ scratch, const int64_t *__restrict__ poff,
-                                  const int32_t *__restrict__ failed) {
+__global__ void __launch_bounds__(256) bgj_update_kernel(int k0, const int32_t *__restrict__ P,
+                                                         const int64_t *__restrict__ off, T *A,
+                                                         const T *__restrict__ scratch,
+                                                         const int64_t *__restrict__ poff,
+                                                         const int32_t *__restrict__ failed) {
   const int b = blockIdx.z;
   const int p = P[b];
   if (k0 >= p || failed[b]) return;
@@ -312,13 +321,14 @@ __global__ void bgj_update_kernel(int k0, const int32_t *__restrict__ P, const i
   const T *Pcol = scr + 2 * (int64_t)NB * p;
   const T *Rnew = scr + 3 * (int64_t)NB * p;
   const T *a11inv = scr + 4 * (int64_t)NB * p;
-  __shared__ T Ps[DD_BGJ_TILE][NB + 1];
-  __shared__ T Rs[NB][DD_BGJ_TILE + 1];
-  const int tid = threadIdx.x;  // 256 threads: 16 x 16, each 4 x 4 outputs
+  constexpr int LD = DD_BGJ_TILE + 4;  // keeps every row 16-byte aligned
+  __shared__ __align__(16) T Pt[NB][LD];  // Pt[c][r] = Pcol(i0 + r, c)
+  __shared__ __align__(16) T Rs[NB][LD];  // Rs[c][q] = new row c at column j0 + q
+  const int tid = threadIdx.x;
   for (int e = tid; e < DD_BGJ_TILE * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
     const int i = i0 + r;
-    Ps[r][c] = (i < p) ? Pcol[(int64_t)i * NB + c] : T(0);
+    Pt[c][r] = (i < p) ? Pcol[(int64_t)i * NB + c] : T(0);
   }
   for (int e = tid; e < NB * DD_BGJ_TILE; e += blockDim.x) {
     const int c = e / DD_BGJ_TILE, q = e % DD_BGJ_TILE;
@@ -328,26 +338,44 @@ __global__ void bgj_update_kernel(int k0, const int32_t *__restrict__ P, const i
     Rs[c][q] = v;
   }
   __syncthreads();
-  const int tr = tid / 16, tc = tid % 16;
+  const int tr = tid >> 4, tc = tid & 15;
+  const int rb = 4 * tr, qb = 4 * tc;
+  T acc[4][4];
 #pragma unroll
-  for (int ii = 0; ii < 4; ++ii) {
-    const int r = tr + 16 * ii, i = i0 + r;
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    T pv[4], rv[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) { pv[x] = Pt[c][rb + x]; rv[x] = Rs[c][qb + x]; }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] += pv[x] * rv[y];
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = i0 + rb + x;
     if (i >= p) continue;
     const bool pivot_row = (i >= k0 && i < k0 + nbe);
+    T *o = &a[(int64_t)i * p + j0 + qb];
+    if (pivot_row) {
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int q = tc + 16 * jj, j = j0 + q;
+      for (int y = 0; y < 4; ++y)
+        if (j0 + qb + y < p) o[y] = Rs[i - k0][qb + y];
+      continue;
+    }
+    T cur[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) cur[y] = (j0 + qb + y < p) ? o[y] : T(0);
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int j = j0 + qb + y;
       if (j >= p) continue;
       const bool panel_col = (j >= k0 && j < k0 + nbe);
-      T *o = &a[(int64_t)i * p + j];
-      if (pivot_row) {
-        *o = Rs[i - k0][q];
-      } else {
-        T s2 = T(0);
-#pragma unroll
-        for (int c = 0; c < NB; ++c) s2 += Ps[r][c] * Rs[c][q];
-        *o = panel_col ? -s2 : *o - s2;
-      }
+      o[y] = panel_col ? -acc[x][y] : cur[y] - acc[x][y];
     }
   }
 }
