@@ -102,7 +102,9 @@ typedef struct {
   int32_t autotune;   /* 1: dd_setup times the apply's sweep kernels for each
                          candidate ring-stage size (and with it CTAs per SM)
                          and keeps the fastest; 0: the fixed default           */
-  int32_t reserved[3];
+  int32_t krylov_ctas_per_sm; /* CTAs per SM of the Krylov kernels (CGS2 and the
+                         batched norms); <= 0 selects 2                          */
+  int32_t reserved[2];
   const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
                               (format under dd_mlp_*); ignored otherwise       */
 } dd_opts;

@@ -36,6 +36,7 @@ struct DDHandle {
   int64_t n = 0, nnz = 0;
   int m = 0, nI = 0, nG = 0, nagg = 0, pmax = 0;
   int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0;
+  int tb = DD_NB;              // columns of a sweep tile (DD_NB or DD_TB_WIDE)
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
   std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
   std::vector<TileMeta> h_tm;
@@ -83,6 +84,7 @@ struct DDHandle {
   double *bcat = nullptr, *xcat = nullptr, *bn2 = nullptr, *rn2 = nullptr;
   // CUDA graphs of the Arnoldi steps (use_graph), one per step index
   int use_graph = 0, graph_key = -1;
+  int krylov_per_sm = 2;
   std::vector<cudaGraphExec_t> gexec;
   std::vector<int64_t> glaunch;
   cudaStream_t gstream = nullptr;
@@ -348,18 +350,18 @@ namespace {
 // one subdomain whose packed bytes fit a stage (a larger tile is a job of
 // its own); forward jobs ascend, backward jobs descend.
 void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, size_t stage, size_t es,
-                std::vector<SweepJob> &jobs) {
+                int tb, std::vector<SweepJob> &jobs) {
   jobs.clear();
   for (BandInfo &b : info) {
     b.jf0 = (int32_t)jobs.size();
-    for (int lo = 0; lo < b.ntiles;) {
+    for (int lo = 0; lo < b.nst;) {
       size_t bytes = 0;
       int hi = lo;
-      while (hi < b.ntiles) {
+      while (hi < b.nst) {
         const TileMeta &q = tm[b.tile0 + hi];
-        const size_t tb = (size_t)q.wl * DD_NB * es + (size_t)round4(q.wl) * 4;
-        if (hi > lo && bytes + tb > stage) break;
-        bytes += tb;
+        const size_t nb = (size_t)q.wl * tb * es + (size_t)round4(q.wl) * 4;
+        if (hi > lo && bytes + nb > stage) break;
+        bytes += nb;
         ++hi;
       }
       jobs.push_back(SweepJob{lo, hi});
@@ -367,14 +369,14 @@ void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, si
     }
     b.njf = (int32_t)jobs.size() - b.jf0;
     b.jb0 = (int32_t)jobs.size();
-    for (int hi = b.ntiles; hi > 0;) {
+    for (int hi = b.nst; hi > 0;) {
       size_t bytes = 0;
       int lo = hi;
       while (lo > 0) {
         const TileMeta &q = tm[b.tile0 + lo - 1];
-        const size_t tb = (size_t)DD_NB * q.wu * es;
-        if (lo < hi && bytes + tb > stage) break;
-        bytes += tb;
+        const size_t nb = (size_t)tb * q.wu * es;
+        if (lo < hi && bytes + nb > stage) break;
+        bytes += nb;
         --lo;
       }
       jobs.push_back(SweepJob{lo, hi});
@@ -422,14 +424,14 @@ int sm_count() {
 template <typename T>
 dd_status set_sweep_plan(DDHandle *h, size_t stage) {
   std::vector<SweepJob> jobs;
-  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), jobs);
+  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), h->tb, jobs);
   const int m = h->m;
   if (!h->jobs) TRY(dalloc(h, &h->jobs, 2 * std::max<size_t>(h->h_tm.size(), 1)));
   if (!jobs.empty())
     CK(cudaMemcpyAsync(h->jobs, jobs.data(), sizeof(SweepJob) * jobs.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_info, h->h_info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, h->stream));
   h->plan.stage_bytes = (uint32_t)stage;
-  h->plan.threads = 8 * DD_NB;
+  h->plan.threads = 8 * h->tb;
   const int occ = band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, h->plan.threads, h->plan.stage_bytes);
   if (occ <= 0) {
     h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
@@ -443,11 +445,11 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage) {
     for (int j = 0; j < m; ++j) {
       const BandInfo &b = h->h_info[j];
       double bytes = 0;
-      for (int t = 0; t < b.ntiles; ++t) {
+      for (int t = 0; t < b.nst; ++t) {
         const TileMeta &q = h->h_tm[b.tile0 + t];
-        bytes += (double)(q.wl + q.wu) * DD_NB * sizeof(T);
+        bytes += (double)(q.wl + q.wu) * h->tb * sizeof(T);
       }
-      cost[j] = 2.0 * b.ntiles + bytes / 32768.0;  // dependent tile steps + streamed bytes
+      cost[j] = 2.0 * b.nst + bytes / 32768.0;  // dependent tile steps + streamed bytes
     }
     std::vector<int32_t> sched, off;
     lpt_schedule(cost, slots, sched, off);
@@ -689,7 +691,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   // ---- interior factors: geometry
   std::vector<BandInfo> info(m);
   int64_t band = 0, lraw = 0, pivo = 0, fac_nz = 0;
-  int32_t tiles = 0;
+  int32_t tiles = 0, panels = 0;
+  int max_panels = 0;
   h->max_n = h->max_kl = h->max_ku = h->max_ku2 = h->max_tiles = 0;
   for (int j = 0; j < m; ++j) {
     BandInfo &b = info[j];
@@ -702,19 +705,17 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     b.band_off = band; band += (int64_t)b.n * bi_wd(b);
     b.lraw_off = lraw; lraw += (int64_t)b.ntiles * bi_lraw_elems(b);
     b.piv_off = pivo; pivo += b.n;
-    b.tile0 = tiles; tiles += b.ntiles;
-    h->max_n = std::max(h->max_n, b.ntiles * DD_NB);
+    b.panel0 = panels; panels += b.ntiles;
     h->max_kl = std::max(h->max_kl, b.kl);
     h->max_ku = std::max(h->max_ku, b.ku);
     h->max_ku2 = std::max(h->max_ku2, b.kl + b.ku);
-    h->max_tiles = std::max(h->max_tiles, b.ntiles);
+    max_panels = std::max(max_panels, b.ntiles);
     // in-band entries of L (kl per column) and U (kl+ku+1 per row), clipped
     for (int i = 0; i < b.n; ++i) fac_nz += std::min(b.kl, b.n - 1 - i) + std::min(b.kl + b.ku, b.n - 1 - i) + 1;
   }
   h->stats.factor_nonzeros = fac_nz;
   h->stats.kl_max = h->max_kl;
   h->stats.ku_max = h->max_ku;
-  h->stats.tile = DD_NB;
   TRY(upload(h, &h->d_info, info));
   TRY(dalloc(h, &B.band, band));
   CK(cudaMemsetAsync(B.band, 0, sizeof(T) * std::max<int64_t>(band, 1), s));
@@ -763,32 +764,76 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   // ---- packed sweep tiles: widths from the factors, offsets and jobs here
   {
     int32_t *d_wl = nullptr, *d_wu = nullptr;
-    TRY(dalloc(h, &d_wl, tiles));
-    TRY(dalloc(h, &d_wu, tiles));
-    CK(launch_tile_widths<T>(h->d_info, m, h->max_tiles, B.band, B.lm, h->piv, d_wl, d_wu, s));
-    std::vector<int32_t> wl(tiles), wu(tiles);
-    if (tiles) {
-      CK(cudaMemcpyAsync(wl.data(), d_wl, sizeof(int32_t) * tiles, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(wu.data(), d_wu, sizeof(int32_t) * tiles, cudaMemcpyDeviceToHost, s));
+    TRY(dalloc(h, &d_wl, panels));
+    TRY(dalloc(h, &d_wu, panels));
+    CK(launch_tile_widths<T>(h->d_info, m, max_panels, B.band, B.lm, h->piv, d_wl, d_wu, s));
+    std::vector<int32_t> pwl(panels), pwu(panels);
+    if (panels) {
+      CK(cudaMemcpyAsync(pwl.data(), d_wl, sizeof(int32_t) * panels, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(pwu.data(), d_wu, sizeof(int32_t) * panels, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
     }
-    std::vector<TileMeta> tm(tiles);
+    // A sweep tile's widths cover those of its panels (offset by the
+    // panel's start within the tile).  The wide tile is taken when two ring
+    // stages of its largest tile fit beside the resident vectors.
+    std::vector<int32_t> wl, wu;
+    std::vector<TileMeta> tm;
     int64_t lofs = 0, uofs = 0, sofs = 0;
-    size_t max_tile = 0;
-    for (int t = 0; t < tiles; ++t) {
-      tm[t].lofs = lofs; tm[t].uofs = uofs; tm[t].sofs = sofs;
-      tm[t].wl = wl[t]; tm[t].wu = wu[t];
-      lofs += (int64_t)wl[t] * DD_NB;
-      uofs += (int64_t)DD_NB * wu[t];
-      sofs += round4(wl[t]);
-      max_tile = std::max(max_tile, std::max((size_t)wl[t] * DD_NB * sizeof(T) + (size_t)round4(wl[t]) * 4,
-                                             (size_t)DD_NB * wu[t] * sizeof(T)));
+    size_t max_tile = 0, smax = 0;
+    int tb = 0;
+    for (int cand : {DD_TB_WIDE, DD_NB}) {
+      tiles = 0;
+      int max_n = 0, max_t = 0;
+      for (int j = 0; j < m; ++j) {
+        BandInfo &b = info[j];
+        b.nst = (b.n + cand - 1) / cand;
+        b.tile0 = tiles;
+        tiles += b.nst;
+        max_n = std::max(max_n, b.nst * cand);
+        max_t = std::max(max_t, b.nst);
+      }
+      wl.assign(tiles, 0);
+      wu.assign(tiles, 0);
+      for (int j = 0; j < m; ++j) {
+        const BandInfo &b = info[j];
+        for (int t = 0; t < b.nst; ++t) {
+          int l = cand, u = cand;
+          for (int q = 0; q < cand / DD_NB; ++q) {
+            const int pn = t * (cand / DD_NB) + q;
+            if (pn >= b.ntiles) break;
+            l = std::max(l, q * DD_NB + pwl[b.panel0 + pn]);
+            u = std::max(u, q * DD_NB + pwu[b.panel0 + pn]);
+          }
+          wl[b.tile0 + t] = round4(l);
+          wu[b.tile0 + t] = round4(u);
+        }
+      }
+      tm.assign(tiles, TileMeta{});
+      lofs = uofs = sofs = 0;
+      max_tile = 0;
+      for (int t = 0; t < tiles; ++t) {
+        tm[t].lofs = lofs; tm[t].uofs = uofs; tm[t].sofs = sofs;
+        tm[t].wl = wl[t]; tm[t].wu = wu[t];
+        lofs += (int64_t)wl[t] * cand;
+        uofs += (int64_t)cand * wu[t];
+        sofs += round4(wl[t]);
+        max_tile = std::max(max_tile, std::max((size_t)wl[t] * cand * sizeof(T) + (size_t)round4(wl[t]) * 4,
+                                               (size_t)cand * wu[t] * sizeof(T)));
+      }
+      smax = band_sweep_max_stage(max_n, h->max_kl, h->max_ku2, sizeof(T), cand);
+      if (((max_tile + 127) & ~(size_t)127) <= smax || cand == DD_NB) {
+        tb = cand;
+        h->max_n = max_n;
+        h->max_tiles = max_t;
+        break;
+      }
     }
+    h->tb = tb;
+    h->stats.tile = tb;
     // stage: ~84 KiB, or one whole tile when a tile is larger; smaller when
     // two such stages do not fit beside the resident vectors
     size_t stage = std::max<size_t>(84 * 1024, max_tile);
     stage = (stage + 127) & ~(size_t)127;
-    const size_t smax = band_sweep_max_stage(h->max_n, h->max_kl, h->max_ku2, sizeof(T));
     if (stage > smax) stage = std::max((max_tile + 127) & ~(size_t)127, smax);
     h->max_tile = max_tile;
     h->h_info = info;
@@ -800,7 +845,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     TRY(dalloc(h, &B.utile, uofs));
     TRY(dalloc(h, &h->src, sofs));
     h->stats.factor_bytes = (lofs + uofs) * (int64_t)sizeof(T) + sofs * (int64_t)sizeof(int32_t);
-    CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tm, B.band, B.lm, h->piv,
+    CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tb, h->tm, B.band, B.lm, h->piv,
                             B.ltile, B.utile, h->src, s));
   }
   // ---- couplings E (interior x interface) and F (interface x interior)
@@ -933,7 +978,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(cudaMemsetAsync(B.X, 0, sizeof(T) * std::max<int64_t>(xoff[m], 1), s));
     CK(launch_scatter_coo<T>((int64_t)xidx.size(), d_xidx, d_xval, B.X, s));
     // X_j = A_jj^-1 E(I_j, gam_j)
-    CK(launch_band_solve_multi<T>(h->d_info, m, d_ncols, d_xoff, max_gam, h->max_kl, h->max_ku2,
+    CK(launch_band_solve_multi<T>(h->d_info, m, d_ncols, d_xoff, max_gam, h->max_kl, h->max_ku2, h->tb,
                                   h->tm, B.ltile, B.utile, h->src, B.X, s));
     // S(R_a,R_a) -= F(R_a, I_j) X_j
     CK(launch_schur_accumulate<T>(m, d_fr_ptr, d_fr_row, d_fr_agg, d_fs_ptr, d_fs_col, B.fsub_val,
@@ -1075,7 +1120,7 @@ dd_status alloc_krylov(DDHandle *h, int R) {
   TRY(dalloc(h, &h->hc2, (size_t)S * (R + 2)));
   TRY(dalloc(h, &h->nsq, 4));
   TRY(dalloc(h, &h->out, (size_t)S * 4));
-  h->cgs_blocks = cgs2_blocks(304);
+  h->cgs_blocks = cgs2_blocks(h->krylov_per_sm, 1024);
   if (h->cgs_blocks <= 0) { h->err = "no resident blocks for the cooperative CGS2 kernel"; return DD_ERR_CUDA; }
   TRY(dalloc(h, &h->partial, 3 * (size_t)std::max(h->nblocks, h->cgs_blocks) * (R + 2)));
   TRY(dalloc(h, &h->r, h->ldv));
@@ -1484,8 +1529,8 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
   float best_ms = 1e30f;
   int tried = 0;
   for (size_t st : cand) {
-    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, 8 * DD_NB, sizeof(T), (uint32_t)st) < 2) continue;
-    if (band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, 8 * DD_NB, (uint32_t)st) <= 0) continue;
+    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, 8 * h->tb, sizeof(T), (uint32_t)st) < 2) continue;
+    if (band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, 8 * h->tb, (uint32_t)st) <= 0) continue;
     dd_status rc = set_sweep_plan<T>(h, st);
     if (rc != DD_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     float tmin = 1e30f;
@@ -1527,6 +1572,7 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->prec = o.prec;
   h->kind = approx;
   h->use_graph = o.use_graph != 0;
+  h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : 2;
   const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
   const int R = o.max_restart > 0 ? o.max_restart : 50;
   if (R > 120) { h->err = "max_restart must be <= 120"; return DD_ERR_INVALID_ARG; }

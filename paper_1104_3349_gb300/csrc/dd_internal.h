@@ -11,17 +11,24 @@
 
 // Tile width of the blocked band sweeps: one warp owns a tile's columns.
 #define DD_NB 32
+// Columns of a sweep tile: 64 (two LU panels, so a sweep takes half as many
+// dependent tile steps) when two ring stages of such tiles fit in shared
+// memory beside the resident vectors, else 32 (one panel).  Chosen per
+// handle at setup; the sweep kernels run 8 threads per tile row.
+#define DD_TB_WIDE 64
 
 // Per-subdomain geometry of the interior factors (device-visible).
 struct BandInfo {
   int32_t n;        // rows of A_jj
   int32_t kl, ku;   // lower / upper bandwidth of A_jj in its local order
-  int32_t ntiles;   // ceil(n / DD_NB)
+  int32_t ntiles;   // LU panels: ceil(n / DD_NB)
+  int32_t nst;      // sweep tiles: ceil(n / tile width)
+  int32_t panel0;   // index of the first panel in the per-panel width tables
   int64_t band_off; // band rows (elements): row i at band_off + i*wd
   int64_t lraw_off; // the LU's per-tile multipliers, (NB+kl) x NB column-major each
   int64_t piv_off;  // pivots (n entries)
   int32_t row0;     // first row in the permuted interior numbering
-  int32_t tile0;    // index of the first tile in the packed tile tables
+  int32_t tile0;    // index of the first sweep tile in the packed tile tables
   int32_t jf0, njf; // forward jobs [jf0, jf0 + njf) of the sweep ring
   int32_t jb0, njb; // backward jobs
 };
@@ -96,7 +103,7 @@ struct Workspace;  // defined in dd_api.cu
 int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
                       uint32_t stage_bytes);
 // largest stage size that leaves room for two stages (0: the vectors alone do not fit)
-size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size);
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb);
 // Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
 // column-major, exchanged), wscratch holds the windows when they do not fit
 // in shared memory (band_lu_window_bytes per subdomain, else unused).
@@ -113,11 +120,11 @@ int band_lu_occupancy(int max_kl, int max_ku, int threads);
 // Widths of every tile (forward rows wl and backward columns wu that hold
 // nonzeros after the factorisation), written to wl/wu at tile0 + t.
 template <typename T>
-cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_tiles, const T *band,
+cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_panels, const T *band,
                                const T *lraw, const int32_t *piv, int32_t *wl, int32_t *wu,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
+cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl, int tb,
                               const TileMeta *tm, const T *band, const T *lraw, const int32_t *piv,
                               T *ltile, T *utile, int32_t *src, cudaStream_t s);
 // z = A_jj^-1 y_j per subdomain; y gathered through perm (original
@@ -143,7 +150,7 @@ int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32
 // at x_off[j], ncols[j] columns.
 template <typename T>
 cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t *ncols,
-                                    const int64_t *x_off, int max_cols, int max_kl, int max_ku2,
+                                    const int64_t *x_off, int max_cols, int max_kl, int max_ku2, int tb,
                                     const TileMeta *tm, const T *ltile, const T *utile,
                                     const int32_t *src, T *X, cudaStream_t s);
 
@@ -212,7 +219,7 @@ cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
 // One Arnoldi orthogonalisation step (CGS2 + Givens + normalisation) as a
 // single cooperative kernel; partial holds nblocks * pk doubles, pk >= R + 2.
-int cgs2_blocks(int cap);
+int cgs2_blocks(int per_sm, int cap);
 cudaError_t launch_cgs2(int64_t n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
                         int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
                         const double *bn2, double *scal, const SegMap &sm, int nblocks, cudaStream_t s);

@@ -8,16 +8,20 @@
 //   lraw   per tile of DD_NB = 32 columns, the multipliers in the row order
 //          after the tile's exchanges, (NB+kl) x NB column-major
 //   piv    row exchanged with k at step k
-// Packed sweep tiles (TileMeta), trimmed to the rows / columns that hold
-// nonzeros after the factorisation:
-//   forward tile t, window rows c0 .. c0+wl-1 (c0 = t*NB):
+// Packed sweep tiles (TileMeta) of TB = 64 columns (two LU panels) in FP32
+// and 32 in FP64, trimmed to the rows / columns that hold nonzeros after the
+// factorisation:
+//   forward tile t, window rows c0 .. c0+wl-1 (c0 = t*TB):
 //     src[q]   window position whose value moves to q once the tile's row
-//              exchanges are applied in order
-//     K        wl x NB: rows 0..NB-1 hold Linv, the inverse of the tile's
-//              unit lower triangle L11; rows NB.. hold -L21 Linv.  The tile
-//              step is w <- [0; w_B] + K w_T on the exchanged window w.
-//   backward tile t, rows r0 .. r0+NB-1:
-//     Kb       NB x wu: [Uinv | -Uinv U12], Uinv the inverse of the tile's
+//              exchanges (both panels', in order) are applied
+//     K        wl x TB: rows 0..TB-1 hold Linv, the inverse of the tile's
+//              unit lower triangle L11; rows TB.. hold -L21 Linv.  L is in
+//              the row order after all of the tile's exchanges (the second
+//              panel's exchanges also move the first panel's multipliers).
+//              The tile step is w <- [0; w_B] + K w_T on the exchanged
+//              window w.
+//   backward tile t, rows r0 .. r0+TB-1:
+//     Kb       TB x wu: [Uinv | -Uinv U12], Uinv the inverse of the tile's
 //              upper triangle, so x_T = Kb [b_T; x_next].
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,7 +36,7 @@ __host__ __device__ inline int src_stride_w(int w) { return round4(w); }
 // zero padding beyond the tiles of the resident vectors: room for the
 // widest window or row of a tile, a multiple of 32 elements
 __host__ __device__ inline int sweep_pad_hd(int max_kl, int max_ku2) {
-  return ((max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_NB + 31) & ~31;
+  return ((max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_TB_WIDE + 31) & ~31;
 }
 
 template <typename T>
@@ -43,10 +47,10 @@ __device__ void set_status(DevStatus *st, int code, int block) {
 }
 
 // element (r, c) of a forward tile K (row-major, 16-byte chunks swizzled by row)
-template <typename T>
+template <typename T, int TB>
 __host__ __device__ __forceinline__ int kidx(int r, int c) {
   constexpr int CH = 16 / sizeof(T);
-  return r * DD_NB + (((c / CH) ^ (r & 7)) * CH) + (c % CH);
+  return r * TB + (((c / CH) ^ (r & 7)) * CH) + (c % CH);
 }
 
 // ---------------------------------------------------------------------------
@@ -231,18 +235,19 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
 
 // ---------------------------------------------------------------------------
 // Tile widths, one warp per (subdomain, tile):
-//   wl = rows of the forward window that the tile touches: the last nonzero
-//        multiplier row of any of its columns, and every pivot row, at
-//        least NB, rounded up to 4;
-//   wu = NB + the columns right of the tile that its U rows reach, rounded
+//   wl = rows of the forward window that the panel touches: the last
+//        nonzero multiplier row of any of its columns, and every pivot row,
+//        at least NB, rounded up to 4;
+//   wu = NB + the columns right of the panel that its U rows reach, rounded
 //        up to 4.
+// The host combines the two panels of a sweep tile.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void tile_widths_kernel(const BandInfo *__restrict__ info, const T *__restrict__ band,
                                    const T *__restrict__ lraw, const int32_t *__restrict__ piv,
                                    int32_t *wl, int32_t *wu) {
   const BandInfo b = info[blockIdx.x];
-  const int t = blockIdx.y;
+  const int t = blockIdx.y;  // LU panel
   if (t >= b.ntiles) return;
   const int n = b.n, kl = b.kl, wd = 2 * b.kl + b.ku + 1, W = DD_NB + kl;
   const int c0 = t * DD_NB, lane = threadIdx.x;
@@ -262,124 +267,137 @@ __global__ void tile_widths_kernel(const BandInfo *__restrict__ info, const T *_
     eu = max(eu, __shfl_xor_sync(0xffffffffu, eu, o));
   }
   if (lane == 0) {
-    wl[b.tile0 + t] = round4(el + 1);
-    wu[b.tile0 + t] = round4(DD_NB + max(eu + 1, 0));
+    wl[b.panel0 + t] = round4(el + 1);
+    wu[b.panel0 + t] = round4(DD_NB + max(eu + 1, 0));
   }
 }
 
 // ---------------------------------------------------------------------------
-// Packed sweep tiles: one warp per (subdomain, tile); lane = tile column / row.
+// Packed sweep tiles: TB threads per (subdomain, tile); thread c is tile
+// column c (forward) and tile row c (backward).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void band_tiles_kernel(const BandInfo *__restrict__ info, const TileMeta *__restrict__ tm,
-                                  const T *__restrict__ band, const T *__restrict__ lraw,
-                                  const int32_t *__restrict__ piv, T *ltile, T *utile,
-                                  int32_t *srcs) {
+template <typename T, int TB>
+__global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restrict__ info,
+                                                           const TileMeta *__restrict__ tm,
+                                                           const T *__restrict__ band,
+                                                           const T *__restrict__ lraw,
+                                                           const int32_t *__restrict__ piv, T *ltile,
+                                                           T *utile, int32_t *srcs) {
   const BandInfo b = info[blockIdx.x];
   const int t = blockIdx.y;
-  if (t >= b.ntiles) return;
+  if (t >= b.nst) return;
   const TileMeta mt = tm[b.tile0 + t];
   const int n = b.n, kl = b.kl, ku2 = b.kl + b.ku, wd = 2 * b.kl + b.ku + 1;
-  const int W = DD_NB + kl, WL = mt.wl, WU = mt.wu;
-  const int c0 = t * DD_NB;
-  const int lane = threadIdx.x;
+  const int W = DD_NB + kl;   // window of one LU panel
+  const int W2 = TB + kl;  // window of the tile
+  const int WL = mt.wl, WU = mt.wu;
+  const int c0 = t * TB;
+  const int tid = threadIdx.x;
+  const int cend = min(c0 + TB, n);
   const int32_t *P = piv + b.piv_off;
   const T *A = band + b.band_off;
   T *K = ltile + mt.lofs;
   T *Kb = utile + mt.uofs;
   int32_t *src = srcs + mt.sofs;
   extern __shared__ __align__(128) unsigned char smraw[];
-  T *L11 = reinterpret_cast<T *>(smraw);  // NB x NB, [row][col]
-  T *vbuf = L11 + DD_NB * DD_NB;          // 32 columns x W
-  T *Lsm = vbuf + (size_t)DD_NB * W;      // NB x NB
-  int32_t *idx = reinterpret_cast<int32_t *>(Lsm + DD_NB * DD_NB);
+  T *L11 = reinterpret_cast<T *>(smraw);    // TB x TB
+  T *vbuf = L11 + TB * TB;            // TB columns x W2
+  T *Lsm = vbuf + (size_t)TB * W2;       // TB x TB
+  int32_t *idx = reinterpret_cast<int32_t *>(Lsm + TB * TB);
 
-  // (1) composite window permutation of the tile's row exchanges
-  if (lane == 0) {
-    for (int q = 0; q < W; ++q) idx[q] = q;
-    for (int c = c0; c < c0 + DD_NB && c < n; ++c) {
-      int a = c - c0, bq = P[c] - c0;
-      int tmp = idx[a]; idx[a] = idx[bq]; idx[bq] = tmp;
+  // (1) composite window permutation of all the tile's row exchanges
+  if (tid == 0) {
+    for (int q = 0; q < W2; ++q) idx[q] = q;
+    for (int c = c0; c < cend; ++c) {
+      const int a = c - c0, bq = P[c] - c0;
+      const int tmp = idx[a]; idx[a] = idx[bq]; idx[bq] = tmp;
     }
   }
-  __syncwarp();
-  for (int q = lane; q < src_stride_w(WL); q += 32) src[q] = (q < W) ? idx[q] : q;
-
-  // (2) multipliers of column c0+lane (already in the exchanged row order)
+  // (2) multipliers of column tid in the tile's final row order: the panel's
+  // own (already exchanged), then the exchanges of the tile's later panels
   {
-    T *v = vbuf + (size_t)lane * W;
-    const T *lr = lraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b) + (int64_t)lane * W;
-    for (int q = 0; q < W; ++q) v[q] = lr[q];
-    for (int q = 0; q < DD_NB; ++q) L11[q * DD_NB + lane] = (q == lane) ? T(1) : (q > lane ? v[q] : T(0));
+    T *v = vbuf + (size_t)tid * W2;
+    for (int q = 0; q < W2; ++q) v[q] = T(0);
+    const int pr = tid / DD_NB, cc = tid % DD_NB, po = pr * DD_NB;
+    const int pnl = t * (TB / DD_NB) + pr;
+    if (pnl < b.ntiles) {
+      const T *lr = lraw + b.lraw_off + (int64_t)pnl * bi_lraw_elems(b) + (int64_t)cc * W;
+      for (int q = 0; q < W; ++q) v[po + q] = lr[q];
+    }
+    for (int c2 = c0 + po + DD_NB; c2 < cend; ++c2) {
+      const int a = c2 - c0, bq = P[c2] - c0;
+      const T tmp = v[a]; v[a] = v[bq]; v[bq] = tmp;
+    }
   }
-  __syncwarp();
-  // (3) Linv (column `lane`), then K = [Linv; -L21 Linv] for rows < WL
+  __syncthreads();
+  for (int q = tid; q < src_stride_w(WL); q += TB) src[q] = (q < W2) ? idx[q] : q;
+  for (int q = 0; q < TB; ++q)
+    L11[q * TB + tid] = (q == tid) ? T(1) : (q > tid ? vbuf[(size_t)tid * W2 + q] : T(0));
+  __syncthreads();
+  // (3) Linv (column tid), then K = [Linv; -L21 Linv] for rows < WL
   {
-    T x[DD_NB];
-#pragma unroll
-    for (int q = 0; q < DD_NB; ++q) x[q] = T(0);
-    x[lane] = T(1);
-    for (int q = lane + 1; q < DD_NB; ++q) {
-      T s = T(0);
-      for (int r = lane; r < q; ++r) s += L11[q * DD_NB + r] * x[r];
-      x[q] = -s;
+    T x[TB];
+    for (int q = 0; q < TB; ++q) x[q] = T(0);
+    x[tid] = T(1);
+    for (int q = tid + 1; q < TB; ++q) {
+      T sacc = T(0);
+      for (int r = tid; r < q; ++r) sacc += L11[q * TB + r] * x[r];
+      x[q] = -sacc;
     }
-    for (int q = 0; q < DD_NB; ++q) {
-      K[kidx<T>(q, lane)] = x[q];
-      Lsm[q * DD_NB + lane] = x[q];
+    for (int q = 0; q < TB; ++q) {
+      K[kidx<T, TB>(q, tid)] = x[q];
+      Lsm[q * TB + tid] = x[q];
     }
   }
-  __syncwarp();
-  for (int r = DD_NB; r < WL; ++r) {
-    T s = T(0);
-    if (r < W)
-      for (int k = 0; k < DD_NB; ++k) s += vbuf[(size_t)k * W + r] * Lsm[k * DD_NB + lane];
-    K[kidx<T>(r, lane)] = -s;
+  __syncthreads();
+  for (int r = TB; r < WL; ++r) {
+    T sacc = T(0);
+    if (r < W2)
+      for (int k = 0; k < TB; ++k) sacc += vbuf[(size_t)k * W2 + r] * Lsm[k * TB + tid];
+    K[kidx<T, TB>(r, tid)] = -sacc;
   }
-  __syncwarp();
+  __syncthreads();
   // (4) U11 (row-major in L11's buffer) and its inverse; Kb = [Uinv | -Uinv U12]
   {
-    const int r = c0 + lane;  // row of this lane
-    for (int c = 0; c < DD_NB; ++c) {
+    const int r = c0 + tid;  // row of this thread
+    for (int c = 0; c < TB; ++c) {
       T v = T(0);
       if (r < n) {
-        int col = c0 + c;
-        int off = col - r + kl;
-        if (c >= lane && col < n && off < wd) v = A[(int64_t)r * wd + off];
-      } else if (c == lane) {
+        const int col = c0 + c, off = col - r + kl;
+        if (c >= tid && col < n && off < wd) v = A[(int64_t)r * wd + off];
+      } else if (c == tid) {
         v = T(1);
       }
-      L11[lane * DD_NB + c] = v;
+      L11[tid * TB + c] = v;
     }
   }
-  __syncwarp();
+  __syncthreads();
   {
-    T x[DD_NB];
-#pragma unroll
-    for (int q = 0; q < DD_NB; ++q) x[q] = T(0);
-    x[lane] = T(1) / L11[lane * DD_NB + lane];
-    for (int q = lane - 1; q >= 0; --q) {
-      T s = T(0);
-      for (int r = q + 1; r <= lane; ++r) s += L11[q * DD_NB + r] * x[r];
-      x[q] = -s / L11[q * DD_NB + q];
+    T x[TB];
+    for (int q = 0; q < TB; ++q) x[q] = T(0);
+    x[tid] = T(1) / L11[tid * TB + tid];
+    for (int q = tid - 1; q >= 0; --q) {
+      T sacc = T(0);
+      for (int r = q + 1; r <= tid; ++r) sacc += L11[q * TB + r] * x[r];
+      x[q] = -sacc / L11[q * TB + q];
     }
-    for (int q = 0; q < DD_NB; ++q) Lsm[q * DD_NB + lane] = x[q];  // Uinv(q, lane)
+    for (int q = 0; q < TB; ++q) Lsm[q * TB + tid] = x[q];  // Uinv(q, tid)
   }
-  __syncwarp();
+  __syncthreads();
   {
-    T *kr = Kb + (int64_t)lane * WU;
-    for (int c = 0; c < DD_NB; ++c) kr[c] = Lsm[lane * DD_NB + c];
-    for (int q = 0; q < WU - DD_NB; ++q) {
-      const int col = c0 + DD_NB + q;
-      T s = T(0);
+    T *kr = Kb + (int64_t)tid * WU;
+    for (int c = 0; c < TB; ++c) kr[c] = Lsm[tid * TB + c];
+    for (int q = 0; q < WU - TB; ++q) {
+      const int col = c0 + TB + q;
+      T sacc = T(0);
       if (col < n && q < ku2)
-        for (int k = lane; k < DD_NB; ++k) {
+        for (int k = tid; k < TB; ++k) {
           const int rk = c0 + k;
           if (rk >= n) break;
           const int off = col - rk + kl;
-          if (off < wd) s += Lsm[lane * DD_NB + k] * A[(int64_t)rk * wd + off];
+          if (off < wd) sacc += Lsm[tid * TB + k] * A[(int64_t)rk * wd + off];
         }
-      kr[DD_NB + q] = -s;
+      kr[TB + q] = -sacc;
     }
   }
 }
@@ -434,7 +452,7 @@ __device__ __forceinline__ SweepJob get_job(const BandInfo &b, const SweepJob *j
   return jobs[fwd ? b.jf0 + q : b.jb0 + (q - b.njf)];
 }
 
-template <typename T>
+template <typename T, int TB>
 __device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                           int q, const T *ltile, const T *utile, const int32_t *srcs,
                                           unsigned char *stage, uint64_t *bar) {
@@ -443,14 +461,14 @@ __device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm,
   const TileMeta &a = tm[b.tile0 + jb.lo];
   if (fwd) {
     const TileMeta &z = tm[b.tile0 + jb.hi - 1];
-    const uint32_t lb = (uint32_t)((z.lofs + (int64_t)z.wl * DD_NB - a.lofs) * sizeof(T));
+    const uint32_t lb = (uint32_t)((z.lofs + (int64_t)z.wl * TB - a.lofs) * sizeof(T));
     const uint32_t sb = (uint32_t)((z.sofs + src_stride_w(z.wl) - a.sofs) * sizeof(int32_t));
     mbar_expect_tx(bar, lb + sb);
     bulk_g2s(stage, ltile + a.lofs, lb, bar);
     bulk_g2s(stage + lb, srcs + a.sofs, sb, bar);
   } else {
     const TileMeta &z = tm[b.tile0 + jb.hi - 1];
-    const uint32_t ub = (uint32_t)((z.uofs + (int64_t)DD_NB * z.wu - a.uofs) * sizeof(T));
+    const uint32_t ub = (uint32_t)((z.uofs + (int64_t)TB * z.wu - a.uofs) * sizeof(T));
     mbar_expect_tx(bar, ub);
     bulk_g2s(stage, utile + a.uofs, ub, bar);
   }
@@ -481,29 +499,37 @@ struct Chunk<double> {
   }
 };
 
+// The first nstages jobs of a task into their stages (thread 0); the stages
+// were last read by generic loads of the previous task.
+template <typename T, int TB>
+__device__ __forceinline__ void issue_first_jobs(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
+                                                 const T *ltile, const T *utile, const int32_t *srcs,
+                                                 unsigned char *ring, uint32_t stage_bytes, int nstages,
+                                                 uint64_t *bars, uint32_t jbase) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const int nj = b.njf + b.njb;
+  for (int q = 0; q < nstages && q < nj; ++q) {
+    const int sq = (int)((jbase + q) % nstages);
+    issue_job<T, TB>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq]);
+  }
+}
+
 // Forward sweep in place over vec, backward sweep from vec into xout (both in
 // shared memory, length >= ntiles*NB + pad, xout zero beyond the tiles).
 // Returns false if a wait expired.
-template <typename T>
+template <typename T, int TB>
 __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ tm,
                                 const SweepJob *__restrict__ jobs, const T *__restrict__ ltile,
                                 const T *__restrict__ utile, const int32_t *__restrict__ srcs,
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
-                                uint32_t &jbase, int task, DevStatus *st) {
+                                uint32_t &jbase, int task, bool issued, DevStatus *st) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nj = b.njf + b.njb;
   // job q of this task is job jbase + q of the CTA: its stage and phase
-  if (tid == 0) {
-    // the stages were last read by generic loads of the previous task
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int q = 0; q < nstages && q < nj; ++q) {
-      const int sq = (int)((jbase + q) % nstages);
-      issue_job<T>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq]);
-    }
-  }
+  if (tid == 0 && !issued) issue_first_jobs<T, TB>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
   bool ok = true;
   int q = 0;
   for (; q < nj; ++q) {
@@ -518,26 +544,28 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     const TileMeta &a = tm[b.tile0 + jb.lo];
     if (fwd) {
       const TileMeta &z = tm[b.tile0 + jb.hi - 1];
-      const size_t kbytes = (size_t)(z.lofs + (int64_t)z.wl * DD_NB - a.lofs) * sizeof(T);
+      const size_t kbytes = (size_t)(z.lofs + (int64_t)z.wl * TB - a.lofs) * sizeof(T);
       for (int t = jb.lo; t < jb.hi; ++t) {
         // forward tile t: w <- [0; w_B] + K w_T on the exchanged window
         const TileMeta &mt = tm[b.tile0 + t];
-        const int c0 = t * DD_NB, WL = mt.wl;
+        const int c0 = t * TB, WL = mt.wl;
         const T *K = reinterpret_cast<const T *>(stage + (mt.lofs - a.lofs) * sizeof(T));
         const int32_t *src = reinterpret_cast<const int32_t *>(stage + kbytes) + (mt.sofs - a.sofs);
         if (got)
           for (int e = tid; e < WL; e += nt) win[e] = vec[c0 + src[e]];
         if (!__syncthreads_and(got)) { ok = false; break; }
         for (int r = tid; r < WL; r += nt) {
-          const CV *kr = reinterpret_cast<const CV *>(K + r * DD_NB);
+          const CV *kr = reinterpret_cast<const CV *>(K + r * TB);
           const CV *wv = reinterpret_cast<const CV *>(win);
-          T a0 = (r < DD_NB) ? T(0) : win[r], a1 = T(0);
+          T a0 = (r < TB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
 #pragma unroll
-          for (int ch = 0; ch < DD_NB / CN; ch += 2) {
+          for (int ch = 0; ch < TB / CN; ch += 4) {
             a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
             a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
+            a2 = Chunk<T>::fmadd(kr[(ch + 2) ^ (r & 7)], wv[ch + 2], a2);
+            a3 = Chunk<T>::fmadd(kr[(ch + 3) ^ (r & 7)], wv[ch + 3], a3);
           }
-          vec[c0 + r] = a0 + a1;
+          vec[c0 + r] = (a0 + a1) + (a2 + a3);
         }
         __syncthreads();
       }
@@ -545,9 +573,9 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     } else {
       for (int t = jb.hi - 1; t >= jb.lo; --t) {
         // backward tile t: x_T = Kb [b_T; x_next]; 8 threads per output row;
-        // the outputs xout[r0..r0+NB) never overlap this tile's inputs
+        // the outputs xout[r0..r0+TB) never overlap this tile's inputs
         const TileMeta &mt = tm[b.tile0 + t];
-        const int r0 = t * DD_NB, WU = mt.wu, nch = WU / CN;
+        const int r0 = t * TB, WU = mt.wu, nch = WU / CN;
         const T *Kb = reinterpret_cast<const T *>(stage + (mt.uofs - a.uofs) * sizeof(T));
         const int i = tid >> 3, h = tid & 7;
         T acc = T(0);
@@ -557,7 +585,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
           const CV *xv = reinterpret_cast<const CV *>(xout + r0);
           T a0 = T(0), a1 = T(0);
           int ch = h;
-          for (; ch < DD_NB / CN; ch += 8) a0 = Chunk<T>::fmadd(kr[ch], bv[ch], a0);
+          for (; ch < TB / CN; ch += 8) a0 = Chunk<T>::fmadd(kr[ch], bv[ch], a0);
           for (; ch + 8 < nch; ch += 16) {
             a0 = Chunk<T>::fmadd(kr[ch], xv[ch], a0);
             a1 = Chunk<T>::fmadd(kr[ch + 8], xv[ch + 8], a1);
@@ -576,7 +604,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     // the stage is free; vec / xout are current
     if (tid == 0 && q + nstages < nj) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_job<T>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
+      issue_job<T, TB>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
     }
   }
   if (!ok) {
@@ -596,7 +624,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
 }
 
 // shared-memory layout: [bars | vec | xout | win | tile table | job table | ring]
-template <typename T>
+template <typename T, int TB>
 __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, int max_kl,
                                       int max_tiles, int max_jobs, uint64_t *&bars, T *&vec,
                                       T *&xout, T *&win, TileMeta *&tms, SweepJob *&jbs,
@@ -605,7 +633,7 @@ __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, 
   vec = reinterpret_cast<T *>(smraw + 64);
   xout = vec + max_n + pad;
   win = xout + max_n + pad;
-  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + DD_NB + max_kl + 8);
+  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + TB + max_kl + 8);
   used = (used + 15) & ~(size_t)15;
   tms = reinterpret_cast<TileMeta *>(smraw + used);
   used += sizeof(TileMeta) * (size_t)max_tiles;
@@ -620,7 +648,7 @@ __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, 
 __device__ __forceinline__ BandInfo stage_tables(BandInfo b, const TileMeta *__restrict__ tm,
                                                  const SweepJob *__restrict__ jobs, TileMeta *tms,
                                                  SweepJob *jbs) {
-  for (int t = threadIdx.x; t < b.ntiles; t += blockDim.x) tms[t] = tm[b.tile0 + t];
+  for (int t = threadIdx.x; t < b.nst; t += blockDim.x) tms[t] = tm[b.tile0 + t];
   for (int q = threadIdx.x; q < b.njf; q += blockDim.x) jbs[q] = jobs[b.jf0 + q];
   for (int q = threadIdx.x; q < b.njb; q += blockDim.x) jbs[b.njf + q] = jobs[b.jb0 + q];
   b.tile0 = 0;
@@ -645,7 +673,7 @@ __device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, in
 }
 
 // z = A_jj^-1 y_j with y gathered from the original numbering.
-template <typename T>
+template <typename T, int TB>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -661,7 +689,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
-  carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
   init_bars(bars, nstages);
   int t0, t1;
   task_range(sched_off, t0, t1);
@@ -672,21 +700,23 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     if (bg.n == 0 || (act && !act[task_sys[task]])) continue;  // empty, or its system is done
     __syncthreads();  // the previous task's reads of the tables and vectors are done
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
-    const int ntot = b.ntiles * DD_NB + pad;
+    __syncthreads();  // the tables are staged: start the first copies, then gather y
+    if (threadIdx.x == 0) issue_first_jobs<T, TB>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
+    const int ntot = b.nst * TB + pad;
     for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
       vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
       xout[i] = T(0);
     }
     __syncthreads();
-    if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, st))
+    if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
+                            nstages, bars, jbase, task, true, st))
       return;
     for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
   }
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
-template <typename T>
+template <typename T, int TB>
 __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -705,7 +735,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
-  carve<T>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
   init_bars(bars, nstages);
   int t0, t1;
   task_range(sched_off, t0, t1);
@@ -716,7 +746,9 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     if (bg.n == 0 || (act && !act[task_sys[task]])) continue;
     __syncthreads();
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
-    const int ntot = b.ntiles * DD_NB + pad;
+    __syncthreads();
+    if (threadIdx.x == 0) issue_first_jobs<T, TB>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
+    const int ntot = b.nst * TB + pad;
     for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
       T v = T(0);
       if (i < b.n) {
@@ -727,8 +759,8 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
       xout[i] = T(0);
     }
     __syncthreads();
-    if (!sweep_pipelined<T>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, st))
+    if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
+                            nstages, bars, jbase, task, true, st))
       return;
     for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
       const int r = b.row0 + i;
@@ -742,7 +774,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
 // chunk of NR columns per CTA; X column-major (leading dimension n_j) in
 // global memory, the tile windows staged in shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, int NR>
+template <typename T, int NR, int TB>
 __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
                                         const int32_t *__restrict__ ncols,
                                         const int64_t *__restrict__ x_off,
@@ -760,9 +792,9 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
   T *win = reinterpret_cast<T *>(smraw);  // max(wl, wu) x NR, [row][r]
   const int tid = threadIdx.x, nt = blockDim.x;
   // forward: X(window) <- [0; X_B] + K X_T on the exchanged window
-  for (int t = 0; t < b.ntiles; ++t) {
+  for (int t = 0; t < b.nst; ++t) {
     const TileMeta mt = tm[b.tile0 + t];
-    const int c0 = t * DD_NB, WL = mt.wl;
+    const int c0 = t * TB, WL = mt.wl;
     const int32_t *src = srcs + mt.sofs;
     const T *K = ltile + mt.lofs;
     for (int e = tid; e < WL * NR; e += nt) {
@@ -773,16 +805,16 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
     __syncthreads();
     for (int e = tid; e < WL * NR; e += nt) {
       int i = e / NR, r = e % NR;
-      T acc = (i < DD_NB) ? T(0) : win[e];
-      for (int c = 0; c < DD_NB; ++c) acc += K[kidx<T>(i, c)] * win[c * NR + r];
+      T acc = (i < TB) ? T(0) : win[e];
+      for (int c = 0; c < TB; ++c) acc += K[kidx<T, TB>(i, c)] * win[c * NR + r];
       if (c0 + i < n && r < nr) X[(int64_t)r * n + c0 + i] = acc;
     }
     __syncthreads();
   }
   // backward: X_T <- Kb [X_T; X_next]
-  for (int t = b.ntiles - 1; t >= 0; --t) {
+  for (int t = b.nst - 1; t >= 0; --t) {
     const TileMeta mt = tm[b.tile0 + t];
-    const int r0 = t * DD_NB, WU = mt.wu;
+    const int r0 = t * TB, WU = mt.wu;
     const T *Kb = utile + mt.uofs;
     for (int e = tid; e < WU * NR; e += nt) {
       int q = e / NR, r = e % NR;
@@ -790,7 +822,7 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
       win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < DD_NB * NR; e += nt) {
+    for (int e = tid; e < TB * NR; e += nt) {
       int i = e / NR, r = e % NR;
       T acc = T(0);
       for (int k = 0; k < WU; ++k) acc += Kb[(int64_t)i * WU + k] * win[k * NR + r];
@@ -811,22 +843,25 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, int max_tiles,
+static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, int tb, int max_tiles,
                                int max_jobs) {
   const int pad = sweep_pad_hd(max_kl, max_ku2);
-  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + DD_NB + max_kl + 8);
+  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + tb + max_kl + 8);
   used = (used + 15) & ~(size_t)15;
   used += sizeof(TileMeta) * (size_t)max_tiles + sizeof(SweepJob) * (size_t)max_jobs;
   return (used + 127) & ~(size_t)127;
 }
 #define DD_SMEM_LIMIT (227 * 1024)
 #define DD_MAX_STAGES 4
+// stages of the ring at this stage size (0: two do not fit); the sweeps
+// run 8 threads per tile row, so the tile width is threads / 8
 int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
                       uint32_t stage_bytes) {
-  (void)threads;
-  // tables: at most max_n / NB tiles and twice as many jobs
-  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, max_n / DD_NB,
-                                 2 * (max_n / DD_NB));
+  const int tb = threads / 8;
+  if (tb != 32 && tb != 64) return 0;
+  // tables: at most max_n / tb tiles and twice as many jobs
+  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, max_n / tb,
+                                 2 * (max_n / tb));
   if (stage_bytes == 0 || base + 2 * (size_t)stage_bytes > DD_SMEM_LIMIT) return 0;
   int s = (int)((DD_SMEM_LIMIT - base) / stage_bytes);
   return s > DD_MAX_STAGES ? DD_MAX_STAGES : s;
@@ -835,9 +870,9 @@ int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_
 #define DD_LU_SMEM (200 * 1024)
 // largest ring stage (multiple of 128 bytes) that still leaves room for two
 // stages next to the resident vectors and tables; 0 if none does
-size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size) {
-  const size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, max_n / DD_NB,
-                                       2 * (max_n / DD_NB));
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb) {
+  const size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, max_n / tb,
+                                       2 * (max_n / tb));
   if (base >= DD_SMEM_LIMIT) return 0;
   return ((DD_SMEM_LIMIT - base) / 2) & ~(size_t)127;
 }
@@ -873,24 +908,51 @@ int band_lu_occupancy(int max_kl, int max_ku, int threads) {
 }
 
 template <typename T>
-cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_tiles, const T *band,
+cudaError_t launch_tile_widths(const BandInfo *d_info, int m, int max_panels, const T *band,
                                const T *lraw, const int32_t *piv, int32_t *wl, int32_t *wu,
                                cudaStream_t s) {
-  if (m <= 0 || max_tiles <= 0) return cudaSuccess;
-  tile_widths_kernel<T><<<dim3(m, max_tiles), 32, 0, s>>>(d_info, band, lraw, piv, wl, wu);
+  if (m <= 0 || max_panels <= 0) return cudaSuccess;
+  tile_widths_kernel<T><<<dim3(m, max_panels), 32, 0, s>>>(d_info, band, lraw, piv, wl, wu);
+  return cudaGetLastError();
+}
+
+template <typename T, int TB>
+static cudaError_t tiles_tb(const BandInfo *d_info, int m, int max_tiles, int max_kl, const TileMeta *tm,
+                            const T *band, const T *lraw, const int32_t *piv, T *ltile, T *utile,
+                            int32_t *src, cudaStream_t s) {
+  const int W = TB + max_kl;
+  const size_t smem = sizeof(T) * (size_t)(2 * TB * TB + TB * W) + sizeof(int32_t) * (size_t)W;
+  cudaError_t e = ensure_smem(band_tiles_kernel<T, TB>, smem);
+  if (e != cudaSuccess) return e;
+  band_tiles_kernel<T, TB><<<dim3(m, max_tiles), TB, smem, s>>>(d_info, tm, band, lraw, piv, ltile, utile, src);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl,
+cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int max_kl, int tb,
                               const TileMeta *tm, const T *band, const T *lraw, const int32_t *piv,
                               T *ltile, T *utile, int32_t *src, cudaStream_t s) {
   if (m <= 0 || max_tiles <= 0) return cudaSuccess;
-  const int W = DD_NB + max_kl;
-  const size_t smem = sizeof(T) * (size_t)(2 * DD_NB * DD_NB + DD_NB * W) + sizeof(int32_t) * (size_t)W;
-  cudaError_t e = ensure_smem(band_tiles_kernel<T>, smem);
+  if (tb == 64) return tiles_tb<T, 64>(d_info, m, max_tiles, max_kl, tm, band, lraw, piv, ltile, utile, src, s);
+  if (tb == 32) return tiles_tb<T, 32>(d_info, m, max_tiles, max_kl, tm, band, lraw, piv, ltile, utile, src, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int TB>
+static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
+                          int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
+                          const int32_t *src, const double *y, const int32_t *perm, T *z, DevStatus *st,
+                          cudaStream_t s) {
+  const int mt = max_n / TB, mj = 2 * mt;
+  const int grid = pl.sched_off ? pl.grid : m;
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * pl.stage_bytes;
+  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T, TB>, smem);
   if (e != cudaSuccess) return e;
-  band_tiles_kernel<T><<<dim3(m, max_tiles), 32, smem, s>>>(d_info, tm, band, lraw, piv, ltile, utile, src);
+  if (grid <= 0) return cudaSuccess;
+  band_solve_fwd_kernel<T, TB><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                              pl.stage_bytes, tm, jobs, ltile, utile, src,
+                                                              y, perm, z, pl.sched, pl.sched_off,
+                                                              pl.task_sys, pl.act, st);
   return cudaGetLastError();
 }
 
@@ -900,19 +962,33 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const double *y, const int32_t *perm, T *z,
                                   DevStatus *st, cudaStream_t s) {
+  // the backward tile step maps exactly 8 threads to each tile row
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
-  // the backward tile step maps exactly 8 threads to each of the 32 rows
-  if (ns < 2 || pl.threads != 8 * DD_NB) return cudaErrorInvalidValue;
-  const int mt = max_n / DD_NB, mj = 2 * mt;
+  if (ns < 2) return cudaErrorInvalidValue;
+  if (pl.threads == 8 * 64)
+    return fwd_tb<T, 64>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  if (pl.threads == 8 * 32)
+    return fwd_tb<T, 32>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int TB>
+static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
+                          int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
+                          const int32_t *src, const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
+                          const T *z2, const T *z1, const int32_t *perm, double *x, DevStatus *st,
+                          cudaStream_t s) {
+  const int mt = max_n / TB, mj = 2 * mt;
   const int grid = pl.sched_off ? pl.grid : m;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * pl.stage_bytes;
-  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T>, smem);
+  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * pl.stage_bytes;
+  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T, TB>, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  band_solve_fwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                          pl.stage_bytes, tm, jobs, ltile, utile, src,
-                                                          y, perm, z, pl.sched, pl.sched_off,
-                                                          pl.task_sys, pl.act, st);
+  band_solve_bwd_kernel<T, TB><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
+                                                              pl.stage_bytes, tm, jobs, ltile, utile, src,
+                                                              e_ptr, e_col, e_val, z2, z1, perm, x,
+                                                              pl.sched, pl.sched_off, pl.task_sys, pl.act,
+                                                              st);
   return cudaGetLastError();
 }
 
@@ -924,19 +1000,28 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
                                   double *x, DevStatus *st, cudaStream_t s) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
-  if (ns < 2 || pl.threads != 8 * DD_NB) return cudaErrorInvalidValue;
-  const int mt = max_n / DD_NB, mj = 2 * mt;
-  const int grid = pl.sched_off ? pl.grid : m;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * pl.stage_bytes;
-  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T>, smem);
-  if (e != cudaSuccess) return e;
-  if (grid <= 0) return cudaSuccess;
-  band_solve_bwd_kernel<T><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                          pl.stage_bytes, tm, jobs, ltile, utile, src,
-                                                          e_ptr, e_col, e_val, z2, z1, perm, x,
-                                                          pl.sched, pl.sched_off, pl.task_sys, pl.act,
-                                                          st);
-  return cudaGetLastError();
+  if (ns < 2) return cudaErrorInvalidValue;
+  if (pl.threads == 8 * 64)
+    return bwd_tb<T, 64>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, e_col,
+                         e_val, z2, z1, perm, x, st, s);
+  if (pl.threads == 8 * 32)
+    return bwd_tb<T, 32>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, e_col,
+                         e_val, z2, z1, perm, x, st, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int TB>
+static int occ_tb(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_bytes) {
+  const int mt = max_n / TB, mj = 2 * mt;
+  const size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * stage_bytes;
+  if (ensure_smem(band_solve_fwd_kernel<T, TB>, smem) != cudaSuccess) return 0;
+  if (ensure_smem(band_solve_bwd_kernel<T, TB>, smem) != cudaSuccess) return 0;
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T, TB>, 8 * TB, smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T, TB>, 8 * TB, smem) != cudaSuccess)
+    return 0;
+  return a < b ? a : b;
 }
 
 // resident CTAs per SM of the two sweep kernels at this shared-memory size
@@ -945,33 +1030,35 @@ template <typename T>
 int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32_t stage_bytes) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
   if (ns < 2) return 0;
-  const int mt = max_n / DD_NB, mj = 2 * mt;
-  const size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), mt, mj) + (size_t)ns * stage_bytes;
-  if (ensure_smem(band_solve_fwd_kernel<T>, smem) != cudaSuccess) return 0;
-  if (ensure_smem(band_solve_bwd_kernel<T>, smem) != cudaSuccess) return 0;
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T>, threads, smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T>, threads, smem) != cudaSuccess)
-    return 0;
-  return a < b ? a : b;
+  if (threads == 8 * 64) return occ_tb<T, 64>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (threads == 8 * 32) return occ_tb<T, 32>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  return 0;
 }
 
 #define DD_MULTI_NR 16
+template <typename T, int TB>
+static cudaError_t multi_tb(const BandInfo *d_info, int m, const int32_t *ncols, const int64_t *x_off,
+                            int max_cols, int max_kl, int max_ku2, const TileMeta *tm, const T *ltile,
+                            const T *utile, const int32_t *src, T *X, cudaStream_t s) {
+  const int w = round4(TB + (max_kl > max_ku2 ? max_kl : max_ku2));
+  size_t smem = sizeof(T) * (size_t)w * DD_MULTI_NR;
+  cudaError_t e = ensure_smem(band_solve_multi_kernel<T, DD_MULTI_NR, TB>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(m, (max_cols + DD_MULTI_NR - 1) / DD_MULTI_NR);
+  band_solve_multi_kernel<T, DD_MULTI_NR, TB><<<grid, 256, smem, s>>>(d_info, ncols, x_off, tm, ltile, utile,
+                                                                      src, X);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t *ncols,
-                                    const int64_t *x_off, int max_cols, int max_kl, int max_ku2,
+                                    const int64_t *x_off, int max_cols, int max_kl, int max_ku2, int tb,
                                     const TileMeta *tm, const T *ltile, const T *utile,
                                     const int32_t *src, T *X, cudaStream_t s) {
   if (max_cols <= 0) return cudaSuccess;
-  const int w = round4(DD_NB + (max_kl > max_ku2 ? max_kl : max_ku2));
-  size_t smem = sizeof(T) * (size_t)w * DD_MULTI_NR;
-  cudaError_t e = ensure_smem(band_solve_multi_kernel<T, DD_MULTI_NR>, smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid(m, (max_cols + DD_MULTI_NR - 1) / DD_MULTI_NR);
-  band_solve_multi_kernel<T, DD_MULTI_NR><<<grid, 256, smem, s>>>(d_info, ncols, x_off, tm, ltile,
-                                                                  utile, src, X);
-  return cudaGetLastError();
+  if (tb == 64) return multi_tb<T, 64>(d_info, m, ncols, x_off, max_cols, max_kl, max_ku2, tm, ltile, utile, src, X, s);
+  if (tb == 32) return multi_tb<T, 32>(d_info, m, ncols, x_off, max_cols, max_kl, max_ku2, tm, ltile, utile, src, X, s);
+  return cudaErrorInvalidValue;
 }
 
 #define DD_INST_BAND(T)                                                                            \
@@ -981,7 +1068,7 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
   template int band_lu_occupancy<T>(int, int, int);                                                \
   template cudaError_t launch_tile_widths<T>(const BandInfo *, int, int, const T *, const T *,     \
                                              const int32_t *, int32_t *, int32_t *, cudaStream_t); \
-  template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, const TileMeta *,     \
+  template cudaError_t launch_band_tiles<T>(const BandInfo *, int, int, int, int, const TileMeta *,\
                                             const T *, const T *, const int32_t *, T *, T *,       \
                                             int32_t *, cudaStream_t);                               \
   template cudaError_t launch_band_solve_fwd<T>(const BandInfo *, int, int, int, int,             \
@@ -995,7 +1082,7 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
       const T *, const T *, const T *, const int32_t *, double *, DevStatus *, cudaStream_t);      \
   template int band_sweep_occupancy<T>(int, int, int, int, uint32_t);                              \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \
-                                                  const int64_t *, int, int, int,                  \
+                                                  const int64_t *, int, int, int, int,             \
                                                   const TileMeta *, const T *, const T *,          \
                                                   const int32_t *, T *, cudaStream_t);
 

@@ -522,17 +522,53 @@ __global__ void schur_gemv_kernel(const int32_t *__restrict__ agg_off, const int
     if (r >= p) break;
     const T *row = Sa + (int64_t)r * p;
     T acc = T(0);
-    // rows start on a 16-byte boundary only when p is a multiple of V
+    // rows start on a 16-byte boundary only when p is a multiple of V; four
+    // 16-byte loads per lane in flight
     if ((p % V) == 0 && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
-      for (int c = lane * V; c < p; c += 32 * V) {
+      T acc1 = T(0), acc2 = T(0), acc3 = T(0);
+      int c = lane * V;
+      for (; c + 3 * 32 * V < p; c += 4 * 32 * V) {
         if (V == 4) {
-          const float4 v = *reinterpret_cast<const float4 *>(row + c);
-          acc += T(v.x) * ts[c] + T(v.y) * ts[c + 1] + T(v.z) * ts[c + 2] + T(v.w) * ts[c + 3];
+          const float4 v0 = *reinterpret_cast<const float4 *>(row + c);
+          const float4 v1 = *reinterpret_cast<const float4 *>(row + c + 32 * V);
+          const float4 v2 = *reinterpret_cast<const float4 *>(row + c + 64 * V);
+          const float4 v3 = *reinterpret_cast<const float4 *>(row + c + 96 * V);
+          // t in 16-byte pieces too: consecutive lanes, conflict-free
+          const float4 t0 = *reinterpret_cast<const float4 *>(ts + c);
+          const float4 t1 = *reinterpret_cast<const float4 *>(ts + c + 32 * V);
+          const float4 t2 = *reinterpret_cast<const float4 *>(ts + c + 64 * V);
+          const float4 t3 = *reinterpret_cast<const float4 *>(ts + c + 96 * V);
+          acc += T(v0.x) * T(t0.x) + T(v0.y) * T(t0.y) + T(v0.z) * T(t0.z) + T(v0.w) * T(t0.w);
+          acc1 += T(v1.x) * T(t1.x) + T(v1.y) * T(t1.y) + T(v1.z) * T(t1.z) + T(v1.w) * T(t1.w);
+          acc2 += T(v2.x) * T(t2.x) + T(v2.y) * T(t2.y) + T(v2.z) * T(t2.z) + T(v2.w) * T(t2.w);
+          acc3 += T(v3.x) * T(t3.x) + T(v3.y) * T(t3.y) + T(v3.z) * T(t3.z) + T(v3.w) * T(t3.w);
         } else {
-          const double2 v = *reinterpret_cast<const double2 *>(row + c);
-          acc += T(v.x) * ts[c] + T(v.y) * ts[c + 1];
+          const double2 v0 = *reinterpret_cast<const double2 *>(row + c);
+          const double2 v1 = *reinterpret_cast<const double2 *>(row + c + 32 * V);
+          const double2 v2 = *reinterpret_cast<const double2 *>(row + c + 64 * V);
+          const double2 v3 = *reinterpret_cast<const double2 *>(row + c + 96 * V);
+          const double2 t0 = *reinterpret_cast<const double2 *>(ts + c);
+          const double2 t1 = *reinterpret_cast<const double2 *>(ts + c + 32 * V);
+          const double2 t2 = *reinterpret_cast<const double2 *>(ts + c + 64 * V);
+          const double2 t3 = *reinterpret_cast<const double2 *>(ts + c + 96 * V);
+          acc += T(v0.x) * T(t0.x) + T(v0.y) * T(t0.y);
+          acc1 += T(v1.x) * T(t1.x) + T(v1.y) * T(t1.y);
+          acc2 += T(v2.x) * T(t2.x) + T(v2.y) * T(t2.y);
+          acc3 += T(v3.x) * T(t3.x) + T(v3.y) * T(t3.y);
         }
       }
+      for (; c < p; c += 32 * V) {
+        if (V == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + c);
+          const float4 t = *reinterpret_cast<const float4 *>(ts + c);
+          acc += T(v.x) * T(t.x) + T(v.y) * T(t.y) + T(v.z) * T(t.z) + T(v.w) * T(t.w);
+        } else {
+          const double2 v = *reinterpret_cast<const double2 *>(row + c);
+          const double2 t = *reinterpret_cast<const double2 *>(ts + c);
+          acc += T(v.x) * T(t.x) + T(v.y) * T(t.y);
+        }
+      }
+      acc = (acc + acc1) + (acc2 + acc3);
     } else {
       for (int c = lane; c < p; c += 32) acc += row[c] * ts[c];
     }

@@ -597,13 +597,14 @@ cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s) {
 }
 
 // blocks of the cooperative CGS2 kernel that can be resident at once (capped)
-int cgs2_blocks(int cap) {
+int cgs2_blocks(int per_sm, int cap) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgs2_kernel, DD_CGS_THREADS, 0) != cudaSuccess)
     return 0;
-  int nb = sms * (per < 2 ? per : 2);
+  const int want = per_sm > 0 ? per_sm : 2;
+  int nb = sms * (per < want ? per : want);
   return nb < cap ? nb : cap;
 }
 

@@ -79,7 +79,8 @@ class dd_partition(ctypes.Structure):
 
 class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2),
                 ("mlp_weights", ctypes.c_char_p)]
 
 
@@ -202,7 +203,7 @@ class DD:
 
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
-                 autotune=False, mlp_weights=None):
+                 autotune=False, mlp_weights=None, krylov_ctas_per_sm=0):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -213,7 +214,8 @@ class DD:
         rp, col, val, pa, pe, ag = self._arrs
         csr = dd_csr(self.n, int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
         pt = dd_partition(int(m), _ptr(pa), _ptr(pe), int(sz), _ptr(ag), 0 if ag is None else len(ag) - 1)
-        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)))
+        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
+                    int(krylov_ctas_per_sm))
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
