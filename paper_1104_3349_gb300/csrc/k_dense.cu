@@ -20,14 +20,26 @@ __device__ void set_status2(DevStatus *st, int code, int block) {
   if (atomicCAS(&st->code, 0, code) == 0) st->block = block;
 }
 
+// largest |A| of every block: CTA (x, b) scans slice x of block b, and the
+// slices meet in an atomic max on the bit pattern (order-independent for
+// non-negative values, so the result is deterministic)
+__device__ __forceinline__ void atomic_max_nonneg(float *a, float v) {
+  atomicMax(reinterpret_cast<unsigned int *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__double_as_longlong(v));
+}
 template <typename T>
 __global__ void block_amax_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
                                   const T *__restrict__ A, T *amax) {
-  const int b = blockIdx.x;
+  const int b = blockIdx.y;
   const int p = P[b];
   const T *a = A + off[b];
+  const int64_t total = (int64_t)p * p;
+  const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t q0 = (int64_t)blockIdx.x * chunk, q1 = min(total, q0 + chunk);
   T mx = T(0);
-  for (int64_t q = threadIdx.x; q < (int64_t)p * p; q += blockDim.x) mx = fmax(mx, tabs(a[q]));
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) mx = fmax(mx, tabs(a[q]));
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ T red[32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -35,7 +47,7 @@ __global__ void block_amax_kernel(const int32_t *__restrict__ P, const int64_t *
   if (threadIdx.x == 0) {
     T m2 = T(0);
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
-    amax[b] = m2;
+    if (m2 > T(0)) atomic_max_nonneg(&amax[b], m2);
   }
 }
 
@@ -121,25 +133,44 @@ __global__ void gj_update_kernel(int k, const int32_t *__restrict__ P, const int
 }
 
 // Undo the row exchanges as column exchanges in reverse order.
-template <typename T>
-__global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                     T *A, const int32_t *__restrict__ ipiv,
-                                     const int64_t *__restrict__ poff,
-                                     const int32_t *__restrict__ failed) {
+// The column exchanges that undo the row exchanges (in reverse order) are
+// one permutation of the columns, the same for every row: cidx[c] = the
+// column whose entry ends in column c.  One CTA per block composes it.
+__global__ void gj_colperm_kernel(const int32_t *__restrict__ P, const int32_t *__restrict__ ipiv,
+                                  const int64_t *__restrict__ poff, const int32_t *__restrict__ failed,
+                                  int32_t *cidx) {
   const int b = blockIdx.x;
   const int p = P[b];
   if (failed[b]) return;
-  T *a = A + off[b];
-  for (int k = p - 1; k >= 0; --k) {
-    const int q = ipiv[poff[b] + k];
-    if (q != k)
-      for (int r = threadIdx.x; r < p; r += blockDim.x) {
-        T t = a[(int64_t)r * p + k];
-        a[(int64_t)r * p + k] = a[(int64_t)r * p + q];
-        a[(int64_t)r * p + q] = t;
-      }
-    __syncthreads();
-  }
+  extern __shared__ __align__(128) unsigned char smraw[];
+  int32_t *ix = reinterpret_cast<int32_t *>(smraw);
+  for (int c = threadIdx.x; c < p; c += blockDim.x) ix[c] = c;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = p - 1; k >= 0; --k) {
+      const int q = ipiv[poff[b] + k];
+      if (q != k) { const int t = ix[k]; ix[k] = ix[q]; ix[q] = t; }
+    }
+  __syncthreads();
+  for (int c = threadIdx.x; c < p; c += blockDim.x) cidx[poff[b] + c] = ix[c];
+}
+
+// row r of block b (CTA (r, b)) gathered through shared memory
+template <typename T>
+__global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                     T *A, const int32_t *__restrict__ cidx,
+                                     const int64_t *__restrict__ poff,
+                                     const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y, r = blockIdx.x;
+  const int p = P[b];
+  if (r >= p || failed[b]) return;
+  T *row = A + off[b] + (int64_t)r * p;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T *ts = reinterpret_cast<T *>(smraw);
+  for (int c = threadIdx.x; c < p; c += blockDim.x) ts[c] = row[c];
+  __syncthreads();
+  const int32_t *ix = cidx + poff[b];
+  for (int c = threadIdx.x; c < p; c += blockDim.x) row[c] = ts[ix[c]];
 }
 
 // ---------------------------------------------------------------------------
@@ -586,7 +617,9 @@ template <typename T>
 cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off, const T *A,
                               T *amax, cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
-  block_amax_kernel<T><<<nblk, 256, 0, s>>>(d_p, d_off, A, amax);
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(T) * nblk, s);
+  if (e != cudaSuccess) return e;
+  block_amax_kernel<T><<<dim3(64, nblk), 256, 0, s>>>(d_p, d_off, A, amax);
   return cudaGetLastError();
 }
 
@@ -626,7 +659,19 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
     bgj_rowblock_kernel<T, NB><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     bgj_update_kernel<T, NB><<<ug, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
   }
-  gj_unscramble_kernel<T><<<nblk, 256, 0, s>>>(d_p, d_off, A, ipiv, d_poff, failed);
+  // the composite column permutation in the (now free) scratch, then the rows
+  int32_t *cidx = reinterpret_cast<int32_t *>(scratch);
+  const size_t psm = sizeof(int32_t) * (size_t)pmax, rsm = sizeof(T) * (size_t)pmax;
+  if (psm > 48 * 1024) {
+    e = cudaFuncSetAttribute(gj_colperm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    if (e != cudaSuccess) return e;
+  }
+  if (rsm > 48 * 1024) {
+    e = cudaFuncSetAttribute(gj_unscramble_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+  }
+  gj_colperm_kernel<<<nblk, 256, psm, s>>>(d_p, ipiv, d_poff, failed, cidx);
+  gj_unscramble_kernel<T><<<dim3(pmax, nblk), 256, rsm, s>>>(d_p, d_off, A, cidx, d_poff, failed);
   return cudaGetLastError();
 }
 
