@@ -98,11 +98,25 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
   for (int t = 0; t < b.ntiles; ++t) {
     const int c0 = t * DD_NB;
     const int nbe = min(DD_NB, n - c0);
-    // load the window
-    for (int e = tid; e < R * Cw; e += nt) {
-      const int r = e / Cw, c = e % Cw;
-      const int gr = c0 + r, gc = c0 + c, off = c - r + kl;
-      W[r * ldw + c] = (gr < n && gc < n && off >= 0 && off < wd) ? A[(int64_t)gr * wd + off] : T(0);
+    // load the window: a warp per row, lanes along the row's band entries,
+    // four loads in flight per lane
+    for (int r = warp; r < R; r += nw) {
+      const int gr = c0 + r;
+      const T *arow = A + (int64_t)gr * wd;
+      T *wrow = W + r * ldw;
+      for (int cb = 0; cb < Cw; cb += 128) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = cb + lane + 32 * u, gc = c0 + c, off = c - r + kl;
+          v[u] = (c < Cw && gr < n && gc < n && off >= 0 && off < wd) ? arow[off] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = cb + lane + 32 * u;
+          if (c < Cw) wrow[c] = v[u];
+        }
+      }
     }
     __syncthreads();
     // panel: column by column
@@ -197,15 +211,17 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
     // multipliers of the panel (strictly below the diagonal), then the window
     // back to the band rows (multiplier positions zero)
     T *lt = ltraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b);
-    for (int e = tid; e < R * DD_NB; e += nt) {
-      const int c = e / R, r = e % R;
-      lt[e] = (r > c && c < nbe) ? W[r * ldw + c] : T(0);
-    }
-    for (int e = tid; e < R * Cw; e += nt) {
-      const int r = e / Cw, c = e % Cw;
-      const int gr = c0 + r, gc = c0 + c, off = c - r + kl;
-      if (gr < n && gc < n && off >= 0 && off < wd)
-        A[(int64_t)gr * wd + off] = (c < DD_NB && r > c) ? T(0) : W[r * ldw + c];
+    for (int c = warp; c < DD_NB; c += nw)  // column c of the multipliers
+      for (int r = lane; r < R; r += 32) lt[(int64_t)c * R + r] = (r > c && c < nbe) ? W[r * ldw + c] : T(0);
+    for (int r = warp; r < R; r += nw) {
+      const int gr = c0 + r;
+      if (gr >= n) continue;
+      T *arow = A + (int64_t)gr * wd;
+      const T *wrow = W + r * ldw;
+      for (int c = lane; c < Cw; c += 32) {
+        const int gc = c0 + c, off = c - r + kl;
+        if (gc < n && off >= 0 && off < wd) arow[off] = (c < DD_NB && r > c) ? T(0) : wrow[c];
+      }
     }
     __syncthreads();
   }

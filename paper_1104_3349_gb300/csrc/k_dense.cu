@@ -654,7 +654,7 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   const dim3 rg((pmax + 255) / 256, nblk);
   const dim3 ug((pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, (pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, nblk);
   for (int k0 = 0; k0 < pmax; k0 += NB) {
-    bgj_panel_kernel<T, NB><<<nblk, 256, smem, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, amax,
+    bgj_panel_kernel<T, NB><<<nblk, 1024, smem, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, amax,
                                                    pivtol, failed, st, status_code, smem_rows);
     bgj_rowblock_kernel<T, NB><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     bgj_update_kernel<T, NB><<<ug, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
