@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "dd_internal.h"
@@ -197,6 +198,23 @@ struct HostBlocks {
   std::vector<double> e_val, f_val;
 };
 
+// Rows [0, n) in contiguous chunks over the host cores; f(w, r0, r1) runs
+// chunk w.  Results that depend on order are merged by chunk index.
+int host_workers(int64_t n) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int64_t by_size = std::max<int64_t>(1, n / 16384);
+  return (int)std::min<int64_t>(std::min<int64_t>(hc ? hc : 1, 32), by_size);
+}
+template <typename F>
+void parallel_rows(int64_t n, int workers, F &&f) {
+  if (workers <= 1) { f(0, (int64_t)0, n); return; }
+  std::vector<std::thread> th;
+  th.reserve(workers);
+  for (int w = 0; w < workers; ++w)
+    th.emplace_back([&, w] { f(w, n * w / workers, n * (w + 1) / workers); });
+  for (auto &t : th) t.join();
+}
+
 dd_status validate_and_order(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb) {
   const int64_t n = csr->n;
   if (n <= 0 || n > INT32_MAX - 1 || !csr->rowptr || !csr->col || !csr->val) {
@@ -207,27 +225,51 @@ dd_status validate_and_order(DDHandle *h, const dd_csr *csr, const dd_partition 
     h->err = "rowptr[0] must be 0 and rowptr[n] == nnz";
     return DD_ERR_INVALID_ARG;
   }
-  for (int64_t i = 0; i < n; ++i) {
-    if (csr->rowptr[i + 1] < csr->rowptr[i]) { h->err = "rowptr decreases"; return DD_ERR_INVALID_ARG; }
-    for (int64_t k = csr->rowptr[i]; k < csr->rowptr[i + 1]; ++k) {
-      if (csr->col[k] < 0 || csr->col[k] >= n) { h->err = "column index out of range"; return DD_ERR_INVALID_ARG; }
-      if (!isfinite(csr->val[k])) { h->err = "non-finite matrix entry"; return DD_ERR_NONFINITE; }
-    }
+  const int nw = host_workers(n);
+  {
+    // first offending row of each chunk; the lowest one is reported
+    std::vector<int64_t> bad(nw, -1);
+    std::vector<int> why(nw, 0);
+    parallel_rows(n, nw, [&](int w, int64_t r0, int64_t r1) {
+      for (int64_t i = r0; i < r1 && bad[w] < 0; ++i) {
+        if (csr->rowptr[i + 1] < csr->rowptr[i]) { bad[w] = i; why[w] = 1; break; }
+        for (int64_t k = csr->rowptr[i]; k < csr->rowptr[i + 1]; ++k) {
+          if (csr->col[k] < 0 || csr->col[k] >= n) { bad[w] = i; why[w] = 2; break; }
+          if (!isfinite(csr->val[k])) { bad[w] = i; why[w] = 3; break; }
+        }
+      }
+    });
+    for (int w = 0; w < nw; ++w)
+      if (bad[w] >= 0) {
+        if (why[w] == 1) { h->err = "rowptr decreases"; return DD_ERR_INVALID_ARG; }
+        if (why[w] == 2) { h->err = "column index out of range"; return DD_ERR_INVALID_ARG; }
+        h->err = "non-finite matrix entry";
+        return DD_ERR_NONFINITE;
+      }
   }
   const int m = pt->m;
   if (m <= 0 || !pt->part) { h->err = "partition needs m >= 1 and part"; return DD_ERR_INVALID_ARG; }
   for (int64_t i = 0; i < n; ++i)
     if (pt->part[i] < -1 || pt->part[i] >= m) { h->err = "part value out of range"; return DD_ERR_INVALID_PARTITION; }
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t k = csr->rowptr[i]; k < csr->rowptr[i + 1]; ++k) {
-      int a = pt->part[i], b = pt->part[csr->col[k]];
-      if (a >= 0 && b >= 0 && a != b && csr->val[k] != 0.0) {
+  {
+    std::vector<int64_t> bad(nw, -1), badk(nw, -1);
+    parallel_rows(n, nw, [&](int w, int64_t r0, int64_t r1) {
+      for (int64_t i = r0; i < r1 && bad[w] < 0; ++i)
+        for (int64_t k = csr->rowptr[i]; k < csr->rowptr[i + 1]; ++k) {
+          const int a = pt->part[i], b = pt->part[csr->col[k]];
+          if (a >= 0 && b >= 0 && a != b && csr->val[k] != 0.0) { bad[w] = i; badk[w] = k; break; }
+        }
+    });
+    for (int w = 0; w < nw; ++w)
+      if (bad[w] >= 0) {
+        const int64_t i = bad[w], k = badk[w];
         char buf[160];
-        snprintf(buf, sizeof buf, "entry (%lld,%d) couples interiors %d and %d", (long long)i, csr->col[k], a, b);
+        snprintf(buf, sizeof buf, "entry (%lld,%d) couples interiors %d and %d", (long long)i, csr->col[k],
+                 pt->part[i], pt->part[csr->col[k]]);
         h->err = buf;
         return DD_ERR_INVALID_PARTITION;
       }
-    }
+  }
   hb.off.assign(m + 1, 0);
   for (int64_t i = 0; i < n; ++i) if (pt->part[i] >= 0) hb.off[pt->part[i] + 1]++;
   for (int j = 0; j < m; ++j) hb.off[j + 1] += hb.off[j];
@@ -287,50 +329,65 @@ dd_status build_aggregates(DDHandle *h, const dd_partition *pt, dd_approx kind, 
 
 void extract_blocks(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb) {
   const int m = h->m, nI = h->nI, nG = h->nG;
+  const int64_t n = h->n;
   hb.kl.assign(m, 0);
   hb.ku.assign(m, 0);
   hb.e_ptr.assign(nI + 1, 0);
   hb.f_ptr.assign(nG + 1, 0);
-  // bandwidths and counts
-  for (int64_t r = 0; r < h->n; ++r) {
-    const int o = hb.perm[r];
-    const int jr = pt->part[o];
-    for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
-      const int c = hb.pos[csr->col[k]];
-      const int jc = pt->part[csr->col[k]];
-      if (jr >= 0 && jc == jr) {
-        hb.kl[jr] = std::max(hb.kl[jr], (int)(r - c));
-        hb.ku[jr] = std::max(hb.ku[jr], (int)(c - r));
-      } else if (jr >= 0 && jc < 0) {
-        hb.e_ptr[r + 1]++;
-      } else if (jr < 0 && jc >= 0) {
-        hb.f_ptr[r - nI + 1]++;
+  const int nw = host_workers(n);
+  // bandwidths (per chunk, merged) and per-row counts, rows in the new numbering
+  std::vector<std::vector<int32_t>> kl(nw), ku(nw);
+  parallel_rows(n, nw, [&](int w, int64_t r0, int64_t r1) {
+    kl[w].assign(m, 0);
+    ku[w].assign(m, 0);
+    for (int64_t r = r0; r < r1; ++r) {
+      const int o = hb.perm[r];
+      const int jr = pt->part[o];
+      int32_t ne = 0;
+      for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
+        const int c = hb.pos[csr->col[k]];
+        const int jc = pt->part[csr->col[k]];
+        if (jr >= 0 && jc == jr) {
+          kl[w][jr] = std::max(kl[w][jr], (int)(r - c));
+          ku[w][jr] = std::max(ku[w][jr], (int)(c - r));
+        } else if ((jr >= 0 && jc < 0) || (jr < 0 && jc >= 0)) {
+          ++ne;
+        }
       }
+      if (jr >= 0) hb.e_ptr[r + 1] = ne;
+      else hb.f_ptr[r - nI + 1] = ne;
     }
-  }
+  });
+  for (int w = 0; w < nw; ++w)
+    for (int j = 0; j < m; ++j) {
+      hb.kl[j] = std::max(hb.kl[j], kl[w][j]);
+      hb.ku[j] = std::max(hb.ku[j], ku[w][j]);
+    }
   for (int i = 0; i < nI; ++i) hb.e_ptr[i + 1] += hb.e_ptr[i];
   for (int i = 0; i < nG; ++i) hb.f_ptr[i + 1] += hb.f_ptr[i];
   hb.e_col.assign(hb.e_ptr[nI], 0);
   hb.e_val.assign(hb.e_ptr[nI], 0.0);
   hb.f_col.assign(hb.f_ptr[nG], 0);
   hb.f_val.assign(hb.f_ptr[nG], 0.0);
-  std::vector<int32_t> ef(hb.e_ptr.begin(), hb.e_ptr.end() - 1), ff(hb.f_ptr.begin(), hb.f_ptr.end() - 1);
-  for (int64_t r = 0; r < h->n; ++r) {
-    const int o = hb.perm[r];
-    const int jr = pt->part[o];
-    for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
-      const int c = hb.pos[csr->col[k]];
-      const int jc = pt->part[csr->col[k]];
-      if (jr >= 0 && jc < 0) {
-        hb.e_col[ef[r]] = c - nI;
-        hb.e_val[ef[r]++] = csr->val[k];
-      } else if (jr < 0 && jc >= 0) {
-        hb.f_col[ff[r - nI]] = c;
-        hb.f_val[ff[r - nI]++] = csr->val[k];
+  // each row fills its own segment, in the order of its entries in C
+  parallel_rows(n, nw, [&](int, int64_t r0, int64_t r1) {
+    for (int64_t r = r0; r < r1; ++r) {
+      const int o = hb.perm[r];
+      const int jr = pt->part[o];
+      int32_t q = (jr >= 0) ? hb.e_ptr[r] : hb.f_ptr[r - nI];
+      for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
+        const int c = hb.pos[csr->col[k]];
+        const int jc = pt->part[csr->col[k]];
+        if (jr >= 0 && jc < 0) {
+          hb.e_col[q] = c - nI;
+          hb.e_val[q++] = csr->val[k];
+        } else if (jr < 0 && jc >= 0) {
+          hb.f_col[q] = c;
+          hb.f_val[q++] = csr->val[k];
+        }
       }
     }
-  }
-  (void)m;
+  });
 }
 
 int64_t launch_cost(const char *call, const DDHandle *h) {
