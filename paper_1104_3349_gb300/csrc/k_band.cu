@@ -293,7 +293,7 @@ __global__ void tile_widths_kernel(const BandInfo *__restrict__ info, const T *_
 // column c (forward) and tile row c (backward).
 // ---------------------------------------------------------------------------
 template <typename T, int TB>
-__global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restrict__ info,
+__global__ void __launch_bounds__(4 * TB) band_tiles_kernel(const BandInfo *__restrict__ info,
                                                            const TileMeta *__restrict__ tm,
                                                            const T *__restrict__ band,
                                                            const T *__restrict__ lraw,
@@ -308,7 +308,9 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
   const int W2 = TB + kl;  // window of the tile
   const int WL = mt.wl, WU = mt.wu;
   const int c0 = t * TB;
-  const int tid = threadIdx.x;
+  // thread (tid, part): column / row tid of the tile, one of four parts of
+  // the long loops; the triangles are part 0's
+  const int tid = threadIdx.x % TB, part = threadIdx.x / TB;
   const int cend = min(c0 + TB, n);
   const int32_t *P = piv + b.piv_off;
   const T *A = band + b.band_off;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
   int32_t *idx = reinterpret_cast<int32_t *>(Lsm + TB * TB);
 
   // (1) composite window permutation of all the tile's row exchanges
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     for (int q = 0; q < W2; ++q) idx[q] = q;
     for (int c = c0; c < cend; ++c) {
       const int a = c - c0, bq = P[c] - c0;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
   }
   // (2) multipliers of column tid in the tile's final row order: the panel's
   // own (already exchanged), then the exchanges of the tile's later panels
-  {
+  if (part == 0) {
     T *v = vbuf + (size_t)tid * W2;
     for (int q = 0; q < W2; ++q) v[q] = T(0);
     const int pr = tid / DD_NB, cc = tid % DD_NB, po = pr * DD_NB;
@@ -346,12 +348,12 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
     }
   }
   __syncthreads();
-  for (int q = tid; q < src_stride_w(WL); q += TB) src[q] = (q < W2) ? idx[q] : q;
-  for (int q = 0; q < TB; ++q)
+  for (int q = threadIdx.x; q < src_stride_w(WL); q += 4 * TB) src[q] = (q < W2) ? idx[q] : q;
+  for (int q = part; q < TB; q += 4)
     L11[q * TB + tid] = (q == tid) ? T(1) : (q > tid ? vbuf[(size_t)tid * W2 + q] : T(0));
   __syncthreads();
   // (3) Linv (column tid), then K = [Linv; -L21 Linv] for rows < WL
-  {
+  if (part == 0) {
     T x[TB];
     for (int q = 0; q < TB; ++q) x[q] = T(0);
     x[tid] = T(1);
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
     }
   }
   __syncthreads();
-  for (int r = TB; r < WL; ++r) {
+  for (int r = TB + part; r < WL; r += 4) {
     T sacc = T(0);
     if (r < W2)
       for (int k = 0; k < TB; ++k) sacc += vbuf[(size_t)k * W2 + r] * Lsm[k * TB + tid];
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
   // (4) U11 (row-major in L11's buffer) and its inverse; Kb = [Uinv | -Uinv U12]
   {
     const int r = c0 + tid;  // row of this thread
-    for (int c = 0; c < TB; ++c) {
+    for (int c = part; c < TB; c += 4) {
       T v = T(0);
       if (r < n) {
         const int col = c0 + c, off = col - r + kl;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
     }
   }
   __syncthreads();
-  {
+  if (part == 0) {
     T x[TB];
     for (int q = 0; q < TB; ++q) x[q] = T(0);
     x[tid] = T(1) / L11[tid * TB + tid];
@@ -402,8 +404,8 @@ __global__ void __launch_bounds__(TB) band_tiles_kernel(const BandInfo *__restri
   __syncthreads();
   {
     T *kr = Kb + (int64_t)tid * WU;
-    for (int c = 0; c < TB; ++c) kr[c] = Lsm[tid * TB + c];
-    for (int q = 0; q < WU - TB; ++q) {
+    for (int c = part; c < TB; c += 4) kr[c] = Lsm[tid * TB + c];
+    for (int q = part; q < WU - TB; q += 4) {
       const int col = c0 + TB + q;
       T sacc = T(0);
       if (col < n && q < ku2)
@@ -940,7 +942,8 @@ static cudaError_t tiles_tb(const BandInfo *d_info, int m, int max_tiles, int ma
   const size_t smem = sizeof(T) * (size_t)(2 * TB * TB + TB * W) + sizeof(int32_t) * (size_t)W;
   cudaError_t e = ensure_smem(band_tiles_kernel<T, TB>, smem);
   if (e != cudaSuccess) return e;
-  band_tiles_kernel<T, TB><<<dim3(m, max_tiles), TB, smem, s>>>(d_info, tm, band, lraw, piv, ltile, utile, src);
+  band_tiles_kernel<T, TB><<<dim3(m, max_tiles), 4 * TB, smem, s>>>(d_info, tm, band, lraw, piv, ltile, utile,
+                                                                     src);
   return cudaGetLastError();
 }
 
