@@ -815,10 +815,12 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
     const int c0 = t * TB, WL = mt.wl;
     const int32_t *src = srcs + mt.sofs;
     const T *K = ltile + mt.lofs;
+    // along each right-hand side column, so neighbouring threads read
+    // neighbouring rows of X
     for (int e = tid; e < WL * NR; e += nt) {
-      int q = e / NR, r = e % NR;
-      int row = c0 + src[q];
-      win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
+      const int r = e / WL, q = e % WL;
+      const int row = c0 + src[q];
+      win[q * NR + r] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
     for (int e = tid; e < WL * NR; e += nt) {
@@ -835,9 +837,9 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
     const int r0 = t * TB, WU = mt.wu;
     const T *Kb = utile + mt.uofs;
     for (int e = tid; e < WU * NR; e += nt) {
-      int q = e / NR, r = e % NR;
-      int row = r0 + q;
-      win[e] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
+      const int r = e / WU, q = e % WU;
+      const int row = r0 + q;
+      win[q * NR + r] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
     for (int e = tid; e < TB * NR; e += nt) {
