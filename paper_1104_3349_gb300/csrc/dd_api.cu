@@ -71,6 +71,7 @@ struct DDHandle {
   int nseg = 1, seg_ctas = 0;
   std::vector<int64_t> seg_row0_h;
   int32_t *cta_seg = nullptr, *seg_cta0 = nullptr, *d_act = nullptr, *d_jl = nullptr;
+  int32_t *cta_seg_act = nullptr, *seg_cta0_act = nullptr, *row_sys = nullptr;
   int64_t *seg_row0 = nullptr;
   int32_t *h_act = nullptr;  // pinned: act then jl, nseg each
   std::vector<int32_t> sub_sys_h, agg_sys_h;  // system of every subdomain / aggregate
@@ -1159,6 +1160,52 @@ dd_status apply_any(DDHandle *h, const double *y, double *x, cudaStream_t s, int
 
 namespace {
 
+// CTAs of the batched Krylov kernels over the systems with act[q] != 0
+// (all when act is null): proportional to the rows, at least one each, all
+// nb CTAs used; c0[q] is system q's first CTA, cseg[c] CTA c's system.
+void assign_ctas(const std::vector<int64_t> &row0, const int32_t *act, int nb, std::vector<int32_t> &c0,
+                 std::vector<int32_t> &cseg) {
+  const int S = (int)row0.size() - 1;
+  std::vector<int64_t> rows(S);
+  int64_t N = 0;
+  int na = 0;
+  for (int q = 0; q < S; ++q) {
+    rows[q] = (!act || act[q]) ? row0[q + 1] - row0[q] : 0;
+    N += rows[q];
+    na += (!act || act[q]) ? 1 : 0;
+  }
+  std::vector<int32_t> cnt(S, 0);
+  int tot = 0;
+  if (na > 0)
+    for (int q = 0; q < S; ++q) {
+      if (act && !act[q]) continue;
+      cnt[q] = (int32_t)std::max<int64_t>(1, (rows[q] * nb) / std::max<int64_t>(N, 1));
+      tot += cnt[q];
+    }
+  while (na > 0 && tot > nb) {  // trim the system with the most CTAs
+    const int q = (int)(std::max_element(cnt.begin(), cnt.end()) - cnt.begin());
+    --cnt[q];
+    --tot;
+  }
+  while (na > 0 && tot < nb) {  // add to the system with the most rows per CTA
+    int best = -1;
+    double worst = -1.0;
+    for (int q = 0; q < S; ++q) {
+      if (cnt[q] == 0) continue;
+      const double per = (double)rows[q] / cnt[q];
+      if (per > worst) { worst = per; best = q; }
+    }
+    ++cnt[best];
+    ++tot;
+  }
+  c0.assign(S + 1, 0);
+  cseg.clear();
+  for (int q = 0; q < S; ++q) {
+    c0[q + 1] = c0[q] + cnt[q];
+    for (int c = 0; c < cnt[q]; ++c) cseg.push_back(q);
+  }
+}
+
 dd_status alloc_krylov(DDHandle *h, int R) {
   const int S = h->nseg;
   h->Rmax = R;
@@ -1187,37 +1234,21 @@ dd_status alloc_krylov(DDHandle *h, int R) {
     // CTAs of the batched Krylov kernels: proportional to the rows, at least one each
     const int nb = h->cgs_blocks;
     if (S > nb) { h->err = "more systems in the batch than resident CTAs of the CGS2 kernel"; return DD_ERR_INVALID_ARG; }
-    const int64_t N = h->seg_row0_h[S];
-    std::vector<int32_t> cnt(S);
-    int tot = 0;
-    for (int q = 0; q < S; ++q) {
-      const int64_t ns = h->seg_row0_h[q + 1] - h->seg_row0_h[q];
-      cnt[q] = (int32_t)std::max<int64_t>(1, (ns * nb) / std::max<int64_t>(N, 1));
-      tot += cnt[q];
-    }
-    while (tot > nb) {  // trim the system with the most CTAs
-      int q = (int)(std::max_element(cnt.begin(), cnt.end()) - cnt.begin());
-      --cnt[q];
-      --tot;
-    }
-    while (tot < nb) {  // add to the system with the most rows per CTA
-      int best = 0;
-      double worst = -1.0;
-      for (int q = 0; q < S; ++q) {
-        const double per = (double)(h->seg_row0_h[q + 1] - h->seg_row0_h[q]) / cnt[q];
-        if (per > worst) { worst = per; best = q; }
-      }
-      ++cnt[best];
-      ++tot;
-    }
-    std::vector<int32_t> c0(S + 1, 0), cseg;
-    for (int q = 0; q < S; ++q) {
-      c0[q + 1] = c0[q] + cnt[q];
-      for (int c = 0; c < cnt[q]; ++c) cseg.push_back(q);
-    }
+    std::vector<int32_t> c0, cseg;
+    assign_ctas(h->seg_row0_h, nullptr, nb, c0, cseg);
     h->seg_ctas = c0[S];
     TRY(upload(h, &h->seg_cta0, c0));
     TRY(upload(h, &h->cta_seg, cseg));
+    // the CGS2 kernel's map over the systems still stepping (rewritten when
+    // that set changes); starts as the full map
+    TRY(upload(h, &h->seg_cta0_act, c0));
+    TRY(upload(h, &h->cta_seg_act, cseg));
+    {
+      std::vector<int32_t> rs(h->n);
+      for (int q = 0; q < S; ++q)
+        for (int64_t i = h->seg_row0_h[q]; i < h->seg_row0_h[q + 1]; ++i) rs[i] = q;
+      TRY(upload(h, &h->row_sys, rs));
+    }
     TRY(upload(h, &h->seg_row0, h->seg_row0_h));
     TRY(dalloc(h, &h->d_act, S));
     TRY(dalloc(h, &h->d_jl, S));
@@ -1255,6 +1286,25 @@ SegMap batch_map(const DDHandle *h) {
   return sm;
 }
 
+// the map of the Arnoldi step: every CTA on a system still stepping
+SegMap step_map(const DDHandle *h) {
+  SegMap sm = batch_map(h);
+  sm.cta_seg = h->cta_seg_act;
+  sm.seg_cta0 = h->seg_cta0_act;
+  return sm;
+}
+
+// new active set: the step map follows it (host copy, then upload)
+dd_status remap_active(DDHandle *h, cudaStream_t s) {
+  std::vector<int32_t> c0, cseg;
+  assign_ctas(h->seg_row0_h, h->h_act, h->cgs_blocks, c0, cseg);
+  if ((int)cseg.size() != h->cgs_blocks) return DD_OK;  // nothing stepping
+  CK(cudaMemcpyAsync(h->seg_cta0_act, c0.data(), sizeof(int32_t) * c0.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->cta_seg_act, cseg.data(), sizeof(int32_t) * cseg.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return DD_OK;
+}
+
 // nsq[slot] = ||v||^2
 dd_status norm_sq(DDHandle *h, const double *v, int slot, cudaStream_t s) {
   CK(launch_multidot((int)h->n, 1, v, h->ldv, v, h->partial, h->nblocks, s));
@@ -1275,7 +1325,10 @@ dd_status arnoldi_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, co
   double *vj = h->V + (int64_t)j * h->ldv, *zj = h->Z + (int64_t)j * h->ldv;
   double *w = h->V + (int64_t)(j + 1) * h->ldv;
   TRY(apply_any(h, vj, zj, s));
-  CK(launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
+  if (sm.nseg > 1)  // a batch: only the rows of systems still stepping
+    CK(launch_spmv_masked((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, h->row_sys, sm.act, s));
+  else
+    CK(launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
   CK(launch_cgs2(h->n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
                  h->sn, h->g, bn2, h->out, sm, ncta, s));
   CK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 4 * sm.nseg, cudaMemcpyDeviceToHost, s));
@@ -1401,6 +1454,7 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
   const int S = h->nseg, nc = h->seg_ctas;
   const int64_t n = h->n;
   const SegMap sm = batch_map(h);
+  const SegMap stm = step_map(h);  // the CGS2 kernel's CTAs on the systems still stepping
   // the apply skips the subdomains and aggregates of systems not stepping
   struct Mask {
     DDHandle *h;
@@ -1438,10 +1492,11 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
     }
     if (nact == 0) break;
     CK(cudaMemcpyAsync(h->d_act, act, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+    TRY(remap_active(h, s));
     CK(launch_seg_norms(n, h->r, h->partial, h->rn2, all, nc, s));
     CK(launch_seg_start(n, h->r, h->rn2, h->V, h->g, sm, nc, s));
     for (int j = 0; j < R && nact > 0; ++j) {
-      TRY(run_step(h, j, R, sm, nc, h->bn2, s));
+      TRY(run_step(h, j, R, stm, nc, h->bn2, s));
       CK(cudaStreamSynchronize(s));
       bool changed = false;
       for (int q = 0; q < S; ++q) {
@@ -1466,7 +1521,7 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
       // copies from pinned memory read it when they run: wait before the next change
       if (changed && nact > 0) {
         CK(cudaMemcpyAsync(h->d_act, act, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
+        TRY(remap_active(h, s));
       }
     }
     CK(cudaMemcpyAsync(h->d_jl, jl, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));

@@ -198,6 +198,10 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
 // Krylov (k_krylov.cu), FP64
 cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                         const double *x, double *y, cudaStream_t s);
+// y = C x on the rows i with act[row_sys[i]] != 0 (the other rows untouched)
+cudaError_t launch_spmv_masked(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                               const double *x, double *y, const int32_t *row_sys, const int32_t *act,
+                               cudaStream_t s);
 cudaError_t launch_residual(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                             const double *x, const double *b, double *r, cudaStream_t s);
 cudaError_t launch_multidot(int n, int k, const double *V, int64_t ldv, const double *w,

@@ -26,6 +26,18 @@ __global__ void spmv_kernel(int n, const int32_t *__restrict__ rowptr, const int
   y[i] = s;
 }
 
+// the same, for the rows whose system is still stepping (act[row_sys[i]])
+__global__ void spmv_masked_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                   const double *__restrict__ val, const double *__restrict__ x,
+                                   double *__restrict__ y, const int32_t *__restrict__ row_sys,
+                                   const int32_t *__restrict__ act) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !act[row_sys[i]]) return;
+  double s = 0.0;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * __ldg(&x[col[k]]);
+  y[i] = s;
+}
+
 __global__ void residual_kernel(int n, const int32_t *__restrict__ rowptr,
                                 const int32_t *__restrict__ col, const double *__restrict__ val,
                                 const double *__restrict__ x, const double *__restrict__ b,
@@ -536,6 +548,13 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                         const double *x, double *y, cudaStream_t s) {
   spmv_kernel<<<nblk(n, 256), 256, 0, s>>>(n, rowptr, col, val, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_masked(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                               const double *x, double *y, const int32_t *row_sys, const int32_t *act,
+                               cudaStream_t s) {
+  spmv_masked_kernel<<<nblk(n, 256), 256, 0, s>>>(n, rowptr, col, val, x, y, row_sys, act);
   return cudaGetLastError();
 }
 
