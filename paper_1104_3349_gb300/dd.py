@@ -300,7 +300,7 @@ class DDBatch:
     """A batch of independent systems behind one handle (dd_setup_batched)."""
 
     def __init__(self, systems, kind="msce_inf", prec=DD_FP64, pivot_tol=0.0, max_restart=50, stream=None,
-                 use_graph=False, autotune=False):
+                 use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0):
         """systems: list of (A, part, m, perm, agg_offsets) with A a CSR (perm, agg_offsets may be None)."""
         lib = load()
         self._lib = lib
@@ -318,7 +318,10 @@ class DDBatch:
             rp, col, val, pa, pe, ag = arrs
             csrs[q] = dd_csr(int(A.n), int(rp[-1]), _ptr(rp), _ptr(col), _ptr(val))
             pts[q] = dd_partition(int(m), _ptr(pa), _ptr(pe), 64, _ptr(ag), 0 if ag is None else len(ag) - 1)
-        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)))
+        o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
+                    int(krylov_ctas_per_sm))
+        self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
+        o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
         h = ctypes.c_void_p()
         rc = lib.dd_setup_batched(self.count, csrs, pts, k, ctypes.byref(o), _stream_handle(stream), ctypes.byref(h))

@@ -197,3 +197,27 @@ def test_learned_apply_matches_oracle_128(env):
     assert np.linalg.norm(xd.cpu().numpy() - xr) <= 1e-4 * np.linalg.norm(xr)
     P.close()
     R.close()
+
+
+def test_learned_in_a_batch_matches_each_oracle(env):
+    # DD_LEARNED over a batch: each system's block of the batched apply equals
+    # that system's own oracle learned preconditioner
+    torch, dd, dev = env
+    wts = _trained_or_skip()
+    ws = W.batch_small(count=5, seed=4300)
+    P = dd.DDBatch([(w.A, w.part, w.m, w.perm, w.agg) for w in ws], "learned", mlp_weights=WEIGHTS)
+    ys = [W.uniform(1 + q, w.A.n) for q, w in enumerate(ws)]
+    yd = torch.from_numpy(np.concatenate(ys)).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    torch.cuda.synchronize()
+    x = xd.cpu().numpy()
+    off = 0
+    for q, w in enumerate(ws):
+        R, _, _, _ = L.learned_oracle(w.A, w.part, w.m, w.perm, w.agg, wts)
+        xr = R.apply(ys[q])
+        xs = x[off:off + w.A.n]
+        off += w.A.n
+        assert np.linalg.norm(xs - xr) <= 1e-4 * np.linalg.norm(xr), q
+        R.close()
+    P.close()
