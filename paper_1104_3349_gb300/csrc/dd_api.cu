@@ -803,7 +803,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   CK(cudaGetLastError());
   {
     // persistent LPT task lists when the subdomains outnumber resident CTAs
-    const int occ = band_lu_occupancy<T>(h->max_kl, h->max_ku, 256);
+    const int lu_threads = sizeof(T) == 4 ? 512 : 256;  // the kernel's launch bound per precision
+    const int occ = band_lu_occupancy<T>(h->max_kl, h->max_ku, lu_threads);
     if (occ <= 0) { h->err = "band LU: no resident CTA fits"; return DD_ERR_CUDA; }
     const int slots = occ * sm_count();
     int32_t *d_sched = nullptr, *d_off = nullptr;
@@ -817,7 +818,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
       TRY(upload(h, &d_off, off));
     }
     CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
-                         static_cast<T *>(h->lu_scratch), pivtol, h->st, 256, slots, d_sched, d_off, s));
+                         static_cast<T *>(h->lu_scratch), pivtol, h->st, lu_threads, slots, d_sched, d_off, s));
   }
   // ---- packed sweep tiles: widths from the factors, offsets and jobs here
   {

@@ -25,6 +25,7 @@
 //              upper triangle, so x_T = Kb [b_T; x_next].
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 #include <algorithm>
 
@@ -37,6 +38,17 @@ __host__ __device__ inline int src_stride_w(int w) { return round4(w); }
 // widest window or row of a tile, a multiple of 32 elements
 __host__ __device__ inline int sweep_pad_hd(int max_kl, int max_ku2) {
   return ((max_kl > max_ku2 ? max_kl : max_ku2) + 2 * DD_TB_WIDE + 31) & ~31;
+}
+
+// The band LU's window: R = NB + kl rows by Cw = NB + kl + ku columns, with
+// three spare rows and a row stride of at least Cw + 3, odd (so that walks
+// down a column are free of bank conflicts).  The rank-NB update then runs in
+// whole 4 x 4 micro-tiles without bounds checks: its rows reach R + 2 and its
+// columns Cw + 2, and entries computed outside R x Cw land in the spare rows
+// and columns, which nothing else reads.
+__host__ __device__ inline int lu_ldw(int kl, int ku) { return (DD_NB + kl + ku + 3) | 1; }
+__host__ __device__ inline int64_t lu_window_elems(int kl, int ku) {
+  return (int64_t)(DD_NB + kl + 3) * lu_ldw(kl, ku);
 }
 
 template <typename T>
@@ -67,11 +79,102 @@ __host__ __device__ __forceinline__ int kidx(int r, int c) {
 // later columns reach the multipliers of earlier columns of the same tile
 // only, which is the order the forward sweep applies them in.
 // ---------------------------------------------------------------------------
+// CTA-wide argmax, ordered by value (larger first) then logical row (lower
+// first): every thread offers (v, L, r); the warps' winners go to buffer buf.
+// Every thread of the CTA must call it.
+template <typename T>
+__device__ __forceinline__ void offer_max(T v, int L, int r, T (*bv)[32], int (*bL)[32], int (*br)[32], int buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oL = __shfl_xor_sync(0xffffffffu, L, o);
+    const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+    if (ov > v || (ov == v && oL < L)) { v = ov; L = oL; r = orr; }
+  }
+  if (lane == 0) { bv[buf][warp] = v; bL[buf][warp] = L; br[buf][warp] = r; }
+}
+
+// Panel factorisation with the row exchanges deferred: window rows stay in
+// place while the panel's pivots are chosen (thread r owns row r, R <=
+// blockDim.x).  Each thread keeps its row's logical position L, the position
+// the exchanges so far would have moved it to, so ties go to the first
+// logical row, as in the column-by-column algorithm.  The next column's
+// candidates are offered as soon as a row is updated, so each column costs
+// one barrier.  The exchanges are then applied, in order, to every column.
+// Returns false (status set) if a pivot fails the test.
+template <typename T>
+__device__ bool lu_panel_lazy(T *W, int ldw, int R, int Cw, int c0, int n, int kl, int nbe, T thresh,
+                              int32_t *P, DevStatus *st, int task) {
+  __shared__ T bv[2][32];
+  __shared__ int bL[2][32], br[2][32];
+  __shared__ int sj[DD_NB];
+  const int tid = threadIdx.x, nw = blockDim.x >> 5;
+  const int r = tid;
+  const bool own = r < R;
+  int L = r;
+  bool chosen = false;
+  {
+    const int last = min(min(R - 1, kl), n - 1 - c0);
+    T v = T(-1);
+    if (own && r <= last) {
+      v = tabs(W[r * ldw]);
+      if (!(v == v)) v = T(-1);
+    }
+    offer_max(v, own ? L : INT_MAX, r, bv, bL, br, 0);
+  }
+  for (int c = 0; c < nbe; ++c) {
+    __syncthreads();  // column c's offers and every update of column c-1 are done
+    const int buf = c & 1;
+    T best = bv[buf][0];
+    int bestL = bL[buf][0], pr = br[buf][0];
+    for (int w = 1; w < nw; ++w) {
+      const T v = bv[buf][w];
+      const int l2 = bL[buf][w];
+      if (v > best || (v == best && l2 < bestL)) { best = v; bestL = l2; pr = br[buf][w]; }
+    }
+    if (!(best > thresh)) {
+      if (tid == 0) set_status(st, DD_ERR_SINGULAR_BLOCK, task);
+      return false;
+    }
+    const int j = bestL;
+    if (tid == 0) { P[c0 + c] = c0 + j; sj[c] = j; }
+    const int last = min(min(R - 1, c + kl), n - 1 - c0);
+    if (own && !chosen && r != pr && r <= last) {
+      const T l = W[r * ldw + c] / W[pr * ldw + c];
+      W[r * ldw + c] = l;
+      for (int q = c + 1; q < DD_NB; ++q) W[r * ldw + q] -= l * W[pr * ldw + q];
+    }
+    if (r == pr) { chosen = true; L = c; }
+    else if (L == c) { L = j; }
+    if (c + 1 < nbe) {
+      const int lastn = min(min(R - 1, c + 1 + kl), n - 1 - c0);
+      T v = T(-1);
+      if (own && !chosen && r <= lastn) {
+        v = tabs(W[r * ldw + c + 1]);
+        if (!(v == v)) v = T(-1);
+      }
+      offer_max(v, (own && !chosen) ? L : INT_MAX, r, bv, bL, br, (c + 1) & 1);
+    }
+  }
+  __syncthreads();  // every update and the exchange list are done
+  for (int q = tid; q < Cw; q += blockDim.x)
+    for (int c = 0; c < nbe; ++c) {
+      const int j = sj[c];
+      if (j != c) {
+        const T t = W[c * ldw + q];
+        W[c * ldw + q] = W[j * ldw + q];
+        W[j * ldw + q] = t;
+      }
+    }
+  __syncthreads();
+  return true;
+}
+
 template <typename T>
 __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int32_t *piv, T *W,
                              double pivtol, DevStatus *st) {
   const int n = b.n, kl = b.kl, ku = b.ku, wd = 2 * kl + ku + 1;
-  const int R = DD_NB + kl, Cw = DD_NB + kl + ku, ldw = Cw | 1;
+  const int R = DD_NB + kl, Cw = DD_NB + kl + ku, ldw = lu_ldw(kl, ku);
   T *A = band + b.band_off;
   int32_t *P = piv + b.piv_off;
   __shared__ T red[32];
@@ -119,7 +222,11 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       }
     }
     __syncthreads();
-    // panel: column by column
+    // panel: column by column (deferred exchanges when a thread owns each
+    // window row, else exchanges as they come)
+    if (R <= nt) {
+      if (!lu_panel_lazy<T>(W, ldw, R, Cw, c0, n, kl, nbe, thresh, P, st, task)) return;
+    } else
     for (int c = 0; c < nbe; ++c) {
       const int last = min(min(R - 1, c + kl), n - 1 - c0);
       if (warp == 0) {
@@ -157,18 +264,30 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       __syncthreads();
     }
     // U12 = L11^-1 A12 (rows 0..NB-1, columns NB..Cw-1): one thread per
-    // column, forward substitution with the unit lower L11 in registers
-    for (int q = DD_NB + tid; q < Cw; q += nt) {
-      T x[DD_NB];
+    // column, forward substitution with the unit lower L11.  FP32 (window in
+    // shared memory, 512 threads) works in place; FP64 (window in global
+    // scratch at the bench's bandwidths, 256 threads) keeps the column in
+    // registers.
+    if constexpr (sizeof(T) == 4) {
+      for (int q = DD_NB + tid; q < Cw; q += nt)
+        for (int c = 0; c < nbe - 1; ++c) {
+          const T xc = W[c * ldw + q];
+#pragma unroll 8
+          for (int r = c + 1; r < DD_NB; ++r) W[r * ldw + q] -= W[r * ldw + c] * xc;
+        }
+    } else {
+      for (int q = DD_NB + tid; q < Cw; q += nt) {
+        T x[DD_NB];
 #pragma unroll
-      for (int r = 0; r < DD_NB; ++r) x[r] = W[r * ldw + q];
+        for (int r = 0; r < DD_NB; ++r) x[r] = W[r * ldw + q];
 #pragma unroll
-      for (int c = 0; c < DD_NB - 1; ++c)
+        for (int c = 0; c < DD_NB - 1; ++c)
 #pragma unroll
-        for (int r = c + 1; r < DD_NB; ++r)
-          if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
+          for (int r = c + 1; r < DD_NB; ++r)
+            if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
 #pragma unroll
-      for (int r = 1; r < DD_NB; ++r) W[r * ldw + q] = x[r];
+        for (int r = 1; r < DD_NB; ++r) W[r * ldw + q] = x[r];
+      }
     }
     __syncthreads();
     // A22 -= L21 U12 (rows NB..R-1, columns NB..Cw-1): each thread 4 rows by
@@ -187,12 +306,9 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
         for (int k = 0; k < nbe; ++k) {
           T lv[4], uv[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) lv[a] = (i0 + a < R) ? W[(i0 + a) * ldw + k] : T(0);
+          for (int a = 0; a < 4; ++a) lv[a] = W[(i0 + a) * ldw + k];
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2) {
-            const int j = jc + c2 * qw;
-            uv[c2] = (j < Cw) ? W[k * ldw + j] : T(0);
-          }
+          for (int c2 = 0; c2 < 4; ++c2) uv[c2] = W[k * ldw + jc + c2 * qw];
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -201,10 +317,7 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2) {
-            const int j = jc + c2 * qw;
-            if (i0 + a < R && j < Cw) W[(i0 + a) * ldw + j] -= acc[a][c2];
-          }
+          for (int c2 = 0; c2 < 4; ++c2) W[(i0 + a) * ldw + jc + c2 * qw] -= acc[a][c2];
       }
     }
     __syncthreads();
@@ -231,7 +344,7 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 // window sits in shared memory when it fits the launch's smem_bytes, else in
 // wscratch (wscratch_stride elements per subdomain).
 template <typename T>
-__global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
                                T *wscratch, int64_t wscratch_stride, int smem_bytes, double pivtol,
                                const int32_t *__restrict__ sched, const int32_t *__restrict__ sched_off,
                                DevStatus *st) {
@@ -242,7 +355,7 @@ __global__ void band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *lt
     const int task = sched ? sched[it] : it;
     const BandInfo b = info[task];
     if (b.n == 0) continue;
-    const int64_t wb = (int64_t)(DD_NB + b.kl) * ((DD_NB + b.kl + b.ku) | 1) * (int64_t)sizeof(T);
+    const int64_t wb = lu_window_elems(b.kl, b.ku) * (int64_t)sizeof(T);
     T *W = (wb <= smem_bytes) ? reinterpret_cast<T *>(smraw) : wscratch + (int64_t)task * wscratch_stride;
     __syncthreads();  // the previous task is done with the window and the shared scalars
     band_lu_task<T>(b, task, band, ltraw, piv, W, pivtol, st);
@@ -898,8 +1011,7 @@ size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, i
 }
 
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
-  const int R = DD_NB + max_kl, Cw = DD_NB + max_kl + max_ku;
-  return (size_t)R * (size_t)(Cw | 1) * elem_size;
+  return (size_t)lu_window_elems(max_kl, max_ku) * elem_size;
 }
 
 template <typename T>
