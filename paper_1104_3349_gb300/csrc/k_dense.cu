@@ -191,7 +191,7 @@ __global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_
 //   [panel p x (NB+1) within 2*NB*p | Pcol p x NB | Rnew NB x p | A11inv NB x NB]
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
-__global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+__global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
                                  T *A, T *scratch, const int64_t *__restrict__ poff,
                                  int32_t *ipiv, const T *__restrict__ amax, double pivtol,
                                  int32_t *failed, DevStatus *st, int code, int smem_rows) {
@@ -218,11 +218,18 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
   }
   __syncthreads();
   const T thresh = T(pivtol) * amax[b];
-  for (int c = 0; c < nbe; ++c) {
+  // Column c: warp 0 picks the pivot row pr among the candidates (largest
+  // |W(r, c)|, then lowest r) and copies rows pr and c; then, in one pass,
+  // row c takes the pivot row, row pr takes the old row c, every row below c
+  // is eliminated, and its entry of column c+1 is offered as the next
+  // candidate.  Two barriers per column; the arithmetic is that of exchanging
+  // rows c and pr and then eliminating.
+  __shared__ T prow[NB], crow[NB];
+  {
     T best = T(-1);
     int besti = rows;
-    for (int r = c + tid; r < rows; r += nt) {
-      T v = tabs(W[r * LD + c]);
+    for (int r = tid; r < rows; r += nt) {
+      const T v = tabs(W[r * LD]);
       if (v > best) { best = v; besti = r; }
     }
     for (int o = 16; o; o >>= 1) {
@@ -231,67 +238,138 @@ __global__ void bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const in
       if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
     }
     if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
-    __syncthreads();
-    if (tid == 0) {
-      T bb = bv[0];
-      int ii = bi[0];
-      for (int w = 1; w < nw; ++w)
-        if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
-      if (!(bb > thresh)) {
-        s_fail = 1;
-        failed[b] = 1;
-        set_status2(st, code, b);
+  }
+  __syncthreads();
+  for (int c = 0; c < nbe; ++c) {
+    if (warp == 0) {
+      T bb = lane < nw ? bv[lane] : T(-1);
+      int ii = lane < nw ? bi[lane] : rows;
+      for (int o = 16; o; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, bb, o);
+        int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+        if (ov > bb || (ov == bb && oi < ii)) { bb = ov; ii = oi; }
       }
-      s_piv = ii;
-      ipiv[poff[b] + k0 + c] = k0 + ii;
+      if (lane == 0) {
+        if (!(bb > thresh)) {
+          s_fail = 1;
+          failed[b] = 1;
+          set_status2(st, code, b);
+        }
+        s_piv = ii;
+        ipiv[poff[b] + k0 + c] = k0 + ii;
+      }
+      if (lane < NB && ii < rows) {
+        prow[lane] = W[ii * LD + lane];
+        crow[lane] = W[c * LD + lane];
+      }
     }
     __syncthreads();
     if (s_fail) return;
     const int pr = s_piv;
-    if (pr != c && tid < NB) {
-      T t = W[c * LD + tid]; W[c * LD + tid] = W[pr * LD + tid]; W[pr * LD + tid] = t;
-    }
-    __syncthreads();
-    const T piv = W[c * LD + c];
+    const T piv = prow[c];
+    if (tid < NB) W[c * LD + tid] = prow[tid];
+    T best = T(-1);
+    int besti = rows;
     for (int r = c + 1 + tid; r < rows; r += nt) {
-      const T l = W[r * LD + c] / piv;
+      const bool sw = (r == pr);
+      const T l = (sw ? crow[c] : W[r * LD + c]) / piv;
       W[r * LD + c] = l;
-      for (int q = c + 1; q < nbe; ++q) W[r * LD + q] -= l * W[c * LD + q];
-    }
-    __syncthreads();
-  }
-  // row exchanges on whole rows of A, in order; every thread applies all of
-  // them to its own columns, so no barrier is needed between exchanges
-  __shared__ int s_q[NB];
-  if (tid < nbe) s_q[tid] = ipiv[poff[b] + k0 + tid];
-  __syncthreads();
-  for (int j = tid; j < p; j += nt)
-    for (int c = 0; c < nbe; ++c) {
-      const int q = s_q[c];
-      if (q != k0 + c) {
-        T t = a[(int64_t)(k0 + c) * p + j];
-        a[(int64_t)(k0 + c) * p + j] = a[(int64_t)q * p + j];
-        a[(int64_t)q * p + j] = t;
+      if (sw)
+        for (int q = 0; q < c; ++q) W[r * LD + q] = crow[q];
+      for (int q = c + 1; q < nbe; ++q) {
+        T t = sw ? crow[q] : W[r * LD + q];
+        t -= l * prow[q];
+        W[r * LD + q] = t;
+      }
+      if (c + 1 < nbe) {
+        const T v = tabs(W[r * LD + c + 1]);
+        if (v > best) { best = v; besti = r; }
       }
     }
+    for (int o = 16; o; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+      if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
+    }
+    if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
+    __syncthreads();
+  }
+  // Row exchanges on whole rows of A.  The exchanges k0+c <-> q_c (c in
+  // order, q_c >= k0+c) touch at most 2 nbe rows; destination d ends up
+  // holding the old row tau_0(tau_1(...tau_{nbe-1}(d))), found by walking the
+  // transpositions backwards.  Every thread then loads all touched rows of
+  // its columns before storing any, so the loads are independent.
+  static_assert(2 * NB <= 32, "one warp lists the exchanged rows");
+  __shared__ int s_q[NB];
+  __shared__ int64_t s_so[2 * NB], s_do[2 * NB];
+  __shared__ int s_cnt;
+  if (tid < nbe) s_q[tid] = ipiv[poff[b] + k0 + tid];
   __syncthreads();
-  // A11^-1 = U11^-1 L11^-1, one column per thread of warp 0
+  if (warp == 0) {
+    int d = -1, x = -1;
+    if (lane < 2 * nbe) {
+      d = lane < nbe ? k0 + lane : s_q[lane - nbe];
+      if (lane >= nbe && d < k0 + nbe) d = -1;  // a panel row, already listed
+      x = d;
+      if (d >= 0)
+        for (int c = nbe - 1; c >= 0; --c) {
+          const int q = s_q[c];
+          if (x == k0 + c) x = q;
+          else if (x == q) x = k0 + c;
+        }
+    }
+    const bool moved = d >= 0 && x != d;
+    const unsigned m = __ballot_sync(0xffffffffu, moved);
+    if (moved) {
+      const int pos = __popc(m & ((1u << lane) - 1u));
+      s_so[pos] = (int64_t)x * p;
+      s_do[pos] = (int64_t)d * p;
+    }
+    if (lane == 0) s_cnt = __popc(m);
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  // volatile: the row offsets are re-read from shared memory per column
+  // rather than held in registers across the loop
+  const volatile int64_t *so = s_so, *dof = s_do;
+  for (int j = tid; j < p; j += nt) {
+    T v[2 * NB];
+#pragma unroll
+    for (int t = 0; t < 2 * NB; ++t)
+      if (t < cnt) v[t] = a[so[t] + j];
+#pragma unroll
+    for (int t = 0; t < 2 * NB; ++t)
+      if (t < cnt) a[dof[t] + j] = v[t];
+  }
+  __syncthreads();
+  // A11^-1 = U11^-1 L11^-1, one column per thread of warp 0, unrolled so
+  // that the column stays in registers
   if (tid < nbe) {
     const int j = tid;
     T x[NB];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) x[i] = T(0);
-    x[j] = T(1);
-    for (int i = j + 1; i < nbe; ++i) {  // L11 y = e_j (unit lower)
-      T s2 = T(0);
-      for (int q = j; q < i; ++q) s2 += W[i * LD + q] * x[q];
-      x[i] = -s2;
+    for (int i = 0; i < NB; ++i) x[i] = (i == j) ? T(1) : T(0);
+#pragma unroll
+    for (int i = 1; i < NB; ++i) {  // L11 y = e_j (unit lower); x[q] = 0 for q < j
+      if (i < nbe && i > j) {
+        T s2 = T(0);
+#pragma unroll
+        for (int q = 0; q < i; ++q)
+          if (q >= j) s2 += W[i * LD + q] * x[q];
+        x[i] = -s2;
+      }
     }
-    for (int i = nbe - 1; i >= 0; --i) {  // U11 x = y
-      T s2 = x[i];
-      for (int q = i + 1; q < nbe; ++q) s2 -= W[i * LD + q] * x[q];
-      x[i] = s2 / W[i * LD + i];
+#pragma unroll
+    for (int i = NB - 1; i >= 0; --i) {  // U11 x = y
+      if (i < nbe) {
+        T s2 = x[i];
+#pragma unroll
+        for (int q = i + 1; q < NB; ++q)
+          if (q < nbe) s2 -= W[i * LD + q] * x[q];
+        x[i] = s2 / W[i * LD + i];
+      }
     }
+#pragma unroll
     for (int i = 0; i < NB; ++i) a11inv[i * NB + j] = (i < nbe) ? x[i] : T(0);
   } else if (tid < NB) {
     for (int i = 0; i < NB; ++i) a11inv[i * NB + tid] = T(0);
