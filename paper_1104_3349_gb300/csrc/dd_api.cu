@@ -392,7 +392,7 @@ void extract_blocks(DDHandle *h, const dd_csr *csr, const dd_partition *pt, Host
 }
 
 int64_t launch_cost(const char *call, const DDHandle *h) {
-  if (strstr(call, "launch_gj_inverse")) return 3LL * ((h->pmax + (h->prec == DD_FP32 ? 15 : 7)) / (h->prec == DD_FP32 ? 16 : 8)) + 2;
+  if (strstr(call, "launch_gj_inverse")) return gj_launch_count(h->pmax, h->prec == DD_FP32 ? 4 : 8);
   if (strstr(call, "launch_hess_solve_update")) return 2;
   if (strstr(call, "launch_schur_apply")) return 2;
   if (strstr(call, "launch_seg_norms")) return 2;

@@ -163,6 +163,8 @@ cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off
 // through st with status_code.
 // scratch (elements of T) of launch_gj_inverse for nblk blocks of total size sum_p
 int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size);
+// kernel launches of one launch_gj_inverse call for blocks of size <= pmax
+int64_t gj_launch_count(int pmax, int elem_size);
 template <typename T>
 cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
                               int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,

@@ -174,38 +174,81 @@ __global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_
 }
 
 // ---------------------------------------------------------------------------
-// Blocked Gauss-Jordan inverse.  For each panel of NB columns k0..k0+NB-1:
-//  (1) panel kernel (one CTA per block): LU with partial pivoting of the
-//      panel rows k0..p-1 on a copy in shared memory (or global scratch when
-//      the panel does not fit), the row exchanges applied to whole rows of A,
-//      and A11^-1 = U11^-1 L11^-1 of the pivot block;
-//  (2) row-block kernel: Rnew = A11^-1 A(R, :) and a copy Pcol = A(:, panel);
-//  (3) update kernel (tiled, many CTAs per block):
+// Blocked Gauss-Jordan inverse with two levels of blocking.  For each outer
+// block of NO columns k0..k0+NO-1 (NO = 64 in FP32, 32 in FP64):
+//  (1) copy: W = A(k0:p, panel), a tall p-k0 x NO panel in scratch;
+//  (2) LU with partial pivoting of W, NB columns at a time (NB = 16 / 8):
+//      panel kernel (one CTA per block: pivots, multipliers, the exchanges
+//      on the other columns of W, U12 = L11^-1 A12) then a trailing update
+//      of W's remaining columns (many CTAs per block);
+//  (3) the NO row exchanges on whole rows of A, through a staged copy of
+//      the touched rows;
+//  (4) row block: Rnew = A11^-1 A(R, :) by forward and back substitution
+//      with W's L11 and U11 (the panel columns take identity right-hand
+//      sides, giving A11^-1), and a copy Pcol = A(:, panel);
+//  (5) update kernel (tiled):
 //        A(R, panel) = A11^-1,  A(R, j) = Rnew(:, j),
 //        A(i, panel) = -Pcol(i, :) A11^-1,  A(i, j) -= Pcol(i, :) Rnew(:, j).
-// The pivots are those of LU with partial pivoting (first largest magnitude),
-// so the inverse is the one Gauss-Jordan computes column by column, with the
-// rank-1 passes grouped into rank-NB updates.  The row exchanges are undone
-// as column exchanges at the end.
-// Scratch per block b at 4*NB*poff[b] + NB*NB*b elements:
-//   [panel p x (NB+1) within 2*NB*p | Pcol p x NB | Rnew NB x p | A11inv NB x NB]
+// The pivots are those of LU with partial pivoting (largest magnitude, then
+// lowest row), so in exact arithmetic the result is the inverse Gauss-Jordan
+// computes column by column, with the rank-1 passes grouped into rank-NO
+// updates of the whole matrix.  The row exchanges are undone as column
+// exchanges at the end.
+// Scratch per block b at gj_base(b) = 6*NO*poff[b] + (NO*NO + 4*NO)*b:
+//   [W p x NO | panel copy p x (NB+1) (when it does not fit in shared memory)
+//    within NO*p | Pcol p x NO | Rnew NO x p | staged rows 2NO x p |
+//    A11^-1 NO x NO | exchange list 4*NO int32]
 // ---------------------------------------------------------------------------
-template <typename T, int NB>
-__global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                 T *A, T *scratch, const int64_t *__restrict__ poff,
-                                 int32_t *ipiv, const T *__restrict__ amax, double pivtol,
-                                 int32_t *failed, DevStatus *st, int code, int smem_rows) {
+template <typename T>
+struct BgjNB { static const int value = 16; };
+template <>
+struct BgjNB<double> { static const int value = 8; };
+template <typename T>
+struct BgjNO { static const int value = 64; };
+template <>
+struct BgjNO<double> { static const int value = 32; };
+
+template <typename T, int NO>
+__device__ __forceinline__ T *gj_base(T *scratch, const int64_t *poff, int b) {
+  return scratch + 6 * (int64_t)NO * poff[b] + (int64_t)(NO * NO + 4 * NO) * b;
+}
+
+// (1) W(r, c) = A(k0 + r, k0 + c), zero beyond the matrix
+template <typename T, int NO>
+__global__ void bgj_copy_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
+                                const T *__restrict__ A, T *scratch, const int64_t *__restrict__ poff,
+                                const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int rows = p - k0, nbo = min(NO, rows);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * NO) return;
+  const int r = (int)(e / NO), c = (int)(e % NO);
+  T *W = gj_base<T, NO>(scratch, poff, b);
+  W[e] = (c < nbo) ? A[off[b] + (int64_t)(k0 + r) * p + k0 + c] : T(0);
+}
+
+// (2a) Columns c0..c0+nbe-1 of W (c0 = NB*s), rows c0..: LU with partial
+// pivoting on a copy in shared memory (or scratch), written back; the row
+// exchanges applied to W's other columns; U12 = L11^-1 W(c0:c0+nbe, right).
+template <typename T, int NB, int NO>
+__global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, int s, const int32_t *__restrict__ P,
+                                                            T *scratch, const int64_t *__restrict__ poff,
+                                                            int32_t *ipiv, const T *__restrict__ amax,
+                                                            double pivtol, int32_t *failed, DevStatus *st,
+                                                            int code, int smem_rows) {
   const int b = blockIdx.x;
   const int p = P[b];
   if (k0 >= p || failed[b]) return;
-  const int nbe = min(NB, p - k0), rows = p - k0;
-  T *a = A + off[b];
-  T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
+  const int rows_all = p - k0, nbo = min(NO, rows_all), c0 = NB * s;
+  if (c0 >= nbo) return;
+  const int nbe = min(NB, nbo - c0), rows = rows_all - c0;
+  T *Wg = gj_base<T, NO>(scratch, poff, b);
   extern __shared__ __align__(128) unsigned char smraw[];
   // rows x NB with row stride NB+1 (conflict-free for row- and column-wise access)
   constexpr int LD = NB + 1;
-  T *W = (rows <= smem_rows) ? reinterpret_cast<T *>(smraw) : scr;
-  T *a11inv = scr + 4 * (int64_t)NB * p;
+  T *W = (rows <= smem_rows) ? reinterpret_cast<T *>(smraw) : Wg + (int64_t)NO * p;
   __shared__ T bv[32];
   __shared__ int bi[32];
   __shared__ int s_piv;
@@ -214,7 +257,7 @@ __global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_
   if (tid == 0) s_fail = 0;
   for (int e = tid; e < rows * NB; e += nt) {
     const int r = e / NB, c = e % NB;
-    W[r * LD + c] = (c < nbe) ? a[(int64_t)(k0 + r) * p + k0 + c] : T(0);
+    W[r * LD + c] = (c < nbe) ? Wg[(int64_t)(c0 + r) * NO + c0 + c] : T(0);
   }
   __syncthreads();
   const T thresh = T(pivtol) * amax[b];
@@ -240,6 +283,7 @@ __global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_
     if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
   }
   __syncthreads();
+  __shared__ int s_q[NB];  // W row of the pivot of column c0 + c
   for (int c = 0; c < nbe; ++c) {
     if (warp == 0) {
       T bb = lane < nw ? bv[lane] : T(-1);
@@ -256,7 +300,8 @@ __global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_
           set_status2(st, code, b);
         }
         s_piv = ii;
-        ipiv[poff[b] + k0 + c] = k0 + ii;
+        s_q[c] = c0 + ii;
+        ipiv[poff[b] + k0 + c0 + c] = k0 + c0 + ii;
       }
       if (lane < NB && ii < rows) {
         prow[lane] = W[ii * LD + lane];
@@ -294,127 +339,319 @@ __global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, const int32_
     if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
     __syncthreads();
   }
-  // Row exchanges on whole rows of A.  The exchanges k0+c <-> q_c (c in
-  // order, q_c >= k0+c) touch at most 2 nbe rows; destination d ends up
+  // the factored columns back into W
+  for (int e = tid; e < rows * nbe; e += nt) {
+    const int r = e / nbe, c = e % nbe;
+    Wg[(int64_t)(c0 + r) * NO + c0 + c] = W[r * LD + c];
+  }
+  // The same exchanges on W's other columns.  Exchanges c0+c <-> q_c (c in
+  // order, q_c >= c0+c) touch at most 2 nbe rows; destination d ends up
   // holding the old row tau_0(tau_1(...tau_{nbe-1}(d))), found by walking the
-  // transpositions backwards.  Every thread then loads all touched rows of
-  // its columns before storing any, so the loads are independent.
+  // transpositions backwards.  One thread per column loads all touched rows
+  // before storing any.
   static_assert(2 * NB <= 32, "one warp lists the exchanged rows");
-  __shared__ int s_q[NB];
-  __shared__ int64_t s_so[2 * NB], s_do[2 * NB];
+  __shared__ int s_dst[2 * NB], s_src[2 * NB];
   __shared__ int s_cnt;
-  if (tid < nbe) s_q[tid] = ipiv[poff[b] + k0 + tid];
-  __syncthreads();
   if (warp == 0) {
     int d = -1, x = -1;
     if (lane < 2 * nbe) {
-      d = lane < nbe ? k0 + lane : s_q[lane - nbe];
-      if (lane >= nbe && d < k0 + nbe) d = -1;  // a panel row, already listed
+      d = lane < nbe ? c0 + lane : s_q[lane - nbe];
+      if (lane >= nbe && d < c0 + nbe) d = -1;  // a panel row, already listed
       x = d;
       if (d >= 0)
         for (int c = nbe - 1; c >= 0; --c) {
           const int q = s_q[c];
-          if (x == k0 + c) x = q;
-          else if (x == q) x = k0 + c;
+          if (x == c0 + c) x = q;
+          else if (x == q) x = c0 + c;
         }
     }
     const bool moved = d >= 0 && x != d;
     const unsigned m = __ballot_sync(0xffffffffu, moved);
     if (moved) {
       const int pos = __popc(m & ((1u << lane) - 1u));
-      s_so[pos] = (int64_t)x * p;
-      s_do[pos] = (int64_t)d * p;
+      s_src[pos] = x;
+      s_dst[pos] = d;
     }
     if (lane == 0) s_cnt = __popc(m);
   }
   __syncthreads();
-  const int cnt = s_cnt;
-  // volatile: the row offsets are re-read from shared memory per column
-  // rather than held in registers across the loop
-  const volatile int64_t *so = s_so, *dof = s_do;
-  for (int j = tid; j < p; j += nt) {
-    T v[2 * NB];
+  {
+    const int cnt = s_cnt;
+    const int j = tid < c0 ? tid : tid + nbe;  // the columns outside this step
+    if (tid < nbo - nbe) {
+      T v[2 * NB];
 #pragma unroll
-    for (int t = 0; t < 2 * NB; ++t)
-      if (t < cnt) v[t] = a[so[t] + j];
+      for (int t = 0; t < 2 * NB; ++t)
+        if (t < cnt) v[t] = Wg[(int64_t)s_src[t] * NO + j];
 #pragma unroll
-    for (int t = 0; t < 2 * NB; ++t)
-      if (t < cnt) a[dof[t] + j] = v[t];
+      for (int t = 0; t < 2 * NB; ++t)
+        if (t < cnt) Wg[(int64_t)s_dst[t] * NO + j] = v[t];
+    }
   }
   __syncthreads();
-  // A11^-1 = U11^-1 L11^-1, one column per thread of warp 0, unrolled so
-  // that the column stays in registers
-  if (tid < nbe) {
-    const int j = tid;
-    T x[NB];
+  // U12 = L11^-1 W(c0:c0+nbe, j) for the columns right of this step
+  {
+    const int j = c0 + nbe + tid;
+    if (j < nbo) {
+      T x[NB];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) x[i] = (i == j) ? T(1) : T(0);
+      for (int c = 0; c < NB; ++c) x[c] = (c < nbe) ? Wg[(int64_t)(c0 + c) * NO + j] : T(0);
 #pragma unroll
-    for (int i = 1; i < NB; ++i) {  // L11 y = e_j (unit lower); x[q] = 0 for q < j
-      if (i < nbe && i > j) {
-        T s2 = T(0);
+      for (int c = 1; c < NB; ++c) {
+        if (c < nbe) {
+          T t = x[c];
 #pragma unroll
-        for (int q = 0; q < i; ++q)
-          if (q >= j) s2 += W[i * LD + q] * x[q];
-        x[i] = -s2;
+          for (int q = 0; q < c; ++q) t -= W[c * LD + q] * x[q];
+          x[c] = t;
+        }
       }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nbe) Wg[(int64_t)(c0 + c) * NO + j] = x[c];
     }
-#pragma unroll
-    for (int i = NB - 1; i >= 0; --i) {  // U11 x = y
-      if (i < nbe) {
-        T s2 = x[i];
-#pragma unroll
-        for (int q = i + 1; q < NB; ++q)
-          if (q < nbe) s2 -= W[i * LD + q] * x[q];
-        x[i] = s2 / W[i * LD + i];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) a11inv[i * NB + j] = (i < nbe) ? x[i] : T(0);
-  } else if (tid < NB) {
-    for (int i = 0; i < NB; ++i) a11inv[i * NB + tid] = T(0);
   }
 }
 
-template <typename T, int NB>
-__global__ void bgj_rowblock_kernel(int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                    const T *__restrict__ A, T *scratch, const int64_t *__restrict__ poff,
-                                    const int32_t *__restrict__ failed) {
+// (2b) W(i, j) -= L21(i, :) U12(:, j) for the rows below and the columns
+// right of step s; CTA x takes 64 rows
+template <typename T, int NB, int NO>
+__global__ void __launch_bounds__(256) bgj_trail_kernel(int k0, int s, const int32_t *__restrict__ P,
+                                                        T *scratch, const int64_t *__restrict__ poff,
+                                                        const int32_t *__restrict__ failed) {
   const int b = blockIdx.y;
   const int p = P[b];
   if (k0 >= p || failed[b]) return;
-  const int nbe = min(NB, p - k0);
+  const int rows_all = p - k0, nbo = min(NO, rows_all), c0 = NB * s;
+  if (c0 >= nbo) return;
+  const int nbe = min(NB, nbo - c0), j0 = c0 + nbe, ncol = nbo - j0;
+  const int i0 = j0 + 64 * blockIdx.x;
+  if (ncol <= 0 || i0 >= rows_all) return;
+  const int nr = min(64, rows_all - i0);
+  T *Wg = gj_base<T, NO>(scratch, poff, b);
+  __shared__ T Us[NB][NO];
+  __shared__ T Ls[64][NB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NO; e += blockDim.x) {
+    const int c = e / NO, q = e % NO;
+    Us[c][q] = (c < nbe && q < ncol) ? Wg[(int64_t)(c0 + c) * NO + j0 + q] : T(0);
+  }
+  for (int e = tid; e < 64 * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    Ls[r][c] = (r < nr && c < nbe) ? Wg[(int64_t)(i0 + r) * NO + c0 + c] : T(0);
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * ncol; e += blockDim.x) {
+    const int r = e / ncol, q = e % ncol;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc += Ls[r][c] * Us[c][q];
+    T *o = &Wg[(int64_t)(i0 + r) * NO + j0 + q];
+    *o = *o - acc;
+  }
+}
+
+// (3) The outer block's exchanges k0+c <-> ipiv(k0+c), c < nbo, in order, on
+// whole rows of A: every CTA lists the touched rows (destination d holds the
+// old row found by walking the exchanges backwards; at most 2 nbo rows),
+// CTA 0 stores the list, and each thread stages its column of the touched
+// rows.  The write kernel then stores them in their new places.
+template <int NO>
+__device__ __forceinline__ void gj_exchange_list(int k0, int nbo, const int32_t *ip, int *s_q, int *s_dst,
+                                                 int *s_src) {
+  const int tid = threadIdx.x;
+  if (tid < nbo) s_q[tid] = ip[k0 + tid];
+  __syncthreads();
+  if (tid < 2 * NO) {
+    int d = -1, x = -1;
+    if (tid < 2 * nbo) {
+      d = tid < nbo ? k0 + tid : s_q[tid - nbo];
+      if (tid >= nbo && d < k0 + nbo) d = -1;  // a row of the block, already listed
+      x = d;
+      if (d >= 0)
+        for (int c = nbo - 1; c >= 0; --c) {
+          const int q = s_q[c];
+          if (x == k0 + c) x = q;
+          else if (x == q) x = k0 + c;
+        }
+    }
+    s_dst[tid] = (d >= 0 && x != d) ? d : -1;
+    s_src[tid] = x;
+  }
+  __syncthreads();
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) bgj_stage_kernel(int k0, const int32_t *__restrict__ P,
+                                                        const int64_t *__restrict__ off, const T *__restrict__ A,
+                                                        T *scratch, const int64_t *__restrict__ poff,
+                                                        const int32_t *__restrict__ ipiv,
+                                                        const int32_t *__restrict__ failed) {
+  static_assert(2 * NO <= 256, "one thread per listed row");
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbo = min(NO, p - k0);
+  T *base = gj_base<T, NO>(scratch, poff, b);
+  T *Tst = base + 4 * (int64_t)NO * p;
+  int32_t *lst = reinterpret_cast<int32_t *>(base + 6 * (int64_t)NO * p + NO * NO);
+  __shared__ int s_q[NO], s_dst[2 * NO], s_src[2 * NO];
+  gj_exchange_list<NO>(k0, nbo, ipiv + poff[b], s_q, s_dst, s_src);
+  if (blockIdx.x == 0 && threadIdx.x < 2 * NO) {
+    lst[threadIdx.x] = s_dst[threadIdx.x];
+    lst[2 * NO + threadIdx.x] = s_src[threadIdx.x];
+  }
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
   const T *a = A + off[b];
-  T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
-  T *Pcol = scr + 2 * (int64_t)NB * p;
-  T *Rnew = scr + 3 * (int64_t)NB * p;
-  const T *a11inv = scr + 4 * (int64_t)NB * p;
-  __shared__ T ai[NB * NB];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) ai[e] = a11inv[e];
+  for (int t = 0; t < 2 * nbo; ++t)
+    if (s_dst[t] >= 0) Tst[(int64_t)t * p + j] = a[(int64_t)s_src[t] * p + j];
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) bgj_write_kernel(int k0, const int32_t *__restrict__ P,
+                                                        const int64_t *__restrict__ off, T *A,
+                                                        T *scratch, const int64_t *__restrict__ poff,
+                                                        const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbo = min(NO, p - k0);
+  T *base = gj_base<T, NO>(scratch, poff, b);
+  const T *Tst = base + 4 * (int64_t)NO * p;
+  const int32_t *lst = reinterpret_cast<const int32_t *>(base + 6 * (int64_t)NO * p + NO * NO);
+  __shared__ int s_dst[2 * NO];
+  if (threadIdx.x < 2 * NO) s_dst[threadIdx.x] = lst[threadIdx.x];
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p) return;
-  // Rnew(:, j) = A11^-1 A(R, j);  Pcol(j, :) = A(j, panel)
-  T col[NB];
-#pragma unroll
-  for (int c = 0; c < NB; ++c) col[c] = (c < nbe) ? a[(int64_t)(k0 + c) * p + j] : T(0);
-#pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    T s2 = T(0);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) s2 += ai[r * NB + c] * col[c];
-    Rnew[(int64_t)r * p + j] = s2;
+  T *a = A + off[b];
+  for (int t = 0; t < 2 * nbo; ++t)
+    if (s_dst[t] >= 0) a[(int64_t)s_dst[t] * p + j] = Tst[(int64_t)t * p + j];
+}
+
+// (4) column j (one warp, 32 columns per CTA): z = U11^-1 L11^-1 x with
+// x = A(k0:k0+nbo, j), or e_(j-k0) for the block's own columns (giving
+// A11^-1).  L11, U11 are W's leading nbo x nbo block.  Lane l holds rows
+// l + 32 u; each step broadcasts the finished entry and the rows below (or
+// above) take their multiple of it.  The columns pass through shared memory
+// so that global loads and stores run along rows.
+#define DD_BGJ_RB_COLS 32
+template <typename T, int NO>
+__global__ void __launch_bounds__(32 * DD_BGJ_RB_COLS) bgj_rowblock_kernel(
+    int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off, const T *__restrict__ A,
+    T *scratch, const int64_t *__restrict__ poff, const int32_t *__restrict__ failed) {
+  constexpr int NC = DD_BGJ_RB_COLS, RU = NO / 32;
+  static_assert(NO % 32 == 0, "whole rows per lane");
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbo = min(NO, p - k0);
+  const int j0 = blockIdx.x * NC;
+  if (j0 >= p) return;
+  T *base = gj_base<T, NO>(scratch, poff, b);
+  T *Rnew = base + 3 * (int64_t)NO * p;
+  T *a11inv = base + 6 * (int64_t)NO * p;
+  __shared__ T LU[NO][NO + 1];
+  __shared__ T X[NO][NC + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T *a = A + off[b];
+  for (int e = tid; e < NO * NO; e += blockDim.x) {
+    const int r = e / NO, c = e % NO;
+    LU[r][c] = (r < nbo && c < nbo) ? base[(int64_t)r * NO + c] : T(0);
   }
+  for (int e = tid; e < NO * NC; e += blockDim.x) {
+    const int c = e / NC, q = e % NC, j = j0 + q;
+    T v = T(0);
+    if (c < nbo && j < p) v = (j >= k0 && j < k0 + nbo) ? T(c == j - k0 ? 1 : 0) : a[(int64_t)(k0 + c) * p + j];
+    X[c][q] = v;
+  }
+  __syncthreads();
+  T x[RU];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) Pcol[(int64_t)j * NB + c] = (c < nbe) ? a[(int64_t)j * p + k0 + c] : T(0);
+  for (int u = 0; u < RU; ++u) x[u] = X[lane + 32 * u][warp];
+  for (int c = 0; c < nbo; ++c) {  // L11 y = x (unit lower), by columns
+    T own = x[0];
+#pragma unroll
+    for (int u = 1; u < RU; ++u)
+      if (u == c / 32) own = x[u];
+    const T xc = __shfl_sync(0xffffffffu, own, c & 31);
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int r = lane + 32 * u;
+      if (r > c && r < nbo) x[u] -= LU[r][c] * xc;
+    }
+  }
+  for (int c = nbo - 1; c >= 0; --c) {  // U11 z = y, by columns
+    const int uo = c / 32;
+    T xc = T(0);
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+      if (u == uo && lane == (c & 31)) { x[u] = x[u] / LU[c][c]; }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+      if (u == uo) xc = x[u];
+    xc = __shfl_sync(0xffffffffu, xc, c & 31);
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int r = lane + 32 * u;
+      if (r < c) x[u] -= LU[r][c] * xc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < RU; ++u) X[lane + 32 * u][warp] = x[u];
+  __syncthreads();
+  for (int e = tid; e < NO * NC; e += blockDim.x) {
+    const int c = e / NC, q = e % NC, j = j0 + q;
+    if (j >= p) continue;
+    const T v = c < nbo ? X[c][q] : T(0);
+    if (j >= k0 && j < k0 + nbo) a11inv[c * NO + (j - k0)] = v;
+    else Rnew[(int64_t)c * p + j] = v;
+  }
+}
+
+// Pcol(i, :) = A(i, k0:k0+nbo) for every row i, zero beyond nbo; consecutive
+// threads copy consecutive columns of a row
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) bgj_pcol_kernel(int k0, const int32_t *__restrict__ P,
+                                                       const int64_t *__restrict__ off, const T *__restrict__ A,
+                                                       T *scratch, const int64_t *__restrict__ poff,
+                                                       const int32_t *__restrict__ failed) {
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbo = min(NO, p - k0);
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)p * NO) return;
+  const int i = (int)(e / NO), c = (int)(e % NO);
+  T *Pcol = gj_base<T, NO>(scratch, poff, b) + 2 * (int64_t)NO * p;
+  Pcol[e] = (c < nbo) ? A[off[b] + (int64_t)i * p + k0 + c] : T(0);
 }
 
 #define DD_BGJ_TILE 64
+// 16-byte vector of T
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void unpack(const float4 &a, float *v) { v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void unpack(const double2 &a, double *v) { v[0] = a.x; v[1] = a.y; }
+};
+
+#define DD_BGJ_RT 4
+#define DD_BGJ_UPD_THREADS ((DD_BGJ_TILE / DD_BGJ_RT) * (DD_BGJ_TILE / DD_BGJ_RT))
 // Rank-NB update of one 64 x 64 tile: each of the 256 threads owns 4
 // consecutive rows by 4 consecutive columns and accumulates the outer
 // products of a transposed P column chunk and an R row chunk in registers.
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) bgj_update_kernel(int k0, const int32_t *__restrict__ P,
+__global__ void __launch_bounds__(DD_BGJ_UPD_THREADS, 3) bgj_update_kernel(int k0, const int32_t *__restrict__ P,
                                                          const int64_t *__restrict__ off, T *A,
                                                          const T *__restrict__ scratch,
                                                          const int64_t *__restrict__ poff,
@@ -426,65 +663,109 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(int k0, const int32_t *
   if (i0 >= p || j0 >= p) return;
   const int nbe = min(NB, p - k0);
   T *a = A + off[b];
-  const T *scr = scratch + 4 * NB * poff[b] + (int64_t)NB * NB * b;
+  const T *scr = gj_base<const T, NB>(scratch, poff, b);
   const T *Pcol = scr + 2 * (int64_t)NB * p;
   const T *Rnew = scr + 3 * (int64_t)NB * p;
-  const T *a11inv = scr + 4 * (int64_t)NB * p;
+  const T *a11inv = scr + 6 * (int64_t)NB * p;
   constexpr int LD = DD_BGJ_TILE + 4;  // keeps every row 16-byte aligned
   __shared__ __align__(16) T Pt[NB][LD];  // Pt[c][r] = Pcol(i0 + r, c)
   __shared__ __align__(16) T Rs[NB][LD];  // Rs[c][q] = new row c at column j0 + q
   const int tid = threadIdx.x;
-  for (int e = tid; e < DD_BGJ_TILE * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    const int i = i0 + r;
-    Pt[c][r] = (i < p) ? Pcol[(int64_t)i * NB + c] : T(0);
+  constexpr int NT = DD_BGJ_UPD_THREADS;
+  {
+    // Pcol rows i0.. are contiguous: 16-byte loads, all issued before the
+    // transposed stores
+    using V = typename Vec16<T>::V;
+    constexpr int VN = Vec16<T>::N;
+    constexpr int NL = DD_BGJ_TILE * NB / VN / NT;
+    static_assert(NB % VN == 0 && (DD_BGJ_TILE * NB / VN) % NT == 0, "whole 16-byte chunks per thread");
+    const V *src = reinterpret_cast<const V *>(Pcol + (int64_t)i0 * NB);
+    V v[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int e = tid + k * NT, r = (e * VN) / NB;
+      if (i0 + r < p) v[k] = src[e];
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int e = tid + k * NT, r = (e * VN) / NB, c = (e * VN) % NB;
+      T u[VN];
+      if (i0 + r < p) Vec16<T>::unpack(v[k], u);
+      else
+        for (int w = 0; w < VN; ++w) u[w] = T(0);
+#pragma unroll
+      for (int w = 0; w < VN; ++w) Pt[c + w][r] = u[w];
+    }
   }
-  for (int e = tid; e < NB * DD_BGJ_TILE; e += blockDim.x) {
-    const int c = e / DD_BGJ_TILE, q = e % DD_BGJ_TILE;
-    const int j = j0 + q;
-    T v = T(0);
-    if (j < p) v = (j >= k0 && j < k0 + nbe) ? a11inv[c * NB + (j - k0)] : Rnew[(int64_t)c * p + j];
-    Rs[c][q] = v;
+  {
+    constexpr int NL = NB * DD_BGJ_TILE / NT;
+    static_assert((NB * DD_BGJ_TILE) % NT == 0, "whole row chunks per thread");
+    T v[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int e = tid + k * NT, c = e / DD_BGJ_TILE, j = j0 + e % DD_BGJ_TILE;
+      v[k] = T(0);
+      if (j < p) v[k] = (j >= k0 && j < k0 + nbe) ? a11inv[c * NB + (j - k0)] : Rnew[(int64_t)c * p + j];
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int e = tid + k * NT;
+      Rs[e / DD_BGJ_TILE][e % DD_BGJ_TILE] = v[k];
+    }
   }
   __syncthreads();
-  const int tr = tid >> 4, tc = tid & 15;
-  const int rb = 4 * tr, qb = 4 * tc;
-  T acc[4][4];
+  constexpr int RT = DD_BGJ_RT, TH = DD_BGJ_TILE / DD_BGJ_RT;
+  const int tr = tid / TH, tc = tid % TH;
+  const int rb = RT * tr, qb = RT * tc;
+  T acc[RT][RT];
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < RT; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
-#pragma unroll
+    for (int y = 0; y < RT; ++y) acc[x][y] = T(0);
+#pragma unroll 8
   for (int c = 0; c < NB; ++c) {
-    T pv[4], rv[4];
+    T pv[RT], rv[RT];
 #pragma unroll
-    for (int x = 0; x < 4; ++x) { pv[x] = Pt[c][rb + x]; rv[x] = Rs[c][qb + x]; }
+    for (int x = 0; x < RT; ++x) { pv[x] = Pt[c][rb + x]; rv[x] = Rs[c][qb + x]; }
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+    for (int x = 0; x < RT; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] += pv[x] * rv[y];
+      for (int y = 0; y < RT; ++y) acc[x][y] += pv[x] * rv[y];
   }
+  // Epilogue through shared memory (over Pt, no longer read), CH rows at a
+  // time, so that consecutive threads update consecutive columns of A.
+  constexpr int SL = DD_BGJ_TILE + 1;
+  constexpr int CH = ((NB * LD) / SL) / RT * RT < DD_BGJ_TILE ? ((NB * LD) / SL) / RT * RT : DD_BGJ_TILE;
+  static_assert(CH >= RT && DD_BGJ_TILE % CH == 0, "whole thread rows per epilogue chunk");
+  T *S = &Pt[0][0];
+  for (int h = 0; h < DD_BGJ_TILE; h += CH) {
+    __syncthreads();
+    if (rb >= h && rb < h + CH) {
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int i = i0 + rb + x;
-    if (i >= p) continue;
-    const bool pivot_row = (i >= k0 && i < k0 + nbe);
-    T *o = &a[(int64_t)i * p + j0 + qb];
-    if (pivot_row) {
+      for (int x = 0; x < RT; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y)
-        if (j0 + qb + y < p) o[y] = Rs[i - k0][qb + y];
-      continue;
+        for (int y = 0; y < RT; ++y) S[(rb - h + x) * SL + qb + y] = acc[x][y];
     }
-    T cur[4];
+    __syncthreads();
+    // every load of the chunk before any store
+    constexpr int NE = CH * DD_BGJ_TILE / NT;
+    static_assert((CH * DD_BGJ_TILE) % NT == 0, "whole chunk per thread");
+    T cur[NE];
 #pragma unroll
-    for (int y = 0; y < 4; ++y) cur[y] = (j0 + qb + y < p) ? o[y] : T(0);
+    for (int k = 0; k < NE; ++k) {
+      const int e = tid + k * NT, i = i0 + h + e / DD_BGJ_TILE, j = j0 + e % DD_BGJ_TILE;
+      cur[k] = (i < p && j < p) ? a[(int64_t)i * p + j] : T(0);
+    }
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int j = j0 + qb + y;
-      if (j >= p) continue;
-      const bool panel_col = (j >= k0 && j < k0 + nbe);
-      o[y] = panel_col ? -acc[x][y] : cur[y] - acc[x][y];
+    for (int k = 0; k < NE; ++k) {
+      const int e = tid + k * NT, r = e / DD_BGJ_TILE, q = e % DD_BGJ_TILE;
+      const int i = i0 + h + r, j = j0 + q;
+      if (i >= p || j >= p) continue;
+      T v;
+      if (i >= k0 && i < k0 + nbe) v = Rs[i - k0][q];            // pivot row
+      else if (j >= k0 && j < k0 + nbe) v = -S[r * SL + q];      // panel column
+      else v = cur[k] - S[r * SL + q];
+      a[(int64_t)i * p + j] = v;
     }
   }
 }
@@ -701,16 +982,16 @@ cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off
   return cudaGetLastError();
 }
 
-template <typename T>
-struct BgjNB { static const int value = 16; };
-template <>
-struct BgjNB<double> { static const int value = 8; };
-
 int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size) {
-  const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
-  return 4 * (int64_t)nb * sum_p + (int64_t)nb * nb * nblk;
+  const int no = elem_size == 8 ? BgjNO<double>::value : BgjNO<float>::value;
+  return 6 * (int64_t)no * sum_p + (int64_t)(no * no + 4 * no) * nblk;
 }
 
+int64_t gj_launch_count(int pmax, int elem_size) {
+  const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
+  const int no = elem_size == 8 ? BgjNO<double>::value : BgjNO<float>::value;
+  return (int64_t)(2 * (no / nb) + 5) * ((pmax + no - 1) / no) + 2;
+}
 // Explicit inverse of every block (in place), blocked Gauss-Jordan; blocks
 // that fail the pivot test are flagged and reported through st.
 template <typename T>
@@ -719,23 +1000,34 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
                               T *scratch, double pivtol, DevStatus *st, int status_code,
                               cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
-  constexpr int NB = BgjNB<T>::value;
+  constexpr int NB = BgjNB<T>::value, NO = BgjNO<T>::value;
+  static_assert(NO % NB == 0 && NO <= DD_BGJ_TILE, "outer block of whole inner panels");
   cudaError_t e = cudaMemsetAsync(failed, 0, sizeof(int32_t) * nblk, s);
   if (e != cudaSuccess) return e;
   const size_t smem_cap = 200 * 1024;
   const int smem_rows = (int)(smem_cap / ((NB + 1) * sizeof(T)));
   const size_t smem = (size_t)std::min(pmax, smem_rows) * (NB + 1) * sizeof(T);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(bgj_panel_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(bgj_panel_kernel<T, NB, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const dim3 rg((pmax + 255) / 256, nblk);
+  const dim3 cg((unsigned)(((int64_t)pmax * NO + 255) / 256), nblk);
+  const dim3 tg((pmax + 63) / 64, nblk);
+  const dim3 sg((pmax + 255) / 256, nblk);
+  const dim3 rg((pmax + DD_BGJ_RB_COLS - 1) / DD_BGJ_RB_COLS, nblk);
   const dim3 ug((pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, (pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, nblk);
-  for (int k0 = 0; k0 < pmax; k0 += NB) {
-    bgj_panel_kernel<T, NB><<<nblk, 1024, smem, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, amax,
-                                                   pivtol, failed, st, status_code, smem_rows);
-    bgj_rowblock_kernel<T, NB><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
-    bgj_update_kernel<T, NB><<<ug, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+  for (int k0 = 0; k0 < pmax; k0 += NO) {
+    bgj_copy_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    for (int sp = 0; sp < NO / NB; ++sp) {
+      bgj_panel_kernel<T, NB, NO><<<nblk, 1024, smem, s>>>(k0, sp, d_p, scratch, d_poff, ipiv, amax, pivtol,
+                                                           failed, st, status_code, smem_rows);
+      if (sp + 1 < NO / NB) bgj_trail_kernel<T, NB, NO><<<tg, 256, 0, s>>>(k0, sp, d_p, scratch, d_poff, failed);
+    }
+    bgj_stage_kernel<T, NO><<<sg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, failed);
+    bgj_write_kernel<T, NO><<<sg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    bgj_rowblock_kernel<T, NO><<<rg, 32 * DD_BGJ_RB_COLS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    bgj_pcol_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    bgj_update_kernel<T, NO><<<ug, DD_BGJ_UPD_THREADS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
   }
   // the composite column permutation in the (now free) scratch, then the rows
   int32_t *cidx = reinterpret_cast<int32_t *>(scratch);
