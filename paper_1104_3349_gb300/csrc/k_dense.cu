@@ -183,9 +183,9 @@ __global__ void gj_unscramble_kernel(const int32_t *__restrict__ P, const int64_
 //      of W's remaining columns (many CTAs per block);
 //  (3) the NO row exchanges on whole rows of A, through a staged copy of
 //      the touched rows;
-//  (4) row block: Rnew = A11^-1 A(R, :) by forward and back substitution
-//      with W's L11 and U11 (the panel columns take identity right-hand
-//      sides, giving A11^-1), and a copy Pcol = A(:, panel);
+//  (4) A11^-1 from W's L11 and U11 (forward and back substitution on the
+//      identity, one warp per column); row block Rnew = A11^-1 A(R, :) as a
+//      small product; and a copy Pcol = A(:, panel);
 //  (5) update kernel (tiled):
 //        A(R, panel) = A11^-1,  A(R, j) = Rnew(:, j),
 //        A(i, panel) = -Pcol(i, :) A11^-1,  A(i, j) -= Pcol(i, :) Rnew(:, j).
@@ -529,47 +529,34 @@ __global__ void __launch_bounds__(256) bgj_write_kernel(int k0, const int32_t *_
     if (s_dst[t] >= 0) a[(int64_t)s_dst[t] * p + j] = Tst[(int64_t)t * p + j];
 }
 
-// (4) column j (one warp, 32 columns per CTA): z = U11^-1 L11^-1 x with
-// x = A(k0:k0+nbo, j), or e_(j-k0) for the block's own columns (giving
-// A11^-1).  L11, U11 are W's leading nbo x nbo block.  Lane l holds rows
-// l + 32 u; each step broadcasts the finished entry and the rows below (or
-// above) take their multiple of it.  The columns pass through shared memory
-// so that global loads and stores run along rows.
-#define DD_BGJ_RB_COLS 32
+// (4a) A11^-1 = U11^-1 L11^-1 from W's leading nbo x nbo block: one warp per
+// column of the identity.  Lane l holds rows l + 32 u; each step broadcasts
+// the finished entry and the rows below (or above) take their multiple of it.
 template <typename T, int NO>
-__global__ void __launch_bounds__(32 * DD_BGJ_RB_COLS) bgj_rowblock_kernel(
-    int k0, const int32_t *__restrict__ P, const int64_t *__restrict__ off, const T *__restrict__ A,
-    T *scratch, const int64_t *__restrict__ poff, const int32_t *__restrict__ failed) {
-  constexpr int NC = DD_BGJ_RB_COLS, RU = NO / 32;
+__global__ void __launch_bounds__(1024) bgj_a11inv_kernel(int k0, const int32_t *__restrict__ P, T *scratch,
+                                                          const int64_t *__restrict__ poff,
+                                                          const int32_t *__restrict__ failed) {
+  constexpr int RU = NO / 32;
   static_assert(NO % 32 == 0, "whole rows per lane");
   const int b = blockIdx.y;
   const int p = P[b];
   if (k0 >= p || failed[b]) return;
   const int nbo = min(NO, p - k0);
-  const int j0 = blockIdx.x * NC;
-  if (j0 >= p) return;
   T *base = gj_base<T, NO>(scratch, poff, b);
-  T *Rnew = base + 3 * (int64_t)NO * p;
   T *a11inv = base + 6 * (int64_t)NO * p;
   __shared__ T LU[NO][NO + 1];
-  __shared__ T X[NO][NC + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T *a = A + off[b];
   for (int e = tid; e < NO * NO; e += blockDim.x) {
     const int r = e / NO, c = e % NO;
     LU[r][c] = (r < nbo && c < nbo) ? base[(int64_t)r * NO + c] : T(0);
   }
-  for (int e = tid; e < NO * NC; e += blockDim.x) {
-    const int c = e / NC, q = e % NC, j = j0 + q;
-    T v = T(0);
-    if (c < nbo && j < p) v = (j >= k0 && j < k0 + nbo) ? T(c == j - k0 ? 1 : 0) : a[(int64_t)(k0 + c) * p + j];
-    X[c][q] = v;
-  }
   __syncthreads();
+  const int col = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (col >= NO) return;  // whole warps leave
   T x[RU];
 #pragma unroll
-  for (int u = 0; u < RU; ++u) x[u] = X[lane + 32 * u][warp];
-  for (int c = 0; c < nbo; ++c) {  // L11 y = x (unit lower), by columns
+  for (int u = 0; u < RU; ++u) x[u] = (lane + 32 * u == col && col < nbo) ? T(1) : T(0);
+  for (int c = col; c < nbo; ++c) {  // L11 y = e_col (unit lower), by columns
     T own = x[0];
 #pragma unroll
     for (int u = 1; u < RU; ++u)
@@ -583,31 +570,66 @@ __global__ void __launch_bounds__(32 * DD_BGJ_RB_COLS) bgj_rowblock_kernel(
   }
   for (int c = nbo - 1; c >= 0; --c) {  // U11 z = y, by columns
     const int uo = c / 32;
-    T xc = T(0);
 #pragma unroll
     for (int u = 0; u < RU; ++u)
-      if (u == uo && lane == (c & 31)) { x[u] = x[u] / LU[c][c]; }
+      if (u == uo && lane == (c & 31)) x[u] = x[u] / LU[c][c];
+    T own = x[0];
 #pragma unroll
-    for (int u = 0; u < RU; ++u)
-      if (u == uo) xc = x[u];
-    xc = __shfl_sync(0xffffffffu, xc, c & 31);
+    for (int u = 1; u < RU; ++u)
+      if (u == uo) own = x[u];
+    const T xc = __shfl_sync(0xffffffffu, own, c & 31);
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const int r = lane + 32 * u;
       if (r < c) x[u] -= LU[r][c] * xc;
     }
   }
-  __syncthreads();
 #pragma unroll
-  for (int u = 0; u < RU; ++u) X[lane + 32 * u][warp] = x[u];
-  __syncthreads();
+  for (int u = 0; u < RU; ++u) a11inv[(lane + 32 * u) * NO + col] = x[u];
+}
+
+// (4b) Rnew(:, j) = A11^-1 A(k0:k0+nbo, j) for the columns outside the block:
+// 64 columns per CTA; thread (g, q) forms rows 16 g .. 16 g + 15 of column
+// j0 + q.
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) bgj_rowblock_kernel(int k0, const int32_t *__restrict__ P,
+                                                           const int64_t *__restrict__ off, const T *__restrict__ A,
+                                                           T *scratch, const int64_t *__restrict__ poff,
+                                                           const int32_t *__restrict__ failed) {
+  constexpr int NC = 64, RG = NO / 4;  // 4 row groups of RG rows
+  const int b = blockIdx.y;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int nbo = min(NO, p - k0);
+  const int j0 = blockIdx.x * NC;
+  if (j0 >= p) return;
+  T *base = gj_base<T, NO>(scratch, poff, b);
+  T *Rnew = base + 3 * (int64_t)NO * p;
+  const T *a11inv = base + 6 * (int64_t)NO * p;
+  __shared__ T Ai[NO][NO];
+  __shared__ T Xs[NO][NC + 1];
+  const int tid = threadIdx.x;
+  const T *a = A + off[b];
+  for (int e = tid; e < NO * NO; e += blockDim.x) Ai[e / NO][e % NO] = a11inv[e];
   for (int e = tid; e < NO * NC; e += blockDim.x) {
     const int c = e / NC, q = e % NC, j = j0 + q;
-    if (j >= p) continue;
-    const T v = c < nbo ? X[c][q] : T(0);
-    if (j >= k0 && j < k0 + nbo) a11inv[c * NO + (j - k0)] = v;
-    else Rnew[(int64_t)c * p + j] = v;
+    Xs[c][q] = (c < nbo && j < p) ? a[(int64_t)(k0 + c) * p + j] : T(0);
   }
+  __syncthreads();
+  const int q = tid % NC, g = tid / NC;
+  const int j = j0 + q;
+  T acc[RG];
+#pragma unroll
+  for (int r = 0; r < RG; ++r) acc[r] = T(0);
+#pragma unroll 8
+  for (int c = 0; c < NO; ++c) {
+    const T xv = Xs[c][q];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] += Ai[g * RG + r][c] * xv;
+  }
+  if (j >= p || (j >= k0 && j < k0 + nbo)) return;
+#pragma unroll
+  for (int r = 0; r < RG; ++r) Rnew[(int64_t)(g * RG + r) * p + j] = acc[r];
 }
 
 // Pcol(i, :) = A(i, k0:k0+nbo) for every row i, zero beyond nbo; consecutive
@@ -990,7 +1012,7 @@ int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size) {
 int64_t gj_launch_count(int pmax, int elem_size) {
   const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
   const int no = elem_size == 8 ? BgjNO<double>::value : BgjNO<float>::value;
-  return (int64_t)(2 * (no / nb) + 5) * ((pmax + no - 1) / no) + 2;
+  return (int64_t)(2 * (no / nb) + 6) * ((pmax + no - 1) / no) + 2;
 }
 // Explicit inverse of every block (in place), blocked Gauss-Jordan; blocks
 // that fail the pivot test are flagged and reported through st.
@@ -1014,7 +1036,8 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   const dim3 cg((unsigned)(((int64_t)pmax * NO + 255) / 256), nblk);
   const dim3 tg((pmax + 63) / 64, nblk);
   const dim3 sg((pmax + 255) / 256, nblk);
-  const dim3 rg((pmax + DD_BGJ_RB_COLS - 1) / DD_BGJ_RB_COLS, nblk);
+  const dim3 rg((pmax + 63) / 64, nblk);
+  const dim3 ag(NO / 32, nblk);
   const dim3 ug((pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, (pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, nblk);
   for (int k0 = 0; k0 < pmax; k0 += NO) {
     bgj_copy_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
@@ -1025,7 +1048,8 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
     }
     bgj_stage_kernel<T, NO><<<sg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, failed);
     bgj_write_kernel<T, NO><<<sg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
-    bgj_rowblock_kernel<T, NO><<<rg, 32 * DD_BGJ_RB_COLS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    bgj_a11inv_kernel<T, NO><<<ag, 1024, 0, s>>>(k0, d_p, scratch, d_poff, failed);
+    bgj_rowblock_kernel<T, NO><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     bgj_pcol_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     bgj_update_kernel<T, NO><<<ug, DD_BGJ_UPD_THREADS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
   }
