@@ -516,9 +516,9 @@ def main():
                     help="FGMRES iteration cap of the stretched 1024x1024 learned measurement")
     ap.add_argument("--skip-cfg5", action="store_true", help="leave out the 1024x1024 learned measurement")
     ap.add_argument("--apply-only", type=int, default=0,
-                    help="profiling driver: one dd_setup, then this many dd_apply calls, no JSON line")
+                    help="profiling mode: one dd_setup, then this many dd_apply calls, no JSON line")
     ap.add_argument("--solve-only", type=int, default=0,
-                    help="profiling driver: one dd_setup, then one solve capped at this many iterations")
+                    help="profiling mode: one dd_setup, then one solve capped at this many iterations")
     args = ap.parse_args()
     if args.apply_only:
         apply_only(args)
