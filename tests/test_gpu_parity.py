@@ -131,6 +131,35 @@ def test_small_and_ragged_cases(torch_dev, grid, m, sz):
         assert err <= 1e-10, (grid, m, kind, err)
 
 
+@pytest.fixture(scope="module")
+def big_iface():
+    """128x128, 32 subdomains: one EXACT interface block of 3340 rows, taller
+    than the Gauss-Jordan panel that fits in shared memory (FP32: 3011 rows,
+    FP64: 2844), so its first panels take the global-scratch path."""
+    w = W.make_workload("t", 128, 0.01, 1.0, W.WIND_FOURIER, 128, 32, sz=64)
+    assert int((w.part < 0).sum()) > 3011
+    R = O.OracleDD(w.A, w.part, w.m, O.EXACT, perm=w.perm)
+    y = W.uniform(3, w.A.n)
+    return w, y, R.apply(y)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)])
+def test_exact_large_interface_block(torch_dev, big_iface, prec, tol):
+    torch, dev = torch_dev
+    from paper_1104_3349_gb300 import dd
+    w, y, xr = big_iface
+    P = dd.DD(w.A, w.part, w.m, "exact", perm=w.perm, prec=prec)
+    assert P.stats()["max_agg"] > 3011
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    torch.cuda.synchronize()
+    x = xd.cpu().numpy()
+    assert np.all(np.isfinite(x))
+    err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+    assert err <= tol, (prec, err)
+
+
 def test_whole_domain_interior(torch_dev):
     """m = 1 and no interface: B = C and GMRES converges in one step."""
     torch, dev = torch_dev
