@@ -51,88 +51,6 @@ __global__ void block_amax_kernel(const int32_t *__restrict__ P, const int64_t *
   }
 }
 
-// Step k, part 1 (one CTA per block): pivot = first row >= k holding the
-// largest |A(i,k)|, exchange rows, normalise the pivot row in place.
-template <typename T>
-__global__ void gj_pivot_kernel(int k, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                T *A, int32_t *ipiv, const int64_t *__restrict__ poff,
-                                const T *__restrict__ amax, double pivtol, int32_t *failed,
-                                DevStatus *st, int code) {
-  const int b = blockIdx.x;
-  const int p = P[b];
-  if (k >= p || failed[b]) return;
-  T *a = A + off[b];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  __shared__ T bv[32];
-  __shared__ int bi[32];
-  __shared__ int s_piv;
-  T best = T(-1);
-  int besti = p;
-  for (int i = k + tid; i < p; i += blockDim.x) {
-    T v = tabs(a[(int64_t)i * p + k]);
-    if (v > best) { best = v; besti = i; }
-  }
-  for (int o = 16; o; o >>= 1) {
-    T ov = __shfl_xor_sync(0xffffffffu, best, o);
-    int oi = __shfl_xor_sync(0xffffffffu, besti, o);
-    if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
-  }
-  if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
-  __syncthreads();
-  if (tid == 0) {
-    T bb = bv[0];
-    int ii = bi[0];
-    for (int w = 1; w < nw; ++w)
-      if (bv[w] > bb || (bv[w] == bb && bi[w] < ii)) { bb = bv[w]; ii = bi[w]; }
-    if (!(bb > T(pivtol) * amax[b])) {
-      failed[b] = 1;
-      set_status2(st, code, b);
-      ii = -1;
-    }
-    s_piv = ii;
-    if (ii >= 0) ipiv[poff[b] + k] = ii;
-  }
-  __syncthreads();
-  const int pr = s_piv;
-  if (pr < 0) return;
-  if (pr != k)
-    for (int c = tid; c < p; c += blockDim.x) {
-      T t = a[(int64_t)k * p + c];
-      a[(int64_t)k * p + c] = a[(int64_t)pr * p + c];
-      a[(int64_t)pr * p + c] = t;
-    }
-  __syncthreads();
-  const T pv = a[(int64_t)k * p + k];
-  __syncthreads();
-  for (int c = tid; c < p; c += blockDim.x) {
-    T v = (c == k) ? T(1) : a[(int64_t)k * p + c];
-    a[(int64_t)k * p + c] = v / pv;
-  }
-}
-
-// Step k, part 2: eliminate column k from every other row (one warp per row).
-template <typename T>
-__global__ void gj_update_kernel(int k, const int32_t *__restrict__ P, const int64_t *__restrict__ off,
-                                 T *A, const int32_t *__restrict__ failed) {
-  const int b = blockIdx.y;
-  const int p = P[b];
-  if (k >= p || failed[b]) return;
-  T *a = A + off[b];
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= p || row == k) return;
-  const T f = a[(int64_t)row * p + k];
-  __syncwarp();
-  if (f == T(0)) return;
-  const T *pk = a + (int64_t)k * p;
-  T *ar = a + (int64_t)row * p;
-  for (int c = lane; c < p; c += 32) {
-    T v = (c == k) ? T(0) : ar[c];
-    ar[c] = v - f * pk[c];
-  }
-}
-
-// Undo the row exchanges as column exchanges in reverse order.
 // The column exchanges that undo the row exchanges (in reverse order) are
 // one permutation of the columns, the same for every row: cidx[c] = the
 // column whose entry ends in column c.  One CTA per block composes it.
