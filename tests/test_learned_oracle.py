@@ -138,3 +138,58 @@ def test_replace_block_with_g_reproduces_lum():
     p = w.agg[1] - w.agg[0]
     assert not R.replace_block(0, np.zeros((p, p)))
     np.testing.assert_allclose(R.apply(y), Lm.apply(y), rtol=0, atol=1e-12 * np.abs(Lm.apply(y)).max())
+
+
+def _packed(W1, b1, w2, b2):
+    """Parameters in the layout of the weight file: W1 (64 x 14, row-major), b1, w2, b2."""
+    return np.concatenate([np.asarray(W1, np.float64).ravel(), b1, w2, [b2]])
+
+
+def test_forward_matches_torch_modules():
+    """The network's forward pass against torch.nn.Linear / ReLU modules built
+    from the same parameters, with BF16 rounding done by torch's own
+    float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    W1 = rng.normal(0, 0.4, (L.N_HID, L.N_IN))
+    b1, w2, b2 = rng.normal(0, 0.3, L.N_HID), rng.normal(0, 0.3, L.N_HID), 0.37
+    X = rng.normal(0, 1.5, (300, L.N_IN))
+
+    def tb(a):  # BF16 round trip in torch
+        return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64)
+    net = torch.nn.Sequential(torch.nn.Linear(L.N_IN, L.N_HID), torch.nn.ReLU(),
+                              torch.nn.Linear(L.N_HID, 1)).double()
+    with torch.no_grad():
+        net[0].weight.copy_(tb(W1))
+        net[0].bias.copy_(tb(b1))
+        net[2].weight.copy_(tb(w2).reshape(1, -1))
+        net[2].bias.copy_(tb([b2]))
+        ref = net(tb(X)).numpy().ravel()
+    out, _ = L.forward(L.bf16(_packed(W1, b1, w2, b2)), L.bf16(X))
+    assert np.abs(out - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_predict_worked_example():
+    """Two entries worked by hand: standardisation (mean 0.5, std 0.25), then
+    BF16 rounding of the standardised features and of the weights, the
+    14 -> 64 (ReLU) -> 1 network and the output scale 10.
+      W1[0,0] = 1 + 2^-8 rounds to 1;  W1[1,1] = -(1 + 3*2^-8) to -(1 + 2^-6);
+      b1 = (0.5, 0.25), w2 = (2, -4), b2 = 0.125, everything else 0.
+    Entry A: x0 = 0.75 + 5*2^-11 standardises to 1 + 5*2^-9, which rounds to
+      1 + 2^-7 (rounding the raw feature first would give 1 + 2^-6);
+      x1 = 1 standardises to 2.  h = (1.5078125, relu(-1.78125) = 0),
+      out = 3.140625, Delta = 31.40625.
+    Entry B: x0 = 0.25 -> -1, x1 = 0.125 -> -1.5.  h = (relu(-0.5) = 0,
+      1.7734375), out = -6.96875, Delta = -69.6875."""
+    W1 = np.zeros((L.N_HID, L.N_IN))
+    W1[0, 0] = 1 + 2.0 ** -8
+    W1[1, 1] = -(1 + 3 * 2.0 ** -8)
+    b1, w2 = np.zeros(L.N_HID), np.zeros(L.N_HID)
+    b1[:2] = (0.5, 0.25)
+    w2[:2] = (2.0, -4.0)
+    wts = dict(out_scale=10.0, mean=np.full(L.N_IN, 0.5), std=np.full(L.N_IN, 0.25),
+               params=_packed(W1, b1, w2, 0.125))
+    X = np.full((2, L.N_IN), 0.5)
+    X[0, :2] = (0.75 + 5 * 2.0 ** -11, 1.0)
+    X[1, :2] = (0.25, 0.125)
+    np.testing.assert_array_equal(L.predict(wts, X), [31.40625, -69.6875])

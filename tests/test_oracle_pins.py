@@ -316,3 +316,83 @@ def test_singular_lum_block_reported():
     with pytest.raises(O.OracleError) as e:
         O.OracleDD(A, part, 1, O.LUM, sz=8)
     assert e.value.status == 4 and e.value.bad_block == 0
+
+
+# --------------------------------------------------------------------------
+# Restarted GMRES(R): the restart path
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cav32_dense():
+    w = W.cavity32()
+    C = w.A.to_dense()
+    return w, C, np.linalg.solve(C, w.b), np.linalg.cond(C)
+
+
+@pytest.mark.parametrize("kind,restart", [(O.MSCE_INF, 5), (O.MSCE_INF, 13), (O.LUM, 25), (O.MSCN, 30)])
+def test_restarted_gmres_reaches_dense_solution(cav32_dense, kind, restart):
+    """Short restart lengths force several cycles (Section 5's restarted GMRES):
+    the final iterate still matches the dense solve of C x = b to cond * 1e-8
+    and its true residual, recomputed here, is below the tolerance."""
+    w, C, x, cond = cav32_dense
+    P = O.OracleDD(w.A, w.part, w.m, kind, perm=w.perm, agg_offsets=w.agg)
+    r = P.fgmres(w.b, tol=1e-8, restart=restart, maxit=3000)
+    assert r["status"] == 0 and r["restarts"] > 0, r["restarts"]
+    assert np.linalg.norm(w.b - C @ r["x"]) <= 1e-8 * np.linalg.norm(w.b)
+    assert abs(r["relres"] - np.linalg.norm(w.b - C @ r["x"]) / np.linalg.norm(w.b)) <= 1e-12
+    assert np.linalg.norm(r["x"] - x) <= cond * 1e-8 * np.linalg.norm(x)
+
+
+def _dense_Binv(A, part, perm, agg, kind):
+    """B^-1 in the original numbering, from the factored form of B (Definition
+    of B_MSCN) with brute-force Schur blocks: no part of the oracle is used."""
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    Sh = sla.block_diag(*_brute_blocks(kind, D, E, F, G, agg))
+    Bp = Cp.copy()
+    Bp[nI:, nI:] = F @ np.linalg.solve(D, E) + Sh
+    Binv_p = np.linalg.inv(Bp)
+    Binv = np.zeros_like(Binv_p)
+    Binv[np.ix_(perm, perm)] = Binv_p
+    return Binv
+
+
+def _gmres_by_definition(C, Binv, b, R, steps):
+    """Right-preconditioned GMRES(R) written from its definition: every cycle
+    starts from the true residual r = b - C x of the current iterate and adds
+    B^-1 u, where u minimises ||r - C B^-1 u|| over the Krylov space
+    K_k(C B^-1, r) (k = R, or the steps left); an orthonormal basis of the
+    Krylov matrix comes from a QR factorisation."""
+    M = C @ Binv
+    x = np.zeros_like(b)
+    left = steps
+    while left > 0:
+        k = min(R, left)
+        r = b - C @ x
+        K = np.empty((len(b), k))
+        v = r / np.linalg.norm(r)
+        for q in range(k):
+            K[:, q] = v
+            v = M @ v
+            v /= np.linalg.norm(v)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(M @ Q, r, rcond=None)
+        x = x + Binv @ (Q @ y)
+        left -= k
+    return x
+
+
+@pytest.mark.parametrize("kind,restart,maxit", [(O.LUM, 5, 10), (O.LUM, 5, 13), (O.MSCE_INF, 4, 11)])
+def test_restart_cycles_match_gmres_definition(kind, restart, maxit):
+    """The iterate after whole and partial cycles equals GMRES(R) computed from
+    its definition with dense linear algebra: a restart from anything but the
+    true residual of the accumulated iterate, or an iterate not accumulated
+    over the cycles, fails this."""
+    A, part, perm, agg = _small(n=6, m=2, sz=9)
+    C = A.to_dense()
+    b = W.uniform(11, A.n)
+    P = O.OracleDD(A, part, 2, kind, perm=perm, agg_offsets=agg)
+    r = P.fgmres(b, tol=1e-15, restart=restart, maxit=maxit)
+    assert r["status"] == 5 and r["iters"] == maxit
+    assert r["restarts"] == (maxit - 1) // restart
+    x = _gmres_by_definition(C, _dense_Binv(A, part, perm, agg, kind), b, restart, maxit)
+    assert np.linalg.norm(r["x"] - x) <= 1e-8 * np.linalg.norm(x)
+    assert abs(r["relres"] - np.linalg.norm(b - C @ x) / np.linalg.norm(b)) <= 1e-8
