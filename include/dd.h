@@ -104,7 +104,11 @@ typedef struct {
                          and keeps the fastest; 0: the fixed default           */
   int32_t krylov_ctas_per_sm; /* CTAs per SM of the Krylov kernels (CGS2 and the
                          batched norms); <= 0 selects 2                          */
-  int32_t reserved[2];
+  int32_t time_kernels;/* 1: gmres_solve times the SpMV and CGS2 launches of
+                         every Arnoldi step with CUDA events (dd_stats
+                         krylov_steps, cgs2_ms, cgs2_fma, spmv_ms); ignored
+                         with use_graph; 0: no events                        */
+  int32_t reserved;
   const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
                               (format under dd_mlp_*); ignored otherwise       */
 } dd_opts;
@@ -144,6 +148,13 @@ typedef struct {
   int64_t learned_entries;   /* DD_LEARNED: entries of the learned patterns      */
   int32_t learned_fallback;  /* DD_LEARNED: aggregates that took MSCE_INF         */
   int32_t pad3;
+  /* opts.time_kernels: summed over the timed Arnoldi steps of gmres_solve */
+  int64_t krylov_steps;      /* Arnoldi steps timed                              */
+  double cgs2_ms;            /* device time of the CGS2 kernel                   */
+  double cgs2_fma;           /* FP64 multiply-adds of those steps' Gram-Schmidt
+                                (both passes' dots and updates and the norm:
+                                (4 (j+1) + 2) n at step j)                       */
+  double spmv_ms;            /* device time of the SpMV w = C z                  */
 } dd_stats;
 
 /*
@@ -247,6 +258,39 @@ dd_status dd_apply_part(void *handle, int32_t part, const double *y, double *x, 
  */
 #define DD_NOALLOC_MAX_ELEMS (1 << 20)
 dd_status dd_apply_noalloc(void *handle, const double *y, double *x, void *stream);
+
+/*
+ * Status of the asynchronous device work of a handle.  The apply's sweep
+ * kernels wait on their own bulk copies with bounded waits; a wait that gives
+ * up records DD_ERR_TIMEOUT (with the subdomain) in the handle's status word,
+ * drains its own copies and returns, leaving part of x unwritten.  dd_apply,
+ * dd_apply_part and dd_apply_noalloc do not synchronise, so they cannot
+ * report it; gmres_solve and gmres_solve_batched clear the word when they
+ * start, return DD_ERR_TIMEOUT when it is set and leave it cleared when they
+ * return.  dd_check_status
+ * synchronises `stream`, returns DD_OK or the recorded status (description in
+ * dd_last_error) and clears the word.
+ */
+dd_status dd_check_status(void *handle, void *stream);
+
+/*
+ * Test hook of the timeout path: the number of polls of the first mbarrier
+ * wait of every CTA of the apply's sweep kernels (0: it gives up at once and
+ * records DD_ERR_TIMEOUT; any value above the normal bound, e.g. UINT32_MAX,
+ * restores the normal bound).  Only that first wait is shortened: the drain of
+ * the copies in flight keeps the full bound, so a CTA never returns with a
+ * copy outstanding.  Drops the handle's captured CUDA graphs.
+ */
+dd_status dd_set_wait_limit(void *handle, uint32_t first_wait_polls);
+
+/*
+ * Measurement helper (the paper has no counterpart): the FP64 fused
+ * multiply-add rate of the current device, from a kernel of independent FMA
+ * chains on every SM timed with CUDA events on `stream` (best of three after
+ * a warm-up, about 10 ms each).  *gfma: host, FP64 FMAs per second / 1e9.
+ * Synchronises the stream.
+ */
+dd_status dd_fp64_peak(double *gfma, void *stream);
 
 /* y = C x with the handle's copy of C (device pointers, n doubles). */
 dd_status dd_spmv(void *handle, const double *x, double *y, void *stream);

@@ -39,6 +39,7 @@ struct DDHandle {
   int max_n = 0, max_kl = 0, max_ku = 0, max_ku2 = 0, max_tiles = 0;
   int tb = DD_NB;              // columns of a sweep tile (DD_NB or DD_TB_WIDE)
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
+  uint32_t first_wait = 0xffffffffu;  // test hook: polls of each sweep CTA's first wait
   std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
   std::vector<TileMeta> h_tm;
   size_t max_tile = 0;           // bytes of the largest packed tile
@@ -57,6 +58,8 @@ struct DDHandle {
   int64_t *s_off = nullptr, *poff = nullptr;
   int32_t *c_rowptr = nullptr, *c_col = nullptr;
   double *c_val = nullptr;
+  SellC sell;                  // C in SELL-32 form for the SpMV and residuals
+  int64_t sell_entries = 0;    // stored entries of sell (nnz plus padding)
   DevStatus *st = nullptr;
   PrecBufs<double> pd;
   PrecBufs<float> pf;
@@ -87,6 +90,8 @@ struct DDHandle {
   // CUDA graphs of the Arnoldi steps (use_graph), one per step index
   int use_graph = 0, graph_key = -1;
   int krylov_per_sm = 2;
+  int time_kernels = 0;        // events around the SpMV and CGS2 of every Arnoldi step
+  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaGraphExec_t> gexec;
   std::vector<int64_t> glaunch;
   cudaStream_t gstream = nullptr;
@@ -740,6 +745,66 @@ dd_status learned_blocks(DDHandle *h, const dd_csr *csr, HostBlocks &hb, const s
   return DD_OK;
 }
 
+// C in SELL-32 form (SellC): inside every window of DD_SELL_WINDOW rows the
+// rows are ordered by decreasing length (a counting sort, ties by row), cut
+// into slices of 32, and each slice is stored entry-major at the width of its
+// longest row, the shorter rows padded with value 0 at their last column.
+dd_status build_sell(DDHandle *h, const dd_csr *csr) {
+  const int64_t n = h->n, ns = (n + 31) / 32, W = DD_SELL_WINDOW;
+  int32_t lmax = 0;
+  for (int64_t i = 0; i < n; ++i) lmax = std::max(lmax, csr->rowptr[i + 1] - csr->rowptr[i]);
+  std::vector<int32_t> order(ns * 32, -1);
+  {
+    std::vector<int32_t> cnt(lmax + 2);
+    for (int64_t w0 = 0; w0 < n; w0 += W) {
+      const int64_t w1 = std::min(n, w0 + W);
+      std::fill(cnt.begin(), cnt.end(), 0);
+      for (int64_t i = w0; i < w1; ++i) ++cnt[lmax - (csr->rowptr[i + 1] - csr->rowptr[i]) + 1];
+      for (int q = 1; q <= lmax + 1; ++q) cnt[q] += cnt[q - 1];
+      for (int64_t i = w0; i < w1; ++i) order[w0 + cnt[lmax - (csr->rowptr[i + 1] - csr->rowptr[i])]++] = (int32_t)i;
+    }
+  }
+  std::vector<int64_t> off(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int32_t w = 0;
+    for (int r = 0; r < 32; ++r) {
+      const int32_t row = order[sl * 32 + r];
+      if (row >= 0) w = std::max(w, csr->rowptr[row + 1] - csr->rowptr[row]);
+    }
+    off[sl + 1] = off[sl] + 32 * (int64_t)w;
+  }
+  std::vector<int32_t> col(std::max<int64_t>(off[ns], 1));
+  std::vector<double> val(std::max<int64_t>(off[ns], 1));
+  parallel_rows(ns, host_workers(n), [&](int, int64_t s0, int64_t s1) {
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      const int w = (int)((off[sl + 1] - off[sl]) / 32);
+      for (int r = 0; r < 32; ++r) {
+        const int32_t row = order[sl * 32 + r];
+        const int32_t k0 = row >= 0 ? csr->rowptr[row] : 0, len = row >= 0 ? csr->rowptr[row + 1] - k0 : 0;
+        for (int k = 0; k < w; ++k) {
+          const int64_t e = off[sl] + 32 * (int64_t)k + r;
+          col[e] = k < len ? csr->col[k0 + k] : (len > 0 ? csr->col[k0 + len - 1] : std::max(row, 0));
+          val[e] = k < len ? csr->val[k0 + k] : 0.0;
+        }
+      }
+    }
+  });
+  int64_t *d_off;
+  int32_t *d_row, *d_col;
+  double *d_val;
+  TRY(upload(h, &d_off, off));
+  TRY(upload(h, &d_row, order));
+  TRY(upload(h, &d_col, col));
+  TRY(upload(h, &d_val, val));
+  h->sell.nslices = ns;
+  h->sell.off = d_off;
+  h->sell.row = d_row;
+  h->sell.col = d_col;
+  h->sell.val = d_val;
+  h->sell_entries = off[ns];
+  return DD_OK;
+}
+
 template <typename T>
 dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb,
                        double pivtol) {
@@ -793,6 +858,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     TRY(upload(h, &h->c_col, cc));
     TRY(upload(h, &h->c_val, vv));
   }
+  TRY(build_sell(h, csr));
   int32_t *d_part = nullptr, *d_pos = nullptr;
   TRY(upload(h, &d_part, std::vector<int32_t>(pt->part, pt->part + h->n)));
   TRY(upload(h, &d_pos, hb.pos));
@@ -1039,10 +1105,39 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     // X_j = A_jj^-1 E(I_j, gam_j)
     CK(launch_band_solve_multi<T>(h->d_info, m, d_ncols, d_xoff, max_gam, h->max_kl, h->max_ku2, h->tb,
                                   h->tm, B.ltile, B.utile, h->src, B.X, s));
-    // S(R_a,R_a) -= F(R_a, I_j) X_j
-    CK(launch_schur_accumulate<T>(m, d_fr_ptr, d_fr_row, d_fr_agg, d_fs_ptr, d_fs_col, B.fsub_val,
-                                  d_gam_ptr, d_gam_idx, d_gam_agg, d_xoff, h->d_info, B.X,
-                                  h->agg_off, h->s_off, Sdst, max_fr, max_gam, s));
+    // S(R_a,R_a) -= F(R_a, I_j) X_j, one launch per colour of subdomains: a
+    // subdomain takes the first colour that no earlier subdomain sharing an
+    // interface row with it holds, so the sum over j of every entry runs in
+    // colour order, the same on every run (no atomics)
+    std::vector<int32_t> color(m, -1), jlist, cptr(1, 0);
+    {
+      std::vector<std::vector<int32_t>> subs_of(nG);  // subdomains of each interface row
+      for (int j = 0; j < m; ++j)
+        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q) subs_of[fr_row[q]].push_back(j);
+      int ncolor = 0;
+      std::vector<int32_t> seen;  // colour -> last subdomain that saw it taken
+      for (int j = 0; j < m; ++j) {
+        seen.assign(ncolor + 1, -1);
+        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q)
+          for (int j2 : subs_of[fr_row[q]])
+            if (j2 < j && color[j2] >= 0) seen[color[j2]] = j;
+        int c = 0;
+        while (c < ncolor && seen[c] == j) ++c;
+        color[j] = c;
+        ncolor = std::max(ncolor, c + 1);
+      }
+      for (int c = 0; c < ncolor; ++c) {
+        for (int j = 0; j < m; ++j)
+          if (color[j] == c) jlist.push_back(j);
+        cptr.push_back((int32_t)jlist.size());
+      }
+    }
+    int32_t *d_jlist;
+    TRY(upload(h, &d_jlist, jlist));
+    for (size_t c = 0; c + 1 < cptr.size(); ++c)
+      CK(launch_schur_accumulate<T>(cptr[c + 1] - cptr[c], d_jlist + cptr[c], d_fr_ptr, d_fr_row, d_fr_agg,
+                                    d_fs_ptr, d_fs_col, B.fsub_val, d_gam_ptr, d_gam_idx, d_gam_agg, d_xoff,
+                                    h->d_info, B.X, h->agg_off, h->s_off, Sdst, max_fr, max_gam, s));
     return DD_OK;
   };
   if (h->kind == DD_MSCE_INF || h->kind == DD_EXACT) {
@@ -1133,6 +1228,7 @@ template <typename T>
 dd_status apply_T(DDHandle *h, const double *y, double *x, cudaStream_t s, int part = -1) {
   PrecBufs<T> &B = bufs<T>(h);
   SweepPlan pl = h->plan;
+  pl.first_wait = h->first_wait;
   const int32_t *agg_sys = nullptr, *act = nullptr;
   if (h->masked) {
     pl.task_sys = h->sub_sys;
@@ -1326,12 +1422,16 @@ dd_status arnoldi_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, co
   double *vj = h->V + (int64_t)j * h->ldv, *zj = h->Z + (int64_t)j * h->ldv;
   double *w = h->V + (int64_t)(j + 1) * h->ldv;
   TRY(apply_any(h, vj, zj, s));
+  const bool timed = h->time_kernels && sm.nseg == 1;
+  if (timed) CK(cudaEventRecord(h->kev[0], s));
   if (sm.nseg > 1)  // a batch: only the rows of systems still stepping
-    CK(launch_spmv_masked((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, h->row_sys, sm.act, s));
+    CK(launch_spmv_masked(h->sell, zj, w, h->row_sys, sm.act, s));
   else
-    CK(launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, zj, w, s));
+    CK(launch_spmv(h->sell, zj, w, s));
+  if (timed) CK(cudaEventRecord(h->kev[1], s));
   CK(launch_cgs2(h->n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
                  h->sn, h->g, bn2, h->out, sm, ncta, s));
+  if (timed) CK(cudaEventRecord(h->kev[2], s));
   CK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 4 * sm.nseg, cudaMemcpyDeviceToHost, s));
   return DD_OK;
 }
@@ -1381,12 +1481,17 @@ dd_status run_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, const 
   return DD_OK;
 }
 
-dd_status device_status(DDHandle *h, cudaStream_t s) {
+// The status word the apply's kernels record into (a bounded wait that gave
+// up); reading it synchronises the stream.  clear: reset it to DD_OK.
+dd_status device_status(DDHandle *h, cudaStream_t s, bool clear = false) {
   DevStatus dst{};
   CK(cudaMemcpyAsync(&dst, h->st, sizeof dst, cudaMemcpyDeviceToHost, s));
+  if (clear) CK(cudaMemsetAsync(h->st, 0, sizeof dst, s));
   CK(cudaStreamSynchronize(s));
   if (dst.code != 0) {
-    h->err = "device wait expired in an apply sweep";
+    char buf[96];
+    snprintf(buf, sizeof buf, "a bounded device wait gave up in an apply sweep (subdomain %d)", dst.block);
+    h->err = buf;
     return (dd_status)dst.code;
   }
   return DD_OK;
@@ -1399,6 +1504,7 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
   double relres = 0.0;
   dd_status rc = DD_ERR_NOT_CONVERGED;
   const SegMap sm = single_map(h);
+  CK(cudaMemsetAsync(h->st, 0, sizeof(DevStatus), s));  // this solve's own status
   CK(launch_zero(x, n, s));
   TRY(norm_sq(h, b, 2, s));
   TRY(read_scalars(h, h->nsq + 2, 1, s));
@@ -1417,20 +1523,34 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
     for (int j = 0; j < R; ++j) {
       TRY(run_step(h, j, R, sm, h->cgs_blocks, h->nsq + 2, s));
       CK(cudaStreamSynchronize(s));
+      if (h->time_kernels) {
+        float t0 = 0.f, t1 = 0.f;
+        CK(cudaEventElapsedTime(&t0, h->kev[0], h->kev[1]));
+        CK(cudaEventElapsedTime(&t1, h->kev[1], h->kev[2]));
+        h->stats.krylov_steps += 1;
+        h->stats.spmv_ms += t0;
+        h->stats.cgs2_ms += t1;
+        h->stats.cgs2_fma += (4.0 * (j + 1) + 2.0) * (double)n;
+      }
       ++iters;
       const double est = h->h_out[2];
       const bool breakdown = h->h_out[1] != 0.0;
       if (info && info->history && iters - 1 < info->history_cap) info->history[iters - 1] = est;
       jlast = j;
-      if (!isfinite(est)) { rc = DD_ERR_NONFINITE; goto done; }
+      if (!isfinite(est)) {
+        // a sweep that gave up leaves z unwritten: report that first
+        const dd_status ds = device_status(h, s, true);
+        rc = ds != DD_OK ? ds : DD_ERR_NONFINITE;
+        goto done;
+      }
       if (est <= tol || breakdown || iters >= maxit) break;
     }
     CK(launch_hess_solve_update(n, jlast, R, h->H, h->g, h->y, h->Z, h->ldv, x, s));
-    CK(launch_residual(n, h->c_rowptr, h->c_col, h->c_val, x, b, h->r, s));
+    CK(launch_residual(h->sell, x, b, h->r, s));
     TRY(norm_sq(h, h->r, 3, s));
     TRY(read_scalars(h, h->nsq + 3, 1, s));
     {
-      const dd_status ds = device_status(h, s);
+      const dd_status ds = device_status(h, s, true);
       if (ds != DD_OK) { rc = ds; break; }
     }
     relres = sqrt(h->h_out[0]) / bnorm;
@@ -1464,6 +1584,7 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
   } mask(h);
   SegMap all = sm;
   all.act = nullptr;
+  CK(cudaMemsetAsync(h->st, 0, sizeof(DevStatus), s));  // this solve's own status
   for (int q = 0; q < S; ++q) {
     const int64_t r0 = h->seg_row0_h[q], ns = h->seg_row0_h[q + 1] - r0;
     if (ns > 0)
@@ -1527,10 +1648,10 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
     }
     CK(cudaMemcpyAsync(h->d_jl, jl, sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
     CK(launch_seg_hess_update(n, R, h->d_jl, h->H, h->g, h->y, h->Z, h->ldv, h->xcat, all, nc, s));
-    CK(launch_residual((int)n, h->c_rowptr, h->c_col, h->c_val, h->xcat, h->bcat, h->r, s));
+    CK(launch_residual(h->sell, h->xcat, h->bcat, h->r, s));
     CK(launch_seg_norms(n, h->r, h->partial, h->rn2, all, nc, s));
     CK(cudaMemcpyAsync(h->h_out, h->rn2, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
-    rc_dev = device_status(h, s);
+    rc_dev = device_status(h, s, true);
     if (rc_dev != DD_OK) break;
     for (int q = 0; q < S; ++q) {
       if (done[q] || jl[q] < 0) continue;
@@ -1562,6 +1683,8 @@ void release(DDHandle *h) {
   drop_graphs(h);
   if (h->gstream) { cudaStreamSynchronize(h->gstream); cudaStreamDestroy(h->gstream); h->gstream = nullptr; }
   for (cudaEvent_t &e : h->gev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
+  for (cudaEvent_t &e : h->kev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
   for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
@@ -1609,12 +1732,14 @@ dd_status apply_scratch_T(DDHandle *h, const double *y, double *x, double *scrat
   const size_t z1_elems = (((size_t)std::max(h->nI, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   const size_t z2_elems = (((size_t)std::max(h->nG, 1) * sizeof(T) + 255) / 256) * 256 / sizeof(T);
   T *z2 = z1 + z1_elems;
-  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+  SweepPlan pl = h->plan;
+  pl.first_wait = h->first_wait;
+  CK(launch_band_solve_fwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, pl,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, y, h->d_perm, z1, h->st, s));
   CK(launch_schur_apply<T>(h->nagg, h->agg_off, h->s_off, h->pmax, B.S, h->f_ptr, h->f_col,
                            B.f_val, y, h->d_perm + h->nI, z1, z2, z2 + z2_elems, h->nG, x, nullptr,
                            nullptr, s));
-  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, h->plan,
+  CK(launch_band_solve_bwd<T>(h->d_info, h->m, h->max_n, h->max_kl, h->max_ku2, pl,
                               h->tm, h->jobs, B.ltile, B.utile, h->src, h->e_ptr, h->e_col, B.e_val,
                               z2, z1, h->d_perm, x, h->st, s));
   return DD_OK;
@@ -1686,6 +1811,7 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->kind = approx;
   h->use_graph = o.use_graph != 0;
   h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : 2;
+  h->time_kernels = o.time_kernels != 0 && !h->use_graph;
   const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
   const int R = o.max_restart > 0 ? o.max_restart : 50;
   if (R > 120) { h->err = "max_restart must be <= 120"; return DD_ERR_INVALID_ARG; }
@@ -1725,6 +1851,9 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
         rc = DD_ERR_CUDA;
       }
     }
+    if (rc == DD_OK && h->time_kernels)
+      for (cudaEvent_t &e : h->kev)
+        if (cudaEventCreate(&e) != cudaSuccess) { h->err = "event creation failed"; rc = DD_ERR_CUDA; break; }
     cudaEventRecord(e1, h->stream);
     cudaError_t se = cudaStreamSynchronize(h->stream);
     if (rc == DD_OK && se != cudaSuccess) { h->err = cudaGetErrorString(se); rc = DD_ERR_CUDA; }
@@ -2036,10 +2165,53 @@ dd_status gmres_solve_batched(void *handle, const double *const *b, double *cons
   return rc;
 }
 
+dd_status dd_fp64_peak(double *gfma, void *stream) {
+  if (!gfma) return DD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return DD_ERR_CUDA;
+  const int blocks = 8 * sms, iters = 2048;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DD_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DD_ERR_CUDA; }
+  float best = 1e30f;
+  dd_status rc = DD_OK;
+  for (int rep = 0; rep < 4 && rc == DD_OK; ++rep) {
+    cudaEventRecord(e0, s);
+    if (launch_fma_probe(blocks, iters, s) != cudaSuccess) rc = DD_ERR_CUDA;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = DD_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms > 0.f) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DD_OK) return rc;
+  *gfma = (double)blocks * 256.0 * 8.0 * iters / (best * 1e-3) / 1e9;
+  return DD_OK;
+}
+
+dd_status dd_check_status(void *handle, void *stream) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h) return DD_ERR_INVALID_ARG;
+  return device_status(h, static_cast<cudaStream_t>(stream), true);
+}
+
+dd_status dd_set_wait_limit(void *handle, uint32_t first_wait_polls) {
+  DDHandle *h = static_cast<DDHandle *>(handle);
+  if (!h) return DD_ERR_INVALID_ARG;
+  h->first_wait = first_wait_polls;
+  drop_graphs(h);  // captured steps hold the old kernel arguments
+  return DD_OK;
+}
+
 dd_status dd_spmv(void *handle, const double *x, double *y, void *stream) {
   DDHandle *h = static_cast<DDHandle *>(handle);
   if (!h || !x || !y) return DD_ERR_INVALID_ARG;
-  cudaError_t e = launch_spmv((int)h->n, h->c_rowptr, h->c_col, h->c_val, x, y, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_spmv(h->sell, x, y, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) { h->err = cudaGetErrorString(e); return DD_ERR_CUDA; }
   return DD_OK;
 }

@@ -86,6 +86,9 @@ struct SweepPlan {
   // system has stopped stepping); null: every subdomain
   const int32_t *task_sys = nullptr;
   const int32_t *act = nullptr;
+  // polls of the first mbarrier wait of every sweep CTA (a test hook of the
+  // timeout path); larger than the normal bound means the normal bound
+  uint32_t first_wait = 0xffffffffu;
 };
 
 // Device-side error word: first failure wins.
@@ -174,7 +177,9 @@ template <typename T>
 cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *val, T *dst,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_schur_accumulate(int m, const int32_t *fr_ptr, const int32_t *fr_row,
+// one colour of subdomains: jlist (device) holds its nj subdomains, no two of
+// which share an interface row
+cudaError_t launch_schur_accumulate(int nj, const int32_t *jlist, const int32_t *fr_ptr, const int32_t *fr_row,
                                     const int32_t *fr_agg, const int32_t *f_ptr,
                                     const int32_t *f_col, const T *f_val, const int32_t *gam_ptr,
                                     const int32_t *gam_idx, const int32_t *gam_agg,
@@ -198,14 +203,28 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                const int32_t *act, cudaStream_t s);
 
 // Krylov (k_krylov.cu), FP64
-cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                        const double *x, double *y, cudaStream_t s);
+// C in SELL-32 form: slices of 32 rows; slice s holds w_s = (off[s+1] -
+// off[s]) / 32 entries per row, stored entry-major (entry k of lane r at
+// off[s] + 32 k + r), each row's entries in CSR order and padded with value 0
+// at its last column.  Rows are sorted by decreasing length inside windows
+// of DD_SELL_WINDOW rows, so a slice's rows have nearly equal lengths;
+// row[32 s + r] is the matrix row of lane r (-1: padding past the last row).
+#define DD_SELL_WINDOW 256
+struct SellC {
+  int64_t nslices = 0;
+  const int64_t *off = nullptr;
+  const int32_t *row = nullptr;
+  const int32_t *col = nullptr;
+  const double *val = nullptr;
+};
+cudaError_t launch_spmv(const SellC &c, const double *x, double *y, cudaStream_t s);
 // y = C x on the rows i with act[row_sys[i]] != 0 (the other rows untouched)
-cudaError_t launch_spmv_masked(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                               const double *x, double *y, const int32_t *row_sys, const int32_t *act,
-                               cudaStream_t s);
-cudaError_t launch_residual(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                            const double *x, const double *b, double *r, cudaStream_t s);
+cudaError_t launch_spmv_masked(const SellC &c, const double *x, double *y, const int32_t *row_sys,
+                               const int32_t *act, cudaStream_t s);
+// FP64 FMA probe: blocks x 256 threads, 8 chains of `iters` FMAs each
+cudaError_t launch_fma_probe(int blocks, int iters, cudaStream_t s);
+// r = b - C x
+cudaError_t launch_residual(const SellC &c, const double *x, const double *b, double *r, cudaStream_t s);
 cudaError_t launch_multidot(int n, int k, const double *V, int64_t ldv, const double *w,
                             double *partial, int nblocks, cudaStream_t s);
 cudaError_t launch_reduce_cols(int nblocks, int k, const double *partial, double *out,

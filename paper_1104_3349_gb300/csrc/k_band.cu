@@ -571,8 +571,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 #define DD_WAIT_LIMIT (1u << 22)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < DD_WAIT_LIMIT; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t limit = DD_WAIT_LIMIT) {
+  limit = min(limit, DD_WAIT_LIMIT);
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -654,7 +656,8 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
                                 const T *__restrict__ utile, const int32_t *__restrict__ srcs,
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
-                                uint32_t &jbase, int task, bool issued, DevStatus *st) {
+                                uint32_t &jbase, int task, bool issued, DevStatus *st,
+                                uint32_t first_wait) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -669,7 +672,9 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     unsigned char *stage = ring + (size_t)sidx * stage_bytes;
     // every thread waits (bounded); the outcome is made uniform at the
     // first barrier of the job, so no thread can leave the loop alone
-    const bool got = mbar_wait_bounded(&bars[sidx], (gq / nstages) & 1u);
+    // (the CTA's first wait may be shortened by the timeout test hook; the
+    // drain below always takes the full bound)
+    const bool got = mbar_wait_bounded(&bars[sidx], (gq / nstages) & 1u, gq == 0 ? first_wait : DD_WAIT_LIMIT);
     bool fwd;
     const SweepJob jb = get_job(b, jobs, q, fwd);
     const TileMeta &a = tm[b.tile0 + jb.lo];
@@ -815,7 +820,8 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
                                       const int32_t *__restrict__ sched,
                                       const int32_t *__restrict__ sched_off,
                                       const int32_t *__restrict__ task_sys,
-                                      const int32_t *__restrict__ act, DevStatus *st) {
+                                      const int32_t *__restrict__ act, DevStatus *st,
+                                      uint32_t first_wait) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -840,7 +846,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     }
     __syncthreads();
     if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, true, st))
+                            nstages, bars, jbase, task, true, st, first_wait))
       return;
     for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
   }
@@ -861,7 +867,8 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       double *x, const int32_t *__restrict__ sched,
                                       const int32_t *__restrict__ sched_off,
                                       const int32_t *__restrict__ task_sys,
-                                      const int32_t *__restrict__ act, DevStatus *st) {
+                                      const int32_t *__restrict__ act, DevStatus *st,
+                                      uint32_t first_wait) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -891,7 +898,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     }
     __syncthreads();
     if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, true, st))
+                            nstages, bars, jbase, task, true, st, first_wait))
       return;
     for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
       const int r = b.row0 + i;
@@ -1085,7 +1092,7 @@ static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   band_solve_fwd_kernel<T, TB><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
                                                               pl.stage_bytes, tm, jobs, ltile, utile, src,
                                                               y, perm, z, pl.sched, pl.sched_off,
-                                                              pl.task_sys, pl.act, st);
+                                                              pl.task_sys, pl.act, st, pl.first_wait);
   return cudaGetLastError();
 }
 
@@ -1121,7 +1128,7 @@ static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
                                                               pl.stage_bytes, tm, jobs, ltile, utile, src,
                                                               e_ptr, e_col, e_val, z2, z1, perm, x,
                                                               pl.sched, pl.sched_off, pl.task_sys, pl.act,
-                                                              st);
+                                                              st, pl.first_wait);
   return cudaGetLastError();
 }
 

@@ -719,9 +719,15 @@ __global__ void scatter_coo_kernel(int64_t nnz, const int64_t *__restrict__ idx,
 
 // S(R_a, R_a) -= F(r, I_j) X_j(:, c) for every interface pair (r, c) that
 // the subdomain j couples (r: rows of F into I_j, c: columns of E from I_j)
-// and that fall into the same aggregate a.
+// and that fall into the same aggregate a, for the subdomains j = jlist[x]
+// of one colour.  No two subdomains of a colour share an interface row, and
+// within one subdomain every (r, c) is a different entry, so the updates are
+// plain read-modify-writes; the colours run one after the other in a fixed
+// order, so the sum over j of every entry is taken in the same order on
+// every run.
 template <typename T>
-__global__ void schur_accumulate_kernel(const int32_t *__restrict__ fr_ptr,
+__global__ void schur_accumulate_kernel(const int32_t *__restrict__ jlist,
+                                        const int32_t *__restrict__ fr_ptr,
                                         const int32_t *__restrict__ fr_row,
                                         const int32_t *__restrict__ fr_agg,
                                         const int32_t *__restrict__ f_ptr,
@@ -734,7 +740,7 @@ __global__ void schur_accumulate_kernel(const int32_t *__restrict__ fr_ptr,
                                         const BandInfo *__restrict__ info, const T *__restrict__ X,
                                         const int32_t *__restrict__ agg_off,
                                         const int64_t *__restrict__ s_off, T *S) {
-  const int j = blockIdx.x;
+  const int j = jlist[blockIdx.x];
   const int r_lo = fr_ptr[j], r_hi = fr_ptr[j + 1];
   const int rr = r_lo + blockIdx.y;
   if (rr >= r_hi) return;
@@ -751,7 +757,7 @@ __global__ void schur_accumulate_kernel(const int32_t *__restrict__ fr_ptr,
     const T *xc = Xj + (int64_t)(g - g_lo) * nj;
     T s = T(0);
     for (int k = f_ptr[rr]; k < f_ptr[rr + 1]; ++k) s += f_val[k] * xc[f_col[k]];
-    atomicAdd(&Sa[(int64_t)(row - agg_off[a]) * p + (col - agg_off[a])], -s);
+    Sa[(int64_t)(row - agg_off[a]) * p + (col - agg_off[a])] -= s;
   }
 }
 
@@ -996,16 +1002,16 @@ cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *va
 }
 
 template <typename T>
-cudaError_t launch_schur_accumulate(int m, const int32_t *fr_ptr, const int32_t *fr_row,
+cudaError_t launch_schur_accumulate(int nj, const int32_t *jlist, const int32_t *fr_ptr, const int32_t *fr_row,
                                     const int32_t *fr_agg, const int32_t *f_ptr,
                                     const int32_t *f_col, const T *f_val, const int32_t *gam_ptr,
                                     const int32_t *gam_idx, const int32_t *gam_agg,
                                     const int64_t *x_off, const BandInfo *d_info, const T *X,
                                     const int32_t *agg_off, const int64_t *s_off, T *S,
                                     int max_fr, int max_gam, cudaStream_t s) {
-  if (m <= 0 || max_fr <= 0 || max_gam <= 0) return cudaSuccess;
-  dim3 grid(m, max_fr);
-  schur_accumulate_kernel<T><<<grid, 128, 0, s>>>(fr_ptr, fr_row, fr_agg, f_ptr, f_col, f_val,
+  if (nj <= 0 || max_fr <= 0 || max_gam <= 0) return cudaSuccess;
+  dim3 grid(nj, max_fr);
+  schur_accumulate_kernel<T><<<grid, 128, 0, s>>>(jlist, fr_ptr, fr_row, fr_agg, f_ptr, f_col, f_val,
                                                   gam_ptr, gam_idx, gam_agg, x_off, d_info, X,
                                                   agg_off, s_off, S);
   return cudaGetLastError();
@@ -1063,6 +1069,7 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                              cudaStream_t);                                        \
   template cudaError_t launch_schur_accumulate<T>(                                                \
       int, const int32_t *, const int32_t *, const int32_t *, const int32_t *, const int32_t *,   \
+      const int32_t *,                                                                            \
       const T *, const int32_t *, const int32_t *, const int32_t *, const int64_t *,              \
       const BandInfo *, const T *, const int32_t *, const int64_t *, T *, int, int, cudaStream_t); \
   template cudaError_t launch_block_gemm<T>(int, const int32_t *, const int64_t *, int, const T *, \

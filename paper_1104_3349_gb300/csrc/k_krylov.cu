@@ -15,38 +15,51 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-// one thread per row; rows of C hold at most a handful of entries
-__global__ void spmv_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ x,
-                            double *__restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * __ldg(&x[col[k]]);
-  y[i] = s;
-}
-
-// the same, for the rows whose system is still stepping (act[row_sys[i]])
-__global__ void spmv_masked_kernel(int n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                   const double *__restrict__ val, const double *__restrict__ x,
-                                   double *__restrict__ y, const int32_t *__restrict__ row_sys,
-                                   const int32_t *__restrict__ act) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || !act[row_sys[i]]) return;
-  double s = 0.0;
-  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * __ldg(&x[col[k]]);
-  y[i] = s;
-}
-
-__global__ void residual_kernel(int n, const int32_t *__restrict__ rowptr,
-                                const int32_t *__restrict__ col, const double *__restrict__ val,
-                                const double *__restrict__ x, const double *__restrict__ b,
-                                double *__restrict__ r) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * __ldg(&x[col[k]]);
-  r[i] = b[i] - s;
+// ---------------------------------------------------------------------------
+// SpMV on C in SELL-32 form (see SellC in dd_internal.h): one thread per row,
+// the 32 rows of a slice in the 32 lanes of a warp, so every load of a column
+// index or a value is one coalesced 128- or 256-byte access of the warp.  The
+// column indices and values of four entries are loaded before their four
+// gathers of x, so each thread has several independent loads in flight.  A
+// row's entries are summed in their CSR order with fused multiply-adds, as
+// the oracle's plain CSR product does; the padding entries (value 0, the
+// row's last column) add nothing.
+//   MODE 0: y = C x;  MODE 1: y = b - C x;  MODE 2: y = C x on the rows whose
+//   system is still stepping (act[row_sys[row]] != 0), others untouched.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) sell_spmv_kernel(SellC c, const double *__restrict__ x,
+                                                        const double *__restrict__ b, double *__restrict__ y,
+                                                        const int32_t *__restrict__ row_sys,
+                                                        const int32_t *__restrict__ act) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sl = gt >> 5;
+  if (sl >= c.nslices) return;
+  const int row = __ldg(&c.row[gt]);
+  if (row < 0) return;  // padding row of the last slice
+  if (MODE == 2 && !__ldg(&act[__ldg(&row_sys[row])])) return;
+  const int64_t o = __ldg(&c.off[sl]);
+  const int w = (int)((__ldg(&c.off[sl + 1]) - o) >> 5);
+  const int32_t *cp = c.col + o + (gt & 31);
+  const double *vp = c.val + o + (gt & 31);
+  double acc = 0.0;
+  for (int k0 = 0; k0 < w; k0 += 4) {
+    int ci[4];
+    double vv[4], xx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u < w) {
+        ci[u] = __ldg(cp + 32 * (k0 + u));
+        vv[u] = __ldg(vp + 32 * (k0 + u));
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u < w) xx[u] = __ldg(x + ci[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u < w) acc = fma(vv[u], xx[u], acc);
+  }
+  y[row] = MODE == 1 ? b[row] - acc : acc;
 }
 
 // partial[b*k + q] = sum over this CTA's rows of V_q[i] * w[i]
@@ -193,67 +206,88 @@ __global__ void zero_kernel(double *p, int64_t n) {
 #define DD_CGS_THREADS 256
 #define DD_CGS_MAXK 128  // restart lengths up to DD_CGS_MAXK - 2
 
-// Sum of 16 per-lane values over a warp with 16 FP64 additions per lane:
-// each butterfly step hands half of the remaining values to the partner lane
-// and keeps the other half.  On return lane l holds the warp sum of value
-// v(l) = 8*bit4 + 4*bit3 + 2*bit2 + bit1 of l (lanes l and l^1 agree).
-__device__ __forceinline__ double warp_sum16(const double (&a)[16]) {
+// Sum over a warp of G per-lane values (G = 4, 8 or 16), transposed: each
+// butterfly step hands half of the remaining values to the partner lane and
+// keeps the other half, then the last value is summed over the lanes that
+// share it.  On return lane l holds the warp sum of value
+// v(l) = sum over the halving steps st of [bit (16 >> st) of l] * (G >> (st+1)),
+// and the lanes with l % (32 / G) == 0 hold distinct values.  G - 1 + 5 -
+// log2(G) FP64 additions per lane: FP64 is the scarce pipe on GB300.
+template <int G>
+__device__ __forceinline__ double warp_sum_t(double (&a)[G]) {
+  constexpr int LOG = G == 16 ? 4 : (G == 8 ? 3 : 2);
+  static_assert((1 << LOG) == G, "G must be 4, 8 or 16");
   const int lane = threadIdx.x & 31;
-  double b[8], c[4], d[2];
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
 #pragma unroll
-  for (int s2 = 0; s2 < 8; ++s2) {
-    const double give = h16 ? a[s2] : a[s2 + 8], keep = h16 ? a[s2 + 8] : a[s2];
-    b[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
-  }
+  for (int st = 0; st < LOG; ++st) {
+    const int off = 16 >> st, half = G >> (st + 1);
+    const bool hi = (lane & off) != 0;
 #pragma unroll
-  for (int s2 = 0; s2 < 4; ++s2) {
-    const double give = h8 ? b[s2] : b[s2 + 4], keep = h8 ? b[s2 + 4] : b[s2];
-    c[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    for (int s2 = 0; s2 < half; ++s2) {
+      const double give = hi ? a[s2] : a[s2 + half], keep = hi ? a[s2 + half] : a[s2];
+      a[s2] = keep + __shfl_xor_sync(0xffffffffu, give, off);
+    }
   }
+  double e = a[0];
 #pragma unroll
-  for (int s2 = 0; s2 < 2; ++s2) {
-    const double give = h4 ? c[s2] : c[s2 + 2], keep = h4 ? c[s2 + 2] : c[s2];
-    d[s2] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
-  }
-  const double give = h2 ? d[0] : d[1], keep = h2 ? d[1] : d[0];
-  double e = keep + __shfl_xor_sync(0xffffffffu, give, 2);
-  return e + __shfl_xor_sync(0xffffffffu, e, 1);
+  for (int off = 16 >> LOG; off >= 1; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+  return e;
 }
 
-// partial dots of 16 columns at a time: 16 independent accumulators per
-// thread over its rows, a butterfly per warp, then the warps through shared
-// memory (fixed order)
-__device__ void block_dots(int i0, int i1, int k, const double *__restrict__ V, int64_t ldv,
+// partial dots of columns q0 .. q0+G-1 (those below ktot): G independent
+// accumulators per thread over its rows, the transposed butterfly per warp,
+// then the warps through shared memory in a fixed order.  Column k is w's
+// own square when `self`.
+template <int G>
+__device__ void dots_group(int i0, int i1, int q0, int k, int ktot, const double *__restrict__ V, int64_t ldv,
                            const double *__restrict__ w, bool self, double *out, double *red) {
+  constexpr int LOG = G == 16 ? 4 : (G == 8 ? 3 : 2);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int ktot = k + (self ? 1 : 0);
-  for (int q0 = 0; q0 < ktot; q0 += 16) {
-    double a[16];
+  double a[G];
 #pragma unroll
-    for (int s2 = 0; s2 < 16; ++s2) a[s2] = 0.0;
+  for (int s2 = 0; s2 < G; ++s2) a[s2] = 0.0;
+  if (q0 + G <= k) {  // every column a basis vector: no tests in the loop
     for (int i = i0 + tid; i < i1; i += blockDim.x) {
       const double wi = w[i];
 #pragma unroll
-      for (int s2 = 0; s2 < 16; ++s2) {
+      for (int s2 = 0; s2 < G; ++s2) a[s2] += V[(int64_t)(q0 + s2) * ldv + i] * wi;
+    }
+  } else {
+    for (int i = i0 + tid; i < i1; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int s2 = 0; s2 < G; ++s2) {
         const int q = q0 + s2;
         if (q < k) a[s2] += V[(int64_t)q * ldv + i] * wi;
         else if (q == k && self) a[s2] += wi * wi;
       }
     }
-    const double ws = warp_sum16(a);
-    if ((lane & 1) == 0) {
-      const int v = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-      red[warp * 16 + v] = ws;
-    }
-    __syncthreads();
-    if (tid < 16 && q0 + tid < ktot) {
-      double t = 0.0;
-      for (int ww = 0; ww < nw; ++ww) t += red[ww * 16 + tid];
-      out[q0 + tid] = t;
-    }
-    __syncthreads();
   }
+  const double ws = warp_sum_t<G>(a);
+  if ((lane & ((32 / G) - 1)) == 0) {
+    int v = 0;
+#pragma unroll
+    for (int st = 0; st < LOG; ++st) v += ((lane >> (4 - st)) & 1) * (G >> (st + 1));
+    red[warp * 16 + v] = ws;
+  }
+  __syncthreads();
+  if (tid < G && q0 + tid < ktot) {
+    double t = 0.0;
+    for (int ww = 0; ww < nw; ++ww) t += red[ww * 16 + tid];
+    out[q0 + tid] = t;
+  }
+  __syncthreads();
+}
+
+// partial dots of all ktot = k (+1 with self) columns in groups of exact
+// width 16, then 8, then 4 (the last group padded by at most 3 columns)
+__device__ void block_dots(int i0, int i1, int k, const double *__restrict__ V, int64_t ldv,
+                           const double *__restrict__ w, bool self, double *out, double *red) {
+  const int ktot = k + (self ? 1 : 0);
+  int q0 = 0;
+  for (; ktot - q0 >= 16; q0 += 16) dots_group<16>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red);
+  if (ktot - q0 >= 8) { dots_group<8>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red); q0 += 8; }
+  for (; q0 < ktot; q0 += 4) dots_group<4>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red);
 }
 
 // w_i - sum_q h_q V_q[i], eight loads in flight per thread
@@ -545,22 +579,48 @@ __global__ void seg_update_x_kernel(int64_t n, const int32_t *__restrict__ jl, c
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_spmv(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                        const double *x, double *y, cudaStream_t s) {
-  spmv_kernel<<<nblk(n, 256), 256, 0, s>>>(n, rowptr, col, val, x, y);
+// ---------------------------------------------------------------------------
+// FP64 multiply-add rate: every thread runs 8 independent chains of dependent
+// FMAs (a <- a * b + c); the result goes to a file-scope sink so the chains
+// are not removed.  FMAs per launch: blocks * 256 * 8 * iters.
+// ---------------------------------------------------------------------------
+__device__ double g_fma_sink;
+
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = 1e-3 * (threadIdx.x + u);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(a[u], b, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) t += a[u];
+  if (t == 12345.678) g_fma_sink = t;  // never true for the probe's inputs
+}
+
+cudaError_t launch_fma_probe(int blocks, int iters, cudaStream_t s) {
+  fma_probe_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spmv_masked(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                               const double *x, double *y, const int32_t *row_sys, const int32_t *act,
-                               cudaStream_t s) {
-  spmv_masked_kernel<<<nblk(n, 256), 256, 0, s>>>(n, rowptr, col, val, x, y, row_sys, act);
+static inline unsigned sell_blocks(const SellC &c) { return (unsigned)((c.nslices * 32 + 255) / 256); }
+
+cudaError_t launch_spmv(const SellC &c, const double *x, double *y, cudaStream_t s) {
+  if (c.nslices <= 0) return cudaSuccess;
+  sell_spmv_kernel<0><<<sell_blocks(c), 256, 0, s>>>(c, x, nullptr, y, nullptr, nullptr);
   return cudaGetLastError();
 }
-
-cudaError_t launch_residual(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                            const double *x, const double *b, double *r, cudaStream_t s) {
-  residual_kernel<<<nblk(n, 256), 256, 0, s>>>(n, rowptr, col, val, x, b, r);
+cudaError_t launch_spmv_masked(const SellC &c, const double *x, double *y, const int32_t *row_sys,
+                               const int32_t *act, cudaStream_t s) {
+  if (c.nslices <= 0) return cudaSuccess;
+  sell_spmv_kernel<2><<<sell_blocks(c), 256, 0, s>>>(c, x, nullptr, y, row_sys, act);
+  return cudaGetLastError();
+}
+cudaError_t launch_residual(const SellC &c, const double *x, const double *b, double *r, cudaStream_t s) {
+  if (c.nslices <= 0) return cudaSuccess;
+  sell_spmv_kernel<1><<<sell_blocks(c), 256, 0, s>>>(c, x, b, r, nullptr, nullptr);
   return cudaGetLastError();
 }
 

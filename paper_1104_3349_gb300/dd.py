@@ -80,7 +80,7 @@ class dd_partition(ctypes.Structure):
 class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2),
+                ("time_kernels", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("mlp_weights", ctypes.c_char_p)]
 
 
@@ -100,10 +100,13 @@ class dd_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("stage_bytes", ctypes.c_int32), ("sweep_grid", ctypes.c_int32),
                 ("sweep_slots", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tuned_us", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32), ("learned_entries", ctypes.c_int64),
-                ("learned_fallback", ctypes.c_int32), ("pad3", ctypes.c_int32)]
+                ("learned_fallback", ctypes.c_int32), ("pad3", ctypes.c_int32),
+                ("krylov_steps", ctypes.c_int64), ("cgs2_ms", ctypes.c_double), ("cgs2_fma", ctypes.c_double),
+                ("spmv_ms", ctypes.c_double)]
 
 
 EXPORTS = ["dd_setup", "dd_setup_batched", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve",
+           "dd_check_status", "dd_set_wait_limit", "dd_fp64_peak",
            "gmres_solve_batched", "dd_spmv", "dd_get_stats", "dd_get_bad_block", "dd_destroy", "dd_last_error",
            "dd_learned_entries", "dd_mlp_create", "dd_mlp_set_data", "dd_mlp_loss_grad", "dd_mlp_adam_step",
            "dd_mlp_predict", "dd_mlp_get", "dd_mlp_set_adam", "dd_mlp_destroy"]
@@ -139,6 +142,12 @@ def load(path: str = LIB_PATH):
     lib.dd_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.dd_apply_part.restype = ctypes.c_int
     lib.dd_apply_part.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
+    lib.dd_check_status.restype = ctypes.c_int
+    lib.dd_check_status.argtypes = [vp, vp]
+    lib.dd_fp64_peak.restype = ctypes.c_int
+    lib.dd_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.dd_set_wait_limit.restype = ctypes.c_int
+    lib.dd_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
     lib.dd_spmv.restype = ctypes.c_int
     lib.dd_spmv.argtypes = [vp, vp, vp, vp]
     lib.dd_get_stats.restype = ctypes.c_int
@@ -203,7 +212,7 @@ class DD:
 
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
-                 autotune=False, mlp_weights=None, krylov_ctas_per_sm=0):
+                 autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -216,6 +225,7 @@ class DD:
         pt = dd_partition(int(m), _ptr(pa), _ptr(pe), int(sz), _ptr(ag), 0 if ag is None else len(ag) - 1)
         o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
                     int(krylov_ctas_per_sm))
+        o.time_kernels = int(bool(time_kernels))
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
@@ -262,6 +272,14 @@ class DD:
         self._check(self._lib.dd_apply_part(self._h, int(part), _dev_ptr(y, self.n), _dev_ptr(x, self.n),
                                             _stream_handle(stream)))
 
+    def check_status(self, stream=None):
+        """Synchronise the stream and return (and clear) the handle's device status word."""
+        return int(self._lib.dd_check_status(self._h, _stream_handle(stream)))
+
+    def set_wait_limit(self, first_wait_polls):
+        """Test hook: polls of the first bounded wait of every sweep CTA (0: give up at once)."""
+        self._check(self._lib.dd_set_wait_limit(self._h, int(first_wait_polls) & 0xFFFFFFFF))
+
     def spmv(self, x, y, stream=None):
         self._check(self._lib.dd_spmv(self._h, _dev_ptr(x, self.n), _dev_ptr(y, self.n), _stream_handle(stream)))
 
@@ -294,6 +312,16 @@ class DD:
         delta = np.zeros(n, np.float32)
         self._check(self._lib.dd_learned_entries(self._h, _ptr(ents), _ptr(feats), _ptr(delta), n, ctypes.byref(cnt)))
         return ents, feats, delta
+
+
+def fp64_peak(stream=None) -> float:
+    """FP64 fused multiply-adds per second / 1e9 of the current device (dd_fp64_peak)."""
+    lib = load()
+    v = ctypes.c_double()
+    rc = lib.dd_fp64_peak(ctypes.byref(v), _stream_handle(stream))
+    if rc != 0:
+        raise DDError(rc, "dd_fp64_peak")
+    return float(v.value)
 
 
 class DDBatch:

@@ -270,6 +270,18 @@ def stretched1024() -> Workload:
     return make_workload("oseen_mac_1024x1024_aspect100_nu1e-3_m1024", 1024, 1e-3, r, WIND_FOURIER, 5000, 1024)
 
 
+def learned64(seed: int) -> Workload:
+    """One problem of the learned correction's family: 64x64 MAC Oseen with nu
+    log-uniform in [1e-3, 1e-2] and wall stretching ratio uniform in [1, 1.03]
+    (both drawn from the seed's stream), the seeded 8-mode Fourier wind, 4
+    subdomains, aggregates of nominal size 64.  The training set uses seeds
+    5000-6999; seeds 9000 and up are held out."""
+    u = uniform(seed, 2, 0.0, 1.0)
+    nu = log_uniform(1e-3, 1e-2, float(u[0]))
+    return make_workload(f"oseen_mac_64x64_learned_seed{seed}", 64, nu, 1.0 + 0.03 * float(u[1]), WIND_FOURIER,
+                         seed, 4, sz=64)
+
+
 def max_aspect(n: int, r: float) -> float:
     h = spacing(n, r)
     return float(h.max() / h.min())

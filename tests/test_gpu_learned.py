@@ -221,3 +221,31 @@ def test_learned_in_a_batch_matches_each_oracle(env):
         assert np.linalg.norm(xs - xr) <= 1e-4 * np.linalg.norm(xr), q
         R.close()
     P.close()
+
+
+def test_learned_gains_over_lum_on_heldout_problems(env):
+    """What the trained network gains: on the eight held-out 64x64 problems
+    (seeds 9000-9007, outside the training seeds 5000-6999), FGMRES(50) with
+    the learned blocks needs fewer iterations than with the lumped blocks G_ii
+    (LUM, the method without the correction) on every problem.  The MSCE_INF
+    blocks the network is trained on are solved too, for the record."""
+    torch, dd, dev = env
+    if not os.path.exists(WEIGHTS):
+        pytest.skip("no trained weights")
+    rows = []
+    for seed in range(9000, 9008):
+        w = W.learned64(seed)
+        its = {}
+        for kind in ("lum", "learned", "msce_inf"):
+            P = dd.DD(w.A, w.part, w.m, kind, perm=w.perm, agg_offsets=w.agg, prec=dd.DD_FP32,
+                      mlp_weights=WEIGHTS if kind == "learned" else None)
+            bd = torch.from_numpy(w.b).to(dev)
+            r = P.gmres(bd, torch.zeros_like(bd), tol=1e-8, restart=50, maxit=3000)
+            P.close()
+            assert r["status"] == 0 and r["relres"] <= 1e-8, (seed, kind, r["status"])
+            its[kind] = r["iters"]
+        rows.append((seed, its))
+    print("held-out iterations (seed: lum / learned / msce_inf): " +
+          ", ".join(f"{s}: {i['lum']}/{i['learned']}/{i['msce_inf']}" for s, i in rows))
+    for seed, its in rows:
+        assert its["learned"] < its["lum"], (seed, its)

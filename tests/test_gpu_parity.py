@@ -143,7 +143,7 @@ def big_iface():
     return w, y, R.apply(y)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
 def test_exact_large_interface_block(torch_dev, big_iface, prec, tol):
     torch, dev = torch_dev
     from paper_1104_3349_gb300 import dd
@@ -157,6 +157,7 @@ def test_exact_large_interface_block(torch_dev, big_iface, prec, tol):
     x = xd.cpu().numpy()
     assert np.all(np.isfinite(x))
     err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+    print(f"EXACT 3340-row interface block, prec {prec}: apply relative error vs oracle {err:.3e}")
     assert err <= tol, (prec, err)
 
 
