@@ -23,6 +23,7 @@ _LIB_PATH = os.path.join(_HERE, "_dd_oracle.so")
 _lib = None
 
 EXACT, MSCE_INF, MSCN, MSCNR, LUM, IDENTITY = 0, 1, 2, 3, 4, -1
+OMSCN, OMSCNR, OLUM, MSCE = 6, 7, 8, 9
 STATUS = {0: "ok", 1: "invalid_arg", 2: "invalid_partition", 3: "singular_block", 4: "singular_schur",
           5: "not_converged", 6: "nonfinite", 8: "oom"}
 
@@ -49,6 +50,15 @@ def _load():
         lib.orc_setup.restype = ctypes.c_int
         lib.orc_setup.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, i32p, i32p, ctypes.c_int32,
                                   i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(vp)]
+        lib.orc_setup2.restype = ctypes.c_int
+        lib.orc_setup2.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, i32p, i32p, ctypes.c_int32,
+                                   i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, i32p, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.POINTER(vp)]
+        lib.orc_block_size.restype = ctypes.c_int32
+        lib.orc_block_size.argtypes = [vp, ctypes.c_int32]
+        lib.orc_overlaps.argtypes = [vp, i32p]
+        lib.orc_schur_dense.restype = ctypes.c_int
+        lib.orc_schur_dense.argtypes = [vp, f64p]
         lib.orc_free.argtypes = [vp]
         lib.orc_apply.restype = ctypes.c_int
         lib.orc_apply.argtypes = [vp, f64p, f64p]
@@ -132,7 +142,11 @@ def spmv(A, x):
 class OracleDD:
     """The preconditioner B of the paper for one kind, built on the CPU."""
 
-    def __init__(self, A, part, m, kind, perm=None, sz=64, agg_offsets=None, pivtol=1e-14, raise_on_error=True):
+    def __init__(self, A, part, m, kind, perm=None, sz=64, agg_offsets=None, pivtol=1e-14, raise_on_error=True,
+                 overlap=0, overlaps=None, radius=0):
+        """overlap / overlaps: the overlap widths of OMSCN, OMSCNR and OLUM (one
+        width for all aggregates, capped by the next aggregate's size, or one
+        per aggregate); radius: the path-length radius of MSCE."""
         lib = _load()
         self._lib = lib
         self.A = A
@@ -141,11 +155,12 @@ class OracleDD:
         perm_a = None if perm is None else np.ascontiguousarray(perm, np.int32)
         agg_a = None if agg_offsets is None else np.ascontiguousarray(agg_offsets, np.int32)
         nagg = 0 if agg_a is None else len(agg_a) - 1
+        ovl_a = None if overlaps is None else np.ascontiguousarray(overlaps, np.int32)
         h = ctypes.c_void_p()
-        rc = lib.orc_setup(A.n, _p(self._keep[0], ctypes.c_int32), _p(self._keep[1], ctypes.c_int32),
-                           _p(self._keep[2], ctypes.c_double), m, _p(self._keep[3], ctypes.c_int32),
-                           _p(perm_a, ctypes.c_int32), nagg, _p(agg_a, ctypes.c_int32), sz, kind, pivtol,
-                           ctypes.byref(h))
+        rc = lib.orc_setup2(A.n, _p(self._keep[0], ctypes.c_int32), _p(self._keep[1], ctypes.c_int32),
+                            _p(self._keep[2], ctypes.c_double), m, _p(self._keep[3], ctypes.c_int32),
+                            _p(perm_a, ctypes.c_int32), nagg, _p(agg_a, ctypes.c_int32), sz, kind, pivtol,
+                            _p(ovl_a, ctypes.c_int32), int(overlap), int(radius), ctypes.byref(h))
         self._h = h
         self.status = int(rc)
         self.bad_block = int(lib.orc_bad_block(h)) if h.value else -1
@@ -188,9 +203,22 @@ class OracleDD:
         self._lib.orc_bandwidths(self._h, _p(o, ctypes.c_int32))
         return o.reshape(self.m, 2)
 
+    def overlaps(self):
+        o = np.zeros(self.nagg, np.int32)
+        self._lib.orc_overlaps(self._h, _p(o, ctypes.c_int32))
+        return o
+
+    def schur_dense(self):
+        """The whole S_hat (n_G x n_G), blocks placed as the apply uses them."""
+        o = np.zeros((self.nG, self.nG))
+        if self._lib.orc_schur_dense(self._h, _p(o, ctypes.c_double)) != 0:
+            raise OracleError(1)
+        return o
+
     def schur_block(self, i):
-        a = self.agg_offsets()
-        p = int(a[i + 1] - a[i])
+        p = int(self._lib.orc_block_size(self._h, int(i)))
+        if p < 0:
+            raise IndexError(i)
         o = np.zeros((p, p))
         if self._lib.orc_schur_block(self._h, i, _p(o, ctypes.c_double)) != 0:
             raise IndexError(i)

@@ -29,6 +29,20 @@
  *     adjacent to the aggregate, so S_ii is the diagonal block of the exact
  *     Schur complement S = G - F D^-1 E (the block-Jacobi reading that
  *     closes Section 3.3).
+ *   - MSCE with a finite radius r: D_{r_i} holds the interior nodes within
+ *     path length r of the aggregate (first step through F or E, then
+ *     through the pattern of D), closed by the D-neighbours of every reached
+ *     node with a zero diagonal (a pressure-like node cut down to one
+ *     velocity coupling would make D_{r_i} singular).  r = 0 gives LUM.
+ *   - Overlapped aggregation (the Remark after eq. aggrV, Algorithm 1):
+ *     block i spans indices r_i .. r_{i+1} - 1 + w_i, with 0 <= w_i <=
+ *     p_{i+1} and w_k = 0 (the paper both bounds w_i by p_i and uses w =
+ *     sz in its tables; the extension stays inside the next aggregate).
+ *     OMSCN / OMSCNR / OLUM are MSCN / MSCNR / LUM on these blocks.  S_hat
+ *     is assembled by placing the blocks in aggregate order, a later block
+ *     overwriting the overlap; it is not block diagonal and is solved whole
+ *     (band LU with partial pivoting), as the Remark says the solve phase
+ *     loses its parallelism.
  *
  * Exact LU of every A_jj (Section 4: "exact triangular factors") with partial
  * pivoting, the pivot being the first row holding the largest magnitude; a
@@ -52,7 +66,10 @@ enum { ORC_OK = 0, ORC_INVALID_ARG = 1, ORC_INVALID_PARTITION = 2, ORC_SINGULAR_
        ORC_SINGULAR_SCHUR = 4, ORC_NOT_CONVERGED = 5, ORC_NONFINITE = 6, ORC_OOM = 8 };
 
 enum { ORC_EXACT = 0, ORC_MSCE_INF = 1, ORC_MSCN = 2, ORC_MSCNR = 3, ORC_LUM = 4,
-       ORC_IDENTITY = -1 };
+       ORC_OMSCN = 6, ORC_OMSCNR = 7, ORC_OLUM = 8, ORC_MSCE = 9, ORC_IDENTITY = -1 };
+
+/* overlapped kinds (Remark on overlapped aggregation, Algorithm 1) */
+static int is_overlapped(int kind) { return kind == ORC_OMSCN || kind == ORC_OMSCNR || kind == ORC_OLUM; }
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -232,6 +249,10 @@ typedef struct orc {
   orc_sp E, F, G;           /* E: interior x interface, F: interface x interior,
                                G: interface x interface (local indices) */
   orc_sp Et;                /* E transposed: interface x interior */
+  int32_t *ovl;             /* overlapped kinds: overlap width w_i of every aggregate */
+  int32_t radius;           /* MSCE: path-length radius r */
+  orc_band Shat;            /* overlapped kinds: the assembled S_hat (band, factored) */
+  double *Shat0;            /* its entries before the factorisation (band rows, unpivoted) */
   double **S;               /* S_hat blocks, row-major (kept unfactored for tests) */
   double **Slu;             /* their LU factors */
   int32_t **Spiv;
@@ -250,6 +271,7 @@ void orc_free(orc *h) {
   sp_free(&h->E); sp_free(&h->F); sp_free(&h->G); sp_free(&h->Et);
   if (h->S) for (int32_t i = 0; i < h->nagg; ++i) { free(h->S[i]); free(h->Slu[i]); free(h->Spiv[i]); }
   free(h->S); free(h->Slu); free(h->Spiv);
+  free(h->ovl); band_free(&h->Shat); free(h->Shat0);
   free(h->rowptr); free(h->ccol); free(h->cval);
   free(h);
 }
@@ -368,11 +390,12 @@ static int schur_msce(orc *h, int32_t i, double *S) {
 }
 
 /* MSCN / MSCNR (Algorithm 1): principal submatrices with the same local
- * index range [a0, a1) in D, E, F and G.
+ * index range [a0, a1) in D, E, F and G (the aggregate, or for OMSCN /
+ * OMSCNR the aggregate extended by its overlap).
  *   MSCN:  S_ii = G_ii - F_ii D_ii^-1 E_ii
  *   MSCNR: S_ii = G_ii - diag(F_ii D_ii^-1 E_ii 1)                          */
-static int schur_mscn(orc *h, int32_t i, double *S, int rowsum, double pivtol) {
-  int32_t a0 = h->agg[i], a1 = h->agg[i + 1], p = a1 - a0;
+static int schur_mscn(orc *h, int32_t a0, int32_t a1, double *S, int rowsum, double pivtol) {
+  int32_t p = a1 - a0;
   if (a1 > h->nI) return ORC_INVALID_ARG;
   double *Dii = (double *)calloc((size_t)p * p, sizeof(double));
   double *Eii = (double *)calloc((size_t)p * p, sizeof(double));
@@ -428,6 +451,139 @@ out:
   return rc;
 }
 
+/* Symmetrised pattern of D (the interior rows and columns of P^T C P):
+ * adjacency lists in CSR form over the interior numbering. */
+static int build_dadj(const orc *h, int32_t **ptr_out, int32_t **adj_out) {
+  int32_t nI = h->nI;
+  int32_t *cnt = (int32_t *)calloc((size_t)nI + 1, sizeof(int32_t));
+  if (!cnt) return ORC_OOM;
+  for (int32_t k = 0; k < nI; ++k) {
+    int32_t o = h->perm[k];
+    for (int32_t q = h->rowptr[o]; q < h->rowptr[o + 1]; ++q) {
+      int32_t j = h->pos[h->ccol[q]];
+      if (j < nI && j != k) { cnt[k + 1]++; cnt[j + 1]++; }
+    }
+  }
+  for (int32_t k = 0; k < nI; ++k) cnt[k + 1] += cnt[k];
+  int32_t *adj = (int32_t *)malloc(sizeof(int32_t) * ((size_t)cnt[nI] + 1));
+  int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nI + 1));
+  if (!adj || !fill) { free(cnt); free(adj); free(fill); return ORC_OOM; }
+  memcpy(fill, cnt, sizeof(int32_t) * (size_t)nI);
+  for (int32_t k = 0; k < nI; ++k) {
+    int32_t o = h->perm[k];
+    for (int32_t q = h->rowptr[o]; q < h->rowptr[o + 1]; ++q) {
+      int32_t j = h->pos[h->ccol[q]];
+      if (j < nI && j != k) { adj[fill[k]++] = j; adj[fill[j]++] = k; }
+    }
+  }
+  free(fill);
+  *ptr_out = cnt;
+  *adj_out = adj;
+  return ORC_OK;
+}
+
+/* value of P^T C P at (new row r, new column c), 0 if absent */
+static double c_at(const orc *h, int32_t r, int32_t c) {
+  double v = 0.0;
+  int32_t o = h->perm[r];
+  for (int32_t q = h->rowptr[o]; q < h->rowptr[o + 1]; ++q) if (h->pos[h->ccol[q]] == c) v += h->cval[q];
+  return v;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* MSCE with a finite radius r (Algorithm 1's mini Schur complement on edge
+ * connectivity): S_ii = G_pi - F_i D_ri^-1 E_i, where D_ri is the principal
+ * submatrix of D on the interior nodes reachable from the aggregate by a
+ * path of length <= r: the first step goes from an aggregate node to an
+ * interior node it is coupled with (an entry of F or E), the others run
+ * through the pattern of D.  Every reached node with a zero diagonal (a
+ * pressure-like node) brings all its neighbours in D, so that no row of
+ * D_ri is cut down to a single coupling.  r = 0: D_ri is empty and
+ * S_ii = G_ii (LUM); r large enough: the whole adjacent interiors, S_ii =
+ * S(R_i, R_i) (MSCE_INF). */
+static int schur_msce_r(orc *h, int32_t i, double *S, const int32_t *dptr, const int32_t *dadj,
+                        double pivtol) {
+  int32_t a0 = h->agg[i], a1 = h->agg[i + 1], p = a1 - a0, nI = h->nI;
+  for (int32_t r = 0; r < p; ++r)
+    for (int32_t c = 0; c < p; ++c) S[(int64_t)r * p + c] = sp_get(&h->G, a0 + r, a0 + c);
+  if (h->radius <= 0 || nI == 0) return ORC_OK;
+  int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)nI);
+  int32_t *set = (int32_t *)malloc(sizeof(int32_t) * (size_t)nI);
+  int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)nI);
+  if (!dist || !set || !loc) { free(dist); free(set); free(loc); return ORC_OOM; }
+  for (int32_t k = 0; k < nI; ++k) { dist[k] = -1; loc[k] = -1; }
+  int32_t d = 0;
+  /* level 1: interior nodes coupled with the aggregate through F or E */
+  for (int32_t g = a0; g < a1; ++g) {
+    for (int32_t q = h->F.ptr[g]; q < h->F.ptr[g + 1]; ++q) {
+      int32_t j = h->F.col[q];
+      if (h->F.val[q] != 0.0 && dist[j] < 0) { dist[j] = 1; set[d++] = j; }
+    }
+    for (int32_t q = h->Et.ptr[g]; q < h->Et.ptr[g + 1]; ++q) {
+      int32_t j = h->Et.col[q];
+      if (h->Et.val[q] != 0.0 && dist[j] < 0) { dist[j] = 1; set[d++] = j; }
+    }
+  }
+  /* levels 2 .. r through the pattern of D (breadth first) */
+  for (int32_t head = 0; head < d; ++head) {
+    int32_t k = set[head];
+    if (dist[k] >= h->radius) continue;
+    for (int32_t q = dptr[k]; q < dptr[k + 1]; ++q) {
+      int32_t j = dadj[q];
+      if (dist[j] < 0) { dist[j] = dist[k] + 1; set[d++] = j; }
+    }
+  }
+  /* closure: a reached pressure-like node brings its neighbours */
+  int32_t d0 = d;
+  for (int32_t q0 = 0; q0 < d0; ++q0) {
+    int32_t k = set[q0];
+    if (c_at(h, k, k) != 0.0) continue;
+    for (int32_t q = dptr[k]; q < dptr[k + 1]; ++q) {
+      int32_t j = dadj[q];
+      if (dist[j] < 0) { dist[j] = h->radius + 1; set[d++] = j; }
+    }
+  }
+  qsort(set, (size_t)d, sizeof(int32_t), cmp_i32);
+  for (int32_t q = 0; q < d; ++q) loc[set[q]] = q;
+  double *Dr = (double *)calloc((size_t)d * d + 1, sizeof(double));
+  double *Er = (double *)calloc((size_t)d * p + 1, sizeof(double));
+  int32_t *piv = (int32_t *)calloc((size_t)d + 1, sizeof(int32_t));
+  double *x = (double *)calloc((size_t)d + 1, sizeof(double));
+  int rc = ORC_OK;
+  if (!Dr || !Er || !piv || !x) { rc = ORC_OOM; goto out; }
+  for (int32_t q = 0; q < d; ++q) {
+    int32_t k = set[q], o = h->perm[k];
+    for (int32_t e = h->rowptr[o]; e < h->rowptr[o + 1]; ++e) {
+      int32_t c = h->pos[h->ccol[e]];
+      if (c < nI && loc[c] >= 0) Dr[(int64_t)q * d + loc[c]] += h->cval[e];
+    }
+    for (int32_t e = h->E.ptr[k]; e < h->E.ptr[k + 1]; ++e) {
+      int32_t c = h->E.col[e];
+      if (c >= a0 && c < a1) Er[(int64_t)q * p + (c - a0)] += h->E.val[e];
+    }
+  }
+  if (d > 0 && orc_dense_lu(d, Dr, piv, pivtol)) { rc = ORC_SINGULAR_SCHUR; goto out; }
+  for (int32_t c = 0; c < p && d > 0; ++c) {
+    for (int32_t q = 0; q < d; ++q) x[q] = Er[(int64_t)q * p + c];
+    orc_dense_lu_solve(d, Dr, piv, x);
+    for (int32_t r = 0; r < p; ++r) {
+      double sacc = 0.0;
+      for (int32_t q = h->F.ptr[a0 + r]; q < h->F.ptr[a0 + r + 1]; ++q) {
+        int32_t j = h->F.col[q];
+        if (loc[j] >= 0) sacc += h->F.val[q] * x[loc[j]];
+      }
+      S[(int64_t)r * p + c] -= sacc;
+    }
+  }
+out:
+  free(dist); free(set); free(loc); free(Dr); free(Er); free(piv); free(x);
+  return rc;
+}
+
 /*
  * Build B for the given approximation kind (Algorithm 1).
  *   C          n x n CSR, original numbering (copied)
@@ -438,12 +594,14 @@ out:
  *              NULL for consecutive chunks of sz (eq. aggrV)
  *   kind       0 EXACT, 1 MSCE_INF, 2 MSCN, 3 MSCNR, 4 LUM, -1 identity
  */
-int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
-              const int32_t *part, const int32_t *perm, int32_t nagg, const int32_t *agg_off,
-              int32_t sz, int32_t kind, double pivtol, orc **out) {
+int orc_setup2(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
+               const int32_t *part, const int32_t *perm, int32_t nagg, const int32_t *agg_off,
+               int32_t sz, int32_t kind, double pivtol, const int32_t *ovl, int32_t ovl_w, int32_t radius,
+               orc **out) {
   *out = NULL;
   if (n <= 0 || m <= 0 || !rowptr || !col || !val || !part) return ORC_INVALID_ARG;
-  if (kind < -1 || kind > 4) return ORC_INVALID_ARG;
+  if (kind < -1 || kind > 9 || kind == 5) return ORC_INVALID_ARG;
+  if (kind == ORC_MSCE && radius < 0) return ORC_INVALID_ARG;
   if (rowptr[0] != 0) return ORC_INVALID_ARG;
   for (int32_t i = 0; i < n; ++i) {
     if (rowptr[i + 1] < rowptr[i]) return ORC_INVALID_ARG;
@@ -462,7 +620,7 @@ int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double
     }
   orc *h = (orc *)calloc(1, sizeof(orc));
   if (!h) return ORC_OOM;
-  h->n = n; h->m = m; h->kind = kind; h->bad_block = -1;
+  h->n = n; h->m = m; h->kind = kind; h->bad_block = -1; h->radius = radius;
   int rc = ORC_OK;
   h->rowptr = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
   h->ccol = (int32_t *)malloc(sizeof(int32_t) * ((size_t)rowptr[n] + 1));
@@ -519,6 +677,19 @@ int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double
   }
   if (h->agg[0] != 0 || h->agg[nagg] != h->nG) { rc = ORC_INVALID_ARG; goto fail; }
   for (int32_t i = 0; i < nagg; ++i) if (h->agg[i + 1] <= h->agg[i]) { rc = ORC_INVALID_ARG; goto fail; }
+  /* overlap widths (Algorithm 1): aggregate i is extended by w_i indices into
+   * aggregate i + 1, 0 <= w_i <= p_{i+1}, and w_k = 0; given per aggregate,
+   * or min(ovl_w, p_{i+1}) */
+  h->ovl = (int32_t *)calloc((size_t)nagg + 1, sizeof(int32_t));
+  if (!h->ovl) { rc = ORC_OOM; goto fail; }
+  if (is_overlapped(kind))
+    for (int32_t i = 0; i + 1 < nagg; ++i) {
+      int32_t pn = h->agg[i + 2] - h->agg[i + 1];
+      int32_t w = ovl ? ovl[i] : (ovl_w < pn ? ovl_w : pn);
+      if (w < 0 || w > pn) { rc = ORC_INVALID_ARG; goto fail; }
+      h->ovl[i] = w;
+    }
+  if (is_overlapped(kind) && ovl && nagg > 0 && ovl[nagg - 1] != 0) { rc = ORC_INVALID_ARG; goto fail; }
   /* blocks of P^T C P = [D E; F G] */
   if (extract_sp(h, 0, h->nI, h->nI, n, &h->E) || extract_sp(h, h->nI, n, 0, h->nI, &h->F) ||
       extract_sp(h, h->nI, n, h->nI, n, &h->G)) { rc = ORC_OOM; goto fail; }
@@ -554,6 +725,8 @@ int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double
     if (bad >= 0) { h->bad_block = bad; rc = brc; goto fail_keep; }
   }
   /* mini Schur complements, aggregates independent */
+  int32_t *dptr = NULL, *dadj = NULL;
+  if (kind == ORC_MSCE && (rc = build_dadj(h, &dptr, &dadj)) != ORC_OK) goto fail;
   h->S = (double **)calloc((size_t)nagg + 1, sizeof(double *));
   h->Slu = (double **)calloc((size_t)nagg + 1, sizeof(double *));
   h->Spiv = (int32_t **)calloc((size_t)nagg + 1, sizeof(int32_t *));
@@ -562,20 +735,23 @@ int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double
     int32_t bad = -1, brc = ORC_OK;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t i = 0; i < nagg; ++i) {
-      int32_t p = h->agg[i + 1] - h->agg[i];
+      /* the block's index range: the aggregate, extended by its overlap */
+      int32_t a0 = h->agg[i], p = h->agg[i + 1] - a0 + h->ovl[i];
       int r = ORC_OK;
       h->S[i] = (double *)calloc((size_t)p * p, sizeof(double));
       h->Slu[i] = (double *)calloc((size_t)p * p, sizeof(double));
       h->Spiv[i] = (int32_t *)calloc((size_t)p, sizeof(int32_t));
       if (!h->S[i] || !h->Slu[i] || !h->Spiv[i]) r = ORC_OOM;
       else if (kind == ORC_EXACT || kind == ORC_MSCE_INF) r = schur_msce(h, i, h->S[i]);
-      else if (kind == ORC_MSCN) r = schur_mscn(h, i, h->S[i], 0, pivtol);
-      else if (kind == ORC_MSCNR) r = schur_mscn(h, i, h->S[i], 1, pivtol);
+      else if (kind == ORC_MSCN || kind == ORC_OMSCN) r = schur_mscn(h, a0, a0 + p, h->S[i], 0, pivtol);
+      else if (kind == ORC_MSCNR || kind == ORC_OMSCNR) r = schur_mscn(h, a0, a0 + p, h->S[i], 1, pivtol);
+      else if (kind == ORC_MSCE) r = schur_msce_r(h, i, h->S[i], dptr, dadj, pivtol);
       else
         for (int32_t a = 0; a < p; ++a)
           for (int32_t c = 0; c < p; ++c)
-            h->S[i][(int64_t)a * p + c] = sp_get(&h->G, h->agg[i] + a, h->agg[i] + c);
-      if (r == ORC_OK) {
+            h->S[i][(int64_t)a * p + c] = sp_get(&h->G, a0 + a, a0 + c);
+      /* overlapped kinds: only the assembled S_hat is factored (below) */
+      if (r == ORC_OK && !is_overlapped(kind)) {
         memcpy(h->Slu[i], h->S[i], sizeof(double) * (size_t)p * p);
         if (orc_dense_lu(p, h->Slu[i], h->Spiv[i], pivtol)) r = ORC_SINGULAR_SCHUR;
       }
@@ -584,7 +760,31 @@ int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double
         { if (bad < 0 || i < bad) { bad = i; brc = r; } }
       }
     }
+    free(dptr);
+    free(dadj);
     if (bad >= 0) { h->bad_block = bad; rc = brc; goto fail_keep; }
+  }
+  if (is_overlapped(kind) && nagg > 0) {
+    /* S_hat with overlapping blocks (the Remark on overlapped aggregation):
+     * every S_ii is placed at its index range, aggregate after aggregate,
+     * a later block overwriting the overlap.  S_hat is then a band matrix,
+     * no longer block diagonal, and is factored whole. */
+    int32_t bw = 0;
+    for (int32_t i = 0; i < nagg; ++i) {
+      int32_t q = h->agg[i + 1] - h->agg[i] + h->ovl[i];
+      if (q - 1 > bw) bw = q - 1;
+    }
+    if (band_alloc(&h->Shat, h->nG, bw, bw)) { rc = ORC_OOM; goto fail; }
+    for (int32_t i = 0; i < nagg; ++i) {
+      int32_t a0 = h->agg[i], q = h->agg[i + 1] - a0 + h->ovl[i];
+      for (int32_t r = 0; r < q; ++r)
+        for (int32_t c = 0; c < q; ++c) *band_at(&h->Shat, a0 + r, a0 + c) = h->S[i][(int64_t)r * q + c];
+    }
+    size_t nb = (size_t)h->nG * h->Shat.wd;
+    h->Shat0 = (double *)malloc(sizeof(double) * (nb + 1));
+    if (!h->Shat0) { rc = ORC_OOM; goto fail; }
+    memcpy(h->Shat0, h->Shat.r, sizeof(double) * nb);
+    if (band_factor(&h->Shat, pivtol)) { h->bad_block = nagg; rc = ORC_SINGULAR_SCHUR; goto fail_keep; }
   }
   *out = h;
   return ORC_OK;
@@ -598,7 +798,44 @@ fail:
   return rc;
 }
 
+int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
+              const int32_t *part, const int32_t *perm, int32_t nagg, const int32_t *agg_off,
+              int32_t sz, int32_t kind, double pivtol, orc **out) {
+  return orc_setup2(n, rowptr, col, val, m, part, perm, nagg, agg_off, sz, kind, pivtol, NULL, 0, 0, out);
+}
+
 int32_t orc_bad_block(const orc *h) { return h ? h->bad_block : -1; }
+
+/* rows of S_hat block i (the aggregate plus its overlap) */
+int32_t orc_block_size(const orc *h, int32_t i) {
+  if (!h || i < 0 || i >= h->nagg) return -1;
+  return h->agg[i + 1] - h->agg[i] + (h->ovl ? h->ovl[i] : 0);
+}
+
+/* the overlap widths w_i (nagg entries) */
+void orc_overlaps(const orc *h, int32_t *o) {
+  for (int32_t i = 0; i < h->nagg; ++i) o[i] = h->ovl ? h->ovl[i] : 0;
+}
+
+/* S_hat as a dense nG x nG row-major matrix (before any factorisation) */
+int orc_schur_dense(const orc *h, double *o) {
+  if (!h->S || h->kind == -2) return -1;
+  int32_t nG = h->nG;
+  memset(o, 0, sizeof(double) * (size_t)nG * nG);
+  if (is_overlapped(h->kind)) {
+    int32_t kl = h->Shat.kl, ku = h->Shat.ku, wd = h->Shat.wd;
+    for (int32_t r = 0; r < nG; ++r)
+      for (int32_t c = r - kl; c <= r + ku; ++c)
+        if (c >= 0 && c < nG) o[(int64_t)r * nG + c] = h->Shat0[(int64_t)r * wd + (c - r + kl)];
+    return 0;
+  }
+  for (int32_t i = 0; i < h->nagg; ++i) {
+    int32_t a0 = h->agg[i], p = h->agg[i + 1] - a0;
+    for (int32_t r = 0; r < p; ++r)
+      for (int32_t c = 0; c < p; ++c) o[(int64_t)(a0 + r) * nG + a0 + c] = h->S[i][(int64_t)r * p + c];
+  }
+  return 0;
+}
 
 /* n, m, nI, nG, nagg, kind */
 void orc_sizes(const orc *h, int64_t *o) {
@@ -635,7 +872,7 @@ int orc_replace_block(orc *h, int32_t i, const double *blk, double pivtol) {
 /* copy S_hat block i (row-major, unfactored) */
 int orc_schur_block(const orc *h, int32_t i, double *o) {
   if (!h->S || i < 0 || i >= h->nagg || !h->S[i]) return -1;
-  int32_t p = h->agg[i + 1] - h->agg[i];
+  int32_t p = orc_block_size(h, i);
   memcpy(o, h->S[i], sizeof(double) * (size_t)p * p);
   return 0;
 }
@@ -662,9 +899,13 @@ int orc_apply(const orc *h, const double *y, double *x) {
     for (int32_t k = h->F.ptr[r]; k < h->F.ptr[r + 1]; ++k) s += h->F.val[k] * z[h->F.col[k]];
     t[r] -= s;
   }
+  if (is_overlapped(h->kind)) {
+    if (nG > 0) band_solve(&h->Shat, t); /* the assembled S_hat: one band solve */
+  } else {
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int32_t i = 0; i < h->nagg; ++i)
-    orc_dense_lu_solve(h->agg[i + 1] - h->agg[i], h->Slu[i], h->Spiv[i], t + h->agg[i]);
+    for (int32_t i = 0; i < h->nagg; ++i)
+      orc_dense_lu_solve(h->agg[i + 1] - h->agg[i], h->Slu[i], h->Spiv[i], t + h->agg[i]);
+  }
   /* backward sweep: x2 = z2, x1 = z1 - D^-1 (E x2) */
   for (int32_t r = 0; r < nI; ++r) {
     double s = 0.0;

@@ -396,3 +396,156 @@ def test_restart_cycles_match_gmres_definition(kind, restart, maxit):
     x = _gmres_by_definition(C, _dense_Binv(A, part, perm, agg, kind), b, restart, maxit)
     assert np.linalg.norm(r["x"] - x) <= 1e-8 * np.linalg.norm(x)
     assert abs(r["relres"] - np.linalg.norm(b - C @ x) / np.linalg.norm(b)) <= 1e-8
+
+
+# --------------------------------------------------------------------------
+# Overlapped aggregates (OMSCN, OMSCNR, OLUM) and MSCE with a finite radius
+# --------------------------------------------------------------------------
+PLAIN_OF = {O.OMSCN: O.MSCN, O.OMSCNR: O.MSCNR, O.OLUM: O.LUM}
+
+
+def _brute_overlapped(kind, D, E, F, G, agg, w):
+    """S_hat of an overlapped kind from its definition: block i is MSCN /
+    MSCNR / LUM on indices agg[i] .. agg[i+1]-1+w[i] (Algorithm 1), placed in
+    aggregate order with a later block overwriting the overlap."""
+    nG = G.shape[0]
+    Sh = np.zeros((nG, nG))
+    blocks = []
+    for i in range(len(agg) - 1):
+        a, e = agg[i], agg[i + 1] + w[i]
+        Dii, Eii, Fii, Gii = D[a:e, a:e], E[a:e, a:e], F[a:e, a:e], G[a:e, a:e]
+        if kind == O.OLUM or not Eii.any() or not Fii.any():
+            S = Gii.copy()
+        elif kind == O.OMSCN:
+            S = Gii - Fii @ np.linalg.solve(Dii, Eii)
+        else:
+            S = Gii - np.diag(Fii @ np.linalg.solve(Dii, Eii) @ np.ones(e - a))
+        blocks.append(S)
+        Sh[a:e, a:e] = S
+    return Sh, blocks
+
+
+@pytest.mark.parametrize("kind", [O.OMSCN, O.OMSCNR, O.OLUM])
+def test_zero_overlap_reproduces_the_plain_kind(kind):
+    w = W.cavity32()
+    P = O.OracleDD(w.A, w.part, w.m, kind, perm=w.perm, agg_offsets=w.agg, overlap=0)
+    Q = O.OracleDD(w.A, w.part, w.m, PLAIN_OF[kind], perm=w.perm, agg_offsets=w.agg)
+    y = W.uniform(1, w.A.n)
+    x, xq = P.apply(y), Q.apply(y)
+    assert np.linalg.norm(x - xq) <= 1e-12 * np.linalg.norm(xq)
+
+
+@pytest.mark.parametrize("kind", [O.OMSCN, O.OMSCNR, O.OLUM])
+@pytest.mark.parametrize("ov", [3, 7])
+def test_overlapped_schur_equals_brute_force(kind, ov):
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, kind, perm=perm, agg_offsets=agg, overlap=ov)
+    w = P.overlaps()
+    assert w[-1] == 0 and all(w[i] == min(ov, agg[i + 2] - agg[i + 1]) for i in range(len(agg) - 2))
+    Sh, blocks = _brute_overlapped(kind, D, E, F, G, agg, w)
+    for i, Sb in enumerate(blocks):
+        assert np.abs(P.schur_block(i) - Sb).max() <= 1e-11 * max(1.0, np.abs(Sb).max()), (kind, i)
+    assert np.abs(P.schur_dense() - Sh).max() <= 1e-11 * max(1.0, np.abs(Sh).max())
+
+
+def test_overlapped_schur_is_not_block_diagonal():
+    """The Remark on overlapped aggregation: S_hat is no longer block diagonal
+    over the aggregates; its entries stay inside the extended blocks."""
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    P = O.OracleDD(A, part, 4, O.OMSCN, perm=perm, agg_offsets=agg, overlap=5)
+    Sh, w = P.schur_dense(), P.overlaps()
+    nG = Sh.shape[0]
+    in_agg = np.zeros((nG, nG), bool)
+    in_ext = np.zeros((nG, nG), bool)
+    for i in range(len(agg) - 1):
+        in_agg[agg[i]:agg[i + 1], agg[i]:agg[i + 1]] = True
+        in_ext[agg[i]:agg[i + 1] + w[i], agg[i]:agg[i + 1] + w[i]] = True
+    assert np.abs(Sh[~in_agg]).max() > 0
+    assert np.abs(Sh[~in_ext]).max() == 0
+
+
+def test_olum_takes_g_on_the_extended_blocks():
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, O.OLUM, perm=perm, agg_offsets=agg, overlap=6)
+    w = P.overlaps()
+    mask = np.zeros(G.shape, bool)
+    for i in range(len(agg) - 1):
+        mask[agg[i]:agg[i + 1] + w[i], agg[i]:agg[i + 1] + w[i]] = True
+    assert np.array_equal(P.schur_dense(), np.where(mask, G, 0.0))
+
+
+@pytest.mark.parametrize("kind", [O.OMSCN, O.OLUM])
+def test_overlapped_apply_and_spectrum(kind):
+    """The apply inverts B = [D E; F, F D^-1 E + S_hat] with the assembled
+    S_hat (Lemma 1), and eig(C B^-1) = {1 (n_I times)} U eig(S S_hat^-1)."""
+    A, part, perm, agg = _small(n=8, m=4, sz=14)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, kind, perm=perm, agg_offsets=agg, overlap=5)
+    Sh, _ = _brute_overlapped(kind, D, E, F, G, agg, P.overlaps())
+    Bp = Cp.copy()
+    Bp[nI:, nI:] = F @ np.linalg.solve(D, E) + Sh
+    y = W.uniform(1, A.n)
+    ref = np.zeros(A.n)
+    ref[perm] = np.linalg.solve(Bp, y[perm])
+    assert np.linalg.norm(P.apply(y) - ref) <= 1e-10 * np.linalg.norm(ref)
+    lam = np.linalg.eigvals(Cp @ np.linalg.inv(Bp))
+    mu = np.linalg.eigvals(_brute_S(D, E, F, G) @ np.linalg.inv(Sh))
+    expect = np.concatenate([np.ones(nI), mu])
+    for v in expect:
+        k = np.argmin(np.abs(lam - v))
+        assert abs(lam[k] - v) <= 1e-6 * max(1.0, abs(v))
+        lam = np.delete(lam, k)
+
+
+def test_overlap_beyond_the_next_aggregate_is_refused():
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    bad = np.zeros(len(agg) - 1, np.int32)
+    bad[0] = agg[2] - agg[1] + 1
+    with pytest.raises(O.OracleError) as e:
+        O.OracleDD(A, part, 4, O.OMSCN, perm=perm, agg_offsets=agg, overlaps=bad)
+    assert e.value.status == 1
+
+
+def _reach_set(Cp, nI, a, e, r):
+    """Interior nodes within path length r of the aggregate [a, e), by
+    boolean matrix powers of the interior pattern, closed by the neighbours
+    of zero-diagonal nodes (the reading of D_r for MSCE)."""
+    Dpat = (Cp[:nI, :nI] != 0) | (Cp[:nI, :nI] != 0).T
+    np.fill_diagonal(Dpat, False)
+    seed = ((Cp[nI + a:nI + e, :nI] != 0).any(axis=0)) | ((Cp[:nI, nI + a:nI + e] != 0).any(axis=1))
+    reach = seed.copy()
+    frontier = seed.copy()
+    for _ in range(r - 1):
+        frontier = (Dpat[frontier].any(axis=0)) & ~reach
+        reach |= frontier
+    zero_diag = np.diag(Cp[:nI, :nI]) == 0
+    closure = Dpat[reach & zero_diag].any(axis=0) if (reach & zero_diag).any() else np.zeros(nI, bool)
+    return np.nonzero(reach | closure)[0]
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_msce_radius_blocks_equal_brute_force(r):
+    A, part, perm, agg = _small(n=10, m=4, sz=12)
+    Cp, nI, D, E, F, G = _perm_blocks(A, part, perm)
+    P = O.OracleDD(A, part, 4, O.MSCE, perm=perm, agg_offsets=agg, radius=r)
+    for i in range(len(agg) - 1):
+        a, e = agg[i], agg[i + 1]
+        idx = _reach_set(Cp, nI, a, e, r)
+        Sb = G[a:e, a:e] - F[a:e][:, idx] @ np.linalg.solve(D[np.ix_(idx, idx)], E[idx][:, a:e])
+        assert np.abs(P.schur_block(i) - Sb).max() <= 1e-11 * max(1.0, np.abs(Sb).max()), (r, i)
+
+
+def test_msce_radius_limits_are_lum_and_msce_inf():
+    """r = 0 keeps no interior node (LUM); a radius beyond every interior's
+    diameter reaches the whole adjacent interiors (MSCE_INF)."""
+    w = W.cavity32()
+    P0 = O.OracleDD(w.A, w.part, w.m, O.MSCE, perm=w.perm, agg_offsets=w.agg, radius=0)
+    PL = O.OracleDD(w.A, w.part, w.m, O.LUM, perm=w.perm, agg_offsets=w.agg)
+    Pr = O.OracleDD(w.A, w.part, w.m, O.MSCE, perm=w.perm, agg_offsets=w.agg, radius=10 ** 6)
+    PI = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=w.agg)
+    for i in range(len(w.agg) - 1):
+        assert np.array_equal(P0.schur_block(i), PL.schur_block(i))
+        Si = PI.schur_block(i)
+        assert np.abs(Pr.schur_block(i) - Si).max() <= 1e-12 * np.abs(Si).max()
