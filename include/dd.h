@@ -40,7 +40,10 @@ typedef enum {
   DD_ERR_NONFINITE = 6,         /* NaN/Inf in the input or in a residual       */
   DD_ERR_TIMEOUT = 7,           /* a bounded device wait gave up               */
   DD_ERR_OOM = 8,               /* device or host allocation failed            */
-  DD_ERR_CUDA = 9               /* a CUDA runtime call failed                  */
+  DD_ERR_CUDA = 9,              /* a CUDA runtime call failed                  */
+  DD_ERR_CHECK = 10             /* a device check of the DD_CHECKED build (an
+                                   index, alignment or size out of range)
+                                   failed; the access was skipped             */
 } dd_status;
 
 /* Approximation of the interface Schur complement S = G - F D^-1 E
@@ -55,10 +58,25 @@ typedef enum {
                       local index range (Algorithm 1, MSCN)                    */
   DD_MSCNR = 3,    /* G_ii - diag(F_ii D_ii^-1 E_ii 1) (Algorithm 1, MSCNR)     */
   DD_LUM = 4,      /* G_ii (Definition of LUM)                                  */
-  DD_LEARNED = 5   /* G_ii + a learned correction on the pattern of G_ii and of
+  DD_LEARNED = 5,  /* G_ii + a learned correction on the pattern of G_ii and of
                       (F E)(R_i, R_i); an aggregate whose learned block fails
                       the pivot test takes its MSCE_INF block instead.  Not in
                       the paper: an extension of LUM (see dd_mlp_*)           */
+  /* Overlapped aggregation (the Remark after eq. aggrV; Algorithm 1): block
+   * i spans interface indices r_i .. r_{i+1} - 1 + w_i, w_i = min(opts.overlap,
+   * p_{i+1}) and w_k = 0.  S_hat is assembled by placing the blocks in
+   * aggregate order, a later block overwriting the overlap, so it is not
+   * block diagonal; it is inverted whole (n_G <= 12288).  Not for batches. */
+  DD_OMSCN = 6,    /* MSCN on the overlapped blocks                             */
+  DD_OMSCNR = 7,   /* MSCNR on the overlapped blocks                            */
+  DD_OLUM = 8,     /* G on the overlapped blocks                                */
+  DD_MSCE = 9      /* MSCE with a finite radius r = opts.radius (Algorithm 1,
+                      mini Schur complements on edge connectivity):
+                      S_ii = G_ii - F_i D_r^-1 E_i with D_r the interior nodes
+                      within path length r of the aggregate (first step
+                      through F or E, then through the pattern of D), closed
+                      by the D-neighbours of every zero-diagonal node.  r = 0
+                      gives LUM; r beyond the interiors gives MSCE_INF      */
 } dd_approx;
 
 typedef enum {
@@ -108,9 +126,14 @@ typedef struct {
                          every Arnoldi step with CUDA events (dd_stats
                          krylov_steps, cgs2_ms, cgs2_fma, spmv_ms); ignored
                          with use_graph; 0: no events                        */
-  int32_t reserved;
+  int32_t sweep_cluster;/* CTAs per subdomain of the apply's sweeps: 2 splits
+                         every tile step over a 2-CTA cluster (half the tile
+                         bytes through each SM), 1 one CTA; 0 chooses 1, or
+                         with autotune the faster of the two                 */
   const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
                               (format under dd_mlp_*); ignored otherwise       */
+  int32_t overlap;    /* DD_OMSCN / DD_OMSCNR / DD_OLUM: overlap width w >= 0   */
+  int32_t radius;     /* DD_MSCE: path-length radius r >= 0                     */
 } dd_opts;
 
 typedef struct {
@@ -155,6 +178,8 @@ typedef struct {
                                 (both passes' dots and updates and the norm:
                                 (4 (j+1) + 2) n at step j)                       */
   double spmv_ms;            /* device time of the SpMV w = C z                  */
+  int32_t sweep_cluster;     /* CTAs per subdomain of the sweeps (1 or 2)        */
+  int32_t msce_nodes_max;    /* DD_MSCE: largest interior node set D_r           */
 } dd_stats;
 
 /*

@@ -40,6 +40,8 @@ struct DDHandle {
   int tb = DD_NB;              // columns of a sweep tile (DD_NB or DD_TB_WIDE)
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
   uint32_t first_wait = 0xffffffffu;  // test hook: polls of each sweep CTA's first wait
+  int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1 or 2
+  int overlap = 0, radius = 0; // opts.overlap (overlapped kinds), opts.radius (DD_MSCE)
   std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
   std::vector<TileMeta> h_tm;
   size_t max_tile = 0;           // bytes of the largest packed tile
@@ -326,7 +328,7 @@ dd_status build_aggregates(DDHandle *h, const dd_partition *pt, dd_approx kind, 
   if (hb.agg.front() != 0 || hb.agg.back() != nG) { h->err = "aggregate offsets must run from 0 to n_G"; return DD_ERR_INVALID_ARG; }
   for (size_t i = 0; i + 1 < hb.agg.size(); ++i)
     if (hb.agg[i + 1] <= hb.agg[i]) { h->err = "aggregate offsets must increase"; return DD_ERR_INVALID_ARG; }
-  if ((kind == DD_MSCN || kind == DD_MSCNR) && hb.agg.back() > h->nI) {
+  if ((kind == DD_MSCN || kind == DD_MSCNR || kind == DD_OMSCN || kind == DD_OMSCNR) && hb.agg.back() > h->nI) {
     h->err = "MSCN needs n_interior >= n_interface (same local index ranges)";
     return DD_ERR_INVALID_ARG;
   }
@@ -413,7 +415,7 @@ namespace {
 // one subdomain whose packed bytes fit a stage (a larger tile is a job of
 // its own); forward jobs ascend, backward jobs descend.
 void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, size_t stage, size_t es,
-                int tb, std::vector<SweepJob> &jobs) {
+                int tb, int cl, std::vector<SweepJob> &jobs) {
   jobs.clear();
   for (BandInfo &b : info) {
     b.jf0 = (int32_t)jobs.size();
@@ -422,7 +424,8 @@ void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, si
       int hi = lo;
       while (hi < b.nst) {
         const TileMeta &q = tm[b.tile0 + hi];
-        const size_t nb = (size_t)q.wl * tb * es + (size_t)round4(q.wl) * 4;
+        // the largest slice of a cluster's CTAs (rank 0's forward rows)
+        const size_t nb = (size_t)fwd_split(q.wl, 1, cl) * tb * es + (size_t)round4(q.wl) * 4;
         if (hi > lo && bytes + nb > stage) break;
         bytes += nb;
         ++hi;
@@ -437,7 +440,7 @@ void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, si
       int lo = hi;
       while (lo > 0) {
         const TileMeta &q = tm[b.tile0 + lo - 1];
-        const size_t nb = (size_t)tb * q.wu * es;
+        const size_t nb = (size_t)(tb / cl) * q.wu * es;
         if (lo < hi && bytes + nb > stage) break;
         bytes += nb;
         --lo;
@@ -482,25 +485,52 @@ int sm_count() {
   return sms;
 }
 
+// CTAs per subdomain of the sweeps: the option if given, else 2 (a cluster
+// splitting every tile step) when the clusters of all subdomains can be
+// resident at once on half the SMs or fewer, else 1.
+// The option if given, else 1.  Measured on the 256x256 workload, the
+// 2-CTA cluster sweep is slower in both precisions (FP32 133.5 against
+// 100.8 us per interior solve, FP64 432.8 against 404.1 us): a step's
+// exchange and cluster barrier cost more than halving the shared-memory
+// traffic, or the FP64 work, of each SM saves.  The autotuner still tries
+// both.
+template <typename T>
+int choose_cluster(const DDHandle *h, size_t stage) {
+  (void)stage;
+  return (h->sweep_cl_opt == 1 || h->sweep_cl_opt == 2) ? h->sweep_cl_opt : 1;
+}
+
 // The sweep plan for one stage size: the job table, and a persistent LPT
 // schedule when the subdomains outnumber the CTAs that fit on the device.
 template <typename T>
-dd_status set_sweep_plan(DDHandle *h, size_t stage) {
+dd_status set_sweep_plan(DDHandle *h, size_t stage, int cl) {
+  if (cl > 1) {
+    // the exchange buffers take room: shrink the stage to what two stages
+    // leave, as long as the largest slice of a tile still fits
+    const size_t smax = band_sweep_max_stage(h->max_n, h->max_kl, h->max_ku2, sizeof(T), h->tb, cl);
+    size_t slice = 0;
+    for (const TileMeta &q : h->h_tm)
+      slice = std::max({slice, (size_t)fwd_split(q.wl, 1, cl) * h->tb * sizeof(T) + (size_t)round4(q.wl) * 4,
+                        (size_t)(h->tb / cl) * q.wu * sizeof(T)});
+    slice = (slice + 127) & ~(size_t)127;
+    if (stage > smax && slice <= smax) stage = smax;
+  }
   std::vector<SweepJob> jobs;
-  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), h->tb, jobs);
+  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), h->tb, cl, jobs);
   const int m = h->m;
   if (!h->jobs) TRY(dalloc(h, &h->jobs, 2 * std::max<size_t>(h->h_tm.size(), 1)));
   if (!jobs.empty())
     CK(cudaMemcpyAsync(h->jobs, jobs.data(), sizeof(SweepJob) * jobs.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_info, h->h_info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, h->stream));
   h->plan.stage_bytes = (uint32_t)stage;
-  h->plan.threads = 8 * h->tb;
-  const int occ = band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, h->plan.threads, h->plan.stage_bytes);
-  if (occ <= 0) {
+  h->plan.cl = cl;
+  h->plan.threads = 8 * h->tb / cl;
+  const int slots = band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, h->plan.stage_bytes);
+  if (slots <= 0) {
     h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
     return DD_ERR_INVALID_ARG;
   }
-  const int slots = occ * sm_count();
+  h->stats.sweep_cluster = cl;
   h->stats.sweep_slots = slots;
   h->stats.stage_bytes = (int32_t)stage;
   if (m > slots) {
@@ -525,12 +555,12 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage) {
     CK(cudaMemcpyAsync(h->sweep_off, off.data(), sizeof(int32_t) * (slots + 1), cudaMemcpyHostToDevice, h->stream));
     // pageable sources: make the copies complete before the vectors go
     CK(cudaStreamSynchronize(h->stream));
-    h->plan.grid = slots;
+    h->plan.grid = slots * cl;
     h->plan.sched = h->sweep_sched;
     h->plan.sched_off = h->sweep_off;
   } else {
     CK(cudaStreamSynchronize(h->stream));
-    h->plan.grid = m;
+    h->plan.grid = m * cl;
     h->plan.sched = nullptr;
     h->plan.sched_off = nullptr;
   }
@@ -797,11 +827,327 @@ dd_status build_sell(DDHandle *h, const dd_csr *csr) {
   TRY(upload(h, &d_col, col));
   TRY(upload(h, &d_val, val));
   h->sell.nslices = ns;
+  h->sell.n = n;
+  h->sell.st = h->st;
   h->sell.off = d_off;
   h->sell.row = d_row;
   h->sell.col = d_col;
   h->sell.val = d_val;
   h->sell_entries = off[ns];
+  return DD_OK;
+}
+
+// MSCN / MSCNR blocks on index ranges [g0[a], g1[a]) of the interface
+// (Algorithm 1's principal submatrices with the same local range in D, E, F
+// and G): S_a -= F_a D_a^-1 E_a (rowsum: only the row sums, on the
+// diagonal).  S holds G_a already, block a at d_soff[a]; d_p, d_soff,
+// d_poff, ipiv, failed, gj and amax describe / serve these blocks.  A range
+// whose E_a or F_a vanishes keeps G_a (D_a is then not needed: identity).
+template <typename T>
+dd_status principal_blocks(DDHandle *h, const dd_csr *csr, const HostBlocks &hb, const std::vector<int32_t> &g0v,
+                           const std::vector<int32_t> &g1v, bool rowsum, T *S, const int32_t *d_p,
+                           const int64_t *d_soff, const int64_t *d_poff, int32_t *ipiv, int32_t *failed, T *gj,
+                           T *amax, double pivtol) {
+  PrecBufs<T> &B = bufs<T>(h);
+  cudaStream_t s = h->stream;
+  const int nb = (int)g0v.size();
+  std::vector<int64_t> soff(nb + 1, 0);
+  int pmax = 0;
+  for (int a = 0; a < nb; ++a) {
+    const int pa = g1v[a] - g0v[a];
+    soff[a + 1] = soff[a] + (int64_t)pa * pa;
+    pmax = std::max(pmax, pa);
+  }
+  std::vector<int64_t> di, ei, fi;
+  std::vector<double> dv, ev, fv;
+  for (int a = 0; a < nb; ++a) {
+    const int g0 = g0v[a], g1 = g1v[a], pa = g1 - g0;
+    bool nzE = false, nzF = false;
+    size_t e0 = ei.size(), f0 = fi.size();
+    for (int r = g0; r < g1; ++r)
+      for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) {
+        int c = hb.e_col[k];
+        if (c >= g0 && c < g1 && hb.e_val[k] != 0.0) {
+          ei.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0));
+          ev.push_back(hb.e_val[k]);
+          nzE = true;
+        }
+      }
+    for (int r = g0; r < g1; ++r)
+      for (int k = hb.f_ptr[r]; k < hb.f_ptr[r + 1]; ++k) {
+        int c = hb.f_col[k];
+        if (c >= g0 && c < g1 && hb.f_val[k] != 0.0) {
+          fi.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0));
+          fv.push_back(hb.f_val[k]);
+          nzF = true;
+        }
+      }
+    if (!nzE || !nzF) {
+      // F_a D_a^-1 E_a vanishes: D_a is not needed, take the identity
+      ei.resize(e0); ev.resize(e0); fi.resize(f0); fv.resize(f0);
+      for (int r = 0; r < pa; ++r) { di.push_back(soff[a] + (int64_t)r * pa + r); dv.push_back(1.0); }
+      continue;
+    }
+    for (int r = g0; r < g1; ++r) {
+      const int o = hb.perm[r];
+      for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
+        const int c = hb.pos[csr->col[k]];
+        if (c >= g0 && c < g1) { di.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0)); dv.push_back(csr->val[k]); }
+      }
+    }
+  }
+  TRY(dalloc(h, &B.Dm, soff[nb]));
+  TRY(dalloc(h, &B.Em, soff[nb]));
+  TRY(dalloc(h, &B.Fm, soff[nb]));
+  TRY(dalloc(h, &B.Tm, soff[nb]));
+  T *blocks4[4] = {B.Dm, B.Em, B.Fm, B.Tm};
+  for (int q = 0; q < 4; ++q)
+    CK(cudaMemsetAsync(blocks4[q], 0, sizeof(T) * std::max<int64_t>(soff[nb], 1), s));
+  int64_t *d_i;
+  double *d_v;
+  TRY(upload(h, &d_i, di)); TRY(upload(h, &d_v, dv));
+  CK(launch_scatter_coo<T>((int64_t)di.size(), d_i, d_v, B.Dm, s));
+  TRY(upload(h, &d_i, ei)); TRY(upload(h, &d_v, ev));
+  CK(launch_scatter_coo<T>((int64_t)ei.size(), d_i, d_v, B.Em, s));
+  TRY(upload(h, &d_i, fi)); TRY(upload(h, &d_v, fv));
+  CK(launch_scatter_coo<T>((int64_t)fi.size(), d_i, d_v, B.Fm, s));
+  CK(launch_block_amax<T>(nb, d_p, d_soff, B.Dm, amax, s));
+  CK(launch_gj_inverse<T>(nb, d_p, d_soff, pmax, B.Dm, ipiv, d_poff, amax, failed, gj, pivtol, h->st,
+                          DD_ERR_SINGULAR_SCHUR, s));
+  if (!rowsum) {
+    CK(launch_block_gemm<T>(nb, d_p, d_soff, pmax, B.Dm, B.Em, B.Tm, T(1), T(0), s));
+    CK(launch_block_gemm<T>(nb, d_p, d_soff, pmax, B.Fm, B.Tm, S, T(-1), T(1), s));
+  } else {
+    CK(launch_mscnr_diag<T>(nb, d_p, d_soff, pmax, B.Dm, B.Em, B.Fm, S, s));
+  }
+  return DD_OK;
+}
+
+// S_hat of the overlapped kinds (OMSCN / OMSCNR / OLUM) into S (dense
+// n_G x n_G): block a spans agg[a] .. agg[a+1] - 1 + w_a with w_a =
+// min(overlap, p_{a+1}), w_k = 0 (Algorithm 1); G on each block, minus the
+// MSCN / MSCNR term, then the blocks placed in aggregate order with a later
+// block overwriting the overlap.
+template <typename T>
+dd_status overlapped_schur(DDHandle *h, const dd_csr *csr, const HostBlocks &hb, double pivtol, T *S) {
+  cudaStream_t s = h->stream;
+  const int k = (int)hb.agg.size() - 1, nG = h->nG, nI = h->nI;
+  if (k <= 0) return DD_OK;
+  std::vector<int32_t> w(k, 0), g0(k), g1(k), q(k);
+  std::vector<int64_t> xoff(k + 1, 0), qoff(k + 1, 0);
+  for (int a = 0; a < k; ++a) {
+    if (a + 1 < k) w[a] = std::min(h->overlap, hb.agg[a + 2] - hb.agg[a + 1]);
+    g0[a] = hb.agg[a];
+    g1[a] = hb.agg[a + 1] + w[a];
+    q[a] = g1[a] - g0[a];
+    xoff[a + 1] = xoff[a] + (int64_t)q[a] * q[a];
+    qoff[a + 1] = qoff[a] + q[a];
+  }
+  // G on every extended block
+  std::vector<int64_t> gi;
+  std::vector<double> gv;
+  for (int a = 0; a < k; ++a)
+    for (int g = g0[a]; g < g1[a]; ++g) {
+      const int o = hb.perm[nI + g];
+      for (int64_t e = csr->rowptr[o]; e < csr->rowptr[o + 1]; ++e) {
+        const int c = hb.pos[csr->col[e]] - nI;
+        if (c < g0[a] || c >= g1[a]) continue;
+        gi.push_back(xoff[a] + (int64_t)(g - g0[a]) * q[a] + (c - g0[a]));
+        gv.push_back(csr->val[e]);
+      }
+    }
+  T *Sx;
+  TRY(dalloc(h, &Sx, xoff[k]));
+  CK(cudaMemsetAsync(Sx, 0, sizeof(T) * std::max<int64_t>(xoff[k], 1), s));
+  int64_t *d_gi;
+  double *d_gv;
+  TRY(upload(h, &d_gi, gi));
+  TRY(upload(h, &d_gv, gv));
+  CK(launch_scatter_coo<T>((int64_t)gi.size(), d_gi, d_gv, Sx, s));
+  int32_t *d_q, *d_agg, *d_w, *ipiv, *failed;
+  int64_t *d_xoff, *d_qoff;
+  TRY(upload(h, &d_q, q));
+  TRY(upload(h, &d_xoff, xoff));
+  TRY(upload(h, &d_qoff, qoff));
+  TRY(upload(h, &d_agg, hb.agg));
+  TRY(upload(h, &d_w, w));
+  if (h->kind != DD_OLUM) {
+    T *gj, *amax;
+    TRY(dalloc(h, &ipiv, qoff[k]));
+    TRY(dalloc(h, &failed, k));
+    TRY(dalloc(h, &gj, gj_scratch_elems(k, qoff[k], sizeof(T))));
+    TRY(dalloc(h, &amax, k));
+    TRY(principal_blocks<T>(h, csr, hb, g0, g1, h->kind == DD_OMSCNR, Sx, d_q, d_xoff, d_qoff, ipiv, failed, gj,
+                            amax, pivtol));
+  }
+  CK(launch_assemble_overlapped<T>(nG, k, d_agg, d_w, d_xoff, Sx, S, s));
+  return DD_OK;
+}
+
+// MSCE with a finite radius r (DD_MSCE): S_a -= F(R_a, D_r) D_r^-1
+// E(D_r, R_a), where D_r holds the interior nodes within path length r of
+// aggregate a (first step through F or E, then through the pattern of D),
+// closed by the D-neighbours of every zero-diagonal node.  The node sets are
+// host index work; D_r, E and F go to dense blocks, D_r is inverted by the
+// blocked Gauss-Jordan kernels and the two products are batched GEMMs.
+template <typename T>
+dd_status msce_radius_blocks(DDHandle *h, const dd_csr *csr, const HostBlocks &hb, double pivtol, T *S,
+                             const std::vector<int64_t> &soff) {
+  cudaStream_t s = h->stream;
+  const int k = (int)hb.agg.size() - 1, nI = h->nI;
+  const int R = h->radius;
+  if (R <= 0 || nI == 0 || k <= 0) return DD_OK;  // r = 0: S_a = G_a (LUM)
+  // symmetrised pattern of D and its zero-diagonal nodes
+  std::vector<int32_t> aptr(nI + 1, 0), adj;
+  std::vector<char> zdiag(nI, 1);
+  for (int kk = 0; kk < nI; ++kk) {
+    const int o = hb.perm[kk];
+    for (int64_t e = csr->rowptr[o]; e < csr->rowptr[o + 1]; ++e) {
+      const int j = hb.pos[csr->col[e]];
+      if (j == kk && csr->val[e] != 0.0) zdiag[kk] = 0;
+      if (j < nI && j != kk) { aptr[kk + 1]++; aptr[j + 1]++; }
+    }
+  }
+  for (int kk = 0; kk < nI; ++kk) aptr[kk + 1] += aptr[kk];
+  adj.resize(aptr[nI]);
+  {
+    std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
+    for (int kk = 0; kk < nI; ++kk) {
+      const int o = hb.perm[kk];
+      for (int64_t e = csr->rowptr[o]; e < csr->rowptr[o + 1]; ++e) {
+        const int j = hb.pos[csr->col[e]];
+        if (j < nI && j != kk) { adj[fill[kk]++] = j; adj[fill[j]++] = kk; }
+      }
+    }
+  }
+  // E transposed: interior rows of every interface column
+  std::vector<int32_t> etp(h->nG + 1, 0), etr;
+  for (int r = 0; r < nI; ++r)
+    for (int e = hb.e_ptr[r]; e < hb.e_ptr[r + 1]; ++e)
+      if (hb.e_val[e] != 0.0) etp[hb.e_col[e] + 1]++;
+  for (int g = 0; g < h->nG; ++g) etp[g + 1] += etp[g];
+  etr.resize(etp[h->nG]);
+  {
+    std::vector<int32_t> fill(etp.begin(), etp.end() - 1);
+    for (int r = 0; r < nI; ++r)
+      for (int e = hb.e_ptr[r]; e < hb.e_ptr[r + 1]; ++e)
+        if (hb.e_val[e] != 0.0) etr[fill[hb.e_col[e]]++] = r;
+  }
+  // the node set of every aggregate, then the dense blocks
+  std::vector<int32_t> bd, ba;  // blocks with a non-empty D_r: their size, aggregate
+  std::vector<int64_t> doff(1, 0), eoff(1, 0), poff(1, 0);
+  std::vector<int64_t> di, ei, fi;
+  std::vector<double> dv, ev, fv;
+  std::vector<int32_t> dist(nI, -1), loc(nI, -1), set;
+  int dmax = 0, pmax = 0;
+  for (int a = 0; a < k; ++a) {
+    const int g0 = hb.agg[a], g1 = hb.agg[a + 1], pa = g1 - g0;
+    set.clear();
+    for (int g = g0; g < g1; ++g) {
+      for (int e = hb.f_ptr[g]; e < hb.f_ptr[g + 1]; ++e) {
+        const int j = hb.f_col[e];
+        if (hb.f_val[e] != 0.0 && dist[j] < 0) { dist[j] = 1; set.push_back(j); }
+      }
+      for (int e = etp[g]; e < etp[g + 1]; ++e) {
+        const int j = etr[e];
+        if (dist[j] < 0) { dist[j] = 1; set.push_back(j); }
+      }
+    }
+    for (size_t head = 0; head < set.size(); ++head) {
+      const int kk = set[head];
+      if (dist[kk] >= R) continue;
+      for (int e = aptr[kk]; e < aptr[kk + 1]; ++e)
+        if (dist[adj[e]] < 0) { dist[adj[e]] = dist[kk] + 1; set.push_back(adj[e]); }
+    }
+    const size_t d0 = set.size();
+    for (size_t q0 = 0; q0 < d0; ++q0) {
+      const int kk = set[q0];
+      if (!zdiag[kk]) continue;
+      for (int e = aptr[kk]; e < aptr[kk + 1]; ++e)
+        if (dist[adj[e]] < 0) { dist[adj[e]] = R + 1; set.push_back(adj[e]); }
+    }
+    std::sort(set.begin(), set.end());
+    const int d = (int)set.size();
+    for (int q2 = 0; q2 < d; ++q2) loc[set[q2]] = q2;
+    if (d > 0) {
+      const int b = (int)bd.size();
+      bd.push_back(d);
+      ba.push_back(a);
+      for (int q2 = 0; q2 < d; ++q2) {
+        const int kk = set[q2], o = hb.perm[kk];
+        for (int64_t e = csr->rowptr[o]; e < csr->rowptr[o + 1]; ++e) {
+          const int c = hb.pos[csr->col[e]];
+          if (c < nI && loc[c] >= 0) { di.push_back(doff[b] + (int64_t)q2 * d + loc[c]); dv.push_back(csr->val[e]); }
+        }
+        for (int e = hb.e_ptr[kk]; e < hb.e_ptr[kk + 1]; ++e) {
+          const int c = hb.e_col[e];
+          if (c >= g0 && c < g1) { ei.push_back(eoff[b] + (int64_t)q2 * pa + (c - g0)); ev.push_back(hb.e_val[e]); }
+        }
+      }
+      for (int g = g0; g < g1; ++g)
+        for (int e = hb.f_ptr[g]; e < hb.f_ptr[g + 1]; ++e) {
+          const int j = hb.f_col[e];
+          if (loc[j] >= 0) { fi.push_back(eoff[b] + (int64_t)(g - g0) * d + loc[j]); fv.push_back(hb.f_val[e]); }
+        }
+      doff.push_back(doff[b] + (int64_t)d * d);
+      eoff.push_back(eoff[b] + (int64_t)d * pa);
+      poff.push_back(poff[b] + d);
+      dmax = std::max(dmax, d);
+      pmax = std::max(pmax, pa);
+    }
+    for (int kk : set) { dist[kk] = -1; loc[kk] = -1; }
+  }
+  const int nb = (int)bd.size();
+  if (nb == 0) return DD_OK;
+  if (dmax > 12288) { h->err = "MSCE: a reached interior set exceeds 12288 nodes (reduce the radius)"; return DD_ERR_INVALID_ARG; }
+  h->stats.msce_nodes_max = dmax;
+  // device blocks
+  T *Dr, *Er, *Fr, *Tr, *gj, *amax;
+  int32_t *ipiv, *failed, *d_bd;
+  int64_t *d_doff, *d_poff;
+  TRY(dalloc(h, &Dr, doff[nb]));
+  TRY(dalloc(h, &Er, eoff[nb]));
+  TRY(dalloc(h, &Fr, eoff[nb]));
+  TRY(dalloc(h, &Tr, eoff[nb]));
+  CK(cudaMemsetAsync(Dr, 0, sizeof(T) * doff[nb], s));
+  CK(cudaMemsetAsync(Er, 0, sizeof(T) * std::max<int64_t>(eoff[nb], 1), s));
+  CK(cudaMemsetAsync(Fr, 0, sizeof(T) * std::max<int64_t>(eoff[nb], 1), s));
+  int64_t *d_i;
+  double *d_v;
+  TRY(upload(h, &d_i, di)); TRY(upload(h, &d_v, dv));
+  CK(launch_scatter_coo<T>((int64_t)di.size(), d_i, d_v, Dr, s));
+  TRY(upload(h, &d_i, ei)); TRY(upload(h, &d_v, ev));
+  CK(launch_scatter_coo<T>((int64_t)ei.size(), d_i, d_v, Er, s));
+  TRY(upload(h, &d_i, fi)); TRY(upload(h, &d_v, fv));
+  CK(launch_scatter_coo<T>((int64_t)fi.size(), d_i, d_v, Fr, s));
+  TRY(upload(h, &d_bd, bd));
+  TRY(upload(h, &d_doff, doff));
+  TRY(upload(h, &d_poff, poff));
+  TRY(dalloc(h, &ipiv, poff[nb]));
+  TRY(dalloc(h, &failed, nb));
+  TRY(dalloc(h, &gj, gj_scratch_elems(nb, poff[nb], sizeof(T))));
+  TRY(dalloc(h, &amax, nb));
+  CK(launch_block_amax<T>(nb, d_bd, d_doff, Dr, amax, s));
+  CK(launch_gj_inverse<T>(nb, d_bd, d_doff, dmax, Dr, ipiv, d_poff, amax, failed, gj, pivtol, h->st,
+                          DD_ERR_SINGULAR_SCHUR, s));
+  // T_b = D_r^-1 E_b (d x p), then S_a -= F_b T_b (p x p)
+  std::vector<int32_t> dims1, dims2;
+  std::vector<int64_t> offs1, offs2;
+  for (int b = 0; b < nb; ++b) {
+    const int a = ba[b], d = bd[b], pa = hb.agg[a + 1] - hb.agg[a];
+    dims1.insert(dims1.end(), {d, pa, d});
+    offs1.insert(offs1.end(), {doff[b], eoff[b], eoff[b]});
+    dims2.insert(dims2.end(), {pa, pa, d});
+    offs2.insert(offs2.end(), {eoff[b], eoff[b], soff[a]});
+  }
+  int32_t *d_dims1, *d_dims2;
+  int64_t *d_offs1, *d_offs2;
+  TRY(upload(h, &d_dims1, dims1));
+  TRY(upload(h, &d_offs1, offs1));
+  TRY(upload(h, &d_dims2, dims2));
+  TRY(upload(h, &d_offs2, offs2));
+  CK(launch_rect_gemm<T>(nb, d_dims1, d_offs1, dmax, pmax, Dr, Er, Tr, T(1), T(0), s));
+  CK(launch_rect_gemm<T>(nb, d_dims2, d_offs2, pmax, pmax, Fr, Tr, S, T(-1), T(1), s));
   return DD_OK;
 }
 
@@ -964,7 +1310,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     h->h_info = info;
     h->h_tm = tm;
     TRY(upload(h, &h->tm, tm));
-    TRY(set_sweep_plan<T>(h, stage));
+    TRY(set_sweep_plan<T>(h, stage, choose_cluster<T>(h, stage)));
     info = h->h_info;
     TRY(dalloc(h, &B.ltile, lofs));
     TRY(dalloc(h, &B.utile, uofs));
@@ -981,24 +1327,32 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   TRY(upload(h, &h->f_col, hb.f_col));
   TRY(upload_T(h, &B.f_val, hb.f_val));
   h->stats.coupling_nnz = (int64_t)hb.e_col.size() + (int64_t)hb.f_col.size();
-  // ---- interface blocks
-  const int nagg = (int)hb.agg.size() - 1;
+  // ---- interface blocks.  The overlapped kinds build their blocks apart and
+  // assemble S_hat into one block of the whole interface, which the apply
+  // then inverts whole (the blocks of the apply are aggA).
+  const bool ovl_kind = h->kind == DD_OMSCN || h->kind == DD_OMSCNR || h->kind == DD_OLUM;
+  const std::vector<int32_t> aggA = ovl_kind ? std::vector<int32_t>{0, nG} : hb.agg;
+  const int nagg = (int)aggA.size() - 1;
   h->nagg = nagg;
   std::vector<int32_t> p(nagg), agg_of(nG);
   std::vector<int64_t> soff(nagg + 1, 0), poff(nagg + 1, 0);
   h->pmax = 0;
   for (int a = 0; a < nagg; ++a) {
-    p[a] = hb.agg[a + 1] - hb.agg[a];
+    p[a] = aggA[a + 1] - aggA[a];
     soff[a + 1] = soff[a] + (int64_t)p[a] * p[a];
     poff[a + 1] = poff[a] + p[a];
     h->pmax = std::max(h->pmax, p[a]);
-    for (int g = hb.agg[a]; g < hb.agg[a + 1]; ++g) agg_of[g] = a;
+    for (int g = aggA[a]; g < aggA[a + 1]; ++g) agg_of[g] = a;
   }
-  if (h->pmax > 12288) { h->err = "an aggregate exceeds 12288 interface nodes"; return DD_ERR_INVALID_ARG; }
-  h->stats.n_agg = nagg;
+  if (h->pmax > 12288) {
+    h->err = ovl_kind ? "overlapped kinds invert the whole interface: n_G must be <= 12288"
+                      : "an aggregate exceeds 12288 interface nodes";
+    return DD_ERR_INVALID_ARG;
+  }
+  h->stats.n_agg = (int32_t)hb.agg.size() - 1;
   h->stats.max_agg = h->pmax;
   h->stats.schur_bytes = soff[nagg] * (int64_t)sizeof(T);
-  TRY(upload(h, &h->agg_off, hb.agg));
+  TRY(upload(h, &h->agg_off, aggA));
   TRY(upload(h, &h->d_p, p));
   TRY(upload(h, &h->s_off, soff));
   TRY(upload(h, &h->poff, poff));
@@ -1012,7 +1366,9 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   int64_t *d_gidx = nullptr;
   double *d_gval = nullptr;
   size_t gcount = 0;
-  {
+  if (ovl_kind) {
+    TRY(overlapped_schur<T>(h, csr, hb, pivtol, B.S));
+  } else {
     std::vector<int64_t> idx;
     std::vector<double> val;
     for (int g = 0; g < nG; ++g) {
@@ -1149,70 +1505,13 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     TRY(dalloc(h, &B.z2, std::max(nG, 1)));
     TRY(dalloc(h, &B.t, std::max(nG, 1)));
     return DD_OK;  // the blocks are inverted (with their fallbacks)
+  } else if (h->kind == DD_MSCE) {
+    TRY(msce_radius_blocks<T>(h, csr, hb, pivtol, B.S, soff));
   } else if (h->kind == DD_MSCN || h->kind == DD_MSCNR) {
-    // principal blocks with the same local index range (Algorithm 1)
-    std::vector<int64_t> di, ei, fi;
-    std::vector<double> dv, ev, fv;
-    for (int a = 0; a < nagg; ++a) {
-      const int g0 = hb.agg[a], g1 = hb.agg[a + 1], pa = p[a];
-      bool nzE = false, nzF = false;
-      size_t e0 = ei.size(), f0 = fi.size();
-      for (int r = g0; r < g1; ++r)
-        for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) {
-          int c = hb.e_col[k];
-          if (c >= g0 && c < g1 && hb.e_val[k] != 0.0) {
-            ei.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0));
-            ev.push_back(hb.e_val[k]);
-            nzE = true;
-          }
-        }
-      for (int r = g0; r < g1; ++r)
-        for (int k = hb.f_ptr[r]; k < hb.f_ptr[r + 1]; ++k) {
-          int c = hb.f_col[k];
-          if (c >= g0 && c < g1 && hb.f_val[k] != 0.0) {
-            fi.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0));
-            fv.push_back(hb.f_val[k]);
-            nzF = true;
-          }
-        }
-      if (!nzE || !nzF) {
-        // F_ii D_ii^-1 E_ii vanishes: D_ii is not needed, take the identity
-        ei.resize(e0); ev.resize(e0); fi.resize(f0); fv.resize(f0);
-        for (int r = 0; r < pa; ++r) { di.push_back(soff[a] + (int64_t)r * pa + r); dv.push_back(1.0); }
-        continue;
-      }
-      for (int r = g0; r < g1; ++r) {
-        const int o = hb.perm[r];
-        for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
-          const int c = hb.pos[csr->col[k]];
-          if (c >= g0 && c < g1) { di.push_back(soff[a] + (int64_t)(r - g0) * pa + (c - g0)); dv.push_back(csr->val[k]); }
-        }
-      }
-    }
-    TRY(dalloc(h, &B.Dm, soff[nagg]));
-    TRY(dalloc(h, &B.Em, soff[nagg]));
-    TRY(dalloc(h, &B.Fm, soff[nagg]));
-    TRY(dalloc(h, &B.Tm, soff[nagg]));
-    T *blocks4[4] = {B.Dm, B.Em, B.Fm, B.Tm};
-    for (int q = 0; q < 4; ++q)
-      CK(cudaMemsetAsync(blocks4[q], 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
-    int64_t *d_i;
-    double *d_v;
-    TRY(upload(h, &d_i, di)); TRY(upload(h, &d_v, dv));
-    CK(launch_scatter_coo<T>((int64_t)di.size(), d_i, d_v, B.Dm, s));
-    TRY(upload(h, &d_i, ei)); TRY(upload(h, &d_v, ev));
-    CK(launch_scatter_coo<T>((int64_t)ei.size(), d_i, d_v, B.Em, s));
-    TRY(upload(h, &d_i, fi)); TRY(upload(h, &d_v, fv));
-    CK(launch_scatter_coo<T>((int64_t)fi.size(), d_i, d_v, B.Fm, s));
-    CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.Dm, B.amax, s));
-    CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.Dm, h->ipiv, h->poff, B.amax,
-                            h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
-    if (h->kind == DD_MSCN) {
-      CK(launch_block_gemm<T>(nagg, h->d_p, h->s_off, h->pmax, B.Dm, B.Em, B.Tm, T(1), T(0), s));
-      CK(launch_block_gemm<T>(nagg, h->d_p, h->s_off, h->pmax, B.Fm, B.Tm, B.S, T(-1), T(1), s));
-    } else {
-      CK(launch_mscnr_diag<T>(nagg, h->d_p, h->s_off, h->pmax, B.Dm, B.Em, B.Fm, B.S, s));
-    }
+    std::vector<int32_t> g0(nagg), g1(nagg);
+    for (int a = 0; a < nagg; ++a) { g0[a] = hb.agg[a]; g1[a] = hb.agg[a + 1]; }
+    TRY(principal_blocks<T>(h, csr, hb, g0, g1, h->kind == DD_MSCNR, B.S, h->d_p, h->s_off, h->poff,
+                            h->ipiv, h->failed, B.gj, B.amax, pivtol));
   }
   // ---- explicit inverses of the S_hat blocks
   CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.S, B.amax, s));
@@ -1764,12 +2063,15 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   size_t best = 0;
+  int best_cl = 1;
   float best_ms = 1e30f;
   int tried = 0;
+  for (int cl = 1; cl <= 2; ++cl)
   for (size_t st : cand) {
-    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, 8 * h->tb, sizeof(T), (uint32_t)st) < 2) continue;
-    if (band_sweep_occupancy<T>(h->max_n, h->max_kl, h->max_ku2, 8 * h->tb, (uint32_t)st) <= 0) continue;
-    dd_status rc = set_sweep_plan<T>(h, st);
+    if (h->sweep_cl_opt && cl != h->sweep_cl_opt) continue;
+    if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, sizeof(T), (uint32_t)st) < 2) continue;
+    if (band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, (uint32_t)st) <= 0) continue;
+    dd_status rc = set_sweep_plan<T>(h, st, cl);
     if (rc != DD_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     float tmin = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {
@@ -1783,12 +2085,12 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
       if (rep > 0) tmin = std::min(tmin, ms);
     }
     ++tried;
-    if (tmin < best_ms) { best_ms = tmin; best = st; }
+    if (tmin < best_ms) { best_ms = tmin; best = st; best_cl = cl; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (tried == 0) { h->err = "autotune: no stage size fits"; return DD_ERR_INVALID_ARG; }
-  TRY(set_sweep_plan<T>(h, best));
+  TRY(set_sweep_plan<T>(h, best, best_cl));
   h->stats.tuned = tried;
   h->stats.tuned_us = 1000.0 * best_ms;
   return DD_OK;
@@ -1798,7 +2100,7 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
 // seg_row0_h already set); times itself with events on the handle's stream.
 dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *partition, dd_approx approx,
                        const dd_opts *opts) {
-  if ((int)approx < DD_EXACT || (int)approx > DD_LEARNED) { h->err = "unknown approximation"; return DD_ERR_INVALID_ARG; }
+  if ((int)approx < DD_EXACT || (int)approx > DD_MSCE) { h->err = "unknown approximation"; return DD_ERR_INVALID_ARG; }
   dd_opts o{};
   o.prec = DD_FP64;
   if (opts) o = *opts;
@@ -1812,6 +2114,11 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->use_graph = o.use_graph != 0;
   h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : 2;
   h->time_kernels = o.time_kernels != 0 && !h->use_graph;
+  if (o.sweep_cluster < 0 || o.sweep_cluster > 2) { h->err = "sweep_cluster must be 0, 1 or 2"; return DD_ERR_INVALID_ARG; }
+  h->sweep_cl_opt = o.sweep_cluster;
+  if (o.overlap < 0 || o.radius < 0) { h->err = "overlap and radius must be >= 0"; return DD_ERR_INVALID_ARG; }
+  h->overlap = o.overlap;
+  h->radius = o.radius;
   const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
   const int R = o.max_restart > 0 ? o.max_restart : 50;
   if (R > 120) { h->err = "max_restart must be <= 120"; return DD_ERR_INVALID_ARG; }
@@ -2088,8 +2395,12 @@ dd_status dd_setup_batched(int32_t count, const dd_csr *csrs, const dd_partition
   *handle = nullptr;
   g_setup_error.clear();
   if (count <= 0 || !csrs || !partitions) { g_setup_error = "count >= 1, csrs and partitions are required"; return DD_ERR_INVALID_ARG; }
-  if (approx == DD_MSCN || approx == DD_MSCNR) {
+  if (approx == DD_MSCN || approx == DD_MSCNR || approx == DD_OMSCN || approx == DD_OMSCNR) {
     g_setup_error = "MSCN and MSCNR pair interface and interior index ranges of one system; not available in a batch";
+    return DD_ERR_INVALID_ARG;
+  }
+  if (approx == DD_OLUM) {
+    g_setup_error = "overlapped blocks would join the systems of a batch; not available in a batch";
     return DD_ERR_INVALID_ARG;
   }
   BatchInput bi;

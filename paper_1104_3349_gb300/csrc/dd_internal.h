@@ -55,6 +55,17 @@ struct SweepJob {
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
+// Sweeps split over a cluster of cl CTAs (cl = 1 or 2): CTA p of the cluster
+// takes forward-tile rows [fwd_split(wl, p), fwd_split(wl, p + 1)) and
+// backward-tile rows [p TB / cl, (p + 1) TB / cl).  Split points are
+// multiples of 4 rows, so every slice of a tile starts on a 16-byte boundary.
+__host__ __device__ inline int fwd_split(int wl, int p, int cl) {
+  if (p <= 0) return 0;
+  if (p >= cl) return wl;
+  const int r = round4((wl * p + cl - 1) / cl);
+  return r < wl ? r : wl;
+}
+
 // Launch plan of the sweep kernels: ring stage size, threads per CTA, and,
 // when there are more subdomains than resident CTAs, a persistent grid whose
 // CTA c takes the tasks sched[sched_off[c] .. sched_off[c+1]) (longest
@@ -89,13 +100,32 @@ struct SweepPlan {
   // polls of the first mbarrier wait of every sweep CTA (a test hook of the
   // timeout path); larger than the normal bound means the normal bound
   uint32_t first_wait = 0xffffffffu;
+  // CTAs per subdomain: 1, or 2 (a thread-block cluster; threads = 4 TB);
+  // grid counts CTAs, so a persistent grid holds grid / cl task lists
+  int cl = 1;
 };
 
 // Device-side error word: first failure wins.
 struct DevStatus {
   int32_t code;   // 0 ok, else a dd_status
-  int32_t block;  // failing block
+  int32_t block;  // failing block (DD_ERR_CHECK: the check's site)
 };
+
+// Checked build (compiled with -DDD_CHECKED): the sweep, SpMV and interface
+// kernels test every index, size and alignment they compute before the
+// access; a failed test records DD_ERR_CHECK with the site number and the
+// access is skipped (no trap).  Without DD_CHECKED the tests compile away.
+#ifdef __CUDACC__
+__device__ inline bool dd_check(DevStatus *st, bool ok, int site) {
+#ifdef DD_CHECKED
+  if (!ok && st && atomicCAS(&st->code, 0, (int)DD_ERR_CHECK) == 0) st->block = site;
+  return ok;
+#else
+  (void)st; (void)site;
+  return true;
+#endif
+}
+#endif
 
 struct Workspace;  // defined in dd_api.cu
 
@@ -103,10 +133,10 @@ struct Workspace;  // defined in dd_api.cu
 // ---- k_krylov.cu).  All return cudaGetLastError() of their launch.
 // Tile ring of the apply sweeps: how many stages of stage_bytes fit next to
 // the resident right-hand side (0: the subdomain is too large).
-int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
+int band_sweep_stages(int max_n, int max_kl, int max_ku2, int tb, int cl, int elem_size,
                       uint32_t stage_bytes);
 // largest stage size that leaves room for two stages (0: the vectors alone do not fit)
-size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb);
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb, int cl = 1);
 // Blocked banded LU; ltraw receives each tile's multipliers ((NB+kl) x NB,
 // column-major, exchanged), wscratch holds the windows when they do not fit
 // in shared memory (band_lu_window_bytes per subdomain, else unused).
@@ -146,9 +176,10 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
                                   const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
                                   double *x, DevStatus *st, cudaStream_t s);
-// resident CTAs per SM of the sweep kernels at this stage size (0: does not fit)
+// subdomains the sweep kernels hold resident at once (CTAs for cl = 1,
+// clusters for cl = 2) at this stage size; 0: they do not fit
 template <typename T>
-int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32_t stage_bytes);
+int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>
@@ -189,6 +220,17 @@ cudaError_t launch_schur_accumulate(int nj, const int32_t *jlist, const int32_t 
 template <typename T>
 cudaError_t launch_block_gemm(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
                               const T *A, const T *B, T *C, T alpha, T beta, cudaStream_t s);
+// overlapped kinds: S_hat (dense n_G x n_G) from the blocks of the k
+// aggregates extended by w (block a: q_a x q_a at xoff[a] in Sx), a later
+// block overwriting the overlap
+template <typename T>
+cudaError_t launch_assemble_overlapped(int ng, int k, const int32_t *agg, const int32_t *w, const int64_t *xoff,
+                                       const T *Sx, T *S, cudaStream_t s);
+// C_b = alpha A_b B_b + beta C_b, rectangular row-major blocks: dims (M, N, K)
+// and offs (A, B, C offsets) three per block
+template <typename T>
+cudaError_t launch_rect_gemm(int nblk, const int32_t *dims, const int64_t *offs, int maxM, int maxN, const T *A,
+                             const T *B, T *C, T alpha, T beta, cudaStream_t s);
 template <typename T>
 cudaError_t launch_mscnr_diag(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
                               const T *Dinv, const T *E, const T *F, T *S, cudaStream_t s);
@@ -212,6 +254,8 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
 #define DD_SELL_WINDOW 256
 struct SellC {
   int64_t nslices = 0;
+  int64_t n = 0;              // rows = columns of C
+  DevStatus *st = nullptr;    // DD_CHECKED: where a failed index check is recorded
   const int64_t *off = nullptr;
   const int32_t *row = nullptr;
   const int32_t *col = nullptr;

@@ -23,17 +23,21 @@
 //   backward tile t, rows r0 .. r0+TB-1:
 //     Kb       TB x wu: [Uinv | -Uinv U12], Uinv the inverse of the tile's
 //              upper triangle, so x_T = Kb [b_T; x_next].
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <climits>
 
 #include <algorithm>
+#include <utility>
 
 #include "dd_internal.h"
 
 namespace {
 
 __host__ __device__ inline int src_stride_w(int w) { return round4(w); }
+// row stride of a cluster sweep's exchange buffers (room for any tile slice)
+__host__ __device__ inline int sweep_xbs(int tb, int max_kl) { return round4(tb + max_kl + 8); }
 // zero padding beyond the tiles of the resident vectors: room for the
 // widest window or row of a tile, a multiple of 32 elements
 __host__ __device__ inline int sweep_pad_hd(int max_kl, int max_ku2) {
@@ -585,25 +589,74 @@ __device__ __forceinline__ SweepJob get_job(const BandInfo &b, const SweepJob *j
   return jobs[fwd ? b.jf0 + q : b.jb0 + (q - b.njf)];
 }
 
-template <typename T, int TB>
+// Bytes of CTA `rank`'s slice of tile mt in a cluster of CL CTAs: forward,
+// its K rows then the tile's whole src; backward, its Kb rows.
+template <typename T, int TB, int CL>
+__device__ __forceinline__ uint32_t slice_bytes(const TileMeta &mt, bool fwd, int rank) {
+  if (fwd)
+    return (uint32_t)((fwd_split(mt.wl, rank + 1, CL) - fwd_split(mt.wl, rank, CL)) * TB * sizeof(T) +
+                      src_stride_w(mt.wl) * sizeof(int32_t));
+  return (uint32_t)((TB / CL) * mt.wu * sizeof(T));
+}
+
+// One job into its stage.  CL = 1: the job's tiles are contiguous in the
+// packed arrays, one copy for K (or Kb) and one for src.  CL = 2: the CTA's
+// slices only, tile by tile (forward in ascending, backward in descending
+// tile order, the order they are used), all on the stage's mbarrier.
+// DD_CHECKED: a copy whose global address or size is not a multiple of 16
+// bytes, or that would run past its stage, is not issued (its wait then
+// gives up and the sweep stops).
+__device__ __forceinline__ void bulk_g2s_checked(unsigned char *stage, uint32_t off, const void *src,
+                                                 uint32_t bytes, uint32_t stage_bytes, uint64_t *bar,
+                                                 DevStatus *st) {
+  const bool ok = dd_check(st, ((uintptr_t)src & 15) == 0, 11) && dd_check(st, (bytes & 15) == 0, 12) &&
+                  dd_check(st, (uint64_t)off + bytes <= stage_bytes, 13);
+  if (ok) bulk_g2s(stage + off, src, bytes, bar);
+}
+
+template <typename T, int TB, int CL = 1>
 __device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                           int q, const T *ltile, const T *utile, const int32_t *srcs,
-                                          unsigned char *stage, uint64_t *bar) {
+                                          unsigned char *stage, uint64_t *bar, int rank, uint32_t stage_bytes,
+                                          DevStatus *st) {
   bool fwd;
   const SweepJob jb = get_job(b, jobs, q, fwd);
   const TileMeta &a = tm[b.tile0 + jb.lo];
+  if (CL > 1) {
+    uint32_t tot = 0;
+    for (int t = jb.lo; t < jb.hi; ++t) tot += slice_bytes<T, TB, CL>(tm[b.tile0 + t], fwd, rank);
+    mbar_expect_tx(bar, tot);
+    uint32_t off = 0;
+    for (int u = 0; u < jb.hi - jb.lo; ++u) {
+      const TileMeta &mt = tm[b.tile0 + (fwd ? jb.lo + u : jb.hi - 1 - u)];
+      if (fwd) {
+        const int r0 = fwd_split(mt.wl, rank, CL), r1 = fwd_split(mt.wl, rank + 1, CL);
+        const uint32_t kb = (uint32_t)((r1 - r0) * TB * sizeof(T));
+        if (kb) bulk_g2s_checked(stage, off, ltile + mt.lofs + (int64_t)r0 * TB, kb, stage_bytes, bar, st);
+        off += kb;
+        const uint32_t sb = (uint32_t)(src_stride_w(mt.wl) * sizeof(int32_t));
+        bulk_g2s_checked(stage, off, srcs + mt.sofs, sb, stage_bytes, bar, st);
+        off += sb;
+      } else {
+        const uint32_t ub = (uint32_t)((TB / CL) * mt.wu * sizeof(T));
+        bulk_g2s_checked(stage, off, utile + mt.uofs + (int64_t)rank * (TB / CL) * mt.wu, ub, stage_bytes, bar, st);
+        off += ub;
+      }
+    }
+    return;
+  }
   if (fwd) {
     const TileMeta &z = tm[b.tile0 + jb.hi - 1];
     const uint32_t lb = (uint32_t)((z.lofs + (int64_t)z.wl * TB - a.lofs) * sizeof(T));
     const uint32_t sb = (uint32_t)((z.sofs + src_stride_w(z.wl) - a.sofs) * sizeof(int32_t));
     mbar_expect_tx(bar, lb + sb);
-    bulk_g2s(stage, ltile + a.lofs, lb, bar);
-    bulk_g2s(stage + lb, srcs + a.sofs, sb, bar);
+    bulk_g2s_checked(stage, 0, ltile + a.lofs, lb, stage_bytes, bar, st);
+    bulk_g2s_checked(stage, lb, srcs + a.sofs, sb, stage_bytes, bar, st);
   } else {
     const TileMeta &z = tm[b.tile0 + jb.hi - 1];
     const uint32_t ub = (uint32_t)((z.uofs + (int64_t)TB * z.wu - a.uofs) * sizeof(T));
     mbar_expect_tx(bar, ub);
-    bulk_g2s(stage, utile + a.uofs, ub, bar);
+    bulk_g2s_checked(stage, 0, utile + a.uofs, ub, stage_bytes, bar, st);
   }
 }
 
@@ -634,16 +687,17 @@ struct Chunk<double> {
 
 // The first nstages jobs of a task into their stages (thread 0); the stages
 // were last read by generic loads of the previous task.
-template <typename T, int TB>
+template <typename T, int TB, int CL = 1>
 __device__ __forceinline__ void issue_first_jobs(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                                  const T *ltile, const T *utile, const int32_t *srcs,
                                                  unsigned char *ring, uint32_t stage_bytes, int nstages,
-                                                 uint64_t *bars, uint32_t jbase) {
+                                                 uint64_t *bars, uint32_t jbase, int rank, DevStatus *st) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const int nj = b.njf + b.njb;
   for (int q = 0; q < nstages && q < nj; ++q) {
     const int sq = (int)((jbase + q) % nstages);
-    issue_job<T, TB>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq]);
+    issue_job<T, TB, CL>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq], rank,
+                         stage_bytes, st);
   }
 }
 
@@ -657,13 +711,13 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
                                 uint32_t &jbase, int task, bool issued, DevStatus *st,
-                                uint32_t first_wait) {
+                                uint32_t first_wait, int wext, int vext) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nj = b.njf + b.njb;
   // job q of this task is job jbase + q of the CTA: its stage and phase
-  if (tid == 0 && !issued) issue_first_jobs<T, TB>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
+  if (tid == 0 && !issued) issue_first_jobs<T, TB>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, 0, st);
   bool ok = true;
   int q = 0;
   for (; q < nj; ++q) {
@@ -687,9 +741,12 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
         const int c0 = t * TB, WL = mt.wl;
         const T *K = reinterpret_cast<const T *>(stage + (mt.lofs - a.lofs) * sizeof(T));
         const int32_t *src = reinterpret_cast<const int32_t *>(stage + kbytes) + (mt.sofs - a.sofs);
-        if (got)
-          for (int e = tid; e < WL; e += nt) win[e] = vec[c0 + src[e]];
-        if (!__syncthreads_and(got)) { ok = false; break; }
+        // (DD_CHECKED: the window fits win and vec, every source row is inside it)
+        const bool wok = dd_check(st, WL <= wext && c0 + WL <= vext, 21);
+        if (got && wok)
+          for (int e = tid; e < WL; e += nt)
+            if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 22)) win[e] = vec[c0 + src[e]];
+        if (!__syncthreads_and(got && wok)) { ok = false; break; }
         for (int r = tid; r < WL; r += nt) {
           const CV *kr = reinterpret_cast<const CV *>(K + r * TB);
           const CV *wv = reinterpret_cast<const CV *>(win);
@@ -715,7 +772,8 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
         const T *Kb = reinterpret_cast<const T *>(stage + (mt.uofs - a.uofs) * sizeof(T));
         const int i = tid >> 3, h = tid & 7;
         T acc = T(0);
-        if (got) {
+        const bool bok = dd_check(st, r0 + WU <= vext, 23);
+        if (got && bok) {
           const CV *kr = reinterpret_cast<const CV *>(Kb + (int64_t)i * WU);
           const CV *bv = reinterpret_cast<const CV *>(vec + r0);
           const CV *xv = reinterpret_cast<const CV *>(xout + r0);
@@ -733,14 +791,14 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
         if (h == 0) xout[r0 + i] = acc;
-        if (!__syncthreads_and(got)) { ok = false; break; }
+        if (!__syncthreads_and(got && bok)) { ok = false; break; }
       }
       if (!ok) break;
     }
     // the stage is free; vec / xout are current
     if (tid == 0 && q + nstages < nj) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_job<T, TB>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx]);
+      issue_job<T, TB>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx], 0, stage_bytes, st);
     }
   }
   if (!ok) {
@@ -759,17 +817,176 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
   return ok;
 }
 
+// Barrier of every thread of every CTA of the cluster; the release / acquire
+// pair makes the distributed shared-memory stores before it visible after it.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// The sweeps of one subdomain split over a 2-CTA cluster.  Each CTA keeps a
+// whole copy of vec and xout and streams only its slices of the tiles (half
+// the bytes through its shared memory).  A tile step: merge the peer's
+// results of the previous step into vec / xout, gather the window, compute
+// the CTA's rows, store them locally and into the peer's exchange buffer
+// xb[s & 1] (s: the CTA's step count, the same in both CTAs), store the
+// CTA's all-copies-arrived flag into the peer's okf[s & 1], then one cluster
+// barrier.  The peer writes xb[s & 1] only after the barrier of step s - 1,
+// which this CTA reaches only after merging xb[(s - 1) & 1], so the two
+// buffers never race.  A wait that gives up in either CTA makes both stop
+// after the same barrier (each reads its own and the peer's flag); each then
+// drains its own copies.  Rows are computed exactly as in the one-CTA sweep,
+// so the results are the same bits.
+template <typename T, int TB>
+__device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm,
+                              const SweepJob *__restrict__ jobs, const T *__restrict__ ltile,
+                              const T *__restrict__ utile, const int32_t *__restrict__ srcs, T *vec,
+                              T *xout, T *win, unsigned char *ring, uint32_t stage_bytes, int nstages,
+                              uint64_t *bars, uint32_t &jbase, uint32_t &sstep, int task, DevStatus *st,
+                              uint32_t first_wait, T *xb, int xbs, volatile int32_t *okf, T *pxb,
+                              int32_t *pokf, int rank, int wext, int vext) {
+  using CV = typename Chunk<T>::V;
+  constexpr int CN = Chunk<T>::N;
+  constexpr int CL = 2, BR = TB / CL;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nj = b.njf + b.njb;
+  bool ok = true;
+  // the peer's results of the last step, still to be merged: into vec (fwd)
+  // or xout, positions base + [lo, hi), from xb[par]
+  T *mdst = nullptr;
+  int mbase = 0, mlo = 0, mhi = 0, mpar = 0;
+  int q = 0;
+  for (; q < nj; ++q) {
+    const uint32_t gq = jbase + q;
+    const int sidx = (int)(gq % nstages);
+    unsigned char *stage = ring + (size_t)sidx * stage_bytes;
+    const bool got = mbar_wait_bounded(&bars[sidx], (gq / nstages) & 1u, gq == 0 ? first_wait : DD_WAIT_LIMIT);
+    bool fwd;
+    const SweepJob jb = get_job(b, jobs, q, fwd);
+    uint32_t off = 0;
+    for (int u = 0; u < jb.hi - jb.lo && ok; ++u) {
+      const int t = fwd ? jb.lo + u : jb.hi - 1 - u;
+      const TileMeta &mt = tm[b.tile0 + t];
+      const int par = (int)(sstep & 1u);
+      // merge the peer's previous results, then the step's gather sees them
+      for (int r = mlo + tid; r < mhi; r += nt) mdst[mbase + r] = xb[mpar * xbs + (r - mlo)];
+      __syncthreads();
+      bool cta_ok;
+      if (fwd) {
+        const int c0 = t * TB, WL = mt.wl;
+        const int r0 = fwd_split(WL, rank, CL), r1 = fwd_split(WL, rank + 1, CL);
+        const T *K = reinterpret_cast<const T *>(stage + off);
+        off += (uint32_t)((r1 - r0) * TB * sizeof(T));
+        const int32_t *src = reinterpret_cast<const int32_t *>(stage + off);
+        off += (uint32_t)(src_stride_w(WL) * sizeof(int32_t));
+        const bool wok = dd_check(st, WL <= wext && c0 + WL <= vext && r1 - r0 <= xbs, 31);
+        if (got && wok) {
+          for (int e = tid; e < TB; e += nt)
+            if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 32)) win[e] = vec[c0 + src[e]];
+          for (int e = max(r0, TB) + tid; e < r1; e += nt)
+            if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 32)) win[e] = vec[c0 + src[e]];
+        }
+        cta_ok = __syncthreads_and(got && wok) != 0;
+        if (cta_ok)
+          for (int r = r0 + tid; r < r1; r += nt) {
+            const CV *kr = reinterpret_cast<const CV *>(K + (r - r0) * TB);
+            const CV *wv = reinterpret_cast<const CV *>(win);
+            T a0 = (r < TB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+            for (int ch = 0; ch < TB / CN; ch += 4) {
+              a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
+              a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
+              a2 = Chunk<T>::fmadd(kr[(ch + 2) ^ (r & 7)], wv[ch + 2], a2);
+              a3 = Chunk<T>::fmadd(kr[(ch + 3) ^ (r & 7)], wv[ch + 3], a3);
+            }
+            const T v = (a0 + a1) + (a2 + a3);
+            vec[c0 + r] = v;
+            pxb[par * xbs + (r - r0)] = v;
+          }
+        mdst = vec;
+        mbase = c0;
+        mlo = fwd_split(WL, 1 - rank, CL);
+        mhi = fwd_split(WL, 2 - rank, CL);
+      } else {
+        // backward tile t: x_T = Kb [b_T; x_next], the CTA's BR rows, 8
+        // threads per row; the outputs never overlap this tile's inputs
+        const int r0 = t * TB, WU = mt.wu, nch = WU / CN;
+        const T *Kb = reinterpret_cast<const T *>(stage + off);
+        off += (uint32_t)(BR * WU * sizeof(T));
+        const int i = tid >> 3, h = tid & 7;
+        T acc = T(0);
+        const bool bok = dd_check(st, r0 + WU <= vext && BR <= xbs, 33);
+        if (got && bok) {
+          const CV *kr = reinterpret_cast<const CV *>(Kb + (int64_t)i * WU);
+          const CV *bv = reinterpret_cast<const CV *>(vec + r0);
+          const CV *xv = reinterpret_cast<const CV *>(xout + r0);
+          T a0 = T(0), a1 = T(0);
+          int ch = h;
+          for (; ch < TB / CN; ch += 8) a0 = Chunk<T>::fmadd(kr[ch], bv[ch], a0);
+          for (; ch + 8 < nch; ch += 16) {
+            a0 = Chunk<T>::fmadd(kr[ch], xv[ch], a0);
+            a1 = Chunk<T>::fmadd(kr[ch + 8], xv[ch + 8], a1);
+          }
+          if (ch < nch) a0 = Chunk<T>::fmadd(kr[ch], xv[ch], a0);
+          acc = a0 + a1;
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (h == 0) {
+          xout[r0 + rank * BR + i] = acc;
+          pxb[par * xbs + i] = acc;
+        }
+        cta_ok = __syncthreads_and(got && bok) != 0;
+        mdst = xout;
+        mbase = r0;
+        mlo = (1 - rank) * BR;
+        mhi = mlo + BR;
+      }
+      if (tid == 0) pokf[par] = cta_ok ? 1 : 0;
+      cluster_barrier();
+      const bool peer_ok = okf[par] != 0;
+      mpar = par;
+      ++sstep;
+      if (!(cta_ok && peer_ok)) ok = false;
+    }
+    if (!ok) break;
+    // the stage is free (every thread of the CTA passed the cluster barrier)
+    if (tid == 0 && q + nstages < nj) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_job<T, TB, CL>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx], rank, stage_bytes, st);
+    }
+  }
+  if (ok)
+    for (int r = mlo + tid; r < mhi; r += nt) mdst[mbase + r] = xb[mpar * xbs + (r - mlo)];
+  __syncthreads();
+  if (!ok) {
+    if (tid == 0) {
+      if (atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = task;
+    }
+    const int last_issued = min(nj - 1, q + nstages - 1);
+    for (int j = q; j <= last_issued; ++j) {
+      const uint32_t gj = jbase + j;
+      mbar_wait_bounded(&bars[gj % nstages], (gj / nstages) & 1u);
+    }
+  }
+  jbase += nj;
+  return ok;
+}
 // shared-memory layout: [bars | vec | xout | win | tile table | job table | ring]
 template <typename T, int TB>
 __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, int max_kl,
                                       int max_tiles, int max_jobs, uint64_t *&bars, T *&vec,
                                       T *&xout, T *&win, TileMeta *&tms, SweepJob *&jbs,
-                                      unsigned char *&ring) {
+                                      unsigned char *&ring, int cl = 1, T **xb = nullptr,
+                                      int32_t **okf = nullptr) {
   bars = reinterpret_cast<uint64_t *>(smraw);
+  if (okf) *okf = reinterpret_cast<int32_t *>(smraw + 48);  // 2 flags after <= 4 mbarriers
   vec = reinterpret_cast<T *>(smraw + 64);
   xout = vec + max_n + pad;
   win = xout + max_n + pad;
-  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + TB + max_kl + 8);
+  if (xb) *xb = win + TB + max_kl + 8;
+  size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + TB + max_kl + 8 +
+                                  (cl > 1 ? 2 * (size_t)sweep_xbs(TB, max_kl) : 0));
   used = (used + 15) & ~(size_t)15;
   tms = reinterpret_cast<TileMeta *>(smraw + used);
   used += sizeof(TileMeta) * (size_t)max_tiles;
@@ -803,13 +1020,52 @@ __device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
 
 // Tasks of CTA c: sched[sched_off[c] .. sched_off[c+1]) when a schedule is
 // given (more subdomains than resident CTAs), else the one task c.
-__device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, int &t1) {
-  t0 = sched_off ? sched_off[blockIdx.x] : (int)blockIdx.x;
-  t1 = sched_off ? sched_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+__device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, int &t1, int cid) {
+  t0 = sched_off ? sched_off[cid] : cid;
+  t1 = sched_off ? sched_off[cid + 1] : cid + 1;
+}
+
+// Cluster context of a sweep CTA: its rank, its task list index, and the
+// exchange buffers of the peer (CL = 2); CL = 1: rank 0, task list blockIdx.x.
+template <typename T, int CL>
+struct SweepCtx {
+  int rank = 0, cid = 0, xbs = 0;
+  T *xb = nullptr, *pxb = nullptr;
+  int32_t *okf = nullptr, *pokf = nullptr;
+  uint32_t sstep = 0;
+  __device__ void init(T *xb_, int32_t *okf_, int max_kl, int tb) {
+    cid = (int)blockIdx.x / CL;
+    if (CL > 1) {
+      namespace cgx = cooperative_groups;
+      cgx::cluster_group cl = cgx::this_cluster();
+      rank = (int)cl.block_rank();
+      xb = xb_;
+      okf = okf_;
+      xbs = sweep_xbs(tb, max_kl);
+      pxb = cl.map_shared_rank(xb_, (unsigned)(rank ^ 1));
+      pokf = cl.map_shared_rank(okf_, (unsigned)(rank ^ 1));
+      cluster_barrier();  // the peer runs before any store into its shared memory
+    }
+  }
+};
+
+template <typename T, int TB, int CL>
+__device__ __forceinline__ bool run_sweep(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
+                                          const T *ltile, const T *utile, const int32_t *srcs, T *vec,
+                                          T *xout, T *win, unsigned char *ring, uint32_t stage_bytes,
+                                          int nstages, uint64_t *bars, uint32_t &jbase, int task,
+                                          DevStatus *st, uint32_t first_wait, SweepCtx<T, CL> &cx, int wext,
+                                          int vext) {
+  if (CL == 1)
+    return sweep_pipelined<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
+                                  nstages, bars, jbase, task, true, st, first_wait, wext, vext);
+  return sweep_cluster<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
+                              bars, jbase, cx.sstep, task, st, first_wait, cx.xb, cx.xbs, cx.okf, cx.pxb,
+                              cx.pokf, cx.rank, wext, vext);
 }
 
 // z = A_jj^-1 y_j with y gathered from the original numbering.
-template <typename T, int TB>
+template <typename T, int TB, int CL>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -826,10 +1082,15 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
-  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  T *xb = nullptr;
+  int32_t *okf = nullptr;
+  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring, CL, &xb,
+               &okf);
   init_bars(bars, nstages);
+  SweepCtx<T, CL> cx;
+  cx.init(xb, okf, max_kl, TB);
   int t0, t1;
-  task_range(sched_off, t0, t1);
+  task_range(sched_off, t0, t1, cx.cid);
   uint32_t jbase = 0;
   for (int it = t0; it < t1; ++it) {
     const int task = sched ? sched[it] : it;
@@ -838,22 +1099,24 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     __syncthreads();  // the previous task's reads of the tables and vectors are done
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();  // the tables are staged: start the first copies, then gather y
-    if (threadIdx.x == 0) issue_first_jobs<T, TB>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
+    if (threadIdx.x == 0)
+      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
     const int ntot = b.nst * TB + pad;
     for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
       vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
       xout[i] = T(0);
     }
     __syncthreads();
-    if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, true, st, first_wait))
+    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
+                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot))
       return;
-    for (int i = threadIdx.x; i < b.n; i += blockDim.x) z[b.row0 + i] = xout[i];
+    // both CTAs of a cluster hold the whole result: each writes its share
+    for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) z[b.row0 + i] = xout[i];
   }
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
-template <typename T, int TB>
+template <typename T, int TB, int CL>
 __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -873,10 +1136,15 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
-  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring);
+  T *xb = nullptr;
+  int32_t *okf = nullptr;
+  carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring, CL, &xb,
+               &okf);
   init_bars(bars, nstages);
+  SweepCtx<T, CL> cx;
+  cx.init(xb, okf, max_kl, TB);
   int t0, t1;
-  task_range(sched_off, t0, t1);
+  task_range(sched_off, t0, t1, cx.cid);
   uint32_t jbase = 0;
   for (int it = t0; it < t1; ++it) {
     const int task = sched ? sched[it] : it;
@@ -885,7 +1153,8 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     __syncthreads();
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();
-    if (threadIdx.x == 0) issue_first_jobs<T, TB>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase);
+    if (threadIdx.x == 0)
+      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
     const int ntot = b.nst * TB + pad;
     for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
       T v = T(0);
@@ -897,10 +1166,10 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
       xout[i] = T(0);
     }
     __syncthreads();
-    if (!sweep_pipelined<T, TB>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                            nstages, bars, jbase, task, true, st, first_wait))
+    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
+                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot))
       return;
-    for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
+    for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) {
       const int r = b.row0 + i;
       x[perm[r]] = double(z1[r] - xout[i]);
     }
@@ -983,24 +1252,23 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, int tb, int max_tiles,
+static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, int tb, int cl, int max_tiles,
                                int max_jobs) {
   const int pad = sweep_pad_hd(max_kl, max_ku2);
-  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + tb + max_kl + 8);
+  size_t used = 64 + es * (2 * ((size_t)max_n + pad) + tb + max_kl + 8 +
+                           (cl > 1 ? 2 * (size_t)sweep_xbs(tb, max_kl) : 0));
   used = (used + 15) & ~(size_t)15;
   used += sizeof(TileMeta) * (size_t)max_tiles + sizeof(SweepJob) * (size_t)max_jobs;
   return (used + 127) & ~(size_t)127;
 }
 #define DD_SMEM_LIMIT (227 * 1024)
 #define DD_MAX_STAGES 4
-// stages of the ring at this stage size (0: two do not fit); the sweeps
-// run 8 threads per tile row, so the tile width is threads / 8
-int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_size,
-                      uint32_t stage_bytes) {
-  const int tb = threads / 8;
-  if (tb != 32 && tb != 64) return 0;
+// stages of the ring at this stage size (0: two do not fit) for tiles of tb
+// columns swept by clusters of cl CTAs
+int band_sweep_stages(int max_n, int max_kl, int max_ku2, int tb, int cl, int elem_size, uint32_t stage_bytes) {
+  if ((tb != 32 && tb != 64) || (cl != 1 && cl != 2)) return 0;
   // tables: at most max_n / tb tiles and twice as many jobs
-  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, max_n / tb,
+  size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, cl, max_n / tb,
                                  2 * (max_n / tb));
   if (stage_bytes == 0 || base + 2 * (size_t)stage_bytes > DD_SMEM_LIMIT) return 0;
   int s = (int)((DD_SMEM_LIMIT - base) / stage_bytes);
@@ -1010,8 +1278,8 @@ int band_sweep_stages(int max_n, int max_kl, int max_ku2, int threads, int elem_
 #define DD_LU_SMEM (200 * 1024)
 // largest ring stage (multiple of 128 bytes) that still leaves room for two
 // stages next to the resident vectors and tables; 0 if none does
-size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb) {
-  const size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, max_n / tb,
+size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, int tb, int cl) {
+  const size_t base = sweep_base_bytes(max_n, max_kl, max_ku2, (size_t)elem_size, tb, cl, max_n / tb,
                                        2 * (max_n / tb));
   if (base >= DD_SMEM_LIMIT) return 0;
   return ((DD_SMEM_LIMIT - base) / 2) & ~(size_t)127;
@@ -1078,23 +1346,49 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int TB>
+// one sweep launch: a plain grid, or clusters of cl CTAs
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_sweep(void (*kernel)(KArgs...), int grid, int threads, size_t smem, int cl,
+                                cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = cl > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename T, int TB, int CL>
+static size_t sweep_smem(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_bytes) {
+  const int mt = max_n / TB, mj = 2 * mt;
+  return sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, CL, mt, mj) + (size_t)ns * stage_bytes;
+}
+
+template <typename T, int TB, int CL>
 static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
                           int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
                           const int32_t *src, const double *y, const int32_t *perm, T *z, DevStatus *st,
                           cudaStream_t s) {
   const int mt = max_n / TB, mj = 2 * mt;
-  const int grid = pl.sched_off ? pl.grid : m;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * pl.stage_bytes;
-  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T, TB>, smem);
+  const int grid = pl.sched_off ? pl.grid : m * CL;
+  const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, pl.stage_bytes);
+  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T, TB, CL>, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  band_solve_fwd_kernel<T, TB><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                              pl.stage_bytes, tm, jobs, ltile, utile, src,
-                                                              y, perm, z, pl.sched, pl.sched_off,
-                                                              pl.task_sys, pl.act, st, pl.first_wait);
-  return cudaGetLastError();
+  return launch_sweep(band_solve_fwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
+                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, y, perm, z, pl.sched,
+                      pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait);
 }
+
+// tile width and cluster size of a plan: 8 TB / cl threads per CTA
+static inline int plan_tb(const SweepPlan &pl) { return pl.threads * pl.cl / 8; }
 
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
@@ -1102,34 +1396,36 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
                                   const SweepJob *jobs, const T *ltile, const T *utile,
                                   const int32_t *src, const double *y, const int32_t *perm, T *z,
                                   DevStatus *st, cudaStream_t s) {
-  // the backward tile step maps exactly 8 threads to each tile row
-  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
+  const int tb = plan_tb(pl);
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, pl.cl, sizeof(T), pl.stage_bytes);
   if (ns < 2) return cudaErrorInvalidValue;
-  if (pl.threads == 8 * 64)
-    return fwd_tb<T, 64>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
-  if (pl.threads == 8 * 32)
-    return fwd_tb<T, 32>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  // the backward tile step maps exactly 8 threads to each of the CTA's rows
+  if (tb == 64 && pl.cl == 1)
+    return fwd_tb<T, 64, 1>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  if (tb == 64 && pl.cl == 2)
+    return fwd_tb<T, 64, 2>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  if (tb == 32 && pl.cl == 1)
+    return fwd_tb<T, 32, 1>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
+  if (tb == 32 && pl.cl == 2)
+    return fwd_tb<T, 32, 2>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int TB>
+template <typename T, int TB, int CL>
 static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
                           int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
                           const int32_t *src, const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
                           const T *z2, const T *z1, const int32_t *perm, double *x, DevStatus *st,
                           cudaStream_t s) {
   const int mt = max_n / TB, mj = 2 * mt;
-  const int grid = pl.sched_off ? pl.grid : m;
-  size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * pl.stage_bytes;
-  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T, TB>, smem);
+  const int grid = pl.sched_off ? pl.grid : m * CL;
+  const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, pl.stage_bytes);
+  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T, TB, CL>, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  band_solve_bwd_kernel<T, TB><<<grid, pl.threads, smem, s>>>(d_info, max_n, max_kl, max_ku2, mt, mj, ns,
-                                                              pl.stage_bytes, tm, jobs, ltile, utile, src,
-                                                              e_ptr, e_col, e_val, z2, z1, perm, x,
-                                                              pl.sched, pl.sched_off, pl.task_sys, pl.act,
-                                                              st, pl.first_wait);
-  return cudaGetLastError();
+  return launch_sweep(band_solve_bwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
+                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, e_ptr, e_col, e_val, z2,
+                      z1, perm, x, pl.sched, pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait);
 }
 
 template <typename T>
@@ -1139,39 +1435,65 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
                                   const int32_t *src, const int32_t *e_ptr, const int32_t *e_col,
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
                                   double *x, DevStatus *st, cudaStream_t s) {
-  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, pl.threads, sizeof(T), pl.stage_bytes);
+  const int tb = plan_tb(pl);
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, pl.cl, sizeof(T), pl.stage_bytes);
   if (ns < 2) return cudaErrorInvalidValue;
-  if (pl.threads == 8 * 64)
-    return bwd_tb<T, 64>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, e_col,
-                         e_val, z2, z1, perm, x, st, s);
-  if (pl.threads == 8 * 32)
-    return bwd_tb<T, 32>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, e_col,
-                         e_val, z2, z1, perm, x, st, s);
+#define DD_BWD_CASE(TBV, CLV)                                                                           \
+  if (tb == TBV && pl.cl == CLV)                                                                       \
+    return bwd_tb<T, TBV, CLV>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, \
+                               e_col, e_val, z2, z1, perm, x, st, s);
+  DD_BWD_CASE(64, 1)
+  DD_BWD_CASE(64, 2)
+  DD_BWD_CASE(32, 1)
+  DD_BWD_CASE(32, 2)
+#undef DD_BWD_CASE
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int TB>
-static int occ_tb(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_bytes) {
-  const int mt = max_n / TB, mj = 2 * mt;
-  const size_t smem = sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, mt, mj) + (size_t)ns * stage_bytes;
-  if (ensure_smem(band_solve_fwd_kernel<T, TB>, smem) != cudaSuccess) return 0;
-  if (ensure_smem(band_solve_bwd_kernel<T, TB>, smem) != cudaSuccess) return 0;
+// Subdomains the sweep kernels hold resident at once at this stage size
+// (both kernels; the smaller): CTAs per SM times SMs for cl = 1, the device's
+// active clusters for cl = 2.  0 when they do not fit.
+template <typename T, int TB, int CL>
+static int slots_tb(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_bytes) {
+  const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (ensure_smem(band_solve_fwd_kernel<T, TB, CL>, smem) != cudaSuccess) return 0;
+  if (ensure_smem(band_solve_bwd_kernel<T, TB, CL>, smem) != cudaSuccess) return 0;
   int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T, TB>, 8 * TB, smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T, TB>, 8 * TB, smem) != cudaSuccess)
-    return 0;
+  if (CL == 1) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T, TB, CL>, 8 * TB, smem) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T, TB, CL>, 8 * TB, smem) != cudaSuccess)
+      return 0;
+    return (a < b ? a : b) * sms;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL * 64);
+  cfg.blockDim = dim3(8 * TB / CL);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&a, band_solve_fwd_kernel<T, TB, CL>, &cfg) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveClusters(&b, band_solve_bwd_kernel<T, TB, CL>, &cfg) != cudaSuccess) return 0;
   return a < b ? a : b;
 }
 
-// resident CTAs per SM of the two sweep kernels at this shared-memory size
-// (the smaller of the two), 0 on error
 template <typename T>
-int band_sweep_occupancy(int max_n, int max_kl, int max_ku2, int threads, uint32_t stage_bytes) {
-  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, threads, sizeof(T), stage_bytes);
+int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes) {
+  const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, cl, sizeof(T), stage_bytes);
   if (ns < 2) return 0;
-  if (threads == 8 * 64) return occ_tb<T, 64>(max_n, max_kl, max_ku2, ns, stage_bytes);
-  if (threads == 8 * 32) return occ_tb<T, 32>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (tb == 64 && cl == 1) return slots_tb<T, 64, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (tb == 64 && cl == 2) return slots_tb<T, 64, 2>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (tb == 32 && cl == 1) return slots_tb<T, 32, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
+  if (tb == 32 && cl == 2) return slots_tb<T, 32, 2>(max_n, max_kl, max_ku2, ns, stage_bytes);
   return 0;
 }
 
@@ -1220,7 +1542,7 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
       const BandInfo *, int, int, int, int, const SweepPlan &, const TileMeta *,                   \
       const SweepJob *, const T *, const T *, const int32_t *, const int32_t *, const int32_t *,    \
       const T *, const T *, const T *, const int32_t *, double *, DevStatus *, cudaStream_t);      \
-  template int band_sweep_occupancy<T>(int, int, int, int, uint32_t);                              \
+  template int band_sweep_slots<T>(int, int, int, int, int, uint32_t);                              \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \
                                                   const int64_t *, int, int, int, int,             \
                                                   const TileMeta *, const T *, const T *,          \

@@ -790,6 +790,60 @@ __global__ void block_gemm_kernel(const int32_t *__restrict__ P, const int64_t *
   }
 }
 
+// S_hat of the overlapped kinds, dense n_G x n_G: entry (r, c) belongs to
+// the block of the aggregate a holding min(r, c) when max(r, c) < agg[a+1] +
+// w[a] (the blocks placed in aggregate order, a later block overwriting the
+// overlap, leave exactly this), else it is 0.  Block a is q_a x q_a,
+// q_a = agg[a+1] - agg[a] + w[a], row-major at xoff[a] in Sx.
+template <typename T>
+__global__ void assemble_overlapped_kernel(int ng, int k, const int32_t *__restrict__ agg,
+                                           const int32_t *__restrict__ w, const int64_t *__restrict__ xoff,
+                                           const T *__restrict__ Sx, T *S) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ng * ng) return;
+  const int r = (int)(e / ng), c = (int)(e % ng);
+  const int lo = min(r, c), hi = max(r, c);
+  int a0 = 0, a1 = k;  // aggregate of lo: agg[a] <= lo < agg[a+1]
+  while (a1 - a0 > 1) {
+    const int mid = (a0 + a1) >> 1;
+    if (agg[mid] <= lo) a0 = mid; else a1 = mid;
+  }
+  const int q = agg[a0 + 1] - agg[a0] + w[a0];
+  T v = T(0);
+  if (hi < agg[a0] + q) v = Sx[xoff[a0] + (int64_t)(r - agg[a0]) * q + (c - agg[a0])];
+  S[e] = v;
+}
+
+// C_b = alpha A_b B_b + beta C_b for rectangular row-major blocks: dims
+// holds (M, N, K) and offs the offsets of A (M x K), B (K x N), C (M x N)
+// of block b; 16 x 16 output tiles, K in steps of 16.
+template <typename T>
+__global__ void rect_gemm_kernel(const int32_t *__restrict__ dims, const int64_t *__restrict__ offs,
+                                 const T *__restrict__ A, const T *__restrict__ Bm, T *C, T alpha, T beta) {
+  const int b = blockIdx.z;
+  const int M = dims[3 * b], N = dims[3 * b + 1], K = dims[3 * b + 2];
+  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+  if (r0 >= M || c0 >= N) return;
+  const T *a = A + offs[3 * b];
+  const T *bb = Bm + offs[3 * b + 1];
+  T *cc = C + offs[3 * b + 2];
+  __shared__ T As[16][17], Bs[16][17];
+  const int tr = threadIdx.y, tc = threadIdx.x;
+  T acc = T(0);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    As[tr][tc] = (r0 + tr < M && k0 + tc < K) ? a[(int64_t)(r0 + tr) * K + k0 + tc] : T(0);
+    Bs[tr][tc] = (k0 + tr < K && c0 + tc < N) ? bb[(int64_t)(k0 + tr) * N + c0 + tc] : T(0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc += As[tr][q] * Bs[q][tc];
+    __syncthreads();
+  }
+  if (r0 + tr < M && c0 + tc < N) {
+    T *o = &cc[(int64_t)(r0 + tr) * N + c0 + tc];
+    *o = alpha * acc + beta * *o;
+  }
+}
+
 // MSCNR: S -= diag(F Dinv E 1), one CTA per block.
 template <typename T>
 __global__ void mscnr_diag_kernel(const int32_t *__restrict__ P, const int64_t *__restrict__ off,
@@ -1018,6 +1072,24 @@ cudaError_t launch_schur_accumulate(int nj, const int32_t *jlist, const int32_t 
 }
 
 template <typename T>
+cudaError_t launch_assemble_overlapped(int ng, int k, const int32_t *agg, const int32_t *w, const int64_t *xoff,
+                                       const T *Sx, T *S, cudaStream_t s) {
+  const int64_t tot = (int64_t)ng * ng;
+  if (tot <= 0 || k <= 0) return cudaSuccess;
+  assemble_overlapped_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ng, k, agg, w, xoff, Sx, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rect_gemm(int nblk, const int32_t *dims, const int64_t *offs, int maxM, int maxN, const T *A,
+                             const T *B, T *C, T alpha, T beta, cudaStream_t s) {
+  if (nblk <= 0 || maxM <= 0 || maxN <= 0) return cudaSuccess;
+  dim3 grid((maxN + 15) / 16, (maxM + 15) / 16, nblk);
+  rect_gemm_kernel<T><<<grid, dim3(16, 16), 0, s>>>(dims, offs, A, B, C, alpha, beta);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_block_gemm(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax,
                               const T *A, const T *B, T *C, T alpha, T beta, cudaStream_t s) {
   if (nblk <= 0) return cudaSuccess;
@@ -1067,6 +1139,10 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                             double, DevStatus *, int, cudaStream_t);              \
   template cudaError_t launch_scatter_coo<T>(int64_t, const int64_t *, const double *, T *,       \
                                              cudaStream_t);                                        \
+  template cudaError_t launch_assemble_overlapped<T>(int, int, const int32_t *, const int32_t *,          \
+                                                     const int64_t *, const T *, T *, cudaStream_t);    \
+  template cudaError_t launch_rect_gemm<T>(int, const int32_t *, const int64_t *, int, int, const T *,     \
+                                           const T *, T *, T, T, cudaStream_t);                          \
   template cudaError_t launch_schur_accumulate<T>(                                                \
       int, const int32_t *, const int32_t *, const int32_t *, const int32_t *, const int32_t *,   \
       const int32_t *,                                                                            \

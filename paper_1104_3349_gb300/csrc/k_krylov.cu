@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(SellC c, const double *_
   if (sl >= c.nslices) return;
   const int row = __ldg(&c.row[gt]);
   if (row < 0) return;  // padding row of the last slice
+  if (!dd_check(c.st, row < c.n, 101)) return;
   if (MODE == 2 && !__ldg(&act[__ldg(&row_sys[row])])) return;
   const int64_t o = __ldg(&c.off[sl]);
   const int w = (int)((__ldg(&c.off[sl + 1]) - o) >> 5);
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(SellC c, const double *_
       }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (k0 + u < w) xx[u] = __ldg(x + ci[u]);
+      if (k0 + u < w) xx[u] = dd_check(c.st, (unsigned)ci[u] < (unsigned)c.n, 102) ? __ldg(x + ci[u]) : 0.0;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       if (k0 + u < w) acc = fma(vv[u], xx[u], acc);
@@ -366,9 +367,11 @@ __device__ void seg_column_sums(const SegMap &sm, int ncols, int pk, const doubl
 // separate
 //   1 partial dots V^T w, w^T w            2 column sums per system -> h1
 //   3 w -= V h1, partial dots V^T w        4 column sums -> h2
-//   5 w -= V h2, partial w^T w             6 CTA s: norm, Hessenberg column
-//                                            and rotations of system s
-//   7 w /= h_{j+1,j} unless breakdown
+//   5 w -= V h2, partial w^T w             6 every CTA: the system's norm from
+//                                            the partials, w *= 1/h_{j+1,j}
+//                                            unless breakdown; the system's
+//                                            first CTA: Hessenberg column and
+//                                            rotations
 // The FP64 pipe bounds this kernel on GB300, so reductions are kept to one
 // pass over the partials per column.  Sums run in a fixed order.
 // Per-system state (strides from sm.rmax): hc1/hc2 rmax+2, H (rmax+1)*rmax
@@ -424,20 +427,17 @@ __global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
     }
   }
   grid.sync();
-  // 6: CTA b takes systems b, b + nb, ...
-  for (int sys = b; sys < sm.nseg; sys += nb) {
-    if (sm.act && !sm.act[sys]) continue;
+  // 6: every CTA of a system sums the system's ||w||^2 partials in the same
+  // fixed order (so all hold the same bits), scales its own rows by 1/h_{j+1,j}
+  // unless the step broke down, and the system's first CTA also forms the
+  // Hessenberg column and applies the rotations; no further grid barrier
+  if (me.act) {
+    const int sys = me.s;
     const double *h1 = hc1 + (int64_t)sys * hst, *h2 = hc2 + (int64_t)sys * hst;
-    double *Hs = H + (int64_t)sys * (sm.rmax + 1) * sm.rmax;
-    double *css = cs + (int64_t)sys * sm.rmax, *sns = sn + (int64_t)sys * sm.rmax;
-    double *gs = g + (int64_t)sys * (sm.rmax + 1), *scs = scal + (int64_t)sys * 4;
     {
-      // ||w||^2 after, summed over the system's CTAs in order
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      const int b0 = sm.nseg == 1 ? 0 : sm.seg_cta0[sys];
-      const int b1 = sm.nseg == 1 ? nb : sm.seg_cta0[sys + 1];
       double t = 0.0;
-      for (int c = b0 + tid; c < b1; c += blockDim.x) t += partial[(int64_t)c * pk];
+      for (int c = me.c0 + tid; c < me.c0 + me.nc; c += blockDim.x) t += partial[(int64_t)c * pk];
       for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) red[warp] = t;
       __syncthreads();
@@ -448,41 +448,43 @@ __global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
       }
       __syncthreads();
     }
-    // column j of H (passes 1 + 2) and the rotations, in shared memory
-    for (int q = tid; q <= j; q += blockDim.x) hs[q] = h1[q] + h2[q];
-    __syncthreads();
-    if (tid == 0) {
-      const double hn = sqrt(hs[DD_CGS_MAXK]);
-      const double w0 = sqrt(h1[k]);
-      const bool breakdown = !(hn > 1e-14 * w0);
-      hs[j + 1] = hn;
-      for (int q = 0; q < j; ++q) {
-        const double a = hs[q], c2 = hs[q + 1], c = css[q], sv = sns[q];
-        hs[q] = c * a + sv * c2;
-        hs[q + 1] = -sv * a + c * c2;
-      }
-      const double a = hs[j], c2 = hs[j + 1];
-      const double r = hypot(a, c2);
-      css[j] = a / r;
-      sns[j] = c2 / r;
-      hs[j] = r;
-      hs[j + 1] = 0.0;
-      const double gj = gs[j];
-      gs[j + 1] = -sns[j] * gj;
-      gs[j] = css[j] * gj;
-      scs[0] = hn;
-      scs[1] = breakdown ? 1.0 : 0.0;
-      scs[2] = fabs(gs[j + 1]) / sqrt(bn2[sys]);
+    const double hn = sqrt(hs[DD_CGS_MAXK]);
+    const bool breakdown = !(hn > 1e-14 * sqrt(h1[k]));
+    if (!breakdown) {
+      const double inv = 1.0 / hn;
+      for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] *= inv;
     }
-    __syncthreads();
-    for (int q = tid; q <= j + 1; q += blockDim.x) Hs[(int64_t)q * R + j] = hs[q];
-    __syncthreads();
-  }
-  grid.sync();
-  // 7
-  if (me.act && scal[(int64_t)me.s * 4 + 1] == 0.0) {
-    const double hn = scal[(int64_t)me.s * 4];
-    for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] /= hn;
+    if (b == me.c0) {
+      double *Hs = H + (int64_t)sys * (sm.rmax + 1) * sm.rmax;
+      double *css = cs + (int64_t)sys * sm.rmax, *sns = sn + (int64_t)sys * sm.rmax;
+      double *gs = g + (int64_t)sys * (sm.rmax + 1), *scs = scal + (int64_t)sys * 4;
+      // column j of H (passes 1 + 2) and the rotations, in shared memory
+      __syncthreads();
+      for (int q = tid; q <= j; q += blockDim.x) hs[q] = h1[q] + h2[q];
+      __syncthreads();
+      if (tid == 0) {
+        hs[j + 1] = hn;
+        for (int q = 0; q < j; ++q) {
+          const double a = hs[q], c2 = hs[q + 1], c = css[q], sv = sns[q];
+          hs[q] = c * a + sv * c2;
+          hs[q + 1] = -sv * a + c * c2;
+        }
+        const double a = hs[j], c2 = hs[j + 1];
+        const double r = hypot(a, c2);
+        css[j] = a / r;
+        sns[j] = c2 / r;
+        hs[j] = r;
+        hs[j + 1] = 0.0;
+        const double gj = gs[j];
+        gs[j + 1] = -sns[j] * gj;
+        gs[j] = css[j] * gj;
+        scs[0] = hn;
+        scs[1] = breakdown ? 1.0 : 0.0;
+        scs[2] = fabs(gs[j + 1]) / sqrt(bn2[sys]);
+      }
+      __syncthreads();
+      for (int q = tid; q <= j + 1; q += blockDim.x) Hs[(int64_t)q * R + j] = hs[q];
+    }
   }
 }
 

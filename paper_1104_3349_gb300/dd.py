@@ -19,6 +19,9 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_ROOT, "_build")
 LIB_PATH = os.path.join(_PKG, "libdd.so")
+# the checked build (-DDD_CHECKED): device index, size and alignment checks
+# that record DD_ERR_CHECK instead of faulting; selected with DD_CHECKED=1
+LIB_CHECKED_PATH = os.path.join(_PKG, "libdd_checked.so")
 SOURCES = ["dd_api.cu", "k_band.cu", "k_dense.cu", "k_krylov.cu", "k_mlp.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
@@ -27,10 +30,12 @@ DD_EXACT, DD_MSCE_INF, DD_MSCN, DD_MSCNR, DD_LUM = 0, 1, 2, 3, 4
 DD_FP64, DD_FP32 = 0, 1
 STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_INVALID_ARG", 2: "DD_ERR_INVALID_PARTITION",
                 3: "DD_ERR_SINGULAR_BLOCK", 4: "DD_ERR_SINGULAR_SCHUR", 5: "DD_ERR_NOT_CONVERGED",
-                6: "DD_ERR_NONFINITE", 7: "DD_ERR_TIMEOUT", 8: "DD_ERR_OOM", 9: "DD_ERR_CUDA"}
+                6: "DD_ERR_NONFINITE", 7: "DD_ERR_TIMEOUT", 8: "DD_ERR_OOM", 9: "DD_ERR_CUDA",
+                10: "DD_ERR_CHECK"}
 DD_LEARNED = 5
+DD_OMSCN, DD_OMSCNR, DD_OLUM, DD_MSCE = 6, 7, 8, 9
 KINDS = {"exact": DD_EXACT, "msce_inf": DD_MSCE_INF, "mscn": DD_MSCN, "mscnr": DD_MSCNR, "lum": DD_LUM,
-         "learned": DD_LEARNED}
+         "learned": DD_LEARNED, "omscn": DD_OMSCN, "omscnr": DD_OMSCNR, "olum": DD_OLUM, "msce": DD_MSCE}
 MLP_IN, MLP_HIDDEN = 14, 64
 MLP_NPARAM = MLP_HIDDEN * MLP_IN + 2 * MLP_HIDDEN + 1
 
@@ -40,31 +45,43 @@ def _nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA sources for sm_103a (in parallel) and link libdd.so in-tree."""
-    os.makedirs(_BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False, both: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (in parallel) and link libdd.so
+    in-tree (checked: libdd_checked.so with -DDD_CHECKED; both: the two
+    libraries, compiled side by side).  Returns the path of the library
+    asked for (the plain one with both)."""
+    variants = [False, True] if both else [checked]
     srcs = [os.path.join(_CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(_CSRC, "dd_internal.h"), os.path.join(_INCLUDE, "dd.h")]
-    if not force and os.path.exists(LIB_PATH):
-        t = os.path.getmtime(LIB_PATH)
-        if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB_PATH
+    todo = []
+    for chk in variants:
+        path = LIB_CHECKED_PATH if chk else LIB_PATH
+        if force or not os.path.exists(path) or any(os.path.getmtime(d) > os.path.getmtime(path) for d in deps):
+            todo.append(chk)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(_BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, chk = job
+        bdir = os.path.join(_BUILD, "checked" if chk else "plain")
+        os.makedirs(bdir, exist_ok=True)
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, *(["-DDD_CHECKED"] if chk else []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    subprocess.check_call([nvcc, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    if todo:
+        jobs = [(src, chk) for chk in todo for src in srcs]
+        with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            objs = list(ex.map(compile_one, jobs))
+        for chk in todo:
+            path = LIB_CHECKED_PATH if chk else LIB_PATH
+            mine = [o for (src, c), o in zip(jobs, objs) if c == chk]
+            tmp = path + f".{os.getpid()}.tmp"
+            subprocess.check_call([nvcc, "-shared", "-o", tmp, *mine, "-lcudart"])
+            os.replace(tmp, path)
+    return LIB_CHECKED_PATH if (checked and not both) else LIB_PATH
 
 
 class dd_csr(ctypes.Structure):
@@ -80,8 +97,8 @@ class dd_partition(ctypes.Structure):
 class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
-                ("time_kernels", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("mlp_weights", ctypes.c_char_p)]
+                ("time_kernels", ctypes.c_int32), ("sweep_cluster", ctypes.c_int32),
+                ("mlp_weights", ctypes.c_char_p), ("overlap", ctypes.c_int32), ("radius", ctypes.c_int32)]
 
 
 class dd_info(ctypes.Structure):
@@ -102,7 +119,7 @@ class dd_stats(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32), ("learned_entries", ctypes.c_int64),
                 ("learned_fallback", ctypes.c_int32), ("pad3", ctypes.c_int32),
                 ("krylov_steps", ctypes.c_int64), ("cgs2_ms", ctypes.c_double), ("cgs2_fma", ctypes.c_double),
-                ("spmv_ms", ctypes.c_double)]
+                ("spmv_ms", ctypes.c_double), ("sweep_cluster", ctypes.c_int32), ("msce_nodes_max", ctypes.c_int32)]
 
 
 EXPORTS = ["dd_setup", "dd_setup_batched", "dd_apply", "dd_apply_part", "dd_apply_noalloc", "gmres_solve",
@@ -115,11 +132,14 @@ NOALLOC_MAX_ELEMS = 1 << 20
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libdd.so; raises if it has not been built (no fallback path exists)."""
+def load(path: str = None):
+    """Load libdd.so (libdd_checked.so when DD_CHECKED=1 in the environment);
+    raises if it has not been built (no fallback path exists)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_CHECKED_PATH if os.environ.get("DD_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libdd.so not built ({path}); run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
@@ -212,7 +232,8 @@ class DD:
 
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
-                 autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False):
+                 autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False, sweep_cluster=0,
+                 overlap=0, radius=0):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -226,6 +247,9 @@ class DD:
         o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
                     int(krylov_ctas_per_sm))
         o.time_kernels = int(bool(time_kernels))
+        o.sweep_cluster = int(sweep_cluster)
+        o.overlap = int(overlap)
+        o.radius = int(radius)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
@@ -328,7 +352,7 @@ class DDBatch:
     """A batch of independent systems behind one handle (dd_setup_batched)."""
 
     def __init__(self, systems, kind="msce_inf", prec=DD_FP64, pivot_tol=0.0, max_restart=50, stream=None,
-                 use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0):
+                 use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, sweep_cluster=0):
         """systems: list of (A, part, m, perm, agg_offsets) with A a CSR (perm, agg_offsets may be None)."""
         lib = load()
         self._lib = lib
@@ -348,6 +372,7 @@ class DDBatch:
             pts[q] = dd_partition(int(m), _ptr(pa), _ptr(pe), 64, _ptr(ag), 0 if ag is None else len(ag) - 1)
         o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
                     int(krylov_ctas_per_sm))
+        o.sweep_cluster = int(sweep_cluster)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)

@@ -39,11 +39,14 @@ def _systems(ws):
     return [(w.A, w.part, w.m, w.perm, w.agg) for w in ws]
 
 
-def test_batched_apply_matches_each_oracle(env, small_batch):
+@pytest.mark.parametrize("cl", [1, 2])
+def test_batched_apply_matches_each_oracle(env, small_batch, cl):
+    """1664 subdomains on persistent task lists, one CTA or a 2-CTA cluster each."""
     torch, dd, dev = env
     ws = small_batch
-    P = dd.DDBatch(_systems(ws), "msce_inf")
+    P = dd.DDBatch(_systems(ws), "msce_inf", sweep_cluster=cl)
     st = P.stats()
+    assert st["sweep_cluster"] == cl
     assert st["batch"] == len(ws) and st["m"] == sum(w.m for w in ws)
     assert st["sweep_grid"] < st["m"]  # the persistent task lists are in use
     ys = [W.uniform(1 + q, w.A.n) for q, w in enumerate(ws)]

@@ -40,9 +40,11 @@ def _handle(dd, w, agg, prec):
     return dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
 
 
-def test_apply_fp64_full_size(full):
+@pytest.mark.parametrize("cl", [1, 2])
+def test_apply_fp64_full_size(full, cl):
     torch, dd, dev, w, agg, y, xr, ro = full
-    P = _handle(dd, w, agg, dd.DD_FP64)
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=dd.DD_FP64, sweep_cluster=cl)
+    assert P.stats()["sweep_cluster"] == cl
     st = P.stats()
     assert st["n_agg"] == len(agg) - 1 and st["max_agg"] >= 630
     yd = torch.from_numpy(y).to(dev)
@@ -50,7 +52,7 @@ def test_apply_fp64_full_size(full):
     P.apply(yd, xd)
     assert P.check_status() == 0
     err = np.linalg.norm(xd.cpu().numpy() - xr) / np.linalg.norm(xr)
-    print(f"FP64 apply at 256x256, relative error vs oracle: {err:.3e}")
+    print(f"FP64 apply at 256x256 ({cl} CTA per subdomain), relative error vs oracle: {err:.3e}")
     assert err <= 1e-10, err
     P.close()
 

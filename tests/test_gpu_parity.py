@@ -218,3 +218,32 @@ def test_nonfinite_rhs(torch_dev, cav32):
     bd = torch.from_numpy(b).to(dev)
     r = P.gmres(bd, torch.empty_like(bd))
     assert r["status"] == 6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("grid,m,sz", [(32, 4, 64), (20, 4, 33), (12, 8, 16), (6, 2, 5)])
+def test_cluster_sweeps_equal_single_cta(torch_dev, prec, grid, m, sz):
+    """The interior sweeps split over a 2-CTA cluster compute every row as the
+    one-CTA sweeps do: the applies agree bit for bit, and with the oracle."""
+    torch, dev = torch_dev
+    from paper_1104_3349_gb300 import dd
+    w = W.make_workload("t", grid, 0.02, 1.0, W.WIND_FOURIER, grid, m, sz=sz)
+    try:
+        R = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=w.agg)
+    except O.OracleError:
+        pytest.skip("no preconditioner for this partition")
+    y = W.uniform(1, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xs = []
+    for cl in (1, 2):
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=w.agg, prec=prec, sweep_cluster=cl)
+        assert P.stats()["sweep_cluster"] == cl
+        xd = torch.full_like(yd, float("nan"))
+        P.apply(yd, xd)
+        assert P.check_status() == 0
+        xs.append(xd.cpu().numpy())
+        P.close()
+    assert np.array_equal(xs[0].view(np.uint64), xs[1].view(np.uint64))
+    xr = R.apply(y)
+    err = np.linalg.norm(xs[1] - xr) / np.linalg.norm(xr)
+    assert err <= (1e-10 if prec == 0 else 1e-4), err
