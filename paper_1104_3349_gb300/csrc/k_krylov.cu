@@ -28,7 +28,7 @@ namespace {
 //   system is still stepping (act[row_sys[row]] != 0), others untouched.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(256) sell_spmv_kernel(SellC c, const double *__restrict__ x,
+__global__ void __launch_bounds__(256, 6) sell_spmv_kernel(SellC c, const double *__restrict__ x,
                                                         const double *__restrict__ b, double *__restrict__ y,
                                                         const int32_t *__restrict__ row_sys,
                                                         const int32_t *__restrict__ act) {
@@ -235,73 +235,80 @@ __device__ __forceinline__ double warp_sum_t(double (&a)[G]) {
   return e;
 }
 
-// partial dots of columns q0 .. q0+G-1 (those below ktot): G independent
-// accumulators per thread over its rows, the transposed butterfly per warp,
-// then the warps through shared memory in a fixed order.  Column k is w's
-// own square when `self`.
-template <int G>
-__device__ void dots_group(int i0, int i1, int q0, int k, int ktot, const double *__restrict__ V, int64_t ldv,
-                           const double *__restrict__ w, bool self, double *out, double *red) {
-  constexpr int LOG = G == 16 ? 4 : (G == 8 ? 3 : 2);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  double a[G];
-#pragma unroll
-  for (int s2 = 0; s2 < G; ++s2) a[s2] = 0.0;
-  if (q0 + G <= k) {  // every column a basis vector: no tests in the loop
-    for (int i = i0 + tid; i < i1; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int s2 = 0; s2 < G; ++s2) a[s2] += V[(int64_t)(q0 + s2) * ldv + i] * wi;
-    }
-  } else {
-    for (int i = i0 + tid; i < i1; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int s2 = 0; s2 < G; ++s2) {
-        const int q = q0 + s2;
-        if (q < k) a[s2] += V[(int64_t)q * ldv + i] * wi;
-        else if (q == k && self) a[s2] += wi * wi;
-      }
-    }
-  }
-  const double ws = warp_sum_t<G>(a);
-  if ((lane & ((32 / G) - 1)) == 0) {
-    int v = 0;
-#pragma unroll
-    for (int st = 0; st < LOG; ++st) v += ((lane >> (4 - st)) & 1) * (G >> (st + 1));
-    red[warp * 16 + v] = ws;
-  }
-  __syncthreads();
-  if (tid < G && q0 + tid < ktot) {
-    double t = 0.0;
-    for (int ww = 0; ww < nw; ++ww) t += red[ww * 16 + tid];
-    out[q0 + tid] = t;
-  }
-  __syncthreads();
-}
-
-// partial dots of all ktot = k (+1 with self) columns in groups of exact
-// width 16, then 8, then 4 (the last group padded by at most 3 columns)
+// Partial dots of the ktot = k (+1 with self: w's own square) columns over
+// this CTA's rows.  Columns go in groups of 4; one pass takes up to 8 groups
+// and gives each R threads (R a multiple of 32, so a warp stays inside one
+// group and its loads of a column are coalesced).  A thread accumulates its
+// 4 columns over rows i0 + r, i0 + r + R, ..., two rows per iteration; each
+// warp then sums its 4 values by the transposed butterfly and the warps of a
+// group are summed through shared memory in a fixed order.  Splitting the
+// columns over threads cuts the partial sums to reduce (and the FP64 additions
+// that reduce them) to R per column instead of one per CTA thread.
 __device__ void block_dots(int i0, int i1, int k, const double *__restrict__ V, int64_t ldv,
                            const double *__restrict__ w, bool self, double *out, double *red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   const int ktot = k + (self ? 1 : 0);
-  int q0 = 0;
-  for (; ktot - q0 >= 16; q0 += 16) dots_group<16>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red);
-  if (ktot - q0 >= 8) { dots_group<8>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red); q0 += 8; }
-  for (; q0 < ktot; q0 += 4) dots_group<4>(i0, i1, q0, k, ktot, V, ldv, w, self, out, red);
+  const int ngroups = (ktot + 3) / 4;
+  for (int g0 = 0; g0 < ngroups; g0 += 8) {
+    const int gn = min(8, ngroups - g0);
+    const int R = (nt / gn) & ~31;
+    const int cg = tid / R, rl = tid % R;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    if (cg < gn) {
+      const int q0 = (g0 + cg) * 4;
+      if (q0 + 4 <= k) {  // four basis columns: no tests in the loop
+        const double *v0 = V + (int64_t)q0 * ldv;
+        int i = i0 + rl;
+        for (; i + R < i1; i += 2 * R) {
+          const double wa = w[i], wb = w[i + R];
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2) {
+            a[s2] += v0[(int64_t)s2 * ldv + i] * wa;
+            a[s2] += v0[(int64_t)s2 * ldv + i + R] * wb;
+          }
+        }
+        if (i < i1) {
+          const double wa = w[i];
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2) a[s2] += v0[(int64_t)s2 * ldv + i] * wa;
+        }
+      } else {
+        for (int i = i0 + rl; i < i1; i += R) {
+          const double wi = w[i];
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2) {
+            const int q = q0 + s2;
+            if (q < k) a[s2] += V[(int64_t)q * ldv + i] * wi;
+            else if (q == k && self) a[s2] += wi * wi;
+          }
+        }
+      }
+    }
+    const double ws = warp_sum_t<4>(a);
+    if ((lane & 7) == 0) red[warp * 4 + ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1)] = ws;
+    __syncthreads();
+    if (tid < gn * 4) {
+      const int gg = tid >> 2, s2 = tid & 3, q = (g0 + gg) * 4 + s2;
+      if (q < ktot) {
+        double t = 0.0;
+        for (int ww = gg * (R >> 5); ww < (gg + 1) * (R >> 5); ++ww) t += red[ww * 4 + s2];
+        out[q] = t;
+      }
+    }
+    __syncthreads();
+  }
 }
 
-// w_i - sum_q h_q V_q[i], eight loads in flight per thread
+// w_i - sum_q h_q V_q[i] as one chain of fused multiply-adds: on GB300 the
+// FP64 pipe's issue rate, not its latency, bounds this loop, so extra
+// accumulators would only add the FP64 additions that combine them; the
+// loads are independent of the chain and stay in flight
 __device__ __forceinline__ double row_update(int i, int k, const double *__restrict__ V, int64_t ldv,
                                              const double *hs, double wi) {
-  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int q = 0;
-  for (; q + 8 <= k; q += 8) {
-#pragma unroll
-    for (int s2 = 0; s2 < 8; ++s2) a[s2] += hs[q + s2] * V[(int64_t)(q + s2) * ldv + i];
-  }
-  for (; q < k; ++q) a[0] += hs[q] * V[(int64_t)q * ldv + i];
-  return wi - (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+  double s = wi;
+#pragma unroll 8
+  for (int q = 0; q < k; ++q) s = fma(-hs[q], V[(int64_t)q * ldv + i], s);
+  return s;
 }
 
 // The rows, CTAs and per-system state a CTA works on.  With one system the
