@@ -1102,9 +1102,26 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     if (threadIdx.x == 0)
       issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
     const int ntot = b.nst * TB + pad;
-    for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
-      vec[i] = (i < b.n) ? T(y[perm[b.row0 + i]]) : T(0);
-      xout[i] = T(0);
+    // y gathered through perm: eight indices, then eight values, in flight
+    // per thread (a chain of dependent loads per element took ~8 us)
+    for (int i0 = threadIdx.x; i0 < ntot; i0 += 8 * blockDim.x) {
+      int idx[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        idx[u] = (i < b.n) ? __ldg(&perm[b.row0 + i]) : -1;
+      }
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? __ldg(&y[idx[u]]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < ntot) {
+          vec[i] = T(v[u]);
+          xout[i] = T(0);
+        }
+      }
     }
     __syncthreads();
     if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
@@ -1156,14 +1173,31 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     if (threadIdx.x == 0)
       issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
     const int ntot = b.nst * TB + pad;
-    for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
-      T v = T(0);
-      if (i < b.n) {
-        const int r = b.row0 + i;
-        for (int k = e_ptr[r]; k < e_ptr[r + 1]; ++k) v += e_val[k] * z2[e_col[k]];
+    // (E z2) of the subdomain's rows: the row bounds of eight rows, then their
+    // entries, loaded before use (rows of E hold 0-2 entries)
+    for (int i0 = threadIdx.x; i0 < ntot; i0 += 8 * blockDim.x) {
+      int k0[8], k1[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        k0[u] = (i < b.n) ? __ldg(&e_ptr[b.row0 + i]) : 0;
+        k1[u] = (i < b.n) ? __ldg(&e_ptr[b.row0 + i + 1]) : 0;
       }
-      vec[i] = v;
-      xout[i] = T(0);
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        T acc = T(0);
+        for (int k = k0[u]; k < k1[u]; ++k) acc += e_val[k] * z2[e_col[k]];
+        v[u] = acc;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < ntot) {
+          vec[i] = v[u];
+          xout[i] = T(0);
+        }
+      }
     }
     __syncthreads();
     if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
