@@ -121,7 +121,8 @@ typedef struct {
                          candidate ring-stage size (and with it CTAs per SM)
                          and keeps the fastest; 0: the fixed default           */
   int32_t krylov_ctas_per_sm; /* CTAs per SM of the Krylov kernels (CGS2 and the
-                         batched norms); <= 0 selects 2                          */
+                         batched norms); <= 0 selects 1 with 512-thread CGS2
+                         CTAs, else 2                                           */
   int32_t time_kernels;/* 1: gmres_solve times the SpMV and CGS2 launches of
                          every Arnoldi step with CUDA events (dd_stats
                          krylov_steps, cgs2_ms, cgs2_fma, spmv_ms); ignored
@@ -134,6 +135,10 @@ typedef struct {
                               (format under dd_mlp_*); ignored otherwise       */
   int32_t overlap;    /* DD_OMSCN / DD_OMSCNR / DD_OLUM: overlap width w >= 0   */
   int32_t radius;     /* DD_MSCE: path-length radius r >= 0                     */
+  int32_t krylov_threads; /* threads per CTA of the CGS2 kernel: 256 or 512;
+                         <= 0 selects 512 (then krylov_ctas_per_sm <= 0
+                         selects 1)                                            */
+  int32_t pad_opts;
 } dd_opts;
 
 typedef struct {

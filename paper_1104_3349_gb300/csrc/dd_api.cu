@@ -92,8 +92,10 @@ struct DDHandle {
   // CUDA graphs of the Arnoldi steps (use_graph), one per step index
   int use_graph = 0, graph_key = -1;
   int krylov_per_sm = 2;
+  int krylov_threads = 256;    // threads per CTA of the CGS2 kernel (256 or 512)
   int time_kernels = 0;        // events around the SpMV and CGS2 of every Arnoldi step
   cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t sev[2] = {nullptr, nullptr};  // end of Arnoldi steps j (parity): the host waits on them
   std::vector<cudaGraphExec_t> gexec;
   std::vector<int64_t> glaunch;
   cudaStream_t gstream = nullptr;
@@ -1620,7 +1622,7 @@ dd_status alloc_krylov(DDHandle *h, int R) {
   TRY(dalloc(h, &h->hc2, (size_t)S * (R + 2)));
   TRY(dalloc(h, &h->nsq, 4));
   TRY(dalloc(h, &h->out, (size_t)S * 4));
-  h->cgs_blocks = cgs2_blocks(h->krylov_per_sm, 1024);
+  h->cgs_blocks = cgs2_blocks(h->krylov_per_sm, 1024, h->krylov_threads);
   if (h->cgs_blocks <= 0) { h->err = "no resident blocks for the cooperative CGS2 kernel"; return DD_ERR_CUDA; }
   TRY(dalloc(h, &h->partial, 3 * (size_t)std::max(h->nblocks, h->cgs_blocks) * (R + 2)));
   TRY(dalloc(h, &h->r, h->ldv));
@@ -1729,9 +1731,13 @@ dd_status arnoldi_step(DDHandle *h, int j, int R, const SegMap &sm, int ncta, co
     CK(launch_spmv(h->sell, zj, w, s));
   if (timed) CK(cudaEventRecord(h->kev[1], s));
   CK(launch_cgs2(h->n, j, R, h->V, h->ldv, w, h->partial, h->Rmax + 2, h->hc1, h->hc2, h->H, h->cs,
-                 h->sn, h->g, bn2, h->out, sm, ncta, s));
+                 h->sn, h->g, bn2, h->out, sm, ncta, h->krylov_threads, s));
   if (timed) CK(cudaEventRecord(h->kev[2], s));
-  CK(cudaMemcpyAsync(h->h_out, h->out, sizeof(double) * 4 * sm.nseg, cudaMemcpyDeviceToHost, s));
+  // one system: the scalars of steps j and j + 1 go to different halves of
+  // the pinned buffer, so a step launched ahead cannot overwrite the ones the
+  // host is about to read
+  double *dst = sm.nseg > 1 ? h->h_out : h->h_out + 4 * (j & 1);
+  CK(cudaMemcpyAsync(dst, h->out, sizeof(double) * 4 * sm.nseg, cudaMemcpyDeviceToHost, s));
   return DD_OK;
 }
 
@@ -1818,10 +1824,24 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
     TRY(norm_sq(h, h->r, 0, s));
     CK(launch_init_g(h->g, R, h->nsq, s));
     CK(launch_copy_scaled(n, h->r, h->nsq, h->V, s));
-    int jlast = -1;
+    int jlast = -1, launched = -1;
     for (int j = 0; j < R; ++j) {
-      TRY(run_step(h, j, R, sm, h->cgs_blocks, h->nsq + 2, s));
-      CK(cudaStreamSynchronize(s));
+      // Step j + 1 is launched before the host reads step j's residual
+      // estimate, so the GPU never waits for the host between steps.  When
+      // step j ends the cycle, the extra step has only written column j + 1
+      // of H, g[j + 1] and V_{j+2}, none of which the update of x or the next
+      // cycle reads: the iterates are those of stepping one at a time.
+      if (launched < j) {
+        TRY(run_step(h, j, R, sm, h->cgs_blocks, h->nsq + 2, s));
+        CK(cudaEventRecord(h->sev[j & 1], s));
+        launched = j;
+      }
+      if (!h->time_kernels && j + 1 < R && iters + 1 < maxit) {
+        TRY(run_step(h, j + 1, R, sm, h->cgs_blocks, h->nsq + 2, s));
+        CK(cudaEventRecord(h->sev[(j + 1) & 1], s));
+        launched = j + 1;
+      }
+      CK(cudaEventSynchronize(h->sev[j & 1]));
       if (h->time_kernels) {
         float t0 = 0.f, t1 = 0.f;
         CK(cudaEventElapsedTime(&t0, h->kev[0], h->kev[1]));
@@ -1832,8 +1852,8 @@ dd_status fgmres(DDHandle *h, const double *b, double *x, double tol, int R, int
         h->stats.cgs2_fma += (4.0 * (j + 1) + 2.0) * (double)n;
       }
       ++iters;
-      const double est = h->h_out[2];
-      const bool breakdown = h->h_out[1] != 0.0;
+      const double est = h->h_out[4 * (j & 1) + 2];
+      const bool breakdown = h->h_out[4 * (j & 1) + 1] != 0.0;
       if (info && info->history && iters - 1 < info->history_cap) info->history[iters - 1] = est;
       jlast = j;
       if (!isfinite(est)) {
@@ -1985,6 +2005,8 @@ void release(DDHandle *h) {
     if (e) { cudaEventDestroy(e); e = nullptr; }
   for (cudaEvent_t &e : h->kev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
+  for (cudaEvent_t &e : h->sev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
   for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
   cudaStreamSynchronize(h->stream);
@@ -2112,7 +2134,15 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->prec = o.prec;
   h->kind = approx;
   h->use_graph = o.use_graph != 0;
-  h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : 2;
+  if (o.krylov_threads != 0 && o.krylov_threads != 256 && o.krylov_threads != 512) {
+    h->err = "krylov_threads must be 0, 256 or 512";
+    return DD_ERR_INVALID_ARG;
+  }
+  // default: one 512-thread CTA per SM (fewer CTAs per grid barrier; measured
+  // 80.5 us per CGS2 step on the 256x256 workload against 83.9 with two
+  // 256-thread CTAs per SM)
+  h->krylov_threads = o.krylov_threads > 0 ? o.krylov_threads : 512;
+  h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : (h->krylov_threads == 512 ? 1 : 2);
   h->time_kernels = o.time_kernels != 0 && !h->use_graph;
   if (o.sweep_cluster < 0 || o.sweep_cluster > 2) { h->err = "sweep_cluster must be 0, 1 or 2"; return DD_ERR_INVALID_ARG; }
   h->sweep_cl_opt = o.sweep_cluster;
@@ -2158,6 +2188,11 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
         rc = DD_ERR_CUDA;
       }
     }
+    for (cudaEvent_t &e : h->sev)
+      if (rc == DD_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        h->err = "event creation failed";
+        rc = DD_ERR_CUDA;
+      }
     if (rc == DD_OK && h->time_kernels)
       for (cudaEvent_t &e : h->kev)
         if (cudaEventCreate(&e) != cudaSuccess) { h->err = "event creation failed"; rc = DD_ERR_CUDA; break; }

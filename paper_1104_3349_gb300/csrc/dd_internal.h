@@ -288,10 +288,12 @@ cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s);
 cudaError_t launch_zero(double *p, int64_t n, cudaStream_t s);
 // One Arnoldi orthogonalisation step (CGS2 + Givens + normalisation) as a
 // single cooperative kernel; partial holds nblocks * pk doubles, pk >= R + 2.
-int cgs2_blocks(int per_sm, int cap);
+int cgs2_blocks(int per_sm, int cap, int threads);
+// threads: 256 or 512 per CTA
 cudaError_t launch_cgs2(int64_t n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
                         int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
-                        const double *bn2, double *scal, const SegMap &sm, int nblocks, cudaStream_t s);
+                        const double *bn2, double *scal, const SegMap &sm, int nblocks, int threads,
+                        cudaStream_t s);
 // Batched FGMRES over a SegMap (nseg >= 2, nblocks = seg_cta0[nseg] CTAs):
 // out[s] = ||v_s||^2; v0 = r / ||r_s|| and g_s = ||r_s|| e_0 for active
 // systems; y_s = H_s^-1 g_s and x_s += Z y_s for systems with jl[s] >= 0.

@@ -205,7 +205,31 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
   for (int t = 0; t < b.ntiles; ++t) {
     const int c0 = t * DD_NB;
     const int nbe = min(DD_NB, n - c0);
-    // load the window: a warp per row, lanes along the row's band entries,
+    // load the window.  In shared memory: every element by an asynchronous
+    // copy (positions outside the band or the matrix are filled with zeros by
+    // a zero source size), all in flight before one wait: the warp-per-row
+    // loads below waited ~30 times per panel for a dependent round of loads.
+    if (__isShared(W)) {
+      for (int r = warp; r < R; r += nw) {
+        const int gr = c0 + r;
+        const T *arow = A + (int64_t)min(gr, n - 1) * wd;
+        T *wrow = W + r * ldw;
+        for (int c = lane; c < Cw; c += 32) {
+          const int gc = c0 + c, off = c - r + kl;
+          const bool ok = gr < n && gc < n && off >= 0 && off < wd;
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(wrow + c);
+          const T *src = ok ? arow + off : arow;
+          if (sizeof(T) == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0)
+                         : "memory");
+          else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(src), "r"(ok ? 8 : 0)
+                         : "memory");
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    } else
+    // in global scratch: a warp per row, lanes along the row's band entries,
     // four loads in flight per lane
     for (int r = warp; r < R; r += nw) {
       const int gr = c0 + r;

@@ -150,8 +150,10 @@ __global__ void bgj_copy_kernel(int k0, const int32_t *__restrict__ P, const int
 // (2a) Columns c0..c0+nbe-1 of W (c0 = NB*s), rows c0..: LU with partial
 // pivoting on a copy in shared memory (or scratch), written back; the row
 // exchanges applied to W's other columns; U12 = L11^-1 W(c0:c0+nbe, right).
+// 512 threads: at 1024 the 64-register cap made the kernel spill
+#define DD_GJ_PANEL_THREADS 512
 template <typename T, int NB, int NO>
-__global__ void __launch_bounds__(1024, 1) bgj_panel_kernel(int k0, int s, const int32_t *__restrict__ P,
+__global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k0, int s, const int32_t *__restrict__ P,
                                                             T *scratch, const int64_t *__restrict__ poff,
                                                             int32_t *ipiv, const T *__restrict__ amax,
                                                             double pivtol, int32_t *failed, DevStatus *st,
@@ -1020,7 +1022,7 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   for (int k0 = 0; k0 < pmax; k0 += NO) {
     bgj_copy_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     for (int sp = 0; sp < NO / NB; ++sp) {
-      bgj_panel_kernel<T, NB, NO><<<nblk, 1024, smem, s>>>(k0, sp, d_p, scratch, d_poff, ipiv, amax, pivtol,
+      bgj_panel_kernel<T, NB, NO><<<nblk, DD_GJ_PANEL_THREADS, smem, s>>>(k0, sp, d_p, scratch, d_poff, ipiv, amax, pivtol,
                                                            failed, st, status_code, smem_rows);
       if (sp + 1 < NO / NB) bgj_trail_kernel<T, NB, NO><<<tg, 256, 0, s>>>(k0, sp, d_p, scratch, d_poff, failed);
     }

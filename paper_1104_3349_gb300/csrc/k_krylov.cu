@@ -204,7 +204,6 @@ __global__ void zero_kernel(double *p, int64_t n) {
 // CTAs hold bit-identical coefficients and results do not depend on
 // scheduling.  scal: [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}|/||b||
 // ---------------------------------------------------------------------------
-#define DD_CGS_THREADS 256
 #define DD_CGS_MAXK 128  // restart lengths up to DD_CGS_MAXK - 2
 
 // Sum over a warp of G per-lane values (G = 4, 8 or 16), transposed: each
@@ -385,7 +384,8 @@ __device__ void seg_column_sums(const SegMap &sm, int ncols, int pk, const doubl
 // with row stride R, cs/sn rmax, g rmax+1, bn2 (||b||^2) 1, scal 4:
 // [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}| / ||b||.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
+template <int NT>
+__global__ void __launch_bounds__(NT) cgs2_kernel(
     int64_t n, int j, int R, const double *__restrict__ V, int64_t ldv, double *w, double *partial,
     int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
     const double *__restrict__ bn2, double *scal, SegMap sm) {
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(DD_CGS_THREADS) cgs2_kernel(
   const SegCta me = seg_cta(sm, b, nb, n);
   const int i0 = (int)me.i0, i1 = (int)me.i1;
   const int k = j + 1, hst = sm.rmax + 2;
-  __shared__ double red[8 * 16];
+  __shared__ double red[(NT / 32) * 16];
   __shared__ double hs[DD_CGS_MAXK + 8];
   // 1
   block_dots(i0, i1, k, V, ldv, w, true, partial + (int64_t)b * pk, red);
@@ -685,25 +685,29 @@ cudaError_t launch_init_g(double *g, int R, const double *nsq, cudaStream_t s) {
 }
 
 // blocks of the cooperative CGS2 kernel that can be resident at once (capped)
-int cgs2_blocks(int per_sm, int cap) {
+template <int NT>
+static int cgs2_blocks_t(int per_sm, int cap) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgs2_kernel, DD_CGS_THREADS, 0) != cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgs2_kernel<NT>, NT, 0) != cudaSuccess) return 0;
   const int want = per_sm > 0 ? per_sm : 2;
   int nb = sms * (per < want ? per : want);
   return nb < cap ? nb : cap;
 }
-
+int cgs2_blocks(int per_sm, int cap, int threads) {
+  return threads == 512 ? cgs2_blocks_t<512>(per_sm, cap) : cgs2_blocks_t<256>(per_sm, cap);
+}
 cudaError_t launch_cgs2(int64_t n, int j, int R, const double *V, int64_t ldv, double *w, double *partial,
                         int pk, double *hc1, double *hc2, double *H, double *cs, double *sn, double *g,
-                        const double *bn2, double *scal, const SegMap &sm, int nblocks, cudaStream_t s) {
+                        const double *bn2, double *scal, const SegMap &sm, int nblocks, int threads,
+                        cudaStream_t s) {
   SegMap m2 = sm;
   void *args[] = {&n, &j, &R, (void *)&V, &ldv, &w, &partial, &pk, &hc1, &hc2, &H, &cs, &sn, &g,
                   (void *)&bn2, &scal, &m2};
-  return cudaLaunchCooperativeKernel((const void *)cgs2_kernel, dim3(nblocks), dim3(DD_CGS_THREADS),
-                                     args, 0, s);
+  if (threads == 512)
+    return cudaLaunchCooperativeKernel((const void *)cgs2_kernel<512>, dim3(nblocks), dim3(512), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)cgs2_kernel<256>, dim3(nblocks), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_seg_norms(int64_t n, const double *v, double *partial, double *out, const SegMap &sm,

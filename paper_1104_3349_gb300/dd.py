@@ -98,7 +98,8 @@ class dd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("pivot_tol", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
                 ("time_kernels", ctypes.c_int32), ("sweep_cluster", ctypes.c_int32),
-                ("mlp_weights", ctypes.c_char_p), ("overlap", ctypes.c_int32), ("radius", ctypes.c_int32)]
+                ("mlp_weights", ctypes.c_char_p), ("overlap", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("krylov_threads", ctypes.c_int32), ("pad_opts", ctypes.c_int32)]
 
 
 class dd_info(ctypes.Structure):
@@ -233,7 +234,7 @@ class DD:
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
                  autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False, sweep_cluster=0,
-                 overlap=0, radius=0):
+                 overlap=0, radius=0, krylov_threads=0):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -250,6 +251,7 @@ class DD:
         o.sweep_cluster = int(sweep_cluster)
         o.overlap = int(overlap)
         o.radius = int(radius)
+        o.krylov_threads = int(krylov_threads)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
