@@ -138,7 +138,10 @@ typedef struct {
   int32_t krylov_threads; /* threads per CTA of the CGS2 kernel: 256 or 512;
                          <= 0 selects 512 (then krylov_ctas_per_sm <= 0
                          selects 1)                                            */
-  int32_t pad_opts;
+  int32_t sweep_prefetch; /* the apply's sweeps prefetch into L2
+                         (cp.async.bulk.prefetch) the tile bytes of the job
+                         this many jobs past the ring as they refill a
+                         stage: k > 0 a distance of k jobs, <= 0 none       */
 } dd_opts;
 
 typedef struct {
@@ -175,7 +178,7 @@ typedef struct {
   int32_t graphs;            /* CUDA graphs instantiated so far                  */
   int64_t learned_entries;   /* DD_LEARNED: entries of the learned patterns      */
   int32_t learned_fallback;  /* DD_LEARNED: aggregates that took MSCE_INF         */
-  int32_t pad3;
+  int32_t sweep_prefetch;    /* L2 prefetch distance of the sweeps, in jobs      */
   /* opts.time_kernels: summed over the timed Arnoldi steps of gmres_solve */
   int64_t krylov_steps;      /* Arnoldi steps timed                              */
   double cgs2_ms;            /* device time of the CGS2 kernel                   */

@@ -41,6 +41,7 @@ struct DDHandle {
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
   uint32_t first_wait = 0xffffffffu;  // test hook: polls of each sweep CTA's first wait
   int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1 or 2
+  int sweep_pf_opt = 0;        // opts.sweep_prefetch: k > 0 k jobs, else none
   int overlap = 0, radius = 0; // opts.overlap (overlapped kinds), opts.radius (DD_MSCE)
   std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
   std::vector<TileMeta> h_tm;
@@ -51,6 +52,11 @@ struct DDHandle {
   TileMeta *tm = nullptr;      // packed sweep tiles
   SweepJob *jobs = nullptr;    // jobs of the sweep ring
   cudaStream_t stream = nullptr;
+  // setup: while astream is set, allocations and uploads go to it (the side
+  // stream ustream, so that pageable copies need not wait for the band LU
+  // on stream); uev joins it back into stream
+  cudaStream_t astream = nullptr, ustream = nullptr;
+  cudaEvent_t uev = nullptr;
   std::vector<void *> allocs;
   BandInfo *d_info = nullptr;
   int32_t *piv = nullptr, *src = nullptr;
@@ -124,7 +130,7 @@ dd_status dalloc(DDHandle *h, P **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   void *q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, count * sizeof(P), h->stream);
+  cudaError_t e = cudaMallocAsync(&q, count * sizeof(P), h->astream ? h->astream : h->stream);
   if (e != cudaSuccess) {
     h->err = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : DD_ERR_CUDA;
@@ -138,7 +144,9 @@ template <typename P>
 dd_status upload(DDHandle *h, P **p, const std::vector<P> &v) {
   dd_status s = dalloc(h, p, v.size());
   if (s != DD_OK) return s;
-  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(P), cudaMemcpyHostToDevice, h->stream));
+  if (!v.empty())
+    CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(P), cudaMemcpyHostToDevice,
+                       h->astream ? h->astream : h->stream));
   return DD_OK;
 }
 
@@ -183,7 +191,8 @@ dd_status upload_T(DDHandle *h, T **p, const std::vector<double> &v) {
   TRY(dalloc(h, p, v.size()));
   if (!v.empty()) {
     h->stats.launches += 1;
-    convert_kernel<T><<<(unsigned)((v.size() + 255) / 256), 256, 0, h->stream>>>((int64_t)v.size(), tmp, *p);
+    convert_kernel<T><<<(unsigned)((v.size() + 255) / 256), 256, 0, h->astream ? h->astream : h->stream>>>(
+        (int64_t)v.size(), tmp, *p);
     CK(cudaGetLastError());
   }
   return DD_OK;
@@ -487,10 +496,7 @@ int sm_count() {
   return sms;
 }
 
-// CTAs per subdomain of the sweeps: the option if given, else 2 (a cluster
-// splitting every tile step) when the clusters of all subdomains can be
-// resident at once on half the SMs or fewer, else 1.
-// The option if given, else 1.  Measured on the 256x256 workload, the
+// CTAs per subdomain of the sweeps: the option if given, else 1.  Measured on the 256x256 workload, the
 // 2-CTA cluster sweep is slower in both precisions (FP32 133.5 against
 // 100.8 us per interior solve, FP64 432.8 against 404.1 us): a step's
 // exchange and cluster barrier cost more than halving the shared-memory
@@ -566,6 +572,13 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage, int cl) {
     h->plan.sched = nullptr;
     h->plan.sched_off = nullptr;
   }
+  // L2 prefetch of later jobs: only on request.  A streaming probe with 64
+  // CTAs and a ring of two 84 KB stages copied 103 GB/s per SM with a
+  // prefetch two jobs ahead against 88 without, but the sweeps of the
+  // 256x256 workload (64 CTAs) measured slower with it (forward sweep
+  // 103 against 95 us).
+  h->plan.pf = std::max(h->sweep_pf_opt, 0);
+  h->stats.sweep_prefetch = h->plan.pf;
   h->stats.sweep_grid = h->plan.grid;
   return DD_OK;
 }
@@ -1206,7 +1219,6 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     TRY(upload(h, &h->c_col, cc));
     TRY(upload(h, &h->c_val, vv));
   }
-  TRY(build_sell(h, csr));
   int32_t *d_part = nullptr, *d_pos = nullptr;
   TRY(upload(h, &d_part, std::vector<int32_t>(pt->part, pt->part + h->n)));
   TRY(upload(h, &d_pos, hb.pos));
@@ -1234,6 +1246,205 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
                          static_cast<T *>(h->lu_scratch), pivtol, h->st, lu_threads, slots, d_sched, d_off, s));
   }
+  // ---- host work while the band LU runs.  Its allocations and uploads go
+  // to the side stream: a pageable copy queued behind the LU on the main
+  // stream would hold the host until the LU ends.  The main stream waits
+  // for the side stream before the tile packing.
+  if (!h->ustream) CK(cudaStreamCreateWithFlags(&h->ustream, cudaStreamNonBlocking));
+  if (!h->uev) CK(cudaEventCreateWithFlags(&h->uev, cudaEventDisableTiming));
+  h->astream = h->ustream;
+  TRY(build_sell(h, csr));
+  // ---- couplings E (interior x interface) and F (interface x interior)
+  TRY(upload(h, &h->e_ptr, hb.e_ptr));
+  TRY(upload(h, &h->e_col, hb.e_col));
+  TRY(upload_T(h, &B.e_val, hb.e_val));
+  TRY(upload(h, &h->f_ptr, hb.f_ptr));
+  TRY(upload(h, &h->f_col, hb.f_col));
+  TRY(upload_T(h, &B.f_val, hb.f_val));
+  h->stats.coupling_nnz = (int64_t)hb.e_col.size() + (int64_t)hb.f_col.size();
+  // ---- interface blocks.  The overlapped kinds build their blocks apart and
+  // assemble S_hat into one block of the whole interface, which the apply
+  // then inverts whole (the blocks of the apply are aggA).
+  const bool ovl_kind = h->kind == DD_OMSCN || h->kind == DD_OMSCNR || h->kind == DD_OLUM;
+  const std::vector<int32_t> aggA = ovl_kind ? std::vector<int32_t>{0, nG} : hb.agg;
+  const int nagg = (int)aggA.size() - 1;
+  h->nagg = nagg;
+  std::vector<int32_t> p(nagg), agg_of(nG);
+  std::vector<int64_t> soff(nagg + 1, 0), poff(nagg + 1, 0);
+  h->pmax = 0;
+  for (int a = 0; a < nagg; ++a) {
+    p[a] = aggA[a + 1] - aggA[a];
+    soff[a + 1] = soff[a] + (int64_t)p[a] * p[a];
+    poff[a + 1] = poff[a] + p[a];
+    h->pmax = std::max(h->pmax, p[a]);
+    for (int g = aggA[a]; g < aggA[a + 1]; ++g) agg_of[g] = a;
+  }
+  if (h->pmax > 12288) {
+    h->err = ovl_kind ? "overlapped kinds invert the whole interface: n_G must be <= 12288"
+                      : "an aggregate exceeds 12288 interface nodes";
+    return DD_ERR_INVALID_ARG;
+  }
+  h->stats.n_agg = (int32_t)hb.agg.size() - 1;
+  h->stats.max_agg = h->pmax;
+  h->stats.schur_bytes = soff[nagg] * (int64_t)sizeof(T);
+  TRY(upload(h, &h->agg_off, aggA));
+  TRY(upload(h, &h->d_p, p));
+  TRY(upload(h, &h->s_off, soff));
+  TRY(upload(h, &h->poff, poff));
+  TRY(dalloc(h, &B.S, soff[nagg]));
+  TRY(dalloc(h, &B.amax, nagg));
+  TRY(dalloc(h, &B.gj, gj_scratch_elems(nagg, poff[nagg], sizeof(T))));
+  TRY(dalloc(h, &h->ipiv, poff[nagg]));
+  TRY(dalloc(h, &h->failed, nagg));
+  // G(R_a, R_a): the entries' positions in S (scattered after the join)
+  int64_t *d_gidx = nullptr;
+  double *d_gval = nullptr;
+  size_t gcount = 0;
+  if (!ovl_kind) {
+    std::vector<int64_t> idx;
+    std::vector<double> val;
+    for (int g = 0; g < nG; ++g) {
+      const int o = hb.perm[nI + g];
+      const int a = agg_of[g];
+      for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
+        const int c = hb.pos[csr->col[k]] - nI;
+        if (c < 0 || agg_of[c] != a) continue;
+        idx.push_back(soff[a] + (int64_t)(g - hb.agg[a]) * p[a] + (c - hb.agg[a]));
+        val.push_back(csr->val[k]);
+      }
+    }
+    TRY(upload(h, &d_gidx, idx));
+    TRY(upload(h, &d_gval, val));
+    gcount = idx.size();
+  }
+  // S_dst(R_a, R_a) -= sum_j F(R_a, I_j) A_jj^-1 E(I_j, R_a) (MSCE_INF / EXACT,
+  // and the learned kind's base): per subdomain the interface columns of E
+  // (gam) and interface rows of F (fr), the scatter of E into the columns
+  // X_j, and the colours of the accumulation, all built on the host while
+  // the band LU runs
+  struct MsceLists {
+    int32_t *gam_ptr = nullptr, *gam_idx = nullptr, *gam_agg = nullptr, *fr_ptr = nullptr, *fr_row = nullptr,
+            *fr_agg = nullptr, *fs_ptr = nullptr, *fs_col = nullptr, *ncols = nullptr, *jlist = nullptr;
+    int64_t *xoff = nullptr, *xidx = nullptr;
+    double *xval = nullptr;
+    int64_t nx = 0, xsize = 0;
+    int max_fr = 0, max_gam = 0;
+    std::vector<int32_t> cptr;
+  } ml;
+  auto msce_prep = [&]() -> dd_status {
+    std::vector<int32_t> gam_ptr(m + 1, 0), gam_idx, gam_agg, fr_ptr(m + 1, 0), fr_row, fr_agg;
+    std::vector<int32_t> fs_ptr(1, 0), fs_col;
+    std::vector<double> fs_val;
+    std::vector<int32_t> ncols(m, 0);
+    std::vector<int64_t> xoff(m + 1, 0);
+    std::vector<int32_t> mark(nG, -1);
+    std::vector<std::vector<int32_t>> frs(m);
+    for (int g = 0; g < nG; ++g) {
+      int last = -1;
+      for (int k = hb.f_ptr[g]; k < hb.f_ptr[g + 1]; ++k) {
+        int c = hb.f_col[k];
+        int j = (int)(std::upper_bound(hb.off.begin(), hb.off.end(), c) - hb.off.begin()) - 1;
+        if (j != last && (frs[j].empty() || frs[j].back() != g)) frs[j].push_back(g);
+        last = j;
+      }
+    }
+    std::vector<int64_t> xidx;
+    std::vector<double> xval;
+    for (int j = 0; j < m; ++j) {
+      const int r0 = hb.off[j], r1 = hb.off[j + 1], nj = r1 - r0;
+      std::vector<int32_t> cols;
+      for (int r = r0; r < r1; ++r)
+        for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) cols.push_back(hb.e_col[k]);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      for (size_t q = 0; q < cols.size(); ++q) mark[cols[q]] = (int32_t)q;
+      ncols[j] = (int32_t)cols.size();
+      xoff[j + 1] = xoff[j] + (int64_t)nj * cols.size();
+      for (int c : cols) { gam_idx.push_back(c); gam_agg.push_back(agg_of[c]); }
+      gam_ptr[j + 1] = (int32_t)gam_idx.size();
+      for (int r = r0; r < r1; ++r)
+        for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) {
+          xidx.push_back(xoff[j] + (int64_t)mark[hb.e_col[k]] * nj + (r - r0));
+          xval.push_back(hb.e_val[k]);
+        }
+      for (int c : cols) mark[c] = -1;
+      for (int g : frs[j]) {
+        fr_row.push_back(g);
+        fr_agg.push_back(agg_of[g]);
+        for (int k = hb.f_ptr[g]; k < hb.f_ptr[g + 1]; ++k) {
+          int c = hb.f_col[k];
+          if (c >= r0 && c < r1) { fs_col.push_back(c - r0); fs_val.push_back(hb.f_val[k]); }
+        }
+        fs_ptr.push_back((int32_t)fs_col.size());
+      }
+      fr_ptr[j + 1] = (int32_t)fr_row.size();
+      ml.max_fr = std::max(ml.max_fr, (int)frs[j].size());
+      ml.max_gam = std::max(ml.max_gam, (int)cols.size());
+    }
+    // colours: a subdomain takes the first colour that no earlier subdomain
+    // sharing an interface row with it holds, so the sum over j of every
+    // entry of S runs in colour order, the same on every run (no atomics)
+    std::vector<int32_t> color(m, -1), jlist;
+    ml.cptr.assign(1, 0);
+    {
+      std::vector<std::vector<int32_t>> subs_of(nG);  // subdomains of each interface row
+      for (int j = 0; j < m; ++j)
+        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q) subs_of[fr_row[q]].push_back(j);
+      int ncolor = 0;
+      std::vector<int32_t> seen;  // colour -> last subdomain that saw it taken
+      for (int j = 0; j < m; ++j) {
+        seen.assign(ncolor + 1, -1);
+        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q)
+          for (int j2 : subs_of[fr_row[q]])
+            if (j2 < j && color[j2] >= 0) seen[color[j2]] = j;
+        int c = 0;
+        while (c < ncolor && seen[c] == j) ++c;
+        color[j] = c;
+        ncolor = std::max(ncolor, c + 1);
+      }
+      for (int c = 0; c < ncolor; ++c) {
+        for (int j = 0; j < m; ++j)
+          if (color[j] == c) jlist.push_back(j);
+        ml.cptr.push_back((int32_t)jlist.size());
+      }
+    }
+    TRY(upload(h, &ml.gam_ptr, gam_ptr));
+    TRY(upload(h, &ml.gam_idx, gam_idx));
+    TRY(upload(h, &ml.gam_agg, gam_agg));
+    TRY(upload(h, &ml.fr_ptr, fr_ptr));
+    TRY(upload(h, &ml.fr_row, fr_row));
+    TRY(upload(h, &ml.fr_agg, fr_agg));
+    TRY(upload(h, &ml.fs_ptr, fs_ptr));
+    TRY(upload(h, &ml.fs_col, fs_col));
+    TRY(upload_T(h, &B.fsub_val, fs_val));
+    TRY(upload(h, &ml.ncols, ncols));
+    TRY(upload(h, &ml.xoff, xoff));
+    TRY(upload(h, &ml.xidx, xidx));
+    TRY(upload(h, &ml.xval, xval));
+    TRY(upload(h, &ml.jlist, jlist));
+    TRY(dalloc(h, &B.X, xoff[m]));
+    ml.nx = (int64_t)xidx.size();
+    ml.xsize = xoff[m];
+    return DD_OK;
+  };
+  auto msce_into = [&](T *Sdst) -> dd_status {
+    CK(cudaMemsetAsync(B.X, 0, sizeof(T) * std::max<int64_t>(ml.xsize, 1), s));
+    CK(launch_scatter_coo<T>(ml.nx, ml.xidx, ml.xval, B.X, s));
+    // X_j = A_jj^-1 E(I_j, gam_j)
+    CK(launch_band_solve_multi<T>(h->d_info, m, ml.ncols, ml.xoff, ml.max_gam, h->max_kl, h->max_ku2, h->tb,
+                                  h->tm, B.ltile, B.utile, h->src, B.X, s));
+    // S(R_a,R_a) -= F(R_a, I_j) X_j, one launch per colour of subdomains
+    for (size_t c = 0; c + 1 < ml.cptr.size(); ++c)
+      CK(launch_schur_accumulate<T>(ml.cptr[c + 1] - ml.cptr[c], ml.jlist + ml.cptr[c], ml.fr_ptr, ml.fr_row,
+                                    ml.fr_agg, ml.fs_ptr, ml.fs_col, B.fsub_val, ml.gam_ptr, ml.gam_idx,
+                                    ml.gam_agg, ml.xoff, h->d_info, B.X, h->agg_off, h->s_off, Sdst, ml.max_fr,
+                                    ml.max_gam, s));
+    return DD_OK;
+  };
+  if (h->kind == DD_MSCE_INF || h->kind == DD_EXACT || h->kind == DD_LEARNED) TRY(msce_prep());
+  CK(cudaEventRecord(h->uev, h->ustream));
+  h->astream = nullptr;
+  CK(cudaStreamWaitEvent(s, h->uev, 0));
   // ---- packed sweep tiles: widths from the factors, offsets and jobs here
   {
     int32_t *d_wl = nullptr, *d_wu = nullptr;
@@ -1321,183 +1532,13 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tb, h->tm, B.band, B.lm, h->piv,
                             B.ltile, B.utile, h->src, s));
   }
-  // ---- couplings E (interior x interface) and F (interface x interior)
-  TRY(upload(h, &h->e_ptr, hb.e_ptr));
-  TRY(upload(h, &h->e_col, hb.e_col));
-  TRY(upload_T(h, &B.e_val, hb.e_val));
-  TRY(upload(h, &h->f_ptr, hb.f_ptr));
-  TRY(upload(h, &h->f_col, hb.f_col));
-  TRY(upload_T(h, &B.f_val, hb.f_val));
-  h->stats.coupling_nnz = (int64_t)hb.e_col.size() + (int64_t)hb.f_col.size();
-  // ---- interface blocks.  The overlapped kinds build their blocks apart and
-  // assemble S_hat into one block of the whole interface, which the apply
-  // then inverts whole (the blocks of the apply are aggA).
-  const bool ovl_kind = h->kind == DD_OMSCN || h->kind == DD_OMSCNR || h->kind == DD_OLUM;
-  const std::vector<int32_t> aggA = ovl_kind ? std::vector<int32_t>{0, nG} : hb.agg;
-  const int nagg = (int)aggA.size() - 1;
-  h->nagg = nagg;
-  std::vector<int32_t> p(nagg), agg_of(nG);
-  std::vector<int64_t> soff(nagg + 1, 0), poff(nagg + 1, 0);
-  h->pmax = 0;
-  for (int a = 0; a < nagg; ++a) {
-    p[a] = aggA[a + 1] - aggA[a];
-    soff[a + 1] = soff[a] + (int64_t)p[a] * p[a];
-    poff[a + 1] = poff[a] + p[a];
-    h->pmax = std::max(h->pmax, p[a]);
-    for (int g = aggA[a]; g < aggA[a + 1]; ++g) agg_of[g] = a;
-  }
-  if (h->pmax > 12288) {
-    h->err = ovl_kind ? "overlapped kinds invert the whole interface: n_G must be <= 12288"
-                      : "an aggregate exceeds 12288 interface nodes";
-    return DD_ERR_INVALID_ARG;
-  }
-  h->stats.n_agg = (int32_t)hb.agg.size() - 1;
-  h->stats.max_agg = h->pmax;
-  h->stats.schur_bytes = soff[nagg] * (int64_t)sizeof(T);
-  TRY(upload(h, &h->agg_off, aggA));
-  TRY(upload(h, &h->d_p, p));
-  TRY(upload(h, &h->s_off, soff));
-  TRY(upload(h, &h->poff, poff));
-  TRY(dalloc(h, &B.S, soff[nagg]));
-  CK(cudaMemsetAsync(B.S, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
-  TRY(dalloc(h, &B.amax, nagg));
-  TRY(dalloc(h, &B.gj, gj_scratch_elems(nagg, poff[nagg], sizeof(T))));
-  TRY(dalloc(h, &h->ipiv, poff[nagg]));
-  TRY(dalloc(h, &h->failed, nagg));
   // G(R_a, R_a) into S
-  int64_t *d_gidx = nullptr;
-  double *d_gval = nullptr;
-  size_t gcount = 0;
+  CK(cudaMemsetAsync(B.S, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
   if (ovl_kind) {
     TRY(overlapped_schur<T>(h, csr, hb, pivtol, B.S));
   } else {
-    std::vector<int64_t> idx;
-    std::vector<double> val;
-    for (int g = 0; g < nG; ++g) {
-      const int o = hb.perm[nI + g];
-      const int a = agg_of[g];
-      for (int64_t k = csr->rowptr[o]; k < csr->rowptr[o + 1]; ++k) {
-        const int c = hb.pos[csr->col[k]] - nI;
-        if (c < 0 || agg_of[c] != a) continue;
-        idx.push_back(soff[a] + (int64_t)(g - hb.agg[a]) * p[a] + (c - hb.agg[a]));
-        val.push_back(csr->val[k]);
-      }
-    }
-    TRY(upload(h, &d_gidx, idx));
-    TRY(upload(h, &d_gval, val));
-    gcount = idx.size();
-    CK(launch_scatter_coo<T>((int64_t)idx.size(), d_gidx, d_gval, B.S, s));
+    CK(launch_scatter_coo<T>((int64_t)gcount, d_gidx, d_gval, B.S, s));
   }
-  // S_dst(R_a, R_a) -= sum_j F(R_a, I_j) A_jj^-1 E(I_j, R_a) (MSCE_INF / EXACT)
-  auto msce_into = [&](T *Sdst) -> dd_status {
-    // per subdomain: interface columns of E (gam) and interface rows of F (fr)
-    std::vector<int32_t> gam_ptr(m + 1, 0), gam_idx, gam_agg, fr_ptr(m + 1, 0), fr_row, fr_agg;
-    std::vector<int32_t> fs_ptr(1, 0), fs_col;
-    std::vector<double> fs_val;
-    std::vector<int32_t> ncols(m, 0);
-    std::vector<int64_t> xoff(m + 1, 0);
-    std::vector<int32_t> mark(nG, -1);
-    std::vector<std::vector<int32_t>> frs(m);
-    for (int g = 0; g < nG; ++g) {
-      int last = -1;
-      for (int k = hb.f_ptr[g]; k < hb.f_ptr[g + 1]; ++k) {
-        int c = hb.f_col[k];
-        int j = (int)(std::upper_bound(hb.off.begin(), hb.off.end(), c) - hb.off.begin()) - 1;
-        if (j != last && (frs[j].empty() || frs[j].back() != g)) frs[j].push_back(g);
-        last = j;
-      }
-    }
-    std::vector<int64_t> xidx;
-    std::vector<double> xval;
-    int max_fr = 0, max_gam = 0;
-    for (int j = 0; j < m; ++j) {
-      const int r0 = hb.off[j], r1 = hb.off[j + 1], nj = r1 - r0;
-      std::vector<int32_t> cols;
-      for (int r = r0; r < r1; ++r)
-        for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) cols.push_back(hb.e_col[k]);
-      std::sort(cols.begin(), cols.end());
-      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
-      for (size_t q = 0; q < cols.size(); ++q) mark[cols[q]] = (int32_t)q;
-      ncols[j] = (int32_t)cols.size();
-      xoff[j + 1] = xoff[j] + (int64_t)nj * cols.size();
-      for (int c : cols) { gam_idx.push_back(c); gam_agg.push_back(agg_of[c]); }
-      gam_ptr[j + 1] = (int32_t)gam_idx.size();
-      for (int r = r0; r < r1; ++r)
-        for (int k = hb.e_ptr[r]; k < hb.e_ptr[r + 1]; ++k) {
-          xidx.push_back(xoff[j] + (int64_t)mark[hb.e_col[k]] * nj + (r - r0));
-          xval.push_back(hb.e_val[k]);
-        }
-      for (int c : cols) mark[c] = -1;
-      for (int g : frs[j]) {
-        fr_row.push_back(g);
-        fr_agg.push_back(agg_of[g]);
-        for (int k = hb.f_ptr[g]; k < hb.f_ptr[g + 1]; ++k) {
-          int c = hb.f_col[k];
-          if (c >= r0 && c < r1) { fs_col.push_back(c - r0); fs_val.push_back(hb.f_val[k]); }
-        }
-        fs_ptr.push_back((int32_t)fs_col.size());
-      }
-      fr_ptr[j + 1] = (int32_t)fr_row.size();
-      max_fr = std::max(max_fr, (int)frs[j].size());
-      max_gam = std::max(max_gam, (int)cols.size());
-    }
-    int32_t *d_gam_ptr, *d_gam_idx, *d_gam_agg, *d_fr_ptr, *d_fr_row, *d_fr_agg, *d_fs_ptr, *d_fs_col, *d_ncols;
-    int64_t *d_xoff, *d_xidx;
-    double *d_xval;
-    TRY(upload(h, &d_gam_ptr, gam_ptr));
-    TRY(upload(h, &d_gam_idx, gam_idx));
-    TRY(upload(h, &d_gam_agg, gam_agg));
-    TRY(upload(h, &d_fr_ptr, fr_ptr));
-    TRY(upload(h, &d_fr_row, fr_row));
-    TRY(upload(h, &d_fr_agg, fr_agg));
-    TRY(upload(h, &d_fs_ptr, fs_ptr));
-    TRY(upload(h, &d_fs_col, fs_col));
-    TRY(upload_T(h, &B.fsub_val, fs_val));
-    TRY(upload(h, &d_ncols, ncols));
-    TRY(upload(h, &d_xoff, xoff));
-    TRY(upload(h, &d_xidx, xidx));
-    TRY(upload(h, &d_xval, xval));
-    TRY(dalloc(h, &B.X, xoff[m]));
-    CK(cudaMemsetAsync(B.X, 0, sizeof(T) * std::max<int64_t>(xoff[m], 1), s));
-    CK(launch_scatter_coo<T>((int64_t)xidx.size(), d_xidx, d_xval, B.X, s));
-    // X_j = A_jj^-1 E(I_j, gam_j)
-    CK(launch_band_solve_multi<T>(h->d_info, m, d_ncols, d_xoff, max_gam, h->max_kl, h->max_ku2, h->tb,
-                                  h->tm, B.ltile, B.utile, h->src, B.X, s));
-    // S(R_a,R_a) -= F(R_a, I_j) X_j, one launch per colour of subdomains: a
-    // subdomain takes the first colour that no earlier subdomain sharing an
-    // interface row with it holds, so the sum over j of every entry runs in
-    // colour order, the same on every run (no atomics)
-    std::vector<int32_t> color(m, -1), jlist, cptr(1, 0);
-    {
-      std::vector<std::vector<int32_t>> subs_of(nG);  // subdomains of each interface row
-      for (int j = 0; j < m; ++j)
-        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q) subs_of[fr_row[q]].push_back(j);
-      int ncolor = 0;
-      std::vector<int32_t> seen;  // colour -> last subdomain that saw it taken
-      for (int j = 0; j < m; ++j) {
-        seen.assign(ncolor + 1, -1);
-        for (int q = fr_ptr[j]; q < fr_ptr[j + 1]; ++q)
-          for (int j2 : subs_of[fr_row[q]])
-            if (j2 < j && color[j2] >= 0) seen[color[j2]] = j;
-        int c = 0;
-        while (c < ncolor && seen[c] == j) ++c;
-        color[j] = c;
-        ncolor = std::max(ncolor, c + 1);
-      }
-      for (int c = 0; c < ncolor; ++c) {
-        for (int j = 0; j < m; ++j)
-          if (color[j] == c) jlist.push_back(j);
-        cptr.push_back((int32_t)jlist.size());
-      }
-    }
-    int32_t *d_jlist;
-    TRY(upload(h, &d_jlist, jlist));
-    for (size_t c = 0; c + 1 < cptr.size(); ++c)
-      CK(launch_schur_accumulate<T>(cptr[c + 1] - cptr[c], d_jlist + cptr[c], d_fr_ptr, d_fr_row, d_fr_agg,
-                                    d_fs_ptr, d_fs_col, B.fsub_val, d_gam_ptr, d_gam_idx, d_gam_agg, d_xoff,
-                                    h->d_info, B.X, h->agg_off, h->s_off, Sdst, max_fr, max_gam, s));
-    return DD_OK;
-  };
   if (h->kind == DD_MSCE_INF || h->kind == DD_EXACT) {
     TRY(msce_into(B.S));
   } else if (h->kind == DD_LEARNED) {
@@ -2000,6 +2041,9 @@ dd_status fgmres_batched(DDHandle *h, const double *const *b, double *const *x, 
 
 void release(DDHandle *h) {
   drop_graphs(h);
+  if (h->ustream) { cudaStreamSynchronize(h->ustream); cudaStreamDestroy(h->ustream); h->ustream = nullptr; }
+  if (h->uev) { cudaEventDestroy(h->uev); h->uev = nullptr; }
+  h->astream = nullptr;
   if (h->gstream) { cudaStreamSynchronize(h->gstream); cudaStreamDestroy(h->gstream); h->gstream = nullptr; }
   for (cudaEvent_t &e : h->gev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -2146,6 +2190,7 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->time_kernels = o.time_kernels != 0 && !h->use_graph;
   if (o.sweep_cluster < 0 || o.sweep_cluster > 2) { h->err = "sweep_cluster must be 0, 1 or 2"; return DD_ERR_INVALID_ARG; }
   h->sweep_cl_opt = o.sweep_cluster;
+  h->sweep_pf_opt = o.sweep_prefetch;
   if (o.overlap < 0 || o.radius < 0) { h->err = "overlap and radius must be >= 0"; return DD_ERR_INVALID_ARG; }
   h->overlap = o.overlap;
   h->radius = o.radius;

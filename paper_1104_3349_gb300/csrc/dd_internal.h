@@ -103,6 +103,8 @@ struct SweepPlan {
   // CTAs per subdomain: 1, or 2 (a thread-block cluster; threads = 4 TB);
   // grid counts CTAs, so a persistent grid holds grid / cl task lists
   int cl = 1;
+  // L2 prefetch distance in jobs beyond the ring (0: none)
+  int pf = 0;
 };
 
 // Device-side error word: first failure wins.

@@ -684,6 +684,30 @@ __device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm,
   }
 }
 
+// The bytes of job q (CL = 1 layout) into L2, without a destination in
+// shared memory; a hint that changes no result.  The addresses and sizes are
+// those its copy will use, so they are in bounds and 16-byte aligned.
+template <typename T, int TB>
+__device__ __forceinline__ void prefetch_job(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs, int q,
+                                             const T *ltile, const T *utile, const int32_t *srcs) {
+  bool fwd;
+  const SweepJob jb = get_job(b, jobs, q, fwd);
+  const TileMeta &a = tm[b.tile0 + jb.lo], &z = tm[b.tile0 + jb.hi - 1];
+  const void *p0, *p1 = nullptr;
+  uint32_t n0, n1 = 0;
+  if (fwd) {
+    p0 = ltile + a.lofs;
+    n0 = (uint32_t)((z.lofs + (int64_t)z.wl * TB - a.lofs) * sizeof(T));
+    p1 = srcs + a.sofs;
+    n1 = (uint32_t)((z.sofs + src_stride_w(z.wl) - a.sofs) * sizeof(int32_t));
+  } else {
+    p0 = utile + a.uofs;
+    n0 = (uint32_t)((z.uofs + (int64_t)TB * z.wu - a.uofs) * sizeof(T));
+  }
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p0), "r"(n0) : "memory");
+  if (n1) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p1), "r"(n1) : "memory");
+}
+
 // 16-byte chunk of T values
 template <typename T>
 struct Chunk;
@@ -715,7 +739,8 @@ template <typename T, int TB, int CL = 1>
 __device__ __forceinline__ void issue_first_jobs(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                                  const T *ltile, const T *utile, const int32_t *srcs,
                                                  unsigned char *ring, uint32_t stage_bytes, int nstages,
-                                                 uint64_t *bars, uint32_t jbase, int rank, DevStatus *st) {
+                                                 uint64_t *bars, uint32_t jbase, int rank, DevStatus *st,
+                                                 int pf = 0) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const int nj = b.njf + b.njb;
   for (int q = 0; q < nstages && q < nj; ++q) {
@@ -723,6 +748,8 @@ __device__ __forceinline__ void issue_first_jobs(const BandInfo &b, const TileMe
     issue_job<T, TB, CL>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq], rank,
                          stage_bytes, st);
   }
+  if (CL == 1)
+    for (int q = nstages; q < nstages + pf && q < nj; ++q) prefetch_job<T, TB>(b, tm, jobs, q, ltile, utile, srcs);
 }
 
 // Forward sweep in place over vec, backward sweep from vec into xout (both in
@@ -735,13 +762,13 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
                                 T *vec, T *xout, T *win, unsigned char *ring,
                                 uint32_t stage_bytes, int nstages, uint64_t *bars,
                                 uint32_t &jbase, int task, bool issued, DevStatus *st,
-                                uint32_t first_wait, int wext, int vext) {
+                                uint32_t first_wait, int wext, int vext, int pf) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nj = b.njf + b.njb;
   // job q of this task is job jbase + q of the CTA: its stage and phase
-  if (tid == 0 && !issued) issue_first_jobs<T, TB>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, 0, st);
+  if (tid == 0 && !issued) issue_first_jobs<T, TB>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, 0, st, pf);
   bool ok = true;
   int q = 0;
   for (; q < nj; ++q) {
@@ -823,6 +850,7 @@ __device__ bool sweep_pipelined(const BandInfo &b, const TileMeta *__restrict__ 
     if (tid == 0 && q + nstages < nj) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_job<T, TB>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx], 0, stage_bytes, st);
+      if (pf > 0 && q + nstages + pf < nj) prefetch_job<T, TB>(b, tm, jobs, q + nstages + pf, ltile, utile, srcs);
     }
   }
   if (!ok) {
@@ -1079,10 +1107,10 @@ __device__ __forceinline__ bool run_sweep(const BandInfo &b, const TileMeta *tm,
                                           T *xout, T *win, unsigned char *ring, uint32_t stage_bytes,
                                           int nstages, uint64_t *bars, uint32_t &jbase, int task,
                                           DevStatus *st, uint32_t first_wait, SweepCtx<T, CL> &cx, int wext,
-                                          int vext) {
+                                          int vext, int pf) {
   if (CL == 1)
     return sweep_pipelined<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
-                                  nstages, bars, jbase, task, true, st, first_wait, wext, vext);
+                                  nstages, bars, jbase, task, true, st, first_wait, wext, vext, pf);
   return sweep_cluster<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
                               bars, jbase, cx.sstep, task, st, first_wait, cx.xb, cx.xbs, cx.okf, cx.pxb,
                               cx.pokf, cx.rank, wext, vext);
@@ -1101,7 +1129,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
                                       const int32_t *__restrict__ sched_off,
                                       const int32_t *__restrict__ task_sys,
                                       const int32_t *__restrict__ act, DevStatus *st,
-                                      uint32_t first_wait) {
+                                      uint32_t first_wait, int pf) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -1124,7 +1152,8 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();  // the tables are staged: start the first copies, then gather y
     if (threadIdx.x == 0)
-      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
+      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
+                                  pf);
     const int ntot = b.nst * TB + pad;
     // y gathered through perm: eight indices, then eight values, in flight
     // per thread (a chain of dependent loads per element took ~8 us)
@@ -1149,7 +1178,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     }
     __syncthreads();
     if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
-                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot))
+                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
       return;
     // both CTAs of a cluster hold the whole result: each writes its share
     for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) z[b.row0 + i] = xout[i];
@@ -1172,7 +1201,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       const int32_t *__restrict__ sched_off,
                                       const int32_t *__restrict__ task_sys,
                                       const int32_t *__restrict__ act, DevStatus *st,
-                                      uint32_t first_wait) {
+                                      uint32_t first_wait, int pf) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
@@ -1195,7 +1224,8 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();
     if (threadIdx.x == 0)
-      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st);
+      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
+                                  pf);
     const int ntot = b.nst * TB + pad;
     // (E z2) of the subdomain's rows: the row bounds of eight rows, then their
     // entries, loaded before use (rows of E hold 0-2 entries)
@@ -1225,7 +1255,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     }
     __syncthreads();
     if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
-                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot))
+                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
       return;
     for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) {
       const int r = b.row0 + i;
@@ -1442,7 +1472,7 @@ static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   if (grid <= 0) return cudaSuccess;
   return launch_sweep(band_solve_fwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
                       max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, y, perm, z, pl.sched,
-                      pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait);
+                      pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
 }
 
 // tile width and cluster size of a plan: 8 TB / cl threads per CTA
@@ -1483,7 +1513,7 @@ static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   if (grid <= 0) return cudaSuccess;
   return launch_sweep(band_solve_bwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
                       max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, e_ptr, e_col, e_val, z2,
-                      z1, perm, x, pl.sched, pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait);
+                      z1, perm, x, pl.sched, pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
 }
 
 template <typename T>

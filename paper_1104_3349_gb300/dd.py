@@ -99,7 +99,7 @@ class dd_opts(ctypes.Structure):
                 ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
                 ("time_kernels", ctypes.c_int32), ("sweep_cluster", ctypes.c_int32),
                 ("mlp_weights", ctypes.c_char_p), ("overlap", ctypes.c_int32), ("radius", ctypes.c_int32),
-                ("krylov_threads", ctypes.c_int32), ("pad_opts", ctypes.c_int32)]
+                ("krylov_threads", ctypes.c_int32), ("sweep_prefetch", ctypes.c_int32)]
 
 
 class dd_info(ctypes.Structure):
@@ -118,7 +118,7 @@ class dd_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("stage_bytes", ctypes.c_int32), ("sweep_grid", ctypes.c_int32),
                 ("sweep_slots", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tuned_us", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("graphs", ctypes.c_int32), ("learned_entries", ctypes.c_int64),
-                ("learned_fallback", ctypes.c_int32), ("pad3", ctypes.c_int32),
+                ("learned_fallback", ctypes.c_int32), ("sweep_prefetch", ctypes.c_int32),
                 ("krylov_steps", ctypes.c_int64), ("cgs2_ms", ctypes.c_double), ("cgs2_fma", ctypes.c_double),
                 ("spmv_ms", ctypes.c_double), ("sweep_cluster", ctypes.c_int32), ("msce_nodes_max", ctypes.c_int32)]
 
@@ -234,7 +234,7 @@ class DD:
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
                  autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False, sweep_cluster=0,
-                 overlap=0, radius=0, krylov_threads=0):
+                 overlap=0, radius=0, krylov_threads=0, sweep_prefetch=0):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -252,6 +252,7 @@ class DD:
         o.overlap = int(overlap)
         o.radius = int(radius)
         o.krylov_threads = int(krylov_threads)
+        o.sweep_prefetch = int(sweep_prefetch)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
@@ -354,7 +355,8 @@ class DDBatch:
     """A batch of independent systems behind one handle (dd_setup_batched)."""
 
     def __init__(self, systems, kind="msce_inf", prec=DD_FP64, pivot_tol=0.0, max_restart=50, stream=None,
-                 use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, sweep_cluster=0):
+                 use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, sweep_cluster=0,
+                 sweep_prefetch=0):
         """systems: list of (A, part, m, perm, agg_offsets) with A a CSR (perm, agg_offsets may be None)."""
         lib = load()
         self._lib = lib
@@ -375,6 +377,7 @@ class DDBatch:
         o = dd_opts(int(prec), float(pivot_tol), int(bool(use_graph)), int(max_restart), int(bool(autotune)),
                     int(krylov_ctas_per_sm))
         o.sweep_cluster = int(sweep_cluster)
+        o.sweep_prefetch = int(sweep_prefetch)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)

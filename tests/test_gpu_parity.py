@@ -247,3 +247,26 @@ def test_cluster_sweeps_equal_single_cta(torch_dev, prec, grid, m, sz):
     xr = R.apply(y)
     err = np.linalg.norm(xs[1] - xr) / np.linalg.norm(xr)
     assert err <= (1e-10 if prec == 0 else 1e-4), err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("grid,m,sz", [(32, 4, 64), (20, 4, 33), (6, 2, 5)])
+def test_l2_prefetch_changes_no_bit(torch_dev, prec, grid, m, sz):
+    """The sweeps' L2 prefetch is a hint: off (the default) and distances 1,
+    2 and 5 give the same bits; the distance is reported in the stats."""
+    torch, dev = torch_dev
+    from paper_1104_3349_gb300 import dd
+    w = W.make_workload("t", grid, 0.02, 1.0, W.WIND_FOURIER, grid, m, sz=sz)
+    y = W.uniform(3, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xs = []
+    for pf, want in ((0, 0), (1, 1), (2, 2), (5, 5)):
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=w.agg, prec=prec, sweep_prefetch=pf)
+        assert P.stats()["sweep_prefetch"] == want
+        xd = torch.full_like(yd, float("nan"))
+        P.apply(yd, xd)
+        assert P.check_status() == 0
+        xs.append(xd.cpu().numpy())
+        P.close()
+    for x in xs[1:]:
+        assert np.array_equal(xs[0].view(np.uint64), x.view(np.uint64))
