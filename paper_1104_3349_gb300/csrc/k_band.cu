@@ -1269,13 +1269,44 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
 // chunk of NR columns per CTA; X column-major (leading dimension n_j) in
 // global memory, the tile windows staged in shared memory.
 // ---------------------------------------------------------------------------
+// four consecutive T at a 16-byte aligned address (shared or global)
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+// columns 4ch .. 4ch+3 of row r of a forward tile K (16-byte chunks swizzled
+// by row: four floats, or two pairs of doubles)
+template <typename T, int TB>
+__device__ __forceinline__ void k_row4(const T *__restrict__ K, int r, int ch, T (&o)[4]) {
+  if (sizeof(T) == 4) {
+    ld4(K + r * TB + ((ch ^ (r & 7)) << 2), o);
+  } else {
+    const T *row = K + r * TB;
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(row + (((2 * ch) ^ (r & 7)) << 1)));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(row + (((2 * ch + 1) ^ (r & 7)) << 1)));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+}
+
+// X = A_jj^-1 X for a chunk of NR = 16 columns per CTA (256 threads).  A
+// thread owns 4 right-hand sides (4 rq .. 4 rq + 3) of 4 window rows
+// (forward) or of one tile row (backward) and accumulates them in
+// registers: each tile value loaded serves 4 right-hand sides and each
+// window value 4 rows.  Every output is summed over the tile's columns in
+// ascending order, as a single chain of fused multiply-adds.
 template <typename T, int NR, int TB>
-__global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
-                                        const int32_t *__restrict__ ncols,
-                                        const int64_t *__restrict__ x_off,
-                                        const TileMeta *__restrict__ tm,
-                                        const T *__restrict__ ltile, const T *__restrict__ utile,
-                                        const int32_t *__restrict__ srcs, T *Xall) {
+__global__ void __launch_bounds__(256) band_solve_multi_kernel(const BandInfo *__restrict__ info,
+                                                               const int32_t *__restrict__ ncols,
+                                                               const int64_t *__restrict__ x_off,
+                                                               const TileMeta *__restrict__ tm,
+                                                               const T *__restrict__ ltile,
+                                                               const T *__restrict__ utile,
+                                                               const int32_t *__restrict__ srcs, T *Xall) {
+  static_assert(NR == 16, "4 groups of 4 right-hand sides");
   const BandInfo b = info[blockIdx.x];
   const int nc = ncols[blockIdx.x];
   const int k0 = blockIdx.y * NR;
@@ -1286,6 +1317,7 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
   extern __shared__ __align__(128) unsigned char smraw[];
   T *win = reinterpret_cast<T *>(smraw);  // max(wl, wu) x NR, [row][r]
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int rq = tid & 3, rg = tid >> 2;  // right-hand sides 4 rq.., row group
   // forward: X(window) <- [0; X_B] + K X_T on the exchanged window
   for (int t = 0; t < b.nst; ++t) {
     const TileMeta mt = tm[b.tile0 + t];
@@ -1300,15 +1332,44 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
       win[q * NR + r] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < WL * NR; e += nt) {
-      int i = e / NR, r = e % NR;
-      T acc = (i < TB) ? T(0) : win[e];
-      for (int c = 0; c < TB; ++c) acc += K[kidx<T, TB>(i, c)] * win[c * NR + r];
-      if (c0 + i < n && r < nr) X[(int64_t)r * n + c0 + i] = acc;
+    for (int ib = 0; ib < WL; ib += 256) {
+      T acc[4][4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = min(ib + rg + 64 * k, WL - 1);
+        T w0[4];
+        ld4(win + i * NR + 4 * rq, w0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[k][v] = (i >= TB) ? w0[v] : T(0);
+      }
+#pragma unroll 2
+      for (int ch = 0; ch < TB / 4; ++ch) {
+        T w[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld4(win + (4 * ch + u) * NR + 4 * rq, w[u]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          T kv[4];
+          k_row4<T, TB>(K, min(ib + rg + 64 * k, WL - 1), ch, kv);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[k][v] = fma(kv[u], w[u][v], acc[k][v]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = ib + rg + 64 * k;
+        if (i < WL && c0 + i < n)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (4 * rq + v < nr) X[(int64_t)(4 * rq + v) * n + c0 + i] = acc[k][v];
+      }
     }
     __syncthreads();
   }
-  // backward: X_T <- Kb [X_T; X_next]
+  // backward: X_T <- Kb [X_T; X_next]; thread (row rg & 63, right-hand sides
+  // 4 rq..), TB <= 64 rows
   for (int t = b.nst - 1; t >= 0; --t) {
     const TileMeta mt = tm[b.tile0 + t];
     const int r0 = t * TB, WU = mt.wu;
@@ -1319,11 +1380,25 @@ __global__ void band_solve_multi_kernel(const BandInfo *__restrict__ info,
       win[q * NR + r] = (row < n && r < nr) ? X[(int64_t)r * n + row] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < TB * NR; e += nt) {
-      int i = e / NR, r = e % NR;
-      T acc = T(0);
-      for (int k = 0; k < WU; ++k) acc += Kb[(int64_t)i * WU + k] * win[k * NR + r];
-      if (r0 + i < n && r < nr) X[(int64_t)r * n + r0 + i] = acc;
+    const int i = rg;
+    if (i < TB) {
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      const T *kr = Kb + (int64_t)i * WU;
+#pragma unroll 2
+      for (int k = 0; k < WU; k += 4) {
+        T kv[4], w[4][4];
+        ld4(kr + k, kv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld4(win + (k + u) * NR + 4 * rq, w[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[v] = fma(kv[u], w[u][v], acc[v]);
+      }
+      if (r0 + i < n)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (4 * rq + v < nr) X[(int64_t)(4 * rq + v) * n + r0 + i] = acc[v];
     }
     __syncthreads();
   }
