@@ -50,6 +50,8 @@ struct DDHandle {
   int sweep_sched_cap = 0;
   void *lu_scratch = nullptr;  // windows of the blocked LU (when not in shared memory)
   TileMeta *tm = nullptr;      // packed sweep tiles
+  bool tiles_ready = false;    // the packed tiles are written (or queued)
+  unsigned char *cld = nullptr;  // the tiles in the 2-CTA sweep layout (built on first use)
   SweepJob *jobs = nullptr;    // jobs of the sweep ring
   cudaStream_t stream = nullptr;
   // setup: while astream is set, allocations and uploads go to it (the side
@@ -508,6 +510,38 @@ int choose_cluster(const DDHandle *h, size_t stage) {
   return (h->sweep_cl_opt == 1 || h->sweep_cl_opt == 2) ? h->sweep_cl_opt : 1;
 }
 
+// The tiles in the layout of the 2-CTA sweeps (once per handle, after the
+// packed tiles): CTA p's slices of every subdomain, forward slices in
+// ascending and backward slices in descending tile order, so that a job of
+// either direction is one contiguous copy per CTA.
+template <typename T>
+dd_status build_cluster_layout(DDHandle *h) {
+  if (h->cld) return DD_OK;
+  int64_t off = 0;
+  for (int p = 0; p < 2; ++p)
+    for (const BandInfo &b : h->h_info) {
+      for (int t = 0; t < b.nst; ++t) {
+        int64_t fb, bb;
+        cluster_slice_bytes(h->h_tm[b.tile0 + t], h->tb, (int)sizeof(T), p, fb, bb);
+        h->h_tm[b.tile0 + t].cfo[p] = off;
+        off += fb;
+      }
+      for (int t = b.nst - 1; t >= 0; --t) {
+        int64_t fb, bb;
+        cluster_slice_bytes(h->h_tm[b.tile0 + t], h->tb, (int)sizeof(T), p, fb, bb);
+        h->h_tm[b.tile0 + t].cbo[p] = off;
+        off += bb;
+      }
+    }
+  const int ntiles = (int)h->h_tm.size();
+  if (ntiles)
+    CK(cudaMemcpyAsync(h->tm, h->h_tm.data(), sizeof(TileMeta) * ntiles, cudaMemcpyHostToDevice, h->stream));
+  TRY(dalloc(h, &h->cld, (size_t)std::max<int64_t>(off, 16)));
+  CK(launch_cluster_pack<T>(ntiles, h->tb, h->tm, static_cast<const T *>(bufs<T>(h).ltile),
+                            static_cast<const T *>(bufs<T>(h).utile), h->src, h->cld, h->stream));
+  return DD_OK;
+}
+
 // The sweep plan for one stage size: the job table, and a persistent LPT
 // schedule when the subdomains outnumber the CTAs that fit on the device.
 template <typename T>
@@ -532,6 +566,8 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage, int cl) {
   CK(cudaMemcpyAsync(h->d_info, h->h_info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, h->stream));
   h->plan.stage_bytes = (uint32_t)stage;
   h->plan.cl = cl;
+  if (cl > 1 && h->tiles_ready) TRY(build_cluster_layout<T>(h));
+  h->plan.cld = h->cld;
   h->plan.threads = 8 * h->tb / cl;
   const int slots = band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, h->plan.stage_bytes);
   if (slots <= 0) {
@@ -1531,6 +1567,11 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     h->stats.factor_bytes = (lofs + uofs) * (int64_t)sizeof(T) + sofs * (int64_t)sizeof(int32_t);
     CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tb, h->tm, B.band, B.lm, h->piv,
                             B.ltile, B.utile, h->src, s));
+    h->tiles_ready = true;
+    if (h->plan.cl > 1) {
+      TRY(build_cluster_layout<T>(h));
+      h->plan.cld = h->cld;
+    }
   }
   // G(R_a, R_a) into S
   CK(cudaMemsetAsync(B.S, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));

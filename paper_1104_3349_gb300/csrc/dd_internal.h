@@ -46,6 +46,9 @@ __host__ __device__ inline int64_t bi_lraw_elems(const BandInfo &b) {
 struct TileMeta {
   int64_t lofs, uofs, sofs;
   int32_t wl, wu;
+  // 2-CTA sweeps: byte offsets of CTA p's forward slice (its K rows, then
+  // the tile's src) and backward slice (its Kb rows) in the cluster layout
+  int64_t cfo[2], cbo[2];
 };
 
 // a job of the sweep ring: tiles [lo, hi) of one subdomain, one bulk copy
@@ -105,6 +108,8 @@ struct SweepPlan {
   int cl = 1;
   // L2 prefetch distance in jobs beyond the ring (0: none)
   int pf = 0;
+  // cl = 2: the tiles in the cluster layout (TileMeta cfo / cbo)
+  const unsigned char *cld = nullptr;
 };
 
 // Device-side error word: first failure wins.
@@ -182,6 +187,12 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
 // clusters for cl = 2) at this stage size; 0: they do not fit
 template <typename T>
 int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes);
+// The 2-CTA sweep layout: bytes of CTA p's forward / backward slice of a tile,
+// and the copy of every tile's slices to cld at TileMeta cfo / cbo
+void cluster_slice_bytes(const TileMeta &mt, int tb, int elem_size, int p, int64_t &fwd, int64_t &bwd);
+template <typename T>
+cudaError_t launch_cluster_pack(int ntiles, int tb, const TileMeta *tm, const T *ltile, const T *utile,
+                                const int32_t *srcs, unsigned char *cld, cudaStream_t s);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>

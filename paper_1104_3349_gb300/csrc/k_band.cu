@@ -38,6 +38,9 @@ namespace {
 __host__ __device__ inline int src_stride_w(int w) { return round4(w); }
 // row stride of a cluster sweep's exchange buffers (room for any tile slice)
 __host__ __device__ inline int sweep_xbs(int tb, int max_kl) { return round4(tb + max_kl + 8); }
+// elements of one step's message between the two CTAs of a cluster sweep:
+// sweep_xbs row values, then the sender's flag and padding
+__host__ __device__ inline int sweep_msg(int tb, int max_kl) { return sweep_xbs(tb, max_kl) + 4; }
 // zero padding beyond the tiles of the resident vectors: room for the
 // widest window or row of a tile, a multiple of 32 elements
 __host__ __device__ inline int sweep_pad_hd(int max_kl, int max_ku2) {
@@ -83,18 +86,41 @@ __host__ __device__ __forceinline__ int kidx(int r, int c) {
 // later columns reach the multipliers of earlier columns of the same tile
 // only, which is the order the forward sweep applies them in.
 // ---------------------------------------------------------------------------
+// Warp-wide argmax of (v, L): the largest v, then the lowest L, with v >= 0
+// for candidates and v < 0 (or NaN mapped to < 0) for none.  Positive
+// floating-point values order as their bit patterns, so the maximum is taken
+// with integer warp reductions on the bits; zero, negative and NaN values
+// count as key 0 (a candidate of value 0 still wins over a non-candidate,
+// whose L is INT_MAX; its pivot then fails the threshold test).  Every lane
+// gets the winner's v, L and r.
+__device__ __forceinline__ uint32_t warp_key_max(uint32_t k) { return __reduce_max_sync(0xffffffffu, k); }
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T &v, int &L, int &r) {
+  bool tie;
+  if constexpr (sizeof(T) == 4) {
+    const uint32_t k = v > T(0) ? __float_as_uint((float)v) : 0u;
+    tie = k == warp_key_max(k);
+  } else {
+    const uint64_t b = v > T(0) ? (uint64_t)__double_as_longlong((double)v) : 0ull;
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const bool th = hi == warp_key_max(hi);
+    const uint32_t lm = __reduce_max_sync(0xffffffffu, th ? lo : 0u);
+    tie = th && lo == lm;
+  }
+  const int Lm = __reduce_min_sync(0xffffffffu, tie ? L : INT_MAX);
+  const int src = __ffs(__ballot_sync(0xffffffffu, tie && L == Lm)) - 1;
+  v = __shfl_sync(0xffffffffu, v, src);
+  L = Lm;
+  r = __shfl_sync(0xffffffffu, r, src);
+}
+
 // CTA-wide argmax, ordered by value (larger first) then logical row (lower
 // first): every thread offers (v, L, r); the warps' winners go to buffer buf.
 // Every thread of the CTA must call it.
 template <typename T>
 __device__ __forceinline__ void offer_max(T v, int L, int r, T (*bv)[32], int (*bL)[32], int (*br)[32], int buf) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o; o >>= 1) {
-    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int oL = __shfl_xor_sync(0xffffffffu, L, o);
-    const int orr = __shfl_xor_sync(0xffffffffu, r, o);
-    if (ov > v || (ov == v && oL < L)) { v = ov; L = oL; r = orr; }
-  }
+  warp_argmax(v, L, r);
   if (lane == 0) { bv[buf][warp] = v; bL[buf][warp] = L; br[buf][warp] = r; }
 }
 
@@ -129,13 +155,11 @@ __device__ bool lu_panel_lazy(T *W, int ldw, int R, int Cw, int c0, int n, int k
   for (int c = 0; c < nbe; ++c) {
     __syncthreads();  // column c's offers and every update of column c-1 are done
     const int buf = c & 1;
-    T best = bv[buf][0];
-    int bestL = bL[buf][0], pr = br[buf][0];
-    for (int w = 1; w < nw; ++w) {
-      const T v = bv[buf][w];
-      const int l2 = bL[buf][w];
-      if (v > best || (v == best && l2 < bestL)) { best = v; bestL = l2; pr = br[buf][w]; }
-    }
+    // the warps' winners, one per lane, reduced in every warp
+    const int lane = tid & 31;
+    T best = lane < nw ? bv[buf][lane] : T(-1);
+    int bestL = lane < nw ? bL[buf][lane] : INT_MAX, pr = lane < nw ? br[buf][lane] : 0;
+    warp_argmax(best, bestL, pr);
     if (!(best > thresh)) {
       if (tid == 0) set_status(st, DD_ERR_SINGULAR_BLOCK, task);
       return false;
@@ -292,17 +316,44 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       __syncthreads();
     }
     // U12 = L11^-1 A12 (rows 0..NB-1, columns NB..Cw-1): one thread per
-    // column, forward substitution with the unit lower L11.  FP32 (window in
-    // shared memory, 512 threads) works in place; FP64 (window in global
-    // scratch at the bench's bandwidths, 256 threads) keeps the column in
-    // registers.
+    // column, forward substitution with the unit lower L11, the column in
+    // registers (the L11 entries are the same for every thread).
     if constexpr (sizeof(T) == 4) {
-      for (int q = DD_NB + tid; q < Cw; q += nt)
-        for (int c = 0; c < nbe - 1; ++c) {
-          const T xc = W[c * ldw + q];
-#pragma unroll 8
-          for (int r = c + 1; r < DD_NB; ++r) W[r * ldw + q] -= W[r * ldw + c] * xc;
+      // in two 16-row blocks, at most 17 live values: x = rows 0..15 solved
+      // with L11's leading block; rows 16..31 less their products with x,
+      // each a dot product stored at once; then those rows solved with the
+      // trailing block
+      static_assert(DD_NB == 32, "two 16-row blocks");
+      for (int q = DD_NB + tid; q < Cw; q += nt) {
+        T x[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = W[r * ldw + q];
+#pragma unroll
+        for (int c = 0; c < 15; ++c)
+#pragma unroll
+          for (int r = c + 1; r < 16; ++r)
+            if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) W[r * ldw + q] = x[r];
+#pragma unroll 1
+        for (int r = 16; r < DD_NB; ++r) {
+          T acc = W[r * ldw + q];
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c < nbe - 1) acc -= W[r * ldw + c] * x[c];
+          W[r * ldw + q] = acc;
         }
+        T y[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) y[r] = W[(16 + r) * ldw + q];
+#pragma unroll
+        for (int c = 0; c < 15; ++c)
+#pragma unroll
+          for (int r = c + 1; r < 16; ++r)
+            if (16 + c < nbe - 1) y[r] -= W[(16 + r) * ldw + 16 + c] * y[c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) W[(16 + r) * ldw + q] = y[r];
+      }
     } else {
       for (int q = DD_NB + tid; q < Cw; q += nt) {
         T x[DD_NB];
@@ -372,7 +423,7 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 // window sits in shared memory when it fits the launch's smem_bytes, else in
 // wscratch (wscratch_stride elements per subdomain).
 template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256, 1) band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
                                T *wscratch, int64_t wscratch_stride, int smem_bytes, double pivtol,
                                const int32_t *__restrict__ sched, const int32_t *__restrict__ sched_off,
                                DevStatus *st) {
@@ -642,31 +693,18 @@ template <typename T, int TB, int CL = 1>
 __device__ __forceinline__ void issue_job(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                           int q, const T *ltile, const T *utile, const int32_t *srcs,
                                           unsigned char *stage, uint64_t *bar, int rank, uint32_t stage_bytes,
-                                          DevStatus *st) {
+                                          DevStatus *st, const unsigned char *cld = nullptr) {
   bool fwd;
   const SweepJob jb = get_job(b, jobs, q, fwd);
   const TileMeta &a = tm[b.tile0 + jb.lo];
   if (CL > 1) {
+    // the job's slices of this CTA are contiguous in the cluster layout
+    // (forward ascending, backward descending): one copy
     uint32_t tot = 0;
     for (int t = jb.lo; t < jb.hi; ++t) tot += slice_bytes<T, TB, CL>(tm[b.tile0 + t], fwd, rank);
+    const int64_t o = fwd ? tm[b.tile0 + jb.lo].cfo[rank] : tm[b.tile0 + jb.hi - 1].cbo[rank];
     mbar_expect_tx(bar, tot);
-    uint32_t off = 0;
-    for (int u = 0; u < jb.hi - jb.lo; ++u) {
-      const TileMeta &mt = tm[b.tile0 + (fwd ? jb.lo + u : jb.hi - 1 - u)];
-      if (fwd) {
-        const int r0 = fwd_split(mt.wl, rank, CL), r1 = fwd_split(mt.wl, rank + 1, CL);
-        const uint32_t kb = (uint32_t)((r1 - r0) * TB * sizeof(T));
-        if (kb) bulk_g2s_checked(stage, off, ltile + mt.lofs + (int64_t)r0 * TB, kb, stage_bytes, bar, st);
-        off += kb;
-        const uint32_t sb = (uint32_t)(src_stride_w(mt.wl) * sizeof(int32_t));
-        bulk_g2s_checked(stage, off, srcs + mt.sofs, sb, stage_bytes, bar, st);
-        off += sb;
-      } else {
-        const uint32_t ub = (uint32_t)((TB / CL) * mt.wu * sizeof(T));
-        bulk_g2s_checked(stage, off, utile + mt.uofs + (int64_t)rank * (TB / CL) * mt.wu, ub, stage_bytes, bar, st);
-        off += ub;
-      }
-    }
+    bulk_g2s_checked(stage, 0, cld + o, tot, stage_bytes, bar, st);
     return;
   }
   if (fwd) {
@@ -740,13 +778,13 @@ __device__ __forceinline__ void issue_first_jobs(const BandInfo &b, const TileMe
                                                  const T *ltile, const T *utile, const int32_t *srcs,
                                                  unsigned char *ring, uint32_t stage_bytes, int nstages,
                                                  uint64_t *bars, uint32_t jbase, int rank, DevStatus *st,
-                                                 int pf = 0) {
+                                                 int pf = 0, const unsigned char *cld = nullptr) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const int nj = b.njf + b.njb;
   for (int q = 0; q < nstages && q < nj; ++q) {
     const int sq = (int)((jbase + q) % nstages);
     issue_job<T, TB, CL>(b, tm, jobs, q, ltile, utile, srcs, ring + (size_t)sq * stage_bytes, &bars[sq], rank,
-                         stage_bytes, st);
+                         stage_bytes, st, cld);
   }
   if (CL == 1)
     for (int q = nstages; q < nstages + pf && q < nj; ++q) prefetch_job<T, TB>(b, tm, jobs, q, ltile, utile, srcs);
@@ -875,37 +913,132 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+__device__ __forceinline__ uint32_t map_peer(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+// one element into the peer CTA's shared memory, counted (bytes) on the
+// peer's mbarrier
+__device__ __forceinline__ void st_async_peer(uint32_t raddr, float v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
+               "r"(__float_as_uint(v)), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_peer(uint32_t raddr, double v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
+               "l"(__double_as_longlong(v)), "r"(rbar)
+               : "memory");
+}
+// bounded wait on a local mbarrier whose bytes come from the peer CTA
+// (acquire at cluster scope, so the peer's stores are visible after it)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < DD_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Cluster context of a sweep CTA: its rank and task list index; CL = 2 also
+// the message buffers.  Each step s, each CTA sends the peer one message by
+// st.async into the peer's buffer xb[s & 1], counted on the peer's mbarrier
+// xbar[s & 1]: its flag (1: it had the step's tile bytes and computed its
+// rows), then its rows of the step.  Both CTAs know every step's row counts,
+// so at step s each arms its own xbar[s & 1] for the peer's message of step
+// s (the bytes may arrive before or after the arming).  The phase of step
+// s - 2 on that barrier was taken at step s - 1, and the peer sends step s
+// only after taking step s - 1, which this CTA sends after taking step s - 2:
+// no buffer or barrier phase is overtaken.
+template <typename T, int CL>
+struct SweepCtx {
+  int rank = 0, cid = 0, msg = 0;
+  T *xb = nullptr;
+  uint64_t *xbar = nullptr;
+  uint32_t pxb = 0, pxbar = 0;  // the peer's xb and xbar (shared::cluster addresses)
+  uint32_t sstep = 0;
+  __device__ void init(T *xb_, uint64_t *xbar_, int max_kl, int tb) {
+    cid = (int)blockIdx.x / CL;
+    if (CL > 1) {
+      namespace cgx = cooperative_groups;
+      rank = (int)cgx::this_cluster().block_rank();
+      xb = xb_;
+      xbar = xbar_;
+      msg = sweep_msg(tb, max_kl);
+      if (threadIdx.x == 0) {
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      pxb = map_peer(smem_u32(xb_), (uint32_t)(rank ^ 1));
+      pxbar = map_peer(smem_u32(xbar_), (uint32_t)(rank ^ 1));
+      cluster_barrier();  // the peer's barriers are set up before any message
+    }
+  }
+  // thread 0: expect the peer's message of step s (its flag and n rows)
+  __device__ __forceinline__ void arm(uint32_t s, int n) const {
+    if (threadIdx.x == 0) mbar_expect_tx(&xbar[s & 1u], (uint32_t)((n + 1) * sizeof(T)));
+  }
+  // element e of step s's message (0: the flag, 1 + i: row i) into the
+  // peer's buffer
+  __device__ __forceinline__ void put(uint32_t s, int e, T v) const {
+    const uint32_t q = s & 1u;
+    st_async_peer(pxb + (uint32_t)(((int)q * msg + e) * (int)sizeof(T)), v, pxbar + 8u * q);
+  }
+  // The peer's message of step s (every thread calls it): wait (bounded),
+  // its rows into dst[base + lo .. base + hi).  True when it came and
+  // carries the peer's flag.
+  __device__ bool take(uint32_t s, T *dst, int base, int lo, int hi) {
+    const int q = (int)(s & 1u);
+    const bool got = __syncthreads_and(mbar_wait_cluster(&xbar[q], (s >> 1) & 1u)) != 0;
+    bool pok = false;
+    if (got) {
+      const T *m = xb + q * msg;
+      for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) dst[base + r] = m[1 + r - lo];
+      pok = m[0] != T(0);
+    }
+    __syncthreads();  // every thread has read the message
+    return got && pok;
+  }
+};
+
 // The sweeps of one subdomain split over a 2-CTA cluster.  Each CTA keeps a
 // whole copy of vec and xout and streams only its slices of the tiles (half
-// the bytes through its shared memory).  A tile step: merge the peer's
-// results of the previous step into vec / xout, gather the window, compute
-// the CTA's rows, store them locally and into the peer's exchange buffer
-// xb[s & 1] (s: the CTA's step count, the same in both CTAs), store the
-// CTA's all-copies-arrived flag into the peer's okf[s & 1], then one cluster
-// barrier.  The peer writes xb[s & 1] only after the barrier of step s - 1,
-// which this CTA reaches only after merging xb[(s - 1) & 1], so the two
-// buffers never race.  A wait that gives up in either CTA makes both stop
-// after the same barrier (each reads its own and the peer's flag); each then
-// drains its own copies.  Rows are computed exactly as in the one-CTA sweep,
-// so the results are the same bits.
+// the bytes through its shared memory), one contiguous copy per job from
+// the cluster layout.  A tile step: take the peer's message of the previous
+// step (its rows merged into vec / xout), gather the window, compute the
+// CTA's rows, store them locally and send them to the peer.  No cluster
+// barrier per step: the only wait is for the peer's previous message.  A
+// CTA whose copy wait gives up sends its message with flag 0; the peer stops
+// at its next step, and both take the last message sent to them before
+// stopping, so none is in flight when the kernel's final cluster barrier
+// is reached.  Rows are computed exactly as in the one-CTA sweep, so the
+// results are the same bits.
 template <typename T, int TB>
 __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm,
-                              const SweepJob *__restrict__ jobs, const T *__restrict__ ltile,
-                              const T *__restrict__ utile, const int32_t *__restrict__ srcs, T *vec,
+                              const SweepJob *__restrict__ jobs, const unsigned char *__restrict__ cld, T *vec,
                               T *xout, T *win, unsigned char *ring, uint32_t stage_bytes, int nstages,
-                              uint64_t *bars, uint32_t &jbase, uint32_t &sstep, int task, DevStatus *st,
-                              uint32_t first_wait, T *xb, int xbs, volatile int32_t *okf, T *pxb,
-                              int32_t *pokf, int rank, int wext, int vext) {
+                              uint64_t *bars, uint32_t &jbase, int task, DevStatus *st, uint32_t first_wait,
+                              SweepCtx<T, 2> &cx, int wext, int vext) {
   using CV = typename Chunk<T>::V;
   constexpr int CN = Chunk<T>::N;
   constexpr int CL = 2, BR = TB / CL;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nj = b.njf + b.njb;
+  const int rank = cx.rank, XF = cx.msg - 1;  // rows a message holds
   bool ok = true;
-  // the peer's results of the last step, still to be merged: into vec (fwd)
-  // or xout, positions base + [lo, hi), from xb[par]
+  // the peer's message of the last step, still to be taken: into mdst,
+  // positions mbase + [mlo, mhi)
+  bool pending = false;
   T *mdst = nullptr;
-  int mbase = 0, mlo = 0, mhi = 0, mpar = 0;
+  int mbase = 0, mlo = 0, mhi = 0;
   int q = 0;
   for (; q < nj; ++q) {
     const uint32_t gq = jbase + q;
@@ -915,13 +1048,14 @@ __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm
     bool fwd;
     const SweepJob jb = get_job(b, jobs, q, fwd);
     uint32_t off = 0;
-    for (int u = 0; u < jb.hi - jb.lo && ok; ++u) {
+    for (int u = 0; u < jb.hi - jb.lo; ++u) {
       const int t = fwd ? jb.lo + u : jb.hi - 1 - u;
       const TileMeta &mt = tm[b.tile0 + t];
-      const int par = (int)(sstep & 1u);
-      // merge the peer's previous results, then the step's gather sees them
-      for (int r = mlo + tid; r < mhi; r += nt) mdst[mbase + r] = xb[mpar * xbs + (r - mlo)];
-      __syncthreads();
+      const uint32_t s = cx.sstep;
+      if (pending) {
+        pending = false;
+        if (!cx.take(s - 1, mdst, mbase, mlo, mhi)) { ok = false; break; }
+      }
       bool cta_ok;
       if (fwd) {
         const int c0 = t * TB, WL = mt.wl;
@@ -930,30 +1064,41 @@ __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm
         off += (uint32_t)((r1 - r0) * TB * sizeof(T));
         const int32_t *src = reinterpret_cast<const int32_t *>(stage + off);
         off += (uint32_t)(src_stride_w(WL) * sizeof(int32_t));
-        const bool wok = dd_check(st, WL <= wext && c0 + WL <= vext && r1 - r0 <= xbs, 31);
+        const bool wok = dd_check(st, WL <= wext && c0 + WL <= vext && r1 - r0 <= XF, 31);
         if (got && wok) {
           for (int e = tid; e < TB; e += nt)
             if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 32)) win[e] = vec[c0 + src[e]];
           for (int e = max(r0, TB) + tid; e < r1; e += nt)
             if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 32)) win[e] = vec[c0 + src[e]];
         }
+        cx.arm(s, fwd_split(WL, 2 - rank, CL) - fwd_split(WL, 1 - rank, CL));
         cta_ok = __syncthreads_and(got && wok) != 0;
-        if (cta_ok)
-          for (int r = r0 + tid; r < r1; r += nt) {
-            const CV *kr = reinterpret_cast<const CV *>(K + (r - r0) * TB);
-            const CV *wv = reinterpret_cast<const CV *>(win);
-            T a0 = (r < TB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
+        const int cnt = r1 - r0;
+        // element 1 + e of the message is row r0 + e, computed by the
+        // thread that sends it; element 0 the flag
+        for (int e = tid; e <= cnt; e += nt) {
+          T v = T(0);
+          if (e < cnt) {
+            if (cta_ok) {
+              const int r = r0 + e;
+              const CV *kr = reinterpret_cast<const CV *>(K + e * TB);
+              const CV *wv = reinterpret_cast<const CV *>(win);
+              T a0 = (r < TB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
 #pragma unroll
-            for (int ch = 0; ch < TB / CN; ch += 4) {
-              a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
-              a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
-              a2 = Chunk<T>::fmadd(kr[(ch + 2) ^ (r & 7)], wv[ch + 2], a2);
-              a3 = Chunk<T>::fmadd(kr[(ch + 3) ^ (r & 7)], wv[ch + 3], a3);
+              for (int ch = 0; ch < TB / CN; ch += 4) {
+                a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
+                a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
+                a2 = Chunk<T>::fmadd(kr[(ch + 2) ^ (r & 7)], wv[ch + 2], a2);
+                a3 = Chunk<T>::fmadd(kr[(ch + 3) ^ (r & 7)], wv[ch + 3], a3);
+              }
+              v = (a0 + a1) + (a2 + a3);
+              vec[c0 + r] = v;
             }
-            const T v = (a0 + a1) + (a2 + a3);
-            vec[c0 + r] = v;
-            pxb[par * xbs + (r - r0)] = v;
+            cx.put(s, 1 + e, v);
+          } else {
+            cx.put(s, 0, cta_ok ? T(1) : T(0));
           }
+        }
         mdst = vec;
         mbase = c0;
         mlo = fwd_split(WL, 1 - rank, CL);
@@ -965,9 +1110,11 @@ __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm
         const T *Kb = reinterpret_cast<const T *>(stage + off);
         off += (uint32_t)(BR * WU * sizeof(T));
         const int i = tid >> 3, h = tid & 7;
+        const bool bok = dd_check(st, r0 + WU <= vext && BR <= XF, 33);
+        cx.arm(s, BR);
+        cta_ok = __syncthreads_and(got && bok) != 0;
         T acc = T(0);
-        const bool bok = dd_check(st, r0 + WU <= vext && BR <= xbs, 33);
-        if (got && bok) {
+        if (cta_ok) {
           const CV *kr = reinterpret_cast<const CV *>(Kb + (int64_t)i * WU);
           const CV *bv = reinterpret_cast<const CV *>(vec + r0);
           const CV *xv = reinterpret_cast<const CV *>(xout + r0);
@@ -985,32 +1132,38 @@ __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
         if (h == 0) {
-          xout[r0 + rank * BR + i] = acc;
-          pxb[par * xbs + i] = acc;
+          if (cta_ok) xout[r0 + rank * BR + i] = acc;
+          cx.put(s, 1 + i, cta_ok ? acc : T(0));
         }
-        cta_ok = __syncthreads_and(got && bok) != 0;
+        if (tid == 1) cx.put(s, 0, cta_ok ? T(1) : T(0));
         mdst = xout;
         mbase = r0;
         mlo = (1 - rank) * BR;
         mhi = mlo + BR;
       }
-      if (tid == 0) pokf[par] = cta_ok ? 1 : 0;
-      cluster_barrier();
-      const bool peer_ok = okf[par] != 0;
-      mpar = par;
-      ++sstep;
-      if (!(cta_ok && peer_ok)) ok = false;
+      ++cx.sstep;
+      if (!cta_ok) {
+        // the peer stops at its next step: take its message of this step
+        // (none is then in flight), and stop
+        cx.take(s, mdst, mbase, mlo, mhi);
+        ok = false;
+        break;
+      }
+      pending = true;
     }
     if (!ok) break;
-    // the stage is free (every thread of the CTA passed the cluster barrier)
+    // the stage is free once every thread has finished the job's steps
+    __syncthreads();
     if (tid == 0 && q + nstages < nj) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_job<T, TB, CL>(b, tm, jobs, q + nstages, ltile, utile, srcs, stage, &bars[sidx], rank, stage_bytes, st);
+      issue_job<T, TB, CL>(b, tm, jobs, q + nstages, nullptr, nullptr, nullptr, stage, &bars[sidx], rank,
+                           stage_bytes, st, cld);
     }
   }
-  if (ok)
-    for (int r = mlo + tid; r < mhi; r += nt) mdst[mbase + r] = xb[mpar * xbs + (r - mlo)];
-  __syncthreads();
+  if (ok && pending) {
+    pending = false;
+    if (!cx.take(cx.sstep - 1, mdst, mbase, mlo, mhi)) ok = false;
+  }
   if (!ok) {
     if (tid == 0) {
       if (atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = task;
@@ -1030,15 +1183,15 @@ __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, 
                                       int max_tiles, int max_jobs, uint64_t *&bars, T *&vec,
                                       T *&xout, T *&win, TileMeta *&tms, SweepJob *&jbs,
                                       unsigned char *&ring, int cl = 1, T **xb = nullptr,
-                                      int32_t **okf = nullptr) {
+                                      uint64_t **xbar = nullptr) {
   bars = reinterpret_cast<uint64_t *>(smraw);
-  if (okf) *okf = reinterpret_cast<int32_t *>(smraw + 48);  // 2 flags after <= 4 mbarriers
+  if (xbar) *xbar = reinterpret_cast<uint64_t *>(smraw + 32);  // 2 message barriers after <= 4 ring barriers
   vec = reinterpret_cast<T *>(smraw + 64);
   xout = vec + max_n + pad;
   win = xout + max_n + pad;
   if (xb) *xb = win + TB + max_kl + 8;
   size_t used = 64 + sizeof(T) * (2 * ((size_t)max_n + pad) + TB + max_kl + 8 +
-                                  (cl > 1 ? 2 * (size_t)sweep_xbs(TB, max_kl) : 0));
+                                  (cl > 1 ? 2 * (size_t)sweep_msg(TB, max_kl) : 0));
   used = (used + 15) & ~(size_t)15;
   tms = reinterpret_cast<TileMeta *>(smraw + used);
   used += sizeof(TileMeta) * (size_t)max_tiles;
@@ -1077,43 +1230,19 @@ __device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, in
   t1 = sched_off ? sched_off[cid + 1] : cid + 1;
 }
 
-// Cluster context of a sweep CTA: its rank, its task list index, and the
-// exchange buffers of the peer (CL = 2); CL = 1: rank 0, task list blockIdx.x.
-template <typename T, int CL>
-struct SweepCtx {
-  int rank = 0, cid = 0, xbs = 0;
-  T *xb = nullptr, *pxb = nullptr;
-  int32_t *okf = nullptr, *pokf = nullptr;
-  uint32_t sstep = 0;
-  __device__ void init(T *xb_, int32_t *okf_, int max_kl, int tb) {
-    cid = (int)blockIdx.x / CL;
-    if (CL > 1) {
-      namespace cgx = cooperative_groups;
-      cgx::cluster_group cl = cgx::this_cluster();
-      rank = (int)cl.block_rank();
-      xb = xb_;
-      okf = okf_;
-      xbs = sweep_xbs(tb, max_kl);
-      pxb = cl.map_shared_rank(xb_, (unsigned)(rank ^ 1));
-      pokf = cl.map_shared_rank(okf_, (unsigned)(rank ^ 1));
-      cluster_barrier();  // the peer runs before any store into its shared memory
-    }
-  }
-};
-
 template <typename T, int TB, int CL>
 __device__ __forceinline__ bool run_sweep(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
-                                          const T *ltile, const T *utile, const int32_t *srcs, T *vec,
-                                          T *xout, T *win, unsigned char *ring, uint32_t stage_bytes,
-                                          int nstages, uint64_t *bars, uint32_t &jbase, int task,
-                                          DevStatus *st, uint32_t first_wait, SweepCtx<T, CL> &cx, int wext,
-                                          int vext, int pf) {
-  if (CL == 1)
+                                          const T *ltile, const T *utile, const int32_t *srcs,
+                                          const unsigned char *cld, T *vec, T *xout, T *win,
+                                          unsigned char *ring, uint32_t stage_bytes, int nstages, uint64_t *bars,
+                                          uint32_t &jbase, int task, DevStatus *st, uint32_t first_wait,
+                                          SweepCtx<T, CL> &cx, int wext, int vext, int pf) {
+  if constexpr (CL == 1)
     return sweep_pipelined<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
                                   nstages, bars, jbase, task, true, st, first_wait, wext, vext, pf);
-  return sweep_cluster<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
-                              bars, jbase, cx.sstep, task, st, first_wait, cx.xb, cx.xbs, cx.okf, cx.pxb,
-                              cx.pokf, cx.rank, wext, vext);
+  else
+    return sweep_cluster<T, TB>(b, tm, jobs, cld, vec, xout, win, ring, stage_bytes, nstages, bars, jbase, task,
+                                st, first_wait, cx, wext, vext);
 }
 
 // z = A_jj^-1 y_j with y gathered from the original numbering.
@@ -1123,7 +1252,8 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
                                       uint32_t stage_bytes,
                                       const TileMeta *__restrict__ tm, const SweepJob *__restrict__ jobs,
                                       const T *__restrict__ ltile, const T *__restrict__ utile,
-                                      const int32_t *__restrict__ srcs, const double *__restrict__ y,
+                                      const int32_t *__restrict__ srcs,
+                                      const unsigned char *__restrict__ cld, const double *__restrict__ y,
                                       const int32_t *__restrict__ perm, T *z,
                                       const int32_t *__restrict__ sched,
                                       const int32_t *__restrict__ sched_off,
@@ -1135,12 +1265,12 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
   T *xb = nullptr;
-  int32_t *okf = nullptr;
+  uint64_t *xbar = nullptr;
   carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring, CL, &xb,
-               &okf);
+               &xbar);
   init_bars(bars, nstages);
   SweepCtx<T, CL> cx;
-  cx.init(xb, okf, max_kl, TB);
+  cx.init(xb, xbar, max_kl, TB);
   int t0, t1;
   task_range(sched_off, t0, t1, cx.cid);
   uint32_t jbase = 0;
@@ -1153,7 +1283,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     __syncthreads();  // the tables are staged: start the first copies, then gather y
     if (threadIdx.x == 0)
       issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
-                                  pf);
+                                  pf, cld);
     const int ntot = b.nst * TB + pad;
     // y gathered through perm: eight indices, then eight values, in flight
     // per thread (a chain of dependent loads per element took ~8 us)
@@ -1177,12 +1307,16 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
       }
     }
     __syncthreads();
-    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
+    // a failed sweep stops both CTAs of a cluster at the same step
+    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes, nstages,
                               bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
-      return;
+      break;
     // both CTAs of a cluster hold the whole result: each writes its share
     for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) z[b.row0 + i] = xout[i];
   }
+  // no CTA of a cluster leaves while its peer may still address its shared
+  // memory (every message sent has been taken by then)
+  if (CL > 1) cluster_barrier();
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
@@ -1193,6 +1327,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
                                       const TileMeta *__restrict__ tm, const SweepJob *__restrict__ jobs,
                                       const T *__restrict__ ltile, const T *__restrict__ utile,
                                       const int32_t *__restrict__ srcs,
+                                      const unsigned char *__restrict__ cld,
                                       const int32_t *__restrict__ e_ptr,
                                       const int32_t *__restrict__ e_col,
                                       const T *__restrict__ e_val, const T *__restrict__ z2,
@@ -1207,12 +1342,12 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
   uint64_t *bars; T *vec, *xout, *win; unsigned char *ring;
   TileMeta *tms; SweepJob *jbs;
   T *xb = nullptr;
-  int32_t *okf = nullptr;
+  uint64_t *xbar = nullptr;
   carve<T, TB>(smraw, max_n, pad, max_kl, max_tiles, max_jobs, bars, vec, xout, win, tms, jbs, ring, CL, &xb,
-               &okf);
+               &xbar);
   init_bars(bars, nstages);
   SweepCtx<T, CL> cx;
-  cx.init(xb, okf, max_kl, TB);
+  cx.init(xb, xbar, max_kl, TB);
   int t0, t1;
   task_range(sched_off, t0, t1, cx.cid);
   uint32_t jbase = 0;
@@ -1225,7 +1360,7 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     __syncthreads();
     if (threadIdx.x == 0)
       issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
-                                  pf);
+                                  pf, cld);
     const int ntot = b.nst * TB + pad;
     // (E z2) of the subdomain's rows: the row bounds of eight rows, then their
     // entries, loaded before use (rows of E hold 0-2 entries)
@@ -1254,14 +1389,15 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
       }
     }
     __syncthreads();
-    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes, nstages,
+    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes, nstages,
                               bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
-      return;
+      break;
     for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) {
       const int r = b.row0 + i;
       x[perm[r]] = double(z1[r] - xout[i]);
     }
   }
+  if (CL > 1) cluster_barrier();
 }
 
 // ---------------------------------------------------------------------------
@@ -1419,7 +1555,7 @@ static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, in
                                int max_jobs) {
   const int pad = sweep_pad_hd(max_kl, max_ku2);
   size_t used = 64 + es * (2 * ((size_t)max_n + pad) + tb + max_kl + 8 +
-                           (cl > 1 ? 2 * (size_t)sweep_xbs(tb, max_kl) : 0));
+                           (cl > 1 ? 2 * (size_t)sweep_msg(tb, max_kl) : 0));
   used = (used + 15) & ~(size_t)15;
   used += sizeof(TileMeta) * (size_t)max_tiles + sizeof(SweepJob) * (size_t)max_jobs;
   return (used + 127) & ~(size_t)127;
@@ -1509,6 +1645,60 @@ cudaError_t launch_band_tiles(const BandInfo *d_info, int m, int max_tiles, int 
   return cudaErrorInvalidValue;
 }
 
+// The tiles in the layout of the 2-CTA sweeps: CTA p's forward slice of
+// tile t (its K rows [fwd_split(wl, p), fwd_split(wl, p + 1)), then the
+// tile's src) at byte cfo[p], and its backward slice (Kb rows
+// [p TB / 2, (p + 1) TB / 2)) at cbo[p].  Every piece is a multiple of 16
+// bytes at a 16-byte aligned offset; one CTA per (tile, p, direction).
+template <typename T, int TB>
+__global__ void cluster_pack_kernel(int ntiles, const TileMeta *__restrict__ tm, const T *__restrict__ ltile,
+                                    const T *__restrict__ utile, const int32_t *__restrict__ srcs,
+                                    unsigned char *cld) {
+  const int t = blockIdx.x, p = blockIdx.y;
+  if (t >= ntiles) return;
+  const TileMeta mt = tm[t];
+  const uint4 *src[2];
+  uint4 *dst[2];
+  int64_t n16[2] = {0, 0};
+  if (blockIdx.z == 0) {
+    const int r0 = fwd_split(mt.wl, p, 2), r1 = fwd_split(mt.wl, p + 1, 2);
+    const int64_t kb = (int64_t)(r1 - r0) * TB * sizeof(T);
+    src[0] = reinterpret_cast<const uint4 *>(ltile + mt.lofs + (int64_t)r0 * TB);
+    dst[0] = reinterpret_cast<uint4 *>(cld + mt.cfo[p]);
+    n16[0] = kb / 16;
+    src[1] = reinterpret_cast<const uint4 *>(srcs + mt.sofs);
+    dst[1] = reinterpret_cast<uint4 *>(cld + mt.cfo[p] + kb);
+    n16[1] = (int64_t)src_stride_w(mt.wl) * sizeof(int32_t) / 16;
+  } else {
+    src[0] = reinterpret_cast<const uint4 *>(utile + mt.uofs + (int64_t)p * (TB / 2) * mt.wu);
+    dst[0] = reinterpret_cast<uint4 *>(cld + mt.cbo[p]);
+    n16[0] = (int64_t)(TB / 2) * mt.wu * sizeof(T) / 16;
+    src[1] = nullptr;
+    dst[1] = nullptr;
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int64_t i = threadIdx.x; i < n16[k]; i += blockDim.x) dst[k][i] = src[k][i];
+}
+
+// Bytes of CTA p's forward and backward slices of one tile in the cluster
+// layout (host side of cluster_pack_kernel's offsets).
+void cluster_slice_bytes(const TileMeta &mt, int tb, int elem_size, int p, int64_t &fwd, int64_t &bwd) {
+  const int r0 = fwd_split(mt.wl, p, 2), r1 = fwd_split(mt.wl, p + 1, 2);
+  fwd = (int64_t)(r1 - r0) * tb * elem_size + (int64_t)src_stride_w(mt.wl) * 4;
+  bwd = (int64_t)(tb / 2) * mt.wu * elem_size;
+}
+
+template <typename T>
+cudaError_t launch_cluster_pack(int ntiles, int tb, const TileMeta *tm, const T *ltile, const T *utile,
+                                const int32_t *srcs, unsigned char *cld, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const dim3 grid(ntiles, 2, 2);
+  if (tb == 64) cluster_pack_kernel<T, 64><<<grid, 128, 0, s>>>(ntiles, tm, ltile, utile, srcs, cld);
+  else if (tb == 32) cluster_pack_kernel<T, 32><<<grid, 128, 0, s>>>(ntiles, tm, ltile, utile, srcs, cld);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 // one sweep launch: a plain grid, or clusters of cl CTAs
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_sweep(void (*kernel)(KArgs...), int grid, int threads, size_t smem, int cl,
@@ -1546,7 +1736,7 @@ static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
   return launch_sweep(band_solve_fwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
-                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, y, perm, z, pl.sched,
+                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, pl.cld, y, perm, z, pl.sched,
                       pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
 }
 
@@ -1587,7 +1777,7 @@ static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
   return launch_sweep(band_solve_bwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
-                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, e_ptr, e_col, e_val, z2,
+                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, pl.cld, e_ptr, e_col, e_val, z2,
                       z1, perm, x, pl.sched, pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
 }
 
@@ -1706,6 +1896,8 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
       const SweepJob *, const T *, const T *, const int32_t *, const int32_t *, const int32_t *,    \
       const T *, const T *, const T *, const int32_t *, double *, DevStatus *, cudaStream_t);      \
   template int band_sweep_slots<T>(int, int, int, int, int, uint32_t);                              \
+  template cudaError_t launch_cluster_pack<T>(int, int, const TileMeta *, const T *, const T *,    \
+                                              const int32_t *, unsigned char *, cudaStream_t);      \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \
                                                   const int64_t *, int, int, int, int,             \
                                                   const TileMeta *, const T *, const T *,          \
