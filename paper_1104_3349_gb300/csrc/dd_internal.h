@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 #include <string>
 #include <vector>
@@ -117,6 +118,36 @@ struct DevStatus {
   int32_t code;   // 0 ok, else a dd_status
   int32_t block;  // failing block (DD_ERR_CHECK: the check's site)
 };
+
+#ifdef __CUDACC__
+// Warp-wide argmax of (v, L): the largest v, then the lowest L, with v >= 0
+// for candidates and v < 0 (or NaN mapped to < 0) for none.  Positive
+// floating-point values order as their bit patterns, so the maximum is taken
+// with integer warp reductions on the bits; zero, negative and NaN values
+// count as key 0 (a candidate of value 0 still wins over a non-candidate,
+// whose L is INT_MAX; its pivot then fails the threshold test).  Every lane
+// gets the winner's v, L and r.
+__device__ __forceinline__ uint32_t warp_key_max(uint32_t k) { return __reduce_max_sync(0xffffffffu, k); }
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T &v, int &L, int &r) {
+  bool tie;
+  if constexpr (sizeof(T) == 4) {
+    const uint32_t k = v > T(0) ? __float_as_uint((float)v) : 0u;
+    tie = k == warp_key_max(k);
+  } else {
+    const uint64_t b = v > T(0) ? (uint64_t)__double_as_longlong((double)v) : 0ull;
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const bool th = hi == warp_key_max(hi);
+    const uint32_t lm = __reduce_max_sync(0xffffffffu, th ? lo : 0u);
+    tie = th && lo == lm;
+  }
+  const int Lm = __reduce_min_sync(0xffffffffu, tie ? L : INT_MAX);
+  const int src = __ffs(__ballot_sync(0xffffffffu, tie && L == Lm)) - 1;
+  v = __shfl_sync(0xffffffffu, v, src);
+  L = Lm;
+  r = __shfl_sync(0xffffffffu, r, src);
+}
+#endif
 
 // Checked build (compiled with -DDD_CHECKED): the sweep, SpMV and interface
 // kernels test every index, size and alignment they compute before the

@@ -175,9 +175,19 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k
   __shared__ int s_fail;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   if (tid == 0) s_fail = 0;
-  for (int e = tid; e < rows * NB; e += nt) {
-    const int r = e / NB, c = e % NB;
-    W[r * LD + c] = (c < nbe) ? Wg[(int64_t)(c0 + r) * NO + c0 + c] : T(0);
+  // eight loads in flight per thread before their stores
+  for (int e0 = tid; e0 < rows * NB; e0 += 8 * nt) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt, r = e / NB, c = e % NB;
+      v[u] = (e < rows * NB && c < nbe) ? Wg[(int64_t)(c0 + r) * NO + c0 + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt;
+      if (e < rows * NB) W[(e / NB) * LD + e % NB] = v[u];
+    }
   }
   __syncthreads();
   const T thresh = T(pivtol) * amax[b];
@@ -195,11 +205,8 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k
       const T v = tabs(W[r * LD]);
       if (v > best) { best = v; besti = r; }
     }
-    for (int o = 16; o; o >>= 1) {
-      T ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, besti, o);
-      if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
-    }
+    int unused = 0;
+    warp_argmax(best, besti, unused);
     if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
   }
   __syncthreads();
@@ -207,12 +214,8 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k
   for (int c = 0; c < nbe; ++c) {
     if (warp == 0) {
       T bb = lane < nw ? bv[lane] : T(-1);
-      int ii = lane < nw ? bi[lane] : rows;
-      for (int o = 16; o; o >>= 1) {
-        T ov = __shfl_xor_sync(0xffffffffu, bb, o);
-        int oi = __shfl_xor_sync(0xffffffffu, ii, o);
-        if (ov > bb || (ov == bb && oi < ii)) { bb = ov; ii = oi; }
-      }
+      int ii = lane < nw ? bi[lane] : rows, unused = 0;
+      warp_argmax(bb, ii, unused);
       if (lane == 0) {
         if (!(bb > thresh)) {
           s_fail = 1;
@@ -235,27 +238,35 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k
     if (tid < NB) W[c * LD + tid] = prow[tid];
     T best = T(-1);
     int besti = rows;
+    // the pivot row in registers; each row's entries loaded before any of
+    // its stores (the column loops are unrolled with predicates)
+    T pv[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) pv[q] = prow[q];
     for (int r = c + 1 + tid; r < rows; r += nt) {
       const bool sw = (r == pr);
-      const T l = (sw ? crow[c] : W[r * LD + c]) / piv;
-      W[r * LD + c] = l;
+      T *wr = W + r * LD;
+      const T *src = sw ? crow : wr;
+      const T l = src[c] / piv;
+      T a[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q > c && q < nbe) a[q] = src[q];
+      wr[c] = l;
       if (sw)
-        for (int q = 0; q < c; ++q) W[r * LD + q] = crow[q];
-      for (int q = c + 1; q < nbe; ++q) {
-        T t = sw ? crow[q] : W[r * LD + q];
-        t -= l * prow[q];
-        W[r * LD + q] = t;
-      }
-      if (c + 1 < nbe) {
-        const T v = tabs(W[r * LD + c + 1]);
-        if (v > best) { best = v; besti = r; }
-      }
+        for (int q = 0; q < c; ++q) wr[q] = crow[q];
+      T next = T(-1);
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q > c && q < nbe) {
+          const T t = a[q] - l * pv[q];
+          wr[q] = t;
+          if (q == c + 1) next = tabs(t);
+        }
+      if (next > best) { best = next; besti = r; }
     }
-    for (int o = 16; o; o >>= 1) {
-      T ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, besti, o);
-      if (ov > best || (ov == best && oi < besti)) { best = ov; besti = oi; }
-    }
+    int unused = 0;
+    warp_argmax(best, besti, unused);
     if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
     __syncthreads();
   }
