@@ -147,6 +147,82 @@ __global__ void bgj_copy_kernel(int k0, const int32_t *__restrict__ P, const int
   W[e] = (c < nbo) ? A[off[b] + (int64_t)(k0 + r) * p + k0 + c] : T(0);
 }
 
+// The end of a pivot panel (both panel kernels): the panel's row exchanges
+// applied to W's other columns, then U12 = L11^-1 W(c0:c0+nbe, right) with
+// L11 (unit lower, row stride ldl) in shared memory.  The panel's own
+// columns are already back in Wg.  Every thread of the CTA calls it.
+template <typename T, int NB, int NO>
+__device__ void bgj_panel_tail(T *Wg, const T *L11, int ldl, const int *s_q, int c0, int nbe, int nbo) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __syncthreads();  // the panel is written and s_q complete
+  // The same exchanges on W's other columns.  Exchanges c0+c <-> q_c (c in
+  // order, q_c >= c0+c) touch at most 2 nbe rows; destination d ends up
+  // holding the old row tau_0(tau_1(...tau_{nbe-1}(d))), found by walking the
+  // transpositions backwards.  One thread per column loads all touched rows
+  // before storing any.
+  static_assert(2 * NB <= 32, "one warp lists the exchanged rows");
+  __shared__ int s_dst[2 * NB], s_src[2 * NB];
+  __shared__ int s_cnt;
+  if (warp == 0) {
+    int d = -1, x = -1;
+    if (lane < 2 * nbe) {
+      d = lane < nbe ? c0 + lane : s_q[lane - nbe];
+      if (lane >= nbe && d < c0 + nbe) d = -1;  // a panel row, already listed
+      x = d;
+      if (d >= 0)
+        for (int c = nbe - 1; c >= 0; --c) {
+          const int q = s_q[c];
+          if (x == c0 + c) x = q;
+          else if (x == q) x = c0 + c;
+        }
+    }
+    const bool moved = d >= 0 && x != d;
+    const unsigned m = __ballot_sync(0xffffffffu, moved);
+    if (moved) {
+      const int pos = __popc(m & ((1u << lane) - 1u));
+      s_src[pos] = x;
+      s_dst[pos] = d;
+    }
+    if (lane == 0) s_cnt = __popc(m);
+  }
+  __syncthreads();
+  {
+    const int cnt = s_cnt;
+    const int j = tid < c0 ? tid : tid + nbe;  // the columns outside this step
+    if (tid < nbo - nbe) {
+      T v[2 * NB];
+#pragma unroll
+      for (int t = 0; t < 2 * NB; ++t)
+        if (t < cnt) v[t] = Wg[(int64_t)s_src[t] * NO + j];
+#pragma unroll
+      for (int t = 0; t < 2 * NB; ++t)
+        if (t < cnt) Wg[(int64_t)s_dst[t] * NO + j] = v[t];
+    }
+  }
+  __syncthreads();
+  // U12 = L11^-1 W(c0:c0+nbe, j) for the columns right of this step
+  {
+    const int j = c0 + nbe + tid;
+    if (j < nbo) {
+      T x[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) x[c] = (c < nbe) ? Wg[(int64_t)(c0 + c) * NO + j] : T(0);
+#pragma unroll
+      for (int c = 1; c < NB; ++c) {
+        if (c < nbe) {
+          T t = x[c];
+#pragma unroll
+          for (int q = 0; q < c; ++q) t -= L11[c * ldl + q] * x[q];
+          x[c] = t;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nbe) Wg[(int64_t)(c0 + c) * NO + j] = x[c];
+    }
+  }
+}
+
 // (2a) Columns c0..c0+nbe-1 of W (c0 = NB*s), rows c0..: LU with partial
 // pivoting on a copy in shared memory (or scratch), written back; the row
 // exchanges applied to W's other columns; U12 = L11^-1 W(c0:c0+nbe, right).
@@ -275,72 +351,129 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_kernel(int k
     const int r = e / nbe, c = e % nbe;
     Wg[(int64_t)(c0 + r) * NO + c0 + c] = W[r * LD + c];
   }
-  // The same exchanges on W's other columns.  Exchanges c0+c <-> q_c (c in
-  // order, q_c >= c0+c) touch at most 2 nbe rows; destination d ends up
-  // holding the old row tau_0(tau_1(...tau_{nbe-1}(d))), found by walking the
-  // transpositions backwards.  One thread per column loads all touched rows
-  // before storing any.
-  static_assert(2 * NB <= 32, "one warp lists the exchanged rows");
-  __shared__ int s_dst[2 * NB], s_src[2 * NB];
-  __shared__ int s_cnt;
-  if (warp == 0) {
-    int d = -1, x = -1;
-    if (lane < 2 * nbe) {
-      d = lane < nbe ? c0 + lane : s_q[lane - nbe];
-      if (lane >= nbe && d < c0 + nbe) d = -1;  // a panel row, already listed
-      x = d;
-      if (d >= 0)
-        for (int c = nbe - 1; c >= 0; --c) {
-          const int q = s_q[c];
-          if (x == c0 + c) x = q;
-          else if (x == q) x = c0 + c;
-        }
+  bgj_panel_tail<T, NB, NO>(Wg, W, LD, s_q, c0, nbe, nbo);
+}
+
+
+// (2a') The same panel with every thread's rows in registers: rows
+// r = tid + k * blockDim.x (k < RPT) of the panel's rows_all - c0.  Per
+// column: the warps' winners reduced in every warp, the owners of the
+// pivot row and of row c publish them, one barrier, then each thread
+// exchanges and eliminates its rows without touching shared memory and
+// offers its candidates for the next column.  Same pivots and arithmetic
+// as bgj_panel_kernel; used when the panel's rows fit RPT per thread.
+template <typename T, int NB, int NO, int RPT>
+__global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(int k0, int s,
+                                                                const int32_t *__restrict__ P, T *scratch,
+                                                                const int64_t *__restrict__ poff, int32_t *ipiv,
+                                                                const T *__restrict__ amax, double pivtol,
+                                                                int32_t *failed, DevStatus *st, int code) {
+  const int b = blockIdx.x;
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;
+  const int rows_all = p - k0, nbo = min(NO, rows_all), c0 = NB * s;
+  if (c0 >= nbo) return;
+  const int nbe = min(NB, nbo - c0), rows = rows_all - c0;
+  T *Wg = gj_base<T, NO>(scratch, poff, b);
+  constexpr int LD = NB + 1;
+  __shared__ T bv[32];
+  __shared__ int bi[32];
+  __shared__ T prow[NB], crow[NB];
+  __shared__ T L11[NB * LD];
+  __shared__ int s_q[NB];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  T a[RPT][NB];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = tid + k * nt;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) a[k][q] = (r < rows && q < nbe) ? Wg[(int64_t)(c0 + r) * NO + c0 + q] : T(0);
+  }
+  const T thresh = T(pivtol) * amax[b];
+  {
+    T best = T(-1);
+    int besti = rows, unused = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = tid + k * nt;
+      const T v = tabs(a[k][0]);
+      if (r < rows && v > best) { best = v; besti = r; }
     }
-    const bool moved = d >= 0 && x != d;
-    const unsigned m = __ballot_sync(0xffffffffu, moved);
-    if (moved) {
-      const int pos = __popc(m & ((1u << lane) - 1u));
-      s_src[pos] = x;
-      s_dst[pos] = d;
-    }
-    if (lane == 0) s_cnt = __popc(m);
+    warp_argmax(best, besti, unused);
+    if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
   }
   __syncthreads();
-  {
-    const int cnt = s_cnt;
-    const int j = tid < c0 ? tid : tid + nbe;  // the columns outside this step
-    if (tid < nbo - nbe) {
-      T v[2 * NB];
 #pragma unroll
-      for (int t = 0; t < 2 * NB; ++t)
-        if (t < cnt) v[t] = Wg[(int64_t)s_src[t] * NO + j];
-#pragma unroll
-      for (int t = 0; t < 2 * NB; ++t)
-        if (t < cnt) Wg[(int64_t)s_dst[t] * NO + j] = v[t];
+  for (int c = 0; c < NB; ++c) {
+    if (c >= nbe) break;
+    // the pivot: every warp reduces the warps' winners
+    T bb = lane < nw ? bv[lane] : T(-1);
+    int pr = lane < nw ? bi[lane] : rows, unused = 0;
+    warp_argmax(bb, pr, unused);
+    if (!(bb > thresh)) {
+      if (tid == 0) {
+        failed[b] = 1;
+        set_status2(st, code, b);
+      }
+      return;  // every thread of the CTA takes the same decision
     }
-  }
-  __syncthreads();
-  // U12 = L11^-1 W(c0:c0+nbe, j) for the columns right of this step
-  {
-    const int j = c0 + nbe + tid;
-    if (j < nbo) {
-      T x[NB];
+    if (tid == 0) {
+      s_q[c] = c0 + pr;
+      ipiv[poff[b] + k0 + c0 + c] = k0 + c0 + pr;
+    }
 #pragma unroll
-      for (int c = 0; c < NB; ++c) x[c] = (c < nbe) ? Wg[(int64_t)(c0 + c) * NO + j] : T(0);
+    for (int k = 0; k < RPT; ++k) {
+      const int r = tid + k * nt;
+      if (r == pr)
 #pragma unroll
-      for (int c = 1; c < NB; ++c) {
-        if (c < nbe) {
-          T t = x[c];
+        for (int q = 0; q < NB; ++q) prow[q] = a[k][q];
+      if (r == c)
 #pragma unroll
-          for (int q = 0; q < c; ++q) t -= W[c * LD + q] * x[q];
-          x[c] = t;
+        for (int q = 0; q < NB; ++q) crow[q] = a[k][q];
+    }
+    __syncthreads();  // prow / crow published; every warp has read bv / bi
+    const T piv = prow[c];
+    T best = T(-1);
+    int besti = rows;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = tid + k * nt;
+      if (r == c) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) a[k][q] = prow[q];
+      } else if (r == pr) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) a[k][q] = crow[q];
+      }
+      if (r > c && r < rows) {
+        const T l = a[k][c] / piv;
+        a[k][c] = l;
+#pragma unroll
+        for (int q = c + 1; q < NB; ++q)
+          if (q < nbe) a[k][q] -= l * prow[q];
+        if (c + 1 < nbe) {
+          const T v = tabs(a[k][c + 1]);
+          if (v > best) { best = v; besti = r; }
         }
       }
-#pragma unroll
-      for (int c = 0; c < NB; ++c)
-        if (c < nbe) Wg[(int64_t)(c0 + c) * NO + j] = x[c];
     }
+    warp_argmax(best, besti, unused);
+    if (lane == 0) { bv[warp] = best; bi[warp] = besti; }
+    __syncthreads();  // the offers are in; prow / crow are free again
   }
+  // the factored columns back to Wg; rows 0..nbe-1 (L11 / U11) also to shared memory
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = tid + k * nt;
+    if (r < rows)
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nbe) {
+          Wg[(int64_t)(c0 + r) * NO + c0 + q] = a[k][q];
+          if (r < NB) L11[r * LD + q] = a[k][q];
+        }
+  }
+  bgj_panel_tail<T, NB, NO>(Wg, L11, LD, s_q, c0, nbe, nbo);
 }
 
 // (2b) W(i, j) -= L21(i, :) U12(:, j) for the rows below and the columns
@@ -1033,8 +1166,26 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   for (int k0 = 0; k0 < pmax; k0 += NO) {
     bgj_copy_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     for (int sp = 0; sp < NO / NB; ++sp) {
-      bgj_panel_kernel<T, NB, NO><<<nblk, DD_GJ_PANEL_THREADS, smem, s>>>(k0, sp, d_p, scratch, d_poff, ipiv, amax, pivtol,
-                                                           failed, st, status_code, smem_rows);
+      // the panel's rows in registers when they fit DD_GJ_REG_RPT per thread
+      const int rpt = (pmax - k0 - NB * sp + DD_GJ_PANEL_THREADS - 1) / DD_GJ_PANEL_THREADS;
+#define DD_GJ_REG(R)                                                                                     \
+  case R:                                                                                                \
+    bgj_panel_reg_kernel<T, NB, NO, R><<<nblk, DD_GJ_PANEL_THREADS, 0, s>>>(k0, sp, d_p, scratch, d_poff, \
+                                                                          ipiv, amax, pivtol, failed, st, \
+                                                                          status_code);                   \
+    break;
+      switch (rpt) {
+        DD_GJ_REG(1)
+        DD_GJ_REG(2)
+        DD_GJ_REG(3)
+        DD_GJ_REG(4)
+        DD_GJ_REG(5)
+        default:
+          bgj_panel_kernel<T, NB, NO><<<nblk, DD_GJ_PANEL_THREADS, smem, s>>>(k0, sp, d_p, scratch, d_poff, ipiv,
+                                                                             amax, pivtol, failed, st,
+                                                                             status_code, smem_rows);
+      }
+#undef DD_GJ_REG
       if (sp + 1 < NO / NB) bgj_trail_kernel<T, NB, NO><<<tg, 256, 0, s>>>(k0, sp, d_p, scratch, d_poff, failed);
     }
     bgj_stage_kernel<T, NO><<<sg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, ipiv, failed);

@@ -338,30 +338,24 @@ __device__ __forceinline__ SegCta seg_cta(const SegMap &sm, int b, int nb, int64
   return c;
 }
 
-// Sums over the CTAs of each system, of `ncols` columns of the partials, in
-// a fixed order: pair p = s * ncols + q goes to CTA p mod nctas, which
-// writes dst[s * dstride + q].  Inactive systems are skipped.
-__device__ void seg_column_sums(const SegMap &sm, int ncols, int pk, const double *__restrict__ partial,
-                                double *dst, int dstride, double *red, int cta, int nctas) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int total = sm.nseg * ncols;
-  for (int p = cta; p < total; p += nctas) {
-    const int sys = p / ncols, q = p % ncols;
-    if (sm.act && !sm.act[sys]) continue;
-    const int b0 = sm.nseg == 1 ? 0 : sm.seg_cta0[sys];
-    const int b1 = sm.nseg == 1 ? sm.nctas : sm.seg_cta0[sys + 1];
+// Every CTA of a system sums the system's partials of `ncols` columns over
+// its CTAs itself, in one fixed order, so every CTA holds the same bits and
+// no grid barrier is needed to share the sums: warp w takes columns w,
+// w + nw, ..., lane l the CTAs c0 + l, c0 + l + 32, ..., then a butterfly.
+// out[q] in shared memory; the system's first CTA also stores them to dst.
+__device__ void cta_column_sums(const SegCta &me, int b, int ncols, int pk, const double *__restrict__ partial,
+                                double *out, double *dst) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = warp; q < ncols; q += nw) {
     double t = 0.0;
-    for (int b = b0 + tid; b < b1; b += blockDim.x) t += partial[(int64_t)b * pk + q];
+    for (int c = me.c0 + lane; c < me.c0 + me.nc; c += 32) t += partial[(int64_t)c * pk + q];
     for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[warp] = t;
-    __syncthreads();
-    if (tid == 0) {
-      double u = 0.0;
-      for (int ww = 0; ww < nw; ++ww) u += red[ww];
-      dst[(int64_t)sys * dstride + q] = u;
+    if (lane == 0) {
+      out[q] = t;
+      if (b == me.c0) dst[q] = t;
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -369,17 +363,21 @@ __device__ void seg_column_sums(const SegMap &sm, int ncols, int pk, const doubl
 // Gram-Schmidt applied twice to w = V_{j+1} against V_0..V_j, the norms, the
 // Givens rotation of the new Hessenberg column and the normalisation of w,
 // for one system or for every active system of a batch at once (each system
-// its own rows, CTAs, sums and Hessenberg matrix).  Grid-wide barriers
-// separate
-//   1 partial dots V^T w, w^T w            2 column sums per system -> h1
-//   3 w -= V h1, partial dots V^T w        4 column sums -> h2
-//   5 w -= V h2, partial w^T w             6 every CTA: the system's norm from
+// its own rows, CTAs, sums and Hessenberg matrix).  Three grid-wide
+// barriers follow
+//   1 partial dots V^T w, w^T w            every CTA then sums the system's
+//                                            partials itself -> h1
+//   2 w -= V h1, partial dots V^T w        every CTA: -> h2
+//   3 w -= V h2, partial w^T w             every CTA: the system's norm from
 //                                            the partials, w *= 1/h_{j+1,j}
 //                                            unless breakdown; the system's
 //                                            first CTA: Hessenberg column and
 //                                            rotations
-// The FP64 pipe bounds this kernel on GB300, so reductions are kept to one
-// pass over the partials per column.  Sums run in a fixed order.
+// Every CTA sums the partials in the same fixed order, so all hold the same
+// h1, h2 and norm without a barrier to share them.
+// The FP64 pipe bounds this kernel on GB300; the redundant sums cost each
+// CTA (2k+1) times the system's CTA count additions, against the
+// ~4(k+1)n / CTAs multiply-adds of its rows.
 // Per-system state (strides from sm.rmax): hc1/hc2 rmax+2, H (rmax+1)*rmax
 // with row stride R, cs/sn rmax, g rmax+1, bn2 (||b||^2) 1, scal 4:
 // [0] h_{j+1,j}, [1] breakdown flag, [2] |g_{j+1}| / ||b||.
@@ -397,29 +395,27 @@ __global__ void __launch_bounds__(NT) cgs2_kernel(
   const int k = j + 1, hst = sm.rmax + 2;
   __shared__ double red[(NT / 32) * 16];
   __shared__ double hs[DD_CGS_MAXK + 8];
+  __shared__ double hs1[DD_CGS_MAXK + 8], hs2[DD_CGS_MAXK + 8];
+  // pass 1 and the final norm use the partials in buffer A, pass 2 buffer B
+  // (a CTA may still read pass 1's partials while another writes pass 2's)
+  double *partB = partial + (int64_t)nb * pk;
   // 1
   block_dots(i0, i1, k, V, ldv, w, true, partial + (int64_t)b * pk, red);
   grid.sync();
-  // 2: hc1[0..k-1] and hc1[k] = ||w||^2 before orthogonalisation
-  seg_column_sums(sm, k + 1, pk, partial, hc1, hst, red, b, nb);
-  grid.sync();
+  // 2: every CTA: h1[0..k-1] and h1[k] = ||w||^2 before orthogonalisation
+  if (me.act) cta_column_sums(me, b, k + 1, pk, partial, hs1, hc1 + (int64_t)me.s * hst);
   // 3
-  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc1[(int64_t)me.s * hst + q];
+  for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] = row_update(i, k, V, ldv, hs1, w[i]);
   __syncthreads();
-  for (int i = i0 + tid; i < i1; i += blockDim.x) w[i] = row_update(i, k, V, ldv, hs, w[i]);
-  __syncthreads();
-  block_dots(i0, i1, k, V, ldv, w, false, partial + (int64_t)b * pk, red);
+  block_dots(i0, i1, k, V, ldv, w, false, partB + (int64_t)b * pk, red);
   grid.sync();
-  // 4
-  seg_column_sums(sm, k, pk, partial, hc2, hst, red, b, nb);
-  grid.sync();
+  // 4: every CTA: h2
+  if (me.act) cta_column_sums(me, b, k, pk, partB, hs2, hc2 + (int64_t)me.s * hst);
   // 5
-  for (int q = tid; q < k; q += blockDim.x) hs[q] = hc2[(int64_t)me.s * hst + q];
-  __syncthreads();
   {
     double nn = 0.0;
     for (int i = i0 + tid; i < i1; i += blockDim.x) {
-      const double s2 = row_update(i, k, V, ldv, hs, w[i]);
+      const double s2 = row_update(i, k, V, ldv, hs2, w[i]);
       w[i] = s2;
       nn += s2 * s2;
     }
@@ -440,7 +436,7 @@ __global__ void __launch_bounds__(NT) cgs2_kernel(
   // Hessenberg column and applies the rotations; no further grid barrier
   if (me.act) {
     const int sys = me.s;
-    const double *h1 = hc1 + (int64_t)sys * hst, *h2 = hc2 + (int64_t)sys * hst;
+    const double *h1 = hs1, *h2 = hs2;
     {
       const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
       double t = 0.0;
