@@ -1033,81 +1033,88 @@ __global__ void schur_rhs_kernel(int ng, const int32_t *__restrict__ f_ptr, cons
   t[g] = s;
 }
 
-// z2 = S_hat^-1 t per aggregate: t of the aggregate in shared memory, one warp
-// per row of S_hat^-1 with 16-byte loads; x2 = z2 written to x
-#define DD_SROWS 64
+// z2 = S_hat^-1 t per aggregate, one warp per row of S_hat^-1 with 16-byte
+// loads; x2 = z2 written to x.  A row of p entries starts on a 16-byte
+// boundary only when p (and the block's offset) allow it, so each row takes
+// h = (its misalignment) leading entries one by one, then 16-byte chunks,
+// then the remainder.  The chunks need t shifted by h: shared memory holds
+// V = 16 / sizeof(T) copies, copy h holding t[h..], so every chunk of t is a
+// 16-byte load too.  Eight chunks per lane in flight, 16 rows per CTA (two
+// per warp): enough bytes in flight per SM for HBM.
+#define DD_SROWS 16
 template <typename T>
 __global__ void schur_gemv_kernel(const int32_t *__restrict__ agg_off, const int64_t *__restrict__ s_off,
                                   const T *__restrict__ Sinv, const T *__restrict__ t,
                                   const int32_t *__restrict__ perm_iface, T *z2, double *x,
-                                  const int32_t *__restrict__ agg_sys, const int32_t *__restrict__ act) {
+                                  const int32_t *__restrict__ agg_sys, const int32_t *__restrict__ act,
+                                  int ldt) {
   const int a = blockIdx.y;
   if (act && !act[agg_sys[a]]) return;  // a batched system that has stopped stepping
   const int g0 = agg_off[a], p = agg_off[a + 1] - g0;
   const int rbase = blockIdx.x * DD_SROWS;
   if (rbase >= p) return;
+  constexpr int V = 16 / sizeof(T);
+  using Vt = typename Vec16<T>::V;
   extern __shared__ __align__(128) unsigned char smraw[];
-  T *ts = reinterpret_cast<T *>(smraw);
-  for (int r = threadIdx.x; r < p; r += blockDim.x) ts[r] = t[g0 + r];
+  T *ts = reinterpret_cast<T *>(smraw);  // V copies of ldt entries (ldt a multiple of V)
+  for (int r = threadIdx.x; r < p + V; r += blockDim.x) {
+    const T v = r < p ? t[g0 + r] : T(0);
+#pragma unroll
+    for (int h = 0; h < V; ++h)
+      if (r >= h && r - h < ldt) ts[h * ldt + r - h] = v;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T *Sa = Sinv + s_off[a];
-  constexpr int V = 16 / sizeof(T);
   for (int rr = warp; rr < DD_SROWS; rr += nw) {
     const int r = rbase + rr;
     if (r >= p) break;
     const T *row = Sa + (int64_t)r * p;
-    T acc = T(0);
-    // rows start on a 16-byte boundary only when p is a multiple of V; four
-    // 16-byte loads per lane in flight
-    if ((p % V) == 0 && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
-      T acc1 = T(0), acc2 = T(0), acc3 = T(0);
-      int c = lane * V;
-      for (; c + 3 * 32 * V < p; c += 4 * 32 * V) {
-        if (V == 4) {
-          const float4 v0 = *reinterpret_cast<const float4 *>(row + c);
-          const float4 v1 = *reinterpret_cast<const float4 *>(row + c + 32 * V);
-          const float4 v2 = *reinterpret_cast<const float4 *>(row + c + 64 * V);
-          const float4 v3 = *reinterpret_cast<const float4 *>(row + c + 96 * V);
-          // t in 16-byte pieces too: consecutive lanes, conflict-free
-          const float4 t0 = *reinterpret_cast<const float4 *>(ts + c);
-          const float4 t1 = *reinterpret_cast<const float4 *>(ts + c + 32 * V);
-          const float4 t2 = *reinterpret_cast<const float4 *>(ts + c + 64 * V);
-          const float4 t3 = *reinterpret_cast<const float4 *>(ts + c + 96 * V);
-          acc += T(v0.x) * T(t0.x) + T(v0.y) * T(t0.y) + T(v0.z) * T(t0.z) + T(v0.w) * T(t0.w);
-          acc1 += T(v1.x) * T(t1.x) + T(v1.y) * T(t1.y) + T(v1.z) * T(t1.z) + T(v1.w) * T(t1.w);
-          acc2 += T(v2.x) * T(t2.x) + T(v2.y) * T(t2.y) + T(v2.z) * T(t2.z) + T(v2.w) * T(t2.w);
-          acc3 += T(v3.x) * T(t3.x) + T(v3.y) * T(t3.y) + T(v3.z) * T(t3.z) + T(v3.w) * T(t3.w);
-        } else {
-          const double2 v0 = *reinterpret_cast<const double2 *>(row + c);
-          const double2 v1 = *reinterpret_cast<const double2 *>(row + c + 32 * V);
-          const double2 v2 = *reinterpret_cast<const double2 *>(row + c + 64 * V);
-          const double2 v3 = *reinterpret_cast<const double2 *>(row + c + 96 * V);
-          const double2 t0 = *reinterpret_cast<const double2 *>(ts + c);
-          const double2 t1 = *reinterpret_cast<const double2 *>(ts + c + 32 * V);
-          const double2 t2 = *reinterpret_cast<const double2 *>(ts + c + 64 * V);
-          const double2 t3 = *reinterpret_cast<const double2 *>(ts + c + 96 * V);
-          acc += T(v0.x) * T(t0.x) + T(v0.y) * T(t0.y);
-          acc1 += T(v1.x) * T(t1.x) + T(v1.y) * T(t1.y);
-          acc2 += T(v2.x) * T(t2.x) + T(v2.y) * T(t2.y);
-          acc3 += T(v3.x) * T(t3.x) + T(v3.y) * T(t3.y);
-        }
+    const int h = min(p, (int)((V - (int)((reinterpret_cast<uintptr_t>(row) / sizeof(T)) % V)) % V));
+    const int m = (p - h) / V;  // whole 16-byte chunks
+    const Vt *rv = reinterpret_cast<const Vt *>(row + h);
+    const Vt *tv = reinterpret_cast<const Vt *>(ts + h * ldt);
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+    if (lane < h) acc0 = row[lane] * ts[lane];
+    int k = lane;
+    for (; k + 224 < m; k += 256) {
+      Vt v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = rv[k + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        T a0[V], b0[V];
+        Vec16<T>::unpack(v[u], a0);
+        Vec16<T>::unpack(tv[k + 32 * u], b0);
+        T &acc = (u & 3) == 0 ? acc0 : (u & 3) == 1 ? acc1 : (u & 3) == 2 ? acc2 : acc3;
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc += a0[e] * b0[e];
       }
-      for (; c < p; c += 32 * V) {
-        if (V == 4) {
-          const float4 v = *reinterpret_cast<const float4 *>(row + c);
-          const float4 t = *reinterpret_cast<const float4 *>(ts + c);
-          acc += T(v.x) * T(t.x) + T(v.y) * T(t.y) + T(v.z) * T(t.z) + T(v.w) * T(t.w);
-        } else {
-          const double2 v = *reinterpret_cast<const double2 *>(row + c);
-          const double2 t = *reinterpret_cast<const double2 *>(ts + c);
-          acc += T(v.x) * T(t.x) + T(v.y) * T(t.y);
-        }
-      }
-      acc = (acc + acc1) + (acc2 + acc3);
-    } else {
-      for (int c = lane; c < p; c += 32) acc += row[c] * ts[c];
     }
+    for (; k + 96 < m; k += 128) {
+      const Vt v0 = rv[k], v1 = rv[k + 32], v2 = rv[k + 64], v3 = rv[k + 96];
+      const Vt t0 = tv[k], t1 = tv[k + 32], t2 = tv[k + 64], t3 = tv[k + 96];
+      T a0[V], a1[V], a2[V], a3[V], b0[V], b1[V], b2[V], b3[V];
+      Vec16<T>::unpack(v0, a0); Vec16<T>::unpack(v1, a1); Vec16<T>::unpack(v2, a2); Vec16<T>::unpack(v3, a3);
+      Vec16<T>::unpack(t0, b0); Vec16<T>::unpack(t1, b1); Vec16<T>::unpack(t2, b2); Vec16<T>::unpack(t3, b3);
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        acc0 += a0[u] * b0[u];
+        acc1 += a1[u] * b1[u];
+        acc2 += a2[u] * b2[u];
+        acc3 += a3[u] * b3[u];
+      }
+    }
+    for (; k < m; k += 32) {
+      T a0[V], b0[V];
+      Vec16<T>::unpack(rv[k], a0);
+      Vec16<T>::unpack(tv[k], b0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc0 += a0[u] * b0[u];
+    }
+    const int c = h + m * V + lane;  // the remainder, fewer than V entries
+    if (c < p) acc1 += row[c] * ts[c];
+    T acc = (acc0 + acc1) + (acc2 + acc3);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       z2[g0 + r] = acc;
@@ -1284,14 +1291,17 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                const int32_t *act, cudaStream_t s) {
   if (nagg <= 0) return cudaSuccess;
   schur_rhs_kernel<T><<<(ng + 255) / 256, 256, 0, s>>>(ng, f_ptr, f_col, f_val, y, perm_iface, z1, t);
-  size_t smem = sizeof(T) * (size_t)pmax;
+  // V = 16 / sizeof(T) shifted copies of t, each padded to a multiple of V
+  constexpr int V = 16 / sizeof(T);
+  const int ldt = (pmax + V - 1) / V * V;
+  size_t smem = sizeof(T) * (size_t)ldt * V;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(schur_gemv_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((pmax + DD_SROWS - 1) / DD_SROWS, nagg);
-  schur_gemv_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, t, perm_iface, z2, x, agg_sys, act);
+  schur_gemv_kernel<T><<<grid, 256, smem, s>>>(agg_off, s_off, Sinv, t, perm_iface, z2, x, agg_sys, act, ldt);
   return cudaGetLastError();
 }
 
