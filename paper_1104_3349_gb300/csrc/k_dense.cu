@@ -432,7 +432,9 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
         for (int q = 0; q < NB; ++q) crow[q] = a[k][q];
     }
     __syncthreads();  // prow / crow published; every warp has read bv / bi
-    const T piv = prow[c];
+    // one reciprocal per column: a multiply per row instead of a division
+    // (a rounding of the multipliers, within the parity bounds)
+    const T rpiv = T(1) / prow[c];
     T best = T(-1);
     int besti = rows;
 #pragma unroll
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
         for (int q = 0; q < NB; ++q) a[k][q] = crow[q];
       }
       if (r > c && r < rows) {
-        const T l = a[k][c] / piv;
+        const T l = a[k][c] * rpiv;
         a[k][c] = l;
 #pragma unroll
         for (int q = c + 1; q < NB; ++q)
