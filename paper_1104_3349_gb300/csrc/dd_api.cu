@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <condition_variable>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -142,6 +144,16 @@ dd_status dalloc(DDHandle *h, P **p, size_t count) {
   return DD_OK;
 }
 
+// count values of the caller's host array (pageable: staged at once)
+template <typename P>
+dd_status upload_ptr(DDHandle *h, P **p, const P *src, size_t count) {
+  dd_status s = dalloc(h, p, count);
+  if (s != DD_OK) return s;
+  if (count)
+    CK(cudaMemcpyAsync(*p, src, count * sizeof(P), cudaMemcpyHostToDevice, h->astream ? h->astream : h->stream));
+  return DD_OK;
+}
+
 template <typename P>
 dd_status upload(DDHandle *h, P **p, const std::vector<P> &v) {
   dd_status s = dalloc(h, p, v.size());
@@ -226,14 +238,83 @@ int host_workers(int64_t n) {
   const int64_t by_size = std::max<int64_t>(1, n / 16384);
   return (int)std::min<int64_t>(std::min<int64_t>(hc ? hc : 1, 32), by_size);
 }
+// Host threads kept for the setup's row loops: starting a dozen threads per
+// loop cost more than the loop's work.  One job at a time (callers from
+// several threads take turns); the caller works on the job too.  The
+// threads leave when the process destroys the pool.
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool;
+    return pool;
+  }
+  // f(w) for w = 0 .. n-1, spread over the pool and the caller
+  void run(int n, const std::function<void(int)> &f) {
+    std::lock_guard<std::mutex> turn(run_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      job_ = &f;
+      njob_ = n;
+      next_ = 0;
+      pending_ = n;
+      ++gen_;
+    }
+    cv_.notify_all();
+    std::unique_lock<std::mutex> lk(mu_);
+    work(lk);
+    done_.wait(lk, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (std::thread &t : th_) t.join();
+  }
+
+ private:
+  HostPool() {
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nt = (int)std::min<unsigned>(hc ? hc : 1, 32) - 1;
+    for (int i = 0; i < nt; ++i) th_.emplace_back([this] { loop(); });
+  }
+  // take items of the current job until none is left (mu_ held on entry and exit)
+  void work(std::unique_lock<std::mutex> &lk) {
+    while (job_ && next_ < njob_) {
+      const int w = next_++;
+      const std::function<void(int)> *f = job_;
+      lk.unlock();
+      (*f)(w);
+      lk.lock();
+      if (--pending_ == 0) done_.notify_all();
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      work(lk);
+    }
+  }
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_;
+  std::vector<std::thread> th_;
+  const std::function<void(int)> *job_ = nullptr;
+  int njob_ = 0, next_ = 0, pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
 template <typename F>
 void parallel_rows(int64_t n, int workers, F &&f) {
   if (workers <= 1) { f(0, (int64_t)0, n); return; }
-  std::vector<std::thread> th;
-  th.reserve(workers);
-  for (int w = 0; w < workers; ++w)
-    th.emplace_back([&, w] { f(w, n * w / workers, n * (w + 1) / workers); });
-  for (auto &t : th) t.join();
+  const std::function<void(int)> job = [&](int w) { f(w, n * w / workers, n * (w + 1) / workers); };
+  HostPool::get().run(workers, job);
 }
 
 dd_status validate_and_order(DDHandle *h, const dd_csr *csr, const dd_partition *pt, HostBlocks &hb) {
@@ -1248,15 +1329,11 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   }
   TRY(dalloc(h, &h->piv, pivo));
   // ---- C itself (FP64, original numbering) for the SpMV
-  {
-    std::vector<int32_t> rp(csr->rowptr, csr->rowptr + h->n + 1), cc(csr->col, csr->col + h->nnz);
-    std::vector<double> vv(csr->val, csr->val + h->nnz);
-    TRY(upload(h, &h->c_rowptr, rp));
-    TRY(upload(h, &h->c_col, cc));
-    TRY(upload(h, &h->c_val, vv));
-  }
+  TRY(upload_ptr(h, &h->c_rowptr, csr->rowptr, (size_t)h->n + 1));
+  TRY(upload_ptr(h, &h->c_col, csr->col, (size_t)h->nnz));
+  TRY(upload_ptr(h, &h->c_val, csr->val, (size_t)h->nnz));
   int32_t *d_part = nullptr, *d_pos = nullptr;
-  TRY(upload(h, &d_part, std::vector<int32_t>(pt->part, pt->part + h->n)));
+  TRY(upload_ptr(h, &d_part, pt->part, (size_t)h->n));
   TRY(upload(h, &d_pos, hb.pos));
   TRY(upload(h, &h->d_perm, hb.perm));
   h->stats.launches += 1;
