@@ -129,8 +129,11 @@ typedef struct {
                          with use_graph; 0: no events                        */
   int32_t sweep_cluster;/* CTAs per subdomain of the apply's sweeps: 2 splits
                          every tile step over a 2-CTA cluster (half the tile
-                         bytes through each SM), 1 one CTA; 0 chooses 1, or
-                         with autotune the faster of the two                 */
+                         bytes through each SM, the step's rows exchanged
+                         through distributed shared memory), 1 one CTA; 0
+                         chooses 2 in FP64 when every subdomain's cluster
+                         is resident at once and 1 otherwise, or with
+                         autotune the faster of the two                    */
   const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
                               (format under dd_mlp_*); ignored otherwise       */
   int32_t overlap;    /* DD_OMSCN / DD_OMSCNR / DD_OLUM: overlap width w >= 0   */

@@ -579,16 +579,19 @@ int sm_count() {
   return sms;
 }
 
-// CTAs per subdomain of the sweeps: the option if given, else 1.  Measured on the 256x256 workload, the
-// 2-CTA cluster sweep is slower in both precisions (FP32 133.5 against
-// 100.8 us per interior solve, FP64 432.8 against 404.1 us): a step's
-// exchange and cluster barrier cost more than halving the shared-memory
-// traffic, or the FP64 work, of each SM saves.  The autotuner still tries
-// both.
+// CTAs per subdomain of the sweeps: the option if given; else, in FP64, a
+// 2-CTA cluster when every subdomain's cluster is resident at once on the
+// device's SMs, and one CTA otherwise.  Measured on the 256x256 workload (64
+// subdomains): FP64 interior solves 369 / 391 us with clusters against 398 /
+// 410 us with one CTA (the FP64 multiply-adds of a step are split over two
+// SMs); FP32 105 / 108 against 97 / 96 us (a step's message round trip costs
+// more than halving each SM's shared-memory traffic saves).  The autotuner
+// tries both.
 template <typename T>
 int choose_cluster(const DDHandle *h, size_t stage) {
   (void)stage;
-  return (h->sweep_cl_opt == 1 || h->sweep_cl_opt == 2) ? h->sweep_cl_opt : 1;
+  if (h->sweep_cl_opt == 1 || h->sweep_cl_opt == 2) return h->sweep_cl_opt;
+  return (sizeof(T) == 8 && 2 * h->m <= sm_count()) ? 2 : 1;
 }
 
 // The tiles in the layout of the 2-CTA sweeps (once per handle, after the
