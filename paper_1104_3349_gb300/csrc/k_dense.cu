@@ -126,6 +126,22 @@ struct BgjNO { static const int value = 64; };
 template <>
 struct BgjNO<double> { static const int value = 32; };
 
+// 16-byte vector of T
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void unpack(const float4 &a, float *v) { v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void unpack(const double2 &a, double *v) { v[0] = a.x; v[1] = a.y; }
+};
+
 template <typename T, int NO>
 __device__ __forceinline__ T *gj_base(T *scratch, const int64_t *poff, int b) {
   return scratch + 6 * (int64_t)NO * poff[b] + (int64_t)(NO * NO + 4 * NO) * b;
@@ -383,11 +399,21 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
   __shared__ int s_q[NB];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   T a[RPT][NB];
+  // each row's NB entries in 16-byte loads (rows of Wg start on 16-byte
+  // boundaries: NO and c0 are multiples of 16 / sizeof(T))
+  using Vt = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int r = tid + k * nt;
+    const Vt *src = reinterpret_cast<const Vt *>(Wg + (int64_t)(c0 + r) * NO + c0);
 #pragma unroll
-    for (int q = 0; q < NB; ++q) a[k][q] = (r < rows && q < nbe) ? Wg[(int64_t)(c0 + r) * NO + c0 + q] : T(0);
+    for (int v = 0; v < NB / VN; ++v) {
+      T u[VN];
+      if (r < rows) Vec16<T>::unpack(src[v], u);
+#pragma unroll
+      for (int e = 0; e < VN; ++e) a[k][v * VN + e] = (r < rows && v * VN + e < nbe) ? u[e] : T(0);
+    }
   }
   const T thresh = T(pivtol) * amax[b];
   {
@@ -421,13 +447,15 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
       s_q[c] = c0 + pr;
       ipiv[poff[b] + k0 + c0 + c] = k0 + c0 + pr;
     }
+    // slot k and thread of the pivot row and of row c (uniform over the CTA,
+    // so only one slot's code runs, and only in the owning warp)
+    const int kp = pr / nt, tp = pr % nt, kc = c / nt, tc = c % nt;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-      const int r = tid + k * nt;
-      if (r == pr)
+      if (k == kp && tid == tp)
 #pragma unroll
         for (int q = 0; q < NB; ++q) prow[q] = a[k][q];
-      if (r == c)
+      if (k == kc && tid == tc)
 #pragma unroll
         for (int q = 0; q < NB; ++q) crow[q] = a[k][q];
     }
@@ -440,10 +468,10 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int r = tid + k * nt;
-      if (r == c) {
+      if (k == kc && tid == tc) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) a[k][q] = prow[q];
-      } else if (r == pr) {
+      } else if (k == kp && tid == tp) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) a[k][q] = crow[q];
       }
@@ -717,22 +745,6 @@ __global__ void __launch_bounds__(256) bgj_pcol_kernel(int k0, const int32_t *__
 }
 
 #define DD_BGJ_TILE 64
-// 16-byte vector of T
-template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using V = float4;
-  static constexpr int N = 4;
-  __device__ static void unpack(const float4 &a, float *v) { v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
-};
-template <>
-struct Vec16<double> {
-  using V = double2;
-  static constexpr int N = 2;
-  __device__ static void unpack(const double2 &a, double *v) { v[0] = a.x; v[1] = a.y; }
-};
-
 #define DD_BGJ_RT 4
 #define DD_BGJ_UPD_THREADS ((DD_BGJ_TILE / DD_BGJ_RT) * (DD_BGJ_TILE / DD_BGJ_RT))
 // Rank-NB update of one 64 x 64 tile: each of the 256 threads owns 4
