@@ -58,6 +58,15 @@ __host__ __device__ inline int64_t lu_window_elems(int kl, int ku) {
   return (int64_t)(DD_NB + kl + 3) * lu_ldw(kl, ku);
 }
 
+// four consecutive T at a 16-byte aligned address (shared or global)
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
 
@@ -569,18 +578,49 @@ __global__ void __launch_bounds__(4 * TB) band_tiles_kernel(const BandInfo *__re
   {
     T *kr = Kb + (int64_t)tid * WU;
     for (int c = part; c < TB; c += 4) kr[c] = Lsm[tid * TB + c];
-    for (int q = part; q < WU - TB; q += 4) {
-      const int col = c0 + TB + q;
-      T sacc = T(0);
-      if (col < n && q < ku2)
-        for (int k = tid; k < TB; ++k) {
-          const int rk = c0 + k;
-          if (rk >= n) break;
-          const int off = col - rk + kl;
-          if (off < wd) sacc += Lsm[tid * TB + k] * A[(int64_t)rk * wd + off];
-        }
-      kr[TB + q] = -sacc;
+  }
+  // -Uinv U12 as a product in chunks of TB columns of U12: Uinv transposed
+  // into L11's buffer (UT[k][r] = Uinv(r, k)), the chunk of U12 (TB rows,
+  // zero outside the band and the matrix) staged in vbuf (TB x TB fits its
+  // TB x W2); each thread accumulates 4 rows x CW = TB / 16 columns in
+  // registers over k in ascending order (Uinv's zeros below the diagonal add
+  // exact zeros first, so every output is the same chain as a sum from k =
+  // its row)
+  constexpr int CW = TB / 16;
+  T *UT = L11;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) UT[e] = Lsm[(e % TB) * TB + e / TB];
+  const int ri = threadIdx.x / 16, qi = threadIdx.x % 16;  // rows 4 ri.., columns CW qi.. of a chunk
+  for (int q0 = 0; q0 < WU - TB; q0 += TB) {
+    __syncthreads();  // UT is written; the previous chunk is consumed
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+      const int k = e / TB, q = q0 + e % TB, col = c0 + TB + q, rk = c0 + k;
+      const int off = col - rk + kl;
+      vbuf[e] = (rk < n && col < n && q < ku2 && off < wd) ? A[(int64_t)rk * wd + off] : T(0);
     }
+    __syncthreads();
+    T acc[4][CW];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < CW; ++y) acc[x][y] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < TB; ++k) {
+      T u[4], v[CW];
+      ld4(UT + k * TB + 4 * ri, u);
+#pragma unroll
+      for (int y = 0; y < CW; ++y) v[y] = vbuf[k * TB + CW * qi + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < CW; ++y) acc[x][y] += u[x] * v[y];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < CW; ++y) {
+        const int q = q0 + CW * qi + y;
+        if (q < WU - TB) Kb[(int64_t)(4 * ri + x) * WU + TB + q] = -acc[x][y];
+      }
   }
 }
 
@@ -1377,15 +1417,6 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
 // chunk of NR columns per CTA; X column-major (leading dimension n_j) in
 // global memory, the tile windows staged in shared memory.
 // ---------------------------------------------------------------------------
-// four consecutive T at a 16-byte aligned address (shared or global)
-__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
-  const float4 v = *reinterpret_cast<const float4 *>(p);
-  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
-  const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
 // columns 4ch .. 4ch+3 of row r of a forward tile K (16-byte chunks swizzled
 // by row: four floats, or two pairs of doubles)
 template <typename T, int TB>
