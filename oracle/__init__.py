@@ -54,6 +54,13 @@ def _load():
         lib.orc_setup2.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, i32p, i32p, ctypes.c_int32,
                                    i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, i32p, ctypes.c_int32,
                                    ctypes.c_int32, ctypes.POINTER(vp)]
+        lib.orc_setup3.restype = ctypes.c_int
+        lib.orc_setup3.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_int32, i32p, i32p, ctypes.c_int32,
+                                   i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, i32p, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_double, ctypes.POINTER(vp)]
+        lib.orc_band_ilu_dense.restype = ctypes.c_int
+        lib.orc_band_ilu_dense.argtypes = [ctypes.c_int32, f64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_double, i32p, f64p]
         lib.orc_block_size.restype = ctypes.c_int32
         lib.orc_block_size.argtypes = [vp, ctypes.c_int32]
         lib.orc_overlaps.argtypes = [vp, i32p]
@@ -131,6 +138,17 @@ def band_lu_solve(a: np.ndarray, kl: int, ku: int, b: np.ndarray, pivtol: float 
     return x, piv, int(rc)
 
 
+def band_ilu_solve(a: np.ndarray, kl: int, ku: int, b: np.ndarray, tau: float, pivtol: float = 1e-14):
+    """Incomplete band LU (drop tolerance tau) of the dense matrix a; returns (x, piv, status)."""
+    n = a.shape[0]
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    x = np.ascontiguousarray(b, dtype=np.float64).copy()
+    piv = np.zeros(n, np.int32)
+    rc = _load().orc_band_ilu_dense(n, _p(a, ctypes.c_double), kl, ku, pivtol, float(tau),
+                                    _p(piv, ctypes.c_int32), _p(x, ctypes.c_double))
+    return x, piv, int(rc)
+
+
 def spmv(A, x):
     y = np.zeros(A.n)
     x = np.ascontiguousarray(x, dtype=np.float64)
@@ -143,10 +161,11 @@ class OracleDD:
     """The preconditioner B of the paper for one kind, built on the CPU."""
 
     def __init__(self, A, part, m, kind, perm=None, sz=64, agg_offsets=None, pivtol=1e-14, raise_on_error=True,
-                 overlap=0, overlaps=None, radius=0):
+                 overlap=0, overlaps=None, radius=0, ilu_tol=0.0):
         """overlap / overlaps: the overlap widths of OMSCN, OMSCNR and OLUM (one
         width for all aggregates, capped by the next aggregate's size, or one
-        per aggregate); radius: the path-length radius of MSCE."""
+        per aggregate); radius: the path-length radius of MSCE; ilu_tol: the
+        drop tolerance of the incomplete LU of the interior blocks (0: exact)."""
         lib = _load()
         self._lib = lib
         self.A = A
@@ -157,10 +176,11 @@ class OracleDD:
         nagg = 0 if agg_a is None else len(agg_a) - 1
         ovl_a = None if overlaps is None else np.ascontiguousarray(overlaps, np.int32)
         h = ctypes.c_void_p()
-        rc = lib.orc_setup2(A.n, _p(self._keep[0], ctypes.c_int32), _p(self._keep[1], ctypes.c_int32),
+        rc = lib.orc_setup3(A.n, _p(self._keep[0], ctypes.c_int32), _p(self._keep[1], ctypes.c_int32),
                             _p(self._keep[2], ctypes.c_double), m, _p(self._keep[3], ctypes.c_int32),
                             _p(perm_a, ctypes.c_int32), nagg, _p(agg_a, ctypes.c_int32), sz, kind, pivtol,
-                            _p(ovl_a, ctypes.c_int32), int(overlap), int(radius), ctypes.byref(h))
+                            _p(ovl_a, ctypes.c_int32), int(overlap), int(radius), float(ilu_tol),
+                            ctypes.byref(h))
         self._h = h
         self.status = int(rc)
         self.bad_block = int(lib.orc_bad_block(h)) if h.value else -1

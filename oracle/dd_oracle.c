@@ -165,8 +165,28 @@ static int band_alloc(orc_band *b, int32_t n, int32_t kl, int32_t ku) {
 
 static void band_free(orc_band *b) { free(b->r); free(b->lm); free(b->piv); b->r = 0; b->lm = 0; b->piv = 0; }
 
-/* Factor in place; returns 0 or k+1 for a failed pivot in column k. */
-static int band_factor(orc_band *b, double pivtol) {
+/* 2-norms of the columns of the band (before it is factored): the reference
+ * of the incomplete factorisation's drop test. */
+static void band_colnorms(const orc_band *b, double *cn) {
+  for (int32_t j = 0; j < b->n; ++j) {
+    double s = 0.0;
+    int32_t i0 = j - b->ku > 0 ? j - b->ku : 0, i1 = j + b->kl < b->n - 1 ? j + b->kl : b->n - 1;
+    for (int32_t i = i0; i <= i1; ++i) {
+      double v = b->r[(int64_t)i * b->wd + (j - i + b->kl)];
+      s += v * v;
+    }
+    cn[j] = sqrt(s);
+  }
+}
+
+/* Factor in place; returns 0 or k+1 for a failed pivot in column k.
+ * tau > 0 (with cn the column norms of the unfactored band): the incomplete
+ * factorisation with threshold dropping (Section 5's ILU with tolerance
+ * tolA), read as: at step k, after the row exchange, an entry u_kj (j > k)
+ * of the pivot row is dropped when |u_kj| < tau * |A(:, j)|, and a multiplier
+ * l_ik when |l_ik| < tau * |A(:, k)| / |u_kk|, before either is used in the
+ * step's update; the diagonal is kept.  tau = 0 is the exact LU. */
+static int band_factor(orc_band *b, double pivtol, double tau, const double *cn) {
   int32_t n = b->n, kl = b->kl, ku = b->ku;
   double amax = 0.0;
   for (int64_t q = 0; q < (int64_t)n * b->wd; ++q) if (fabs(b->r[q]) > amax) amax = fabs(b->r[q]);
@@ -186,8 +206,12 @@ static int band_factor(orc_band *b, double pivtol) {
         *band_at(b, p, j) = t;
       }
     double dkk = *band_at(b, k, k);
+    if (tau > 0.0)
+      for (int32_t j = k + 1; j <= jend; ++j)
+        if (fabs(*band_at(b, k, j)) < tau * cn[j]) *band_at(b, k, j) = 0.0;
     for (int32_t i = k + 1; i <= last; ++i) {
       double l = *band_at(b, i, k) / dkk;
+      if (tau > 0.0 && fabs(l) < tau * cn[k] / fabs(dkk)) l = 0.0;
       b->lm[(int64_t)k * kl + (i - k - 1)] = l;
       *band_at(b, i, k) = 0.0;
       if (l != 0.0)
@@ -222,11 +246,33 @@ int orc_band_lu_dense(int32_t n, const double *a, int32_t kl, int32_t ku, double
   for (int32_t i = 0; i < n; ++i)
     for (int32_t j = i - kl; j <= i + ku; ++j)
       if (j >= 0 && j < n) *band_at(&b, i, j) = a[(int64_t)i * n + j];
-  int rc = band_factor(&b, pivtol);
+  int rc = band_factor(&b, pivtol, 0.0, NULL);
   if (rc == 0) {
     memcpy(piv, b.piv, sizeof(int32_t) * n);
     band_solve(&b, x);
   }
+  band_free(&b);
+  return rc;
+}
+
+/* Pin helper: the incomplete band factorisation (drop tolerance tau) of a
+ * dense row-major n x n matrix; returns the pivots and solves one
+ * right-hand side with the incomplete factors. */
+int orc_band_ilu_dense(int32_t n, const double *a, int32_t kl, int32_t ku, double pivtol, double tau,
+                       int32_t *piv, double *x) {
+  orc_band b;
+  double *cn = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+  if (!cn || band_alloc(&b, n, kl, ku)) { free(cn); band_free(&b); return -1; }
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = i - kl; j <= i + ku; ++j)
+      if (j >= 0 && j < n) *band_at(&b, i, j) = a[(int64_t)i * n + j];
+  band_colnorms(&b, cn);
+  int rc = band_factor(&b, pivtol, tau, cn);
+  if (rc == 0) {
+    memcpy(piv, b.piv, sizeof(int32_t) * n);
+    band_solve(&b, x);
+  }
+  free(cn);
   band_free(&b);
   return rc;
 }
@@ -251,6 +297,7 @@ typedef struct orc {
   orc_sp Et;                /* E transposed: interface x interior */
   int32_t *ovl;             /* overlapped kinds: overlap width w_i of every aggregate */
   int32_t radius;           /* MSCE: path-length radius r */
+  double ilu_tol;           /* interior blocks: drop tolerance of the incomplete LU (0: exact) */
   orc_band Shat;            /* overlapped kinds: the assembled S_hat (band, factored) */
   double *Shat0;            /* its entries before the factorisation (band rows, unpivoted) */
   double **S;               /* S_hat blocks, row-major (kept unfactored for tests) */
@@ -335,7 +382,15 @@ static int build_interior(orc *h, int32_t j, double pivtol) {
     }
   }
   if (nj == 0) return ORC_OK;
-  return band_factor(&h->A[j], pivtol) ? ORC_SINGULAR_BLOCK : ORC_OK;
+  double *cn = NULL;
+  if (h->ilu_tol > 0.0) {
+    cn = (double *)malloc(sizeof(double) * (size_t)nj);
+    if (!cn) return ORC_OOM;
+    band_colnorms(&h->A[j], cn);
+  }
+  int f = band_factor(&h->A[j], pivtol, h->ilu_tol, cn);
+  free(cn);
+  return f ? ORC_SINGULAR_BLOCK : ORC_OK;
 }
 
 /* Which subdomain owns interior (new) index i */
@@ -594,11 +649,12 @@ out:
  *              NULL for consecutive chunks of sz (eq. aggrV)
  *   kind       0 EXACT, 1 MSCE_INF, 2 MSCN, 3 MSCNR, 4 LUM, -1 identity
  */
-int orc_setup2(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
+int orc_setup3(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
                const int32_t *part, const int32_t *perm, int32_t nagg, const int32_t *agg_off,
                int32_t sz, int32_t kind, double pivtol, const int32_t *ovl, int32_t ovl_w, int32_t radius,
-               orc **out) {
+               double ilu_tol, orc **out) {
   *out = NULL;
+  if (!(ilu_tol >= 0.0)) return ORC_INVALID_ARG;
   if (n <= 0 || m <= 0 || !rowptr || !col || !val || !part) return ORC_INVALID_ARG;
   if (kind < -1 || kind > 9 || kind == 5) return ORC_INVALID_ARG;
   if (kind == ORC_MSCE && radius < 0) return ORC_INVALID_ARG;
@@ -620,7 +676,7 @@ int orc_setup2(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
     }
   orc *h = (orc *)calloc(1, sizeof(orc));
   if (!h) return ORC_OOM;
-  h->n = n; h->m = m; h->kind = kind; h->bad_block = -1; h->radius = radius;
+  h->n = n; h->m = m; h->kind = kind; h->bad_block = -1; h->radius = radius; h->ilu_tol = ilu_tol;
   int rc = ORC_OK;
   h->rowptr = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
   h->ccol = (int32_t *)malloc(sizeof(int32_t) * ((size_t)rowptr[n] + 1));
@@ -784,7 +840,7 @@ int orc_setup2(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
     h->Shat0 = (double *)malloc(sizeof(double) * (nb + 1));
     if (!h->Shat0) { rc = ORC_OOM; goto fail; }
     memcpy(h->Shat0, h->Shat.r, sizeof(double) * nb);
-    if (band_factor(&h->Shat, pivtol)) { h->bad_block = nagg; rc = ORC_SINGULAR_SCHUR; goto fail_keep; }
+    if (band_factor(&h->Shat, pivtol, 0.0, NULL)) { h->bad_block = nagg; rc = ORC_SINGULAR_SCHUR; goto fail_keep; }
   }
   *out = h;
   return ORC_OK;
@@ -796,6 +852,14 @@ fail_keep:
 fail:
   orc_free(h);
   return rc;
+}
+
+int orc_setup2(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
+               const int32_t *part, const int32_t *perm, int32_t nagg, const int32_t *agg_off,
+               int32_t sz, int32_t kind, double pivtol, const int32_t *ovl, int32_t ovl_w, int32_t radius,
+               orc **out) {
+  return orc_setup3(n, rowptr, col, val, m, part, perm, nagg, agg_off, sz, kind, pivtol, ovl, ovl_w, radius, 0.0,
+                    out);
 }
 
 int orc_setup(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, int32_t m,
