@@ -145,6 +145,15 @@ typedef struct {
                          (cp.async.bulk.prefetch) the tile bytes of the job
                          this many jobs past the ring as they refill a
                          stage: k > 0 a distance of k jobs, <= 0 none       */
+  int32_t pad_opts;
+  double ilu_tol;     /* inexact interior solves (Section 5: an incomplete LU
+                         with tolerance tolA): 0 factors every A_jj exactly;
+                         > 0 drops, during the banded LU with partial
+                         pivoting, each entry of U below ilu_tol times its
+                         column's 2-norm in A_jj and each multiplier below
+                         ilu_tol times the pivot column's norm over the
+                         pivot, before either is used; the factors' tiles
+                         then trim to the entries kept.  < 0: invalid      */
 } dd_opts;
 
 typedef struct {

@@ -45,6 +45,7 @@ struct DDHandle {
   int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1 or 2
   int sweep_pf_opt = 0;        // opts.sweep_prefetch: k > 0 k jobs, else none
   int overlap = 0, radius = 0; // opts.overlap (overlapped kinds), opts.radius (DD_MSCE)
+  double ilu_tol = 0.0;        // opts.ilu_tol: drop tolerance of the incomplete interior LU (0: exact)
   std::vector<BandInfo> h_info;  // host copies of the subdomain and tile tables (re-planning)
   std::vector<TileMeta> h_tm;
   size_t max_tile = 0;           // bytes of the largest packed tile
@@ -1359,8 +1360,11 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
       TRY(upload(h, &d_sched, sched));
       TRY(upload(h, &d_off, off));
     }
+    T *cnorm = nullptr;  // column norms of the incomplete factorisation
+    if (h->ilu_tol > 0) TRY(dalloc(h, &cnorm, std::max(nI, 1)));
     CK(launch_band_lu<T>(h->d_info, m, h->max_kl, h->max_ku, B.band, B.lm, h->piv,
-                         static_cast<T *>(h->lu_scratch), pivtol, h->st, lu_threads, slots, d_sched, d_off, s));
+                         static_cast<T *>(h->lu_scratch), pivtol, h->st, lu_threads, slots, d_sched, d_off,
+                         cnorm, h->ilu_tol, s));
   }
   // ---- host work while the band LU runs.  Its allocations and uploads go
   // to the side stream: a pageable copy queued behind the LU on the main
@@ -2312,6 +2316,8 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   if (o.sweep_cluster < 0 || o.sweep_cluster > 2) { h->err = "sweep_cluster must be 0, 1 or 2"; return DD_ERR_INVALID_ARG; }
   h->sweep_cl_opt = o.sweep_cluster;
   h->sweep_pf_opt = o.sweep_prefetch;
+  if (!(o.ilu_tol >= 0.0) || !std::isfinite(o.ilu_tol)) { h->err = "ilu_tol must be finite and >= 0"; return DD_ERR_INVALID_ARG; }
+  h->ilu_tol = o.ilu_tol;
   if (o.overlap < 0 || o.radius < 0) { h->err = "overlap and radius must be >= 0"; return DD_ERR_INVALID_ARG; }
   h->overlap = o.overlap;
   h->radius = o.radius;

@@ -179,12 +179,16 @@ size_t band_sweep_max_stage(int max_n, int max_kl, int max_ku2, int elem_size, i
 // column-major, exchanged), wscratch holds the windows when they do not fit
 // in shared memory (band_lu_window_bytes per subdomain, else unused).
 // sched / sched_off: optional persistent task lists of `grid` CTAs (as in
-// SweepPlan).
+// SweepPlan).  ilu_tol > 0: the incomplete factorisation (entries of U below
+// ilu_tol times their column's 2-norm, multipliers below ilu_tol times the
+// pivot column's norm over the pivot, dropped before use); cnorm then holds
+// n_I values of scratch for the column norms.
 size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size);
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
                            int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
-                           int grid, const int32_t *sched, const int32_t *sched_off, cudaStream_t s);
+                           int grid, const int32_t *sched, const int32_t *sched_off, T *cnorm,
+                           double ilu_tol, cudaStream_t s);
 // resident CTAs per SM of the band LU (0 on error)
 template <typename T>
 int band_lu_occupancy(int max_kl, int max_ku, int threads);

@@ -115,7 +115,7 @@ __device__ __forceinline__ void offer_max(T v, int L, int r, T (*bv)[32], int (*
 // Returns false (status set) if a pivot fails the test.
 template <typename T>
 __device__ bool lu_panel_lazy(T *W, int ldw, int R, int Cw, int c0, int n, int kl, int nbe, T thresh,
-                              int32_t *P, DevStatus *st, int task) {
+                              int32_t *P, DevStatus *st, int task, const T *cn, T tau) {
   __shared__ T bv[2][32];
   __shared__ int bL[2][32], br[2][32];
   __shared__ int sj[DD_NB];
@@ -149,9 +149,22 @@ __device__ bool lu_panel_lazy(T *W, int ldw, int R, int Cw, int c0, int n, int k
     if (tid == 0) { P[c0 + c] = c0 + j; sj[c] = j; }
     const int last = min(min(R - 1, c + kl), n - 1 - c0);
     if (own && !chosen && r != pr && r <= last) {
-      const T l = W[r * ldw + c] / W[pr * ldw + c];
-      W[r * ldw + c] = l;
-      for (int q = c + 1; q < DD_NB; ++q) W[r * ldw + q] -= l * W[pr * ldw + q];
+      const T pv = W[pr * ldw + c];
+      T l = W[r * ldw + c] / pv;
+      if (tau > T(0)) {
+        // the incomplete factorisation: a small multiplier, and small entries
+        // of the pivot row, are dropped before they are used
+        if (tabs(l) < tau * cn[c0 + c] / tabs(pv)) l = T(0);
+        W[r * ldw + c] = l;
+        for (int q = c + 1; q < DD_NB; ++q) {
+          T u = W[pr * ldw + q];
+          if (c0 + q < n && tabs(u) < tau * cn[c0 + q]) u = T(0);
+          W[r * ldw + q] -= l * u;
+        }
+      } else {
+        W[r * ldw + c] = l;
+        for (int q = c + 1; q < DD_NB; ++q) W[r * ldw + q] -= l * W[pr * ldw + q];
+      }
     }
     if (r == pr) { chosen = true; L = c; }
     else if (L == c) { L = j; }
@@ -181,7 +194,7 @@ __device__ bool lu_panel_lazy(T *W, int ldw, int R, int Cw, int c0, int n, int k
 
 template <typename T>
 __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int32_t *piv, T *W,
-                             double pivtol, DevStatus *st) {
+                             double pivtol, DevStatus *st, T *cnorm, T tau) {
   const int n = b.n, kl = b.kl, ku = b.ku, wd = 2 * kl + ku + 1;
   const int R = DD_NB + kl, Cw = DD_NB + kl + ku, ldw = lu_ldw(kl, ku);
   T *A = band + b.band_off;
@@ -206,6 +219,21 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
   }
   __syncthreads();
   const T thresh = T(pivtol) * s_amax;
+  // the incomplete factorisation's reference: the 2-norm of every column of
+  // the unfactored block (rows ascending; band row i holds column j at
+  // offset j - i + kl)
+  const T *cn = tau > T(0) ? cnorm + b.row0 : nullptr;
+  if (tau > T(0)) {
+    for (int j = tid; j < n; j += nt) {
+      T sq = T(0);
+      for (int i = max(0, j - ku); i <= min(n - 1, j + kl); ++i) {
+        const T v = A[(int64_t)i * wd + (j - i + kl)];
+        sq += v * v;
+      }
+      cnorm[b.row0 + j] = sqrt(sq);
+    }
+    __syncthreads();
+  }
 
   for (int t = 0; t < b.ntiles; ++t) {
     const int c0 = t * DD_NB;
@@ -258,7 +286,7 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
     // panel: column by column (deferred exchanges when a thread owns each
     // window row, else exchanges as they come)
     if (R <= nt) {
-      if (!lu_panel_lazy<T>(W, ldw, R, Cw, c0, n, kl, nbe, thresh, P, st, task)) return;
+      if (!lu_panel_lazy<T>(W, ldw, R, Cw, c0, n, kl, nbe, thresh, P, st, task, cn, tau)) return;
     } else
     for (int c = 0; c < nbe; ++c) {
       const int last = min(min(R - 1, c + kl), n - 1 - c0);
@@ -290,9 +318,23 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       __syncthreads();
       const T dkk = W[c * ldw + c];
       for (int r = c + 1 + tid; r <= last; r += nt) {
-        const T l = W[r * ldw + c] / dkk;
+        T l = W[r * ldw + c] / dkk;
+        if (tau > T(0) && tabs(l) < tau * cn[c0 + c] / tabs(dkk)) l = T(0);
         W[r * ldw + c] = l;
-        for (int q = c + 1; q < DD_NB; ++q) W[r * ldw + q] -= l * W[c * ldw + q];
+        for (int q = c + 1; q < DD_NB; ++q) {
+          T u = W[c * ldw + q];
+          if (tau > T(0) && c0 + q < n && tabs(u) < tau * cn[c0 + q]) u = T(0);
+          W[r * ldw + q] -= l * u;
+        }
+      }
+      __syncthreads();
+    }
+    // the incomplete factorisation: the panel's rows of U as its column
+    // steps used them (entries below tau times their column's norm dropped)
+    if (tau > T(0)) {
+      for (int e = tid; e < nbe * DD_NB; e += nt) {
+        const int c = e / DD_NB, q = e % DD_NB;
+        if (q > c && q < nbe && tabs(W[c * ldw + q]) < tau * cn[c0 + q]) W[c * ldw + q] = T(0);
       }
       __syncthreads();
     }
@@ -306,16 +348,22 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
       // trailing block
       static_assert(DD_NB == 32, "two 16-row blocks");
       for (int q = DD_NB + tid; q < Cw; q += nt) {
+        // the incomplete factorisation: each entry of U12 dropped (below tau
+        // times its column's norm) as soon as it is final, before it is used
+        const T th = (tau > T(0) && c0 + q < n) ? tau * cn[c0 + q] : T(0);
         T x[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = W[r * ldw + q];
 #pragma unroll
-        for (int c = 0; c < 15; ++c)
+        for (int c = 0; c < 15; ++c) {
+          if (tabs(x[c]) < th) x[c] = T(0);
 #pragma unroll
           for (int r = c + 1; r < 16; ++r)
             if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
+        }
+        if (tabs(x[15]) < th) x[15] = T(0);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) W[r * ldw + q] = x[r];
+        for (int r = 0; r < 16; ++r) W[r * ldw + q] = x[r];
 #pragma unroll 1
         for (int r = 16; r < DD_NB; ++r) {
           T acc = W[r * ldw + q];
@@ -328,25 +376,32 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
 #pragma unroll
         for (int r = 0; r < 16; ++r) y[r] = W[(16 + r) * ldw + q];
 #pragma unroll
-        for (int c = 0; c < 15; ++c)
+        for (int c = 0; c < 15; ++c) {
+          if (tabs(y[c]) < th) y[c] = T(0);
 #pragma unroll
           for (int r = c + 1; r < 16; ++r)
             if (16 + c < nbe - 1) y[r] -= W[(16 + r) * ldw + 16 + c] * y[c];
+        }
+        if (tabs(y[15]) < th) y[15] = T(0);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) W[(16 + r) * ldw + q] = y[r];
+        for (int r = 0; r < 16; ++r) W[(16 + r) * ldw + q] = y[r];
       }
     } else {
       for (int q = DD_NB + tid; q < Cw; q += nt) {
+        const T th = (tau > T(0) && c0 + q < n) ? tau * cn[c0 + q] : T(0);
         T x[DD_NB];
 #pragma unroll
         for (int r = 0; r < DD_NB; ++r) x[r] = W[r * ldw + q];
 #pragma unroll
-        for (int c = 0; c < DD_NB - 1; ++c)
+        for (int c = 0; c < DD_NB - 1; ++c) {
+          if (tabs(x[c]) < th) x[c] = T(0);
 #pragma unroll
           for (int r = c + 1; r < DD_NB; ++r)
             if (c < nbe - 1) x[r] -= W[r * ldw + c] * x[c];
+        }
+        if (tabs(x[DD_NB - 1]) < th) x[DD_NB - 1] = T(0);
 #pragma unroll
-        for (int r = 1; r < DD_NB; ++r) W[r * ldw + q] = x[r];
+        for (int r = 0; r < DD_NB; ++r) W[r * ldw + q] = x[r];
       }
     }
     __syncthreads();
@@ -407,7 +462,7 @@ template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256, 1) band_lu_kernel(const BandInfo *__restrict__ info, T *band, T *ltraw, int32_t *piv,
                                T *wscratch, int64_t wscratch_stride, int smem_bytes, double pivtol,
                                const int32_t *__restrict__ sched, const int32_t *__restrict__ sched_off,
-                               DevStatus *st) {
+                               DevStatus *st, T *cnorm, T tau) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const int t0 = sched_off ? sched_off[blockIdx.x] : (int)blockIdx.x;
   const int t1 = sched_off ? sched_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
@@ -418,7 +473,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256, 1) band_lu_kernel(
     const int64_t wb = lu_window_elems(b.kl, b.ku) * (int64_t)sizeof(T);
     T *W = (wb <= smem_bytes) ? reinterpret_cast<T *>(smraw) : wscratch + (int64_t)task * wscratch_stride;
     __syncthreads();  // the previous task is done with the window and the shared scalars
-    band_lu_task<T>(b, task, band, ltraw, piv, W, pivtol, st);
+    band_lu_task<T>(b, task, band, ltraw, piv, W, pivtol, st, cnorm, tau);
   }
 }
 
@@ -1594,15 +1649,17 @@ size_t band_lu_window_bytes(int max_kl, int max_ku, int elem_size) {
 template <typename T>
 cudaError_t launch_band_lu(const BandInfo *d_info, int m, int max_kl, int max_ku, T *band, T *ltraw,
                            int32_t *piv, T *wscratch, double pivtol, DevStatus *st, int threads,
-                           int grid, const int32_t *sched, const int32_t *sched_off, cudaStream_t s) {
+                           int grid, const int32_t *sched, const int32_t *sched_off, T *cnorm, double ilu_tol,
+                           cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
+  if (ilu_tol > 0 && !cnorm) return cudaErrorInvalidValue;
   const size_t wb = band_lu_window_bytes(max_kl, max_ku, sizeof(T));
   const size_t smem = std::min(wb, (size_t)DD_LU_SMEM);
   cudaError_t e = ensure_smem(band_lu_kernel<T>, smem);
   if (e != cudaSuccess) return e;
   band_lu_kernel<T><<<sched_off ? grid : m, threads, smem, s>>>(d_info, band, ltraw, piv, wscratch,
                                                                 (int64_t)(wb / sizeof(T)), (int)smem,
-                                                                pivtol, sched, sched_off, st);
+                                                                pivtol, sched, sched_off, st, cnorm, T(ilu_tol));
   return cudaGetLastError();
 }
 
@@ -1882,7 +1939,7 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
 #define DD_INST_BAND(T)                                                                            \
   template cudaError_t launch_band_lu<T>(const BandInfo *, int, int, int, T *, T *, int32_t *,     \
                                          T *, double, DevStatus *, int, int, const int32_t *,       \
-                                         const int32_t *, cudaStream_t);                            \
+                                         const int32_t *, T *, double, cudaStream_t);               \
   template int band_lu_occupancy<T>(int, int, int);                                                \
   template cudaError_t launch_tile_widths<T>(const BandInfo *, int, int, const T *, const T *,     \
                                              const int32_t *, int32_t *, int32_t *, cudaStream_t); \

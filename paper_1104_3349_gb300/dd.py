@@ -99,7 +99,8 @@ class dd_opts(ctypes.Structure):
                 ("max_restart", ctypes.c_int32), ("autotune", ctypes.c_int32), ("krylov_ctas_per_sm", ctypes.c_int32),
                 ("time_kernels", ctypes.c_int32), ("sweep_cluster", ctypes.c_int32),
                 ("mlp_weights", ctypes.c_char_p), ("overlap", ctypes.c_int32), ("radius", ctypes.c_int32),
-                ("krylov_threads", ctypes.c_int32), ("sweep_prefetch", ctypes.c_int32)]
+                ("krylov_threads", ctypes.c_int32), ("sweep_prefetch", ctypes.c_int32),
+                ("pad_opts", ctypes.c_int32), ("ilu_tol", ctypes.c_double)]
 
 
 class dd_info(ctypes.Structure):
@@ -234,7 +235,7 @@ class DD:
     def __init__(self, A, part, m, kind="msce_inf", perm=None, sz=64, agg_offsets=None, prec=DD_FP64,
                  pivot_tol=0.0, max_restart=50, stream=None, raise_on_error=True, use_graph=False,
                  autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, time_kernels=False, sweep_cluster=0,
-                 overlap=0, radius=0, krylov_threads=0, sweep_prefetch=0):
+                 overlap=0, radius=0, krylov_threads=0, sweep_prefetch=0, ilu_tol=0.0):
         lib = load()
         self._lib = lib
         self.n = int(A.n)
@@ -253,6 +254,7 @@ class DD:
         o.radius = int(radius)
         o.krylov_threads = int(krylov_threads)
         o.sweep_prefetch = int(sweep_prefetch)
+        o.ilu_tol = float(ilu_tol)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
@@ -356,7 +358,7 @@ class DDBatch:
 
     def __init__(self, systems, kind="msce_inf", prec=DD_FP64, pivot_tol=0.0, max_restart=50, stream=None,
                  use_graph=False, autotune=False, mlp_weights=None, krylov_ctas_per_sm=0, sweep_cluster=0,
-                 sweep_prefetch=0):
+                 sweep_prefetch=0, ilu_tol=0.0):
         """systems: list of (A, part, m, perm, agg_offsets) with A a CSR (perm, agg_offsets may be None)."""
         lib = load()
         self._lib = lib
@@ -378,6 +380,7 @@ class DDBatch:
                     int(krylov_ctas_per_sm))
         o.sweep_cluster = int(sweep_cluster)
         o.sweep_prefetch = int(sweep_prefetch)
+        o.ilu_tol = float(ilu_tol)
         self._wpath = None if mlp_weights is None else os.fsencode(mlp_weights)
         o.mlp_weights = self._wpath
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
