@@ -127,13 +127,18 @@ typedef struct {
                          every Arnoldi step with CUDA events (dd_stats
                          krylov_steps, cgs2_ms, cgs2_fma, spmv_ms); ignored
                          with use_graph; 0: no events                        */
-  int32_t sweep_cluster;/* CTAs per subdomain of the apply's sweeps: 2 splits
-                         every tile step over a 2-CTA cluster (half the tile
-                         bytes through each SM, the step's rows exchanged
-                         through distributed shared memory), 1 one CTA; 0
-                         chooses 2 in FP64 when every subdomain's cluster
-                         is resident at once and 1 otherwise, or with
-                         autotune the faster of the two                    */
+  int32_t sweep_cluster;/* CTAs per subdomain of the apply's sweeps: 1 one
+                         CTA; 2 splits every tile step over a 2-CTA cluster
+                         (half the tile bytes through each SM, the step's
+                         rows exchanged through distributed shared memory);
+                         3 a 2-CTA cluster in the lookahead split (CTA 0
+                         runs the forward sweep and the near columns of each
+                         backward step, CTA 1 the far columns one step
+                         ahead, partial sums and x exchanged through
+                         distributed shared memory; invalid argument where
+                         its stages do not fit); 0 chooses (reported in
+                         dd_stats.sweep_cluster), or with autotune the
+                         fastest that fits                                 */
   const char *mlp_weights; /* DD_LEARNED: path of the network's weight file
                               (format under dd_mlp_*); ignored otherwise       */
   int32_t overlap;    /* DD_OMSCN / DD_OMSCNR / DD_OLUM: overlap width w >= 0   */
@@ -198,7 +203,8 @@ typedef struct {
                                 (both passes' dots and updates and the norm:
                                 (4 (j+1) + 2) n at step j)                       */
   double spmv_ms;            /* device time of the SpMV w = C z                  */
-  int32_t sweep_cluster;     /* CTAs per subdomain of the sweeps (1 or 2)        */
+  int32_t sweep_cluster;     /* sweep mode: 1 one CTA, 2 row-split cluster,
+                                3 lookahead cluster (opts.sweep_cluster)         */
   int32_t msce_nodes_max;    /* DD_MSCE: largest interior node set D_r           */
 } dd_stats;
 

@@ -42,7 +42,7 @@ struct DDHandle {
   int tb = DD_NB;              // columns of a sweep tile (DD_NB or DD_TB_WIDE)
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
   uint32_t first_wait = 0xffffffffu;  // test hook: polls of each sweep CTA's first wait
-  int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1 or 2
+  int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1, 2 or 3
   int sweep_pf_opt = 0;        // opts.sweep_prefetch: k > 0 k jobs, else none
   int overlap = 0, radius = 0; // opts.overlap (overlapped kinds), opts.radius (DD_MSCE)
   double ilu_tol = 0.0;        // opts.ilu_tol: drop tolerance of the incomplete interior LU (0: exact)
@@ -55,6 +55,7 @@ struct DDHandle {
   TileMeta *tm = nullptr;      // packed sweep tiles
   bool tiles_ready = false;    // the packed tiles are written (or queued)
   unsigned char *cld = nullptr;  // the tiles in the 2-CTA sweep layout (built on first use)
+  unsigned char *lad = nullptr;  // the backward tiles in the lookahead layout (built on first use)
   SweepJob *jobs = nullptr;    // jobs of the sweep ring
   cudaStream_t stream = nullptr;
   // setup: while astream is set, allocations and uploads go to it (the side
@@ -544,7 +545,42 @@ void build_jobs(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, si
       hi = lo;
     }
     b.njb = (int32_t)jobs.size() - b.jb0;
+    b.jl0 = (int32_t)jobs.size();
+    b.njl = 0;
   }
+}
+
+// Jobs of the lookahead sweeps: the forward jobs of the one-CTA plan, then
+// per subdomain CTA 0's and CTA 1's backward jobs, each sized by that CTA's
+// slices of the tiles (a job of CTA 1 whose tiles have no columns for it
+// copies nothing).
+void build_jobs_la(std::vector<BandInfo> &info, const std::vector<TileMeta> &tm, size_t stage, size_t es,
+                   int tb, std::vector<SweepJob> &jobs) {
+  build_jobs(info, tm, stage, es, tb, 1, jobs);
+  std::vector<SweepJob> out;
+  for (BandInfo &b : info) {
+    const int jf = (int)out.size();
+    for (int q = 0; q < b.njf; ++q) out.push_back(jobs[b.jf0 + q]);
+    b.jf0 = jf;
+    for (int p = 0; p < 2; ++p) {
+      const int j0 = (int)out.size();
+      for (int hi = b.nst; hi > 0;) {
+        size_t bytes = 0;
+        int lo = hi;
+        while (lo > 0) {
+          const size_t nb = (size_t)tb * la_cols(tm[b.tile0 + lo - 1].wu, tb, p) * es;
+          if (lo < hi && bytes + nb > stage) break;
+          bytes += nb;
+          --lo;
+        }
+        out.push_back(SweepJob{lo, hi});
+        hi = lo;
+      }
+      if (p == 0) { b.jb0 = j0; b.njb = (int)out.size() - j0; }
+      else { b.jl0 = j0; b.njl = (int)out.size() - j0; }
+    }
+  }
+  jobs.swap(out);
 }
 
 // Longest processing time first: tasks in order of decreasing cost (ties by
@@ -591,7 +627,7 @@ int sm_count() {
 template <typename T>
 int choose_cluster(const DDHandle *h, size_t stage) {
   (void)stage;
-  if (h->sweep_cl_opt == 1 || h->sweep_cl_opt == 2) return h->sweep_cl_opt;
+  if (h->sweep_cl_opt >= 1 && h->sweep_cl_opt <= 3) return h->sweep_cl_opt;
   return (sizeof(T) == 8 && 2 * h->m <= sm_count()) ? 2 : 1;
 }
 
@@ -627,11 +663,72 @@ dd_status build_cluster_layout(DDHandle *h) {
   return DD_OK;
 }
 
+// The backward tiles in the layout of the lookahead sweeps (once per handle,
+// after the packed tiles): per subdomain, CTA 0's columns of every tile in
+// ascending tile order, then CTA 1's, so that a backward job is one
+// contiguous copy per CTA.
+template <typename T>
+dd_status build_la_layout(DDHandle *h) {
+  if (h->lad) return DD_OK;
+  int64_t off = 0;
+  for (const BandInfo &b : h->h_info)
+    for (int p = 0; p < 2; ++p)
+      for (int t = 0; t < b.nst; ++t) {
+        TileMeta &q = h->h_tm[b.tile0 + t];
+        q.lao[p] = off;
+        off += (int64_t)h->tb * la_cols(q.wu, h->tb, p) * (int64_t)sizeof(T);
+      }
+  const int ntiles = (int)h->h_tm.size();
+  if (ntiles)
+    CK(cudaMemcpyAsync(h->tm, h->h_tm.data(), sizeof(TileMeta) * ntiles, cudaMemcpyHostToDevice, h->stream));
+  TRY(dalloc(h, &h->lad, (size_t)std::max<int64_t>(off, 16)));
+  CK(launch_la_pack<T>(ntiles, h->tb, h->tm, static_cast<const T *>(bufs<T>(h).utile), h->lad, h->stream));
+  return DD_OK;
+}
+
+// The largest piece a CTA of the lookahead sweeps copies: a forward tile
+// with its src (CTA 0), or one CTA's columns of a backward tile
+template <typename T>
+size_t la_max_unit(const DDHandle *h) {
+  size_t u = 0;
+  for (const TileMeta &q : h->h_tm)
+    u = std::max({u, (size_t)q.wl * h->tb * sizeof(T) + (size_t)round4(q.wl) * 4,
+                  (size_t)h->tb * la_cols(q.wu, h->tb, 0) * sizeof(T),
+                  (size_t)h->tb * la_cols(q.wu, h->tb, 1) * sizeof(T)});
+  return u;
+}
+
+// The layout a plan's sweeps stream from, once the packed tiles exist
+template <typename T>
+dd_status plan_layout(DDHandle *h) {
+  if (!h->tiles_ready) return DD_OK;
+  if (h->plan.la) {
+    TRY(build_la_layout<T>(h));
+  } else if (h->plan.cl > 1) {
+    TRY(build_cluster_layout<T>(h));
+  }
+  h->plan.cld = h->cld;
+  h->plan.lad = h->lad;
+  return DD_OK;
+}
+
 // The sweep plan for one stage size: the job table, and a persistent LPT
 // schedule when the subdomains outnumber the CTAs that fit on the device.
+// mode: 1 one CTA per subdomain, 2 a 2-CTA cluster splitting every step's
+// rows, 3 a 2-CTA cluster in the lookahead split (stage 0: its own choice).
 template <typename T>
-dd_status set_sweep_plan(DDHandle *h, size_t stage, int cl) {
-  if (cl > 1) {
+dd_status set_sweep_plan(DDHandle *h, size_t stage, int mode) {
+  const int cl = mode == 1 ? 1 : 2, la = mode == 3 ? 1 : 0;
+  if (la) {
+    // the largest piece either CTA copies; a stage of it or more, three
+    // stages when three fit (two copies in flight while one is read)
+    const size_t unit = (la_max_unit<T>(h) + 127) & ~(size_t)127;
+    const size_t smax = band_sweep_max_stage(h->max_n, h->max_kl, h->max_ku2, sizeof(T), h->tb, cl);
+    const size_t s3 = (smax * 2 / 3) & ~(size_t)127;
+    if (stage == 0) stage = unit <= s3 ? s3 : smax;
+    if (stage > smax && unit <= smax) stage = smax;
+    if (stage < unit) stage = unit;
+  } else if (cl > 1) {
     // the exchange buffers take room: shrink the stage to what two stages
     // leave, as long as the largest slice of a tile still fits
     const size_t smax = band_sweep_max_stage(h->max_n, h->max_kl, h->max_ku2, sizeof(T), h->tb, cl);
@@ -643,23 +740,24 @@ dd_status set_sweep_plan(DDHandle *h, size_t stage, int cl) {
     if (stage > smax && slice <= smax) stage = smax;
   }
   std::vector<SweepJob> jobs;
-  build_jobs(h->h_info, h->h_tm, stage, sizeof(T), h->tb, cl, jobs);
+  if (la) build_jobs_la(h->h_info, h->h_tm, stage, sizeof(T), h->tb, jobs);
+  else build_jobs(h->h_info, h->h_tm, stage, sizeof(T), h->tb, cl, jobs);
   const int m = h->m;
-  if (!h->jobs) TRY(dalloc(h, &h->jobs, 2 * std::max<size_t>(h->h_tm.size(), 1)));
+  if (!h->jobs) TRY(dalloc(h, &h->jobs, 3 * std::max<size_t>(h->h_tm.size(), 1)));
   if (!jobs.empty())
     CK(cudaMemcpyAsync(h->jobs, jobs.data(), sizeof(SweepJob) * jobs.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_info, h->h_info.data(), sizeof(BandInfo) * m, cudaMemcpyHostToDevice, h->stream));
   h->plan.stage_bytes = (uint32_t)stage;
   h->plan.cl = cl;
-  if (cl > 1 && h->tiles_ready) TRY(build_cluster_layout<T>(h));
-  h->plan.cld = h->cld;
-  h->plan.threads = 8 * h->tb / cl;
-  const int slots = band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, h->plan.stage_bytes);
+  h->plan.la = la;
+  TRY(plan_layout<T>(h));
+  h->plan.threads = la ? 8 * h->tb : 8 * h->tb / cl;
+  const int slots = band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, h->plan.stage_bytes, la);
   if (slots <= 0) {
     h->err = "a subdomain is too large for the shared-memory sweep (reduce its size or use FP32)";
     return DD_ERR_INVALID_ARG;
   }
-  h->stats.sweep_cluster = cl;
+  h->stats.sweep_cluster = mode;
   h->stats.sweep_slots = slots;
   h->stats.stage_bytes = (int32_t)stage;
   if (m > slots) {
@@ -1643,7 +1741,8 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     h->h_info = info;
     h->h_tm = tm;
     TRY(upload(h, &h->tm, tm));
-    TRY(set_sweep_plan<T>(h, stage, choose_cluster<T>(h, stage)));
+    const int mode = choose_cluster<T>(h, stage);
+    TRY(set_sweep_plan<T>(h, mode == 3 ? 0 : stage, mode));  // 0: the lookahead split sizes its own stages
     info = h->h_info;
     TRY(dalloc(h, &B.ltile, lofs));
     TRY(dalloc(h, &B.utile, uofs));
@@ -1652,10 +1751,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
     CK(launch_band_tiles<T>(h->d_info, m, h->max_tiles, h->max_kl, h->tb, h->tm, B.band, B.lm, h->piv,
                             B.ltile, B.utile, h->src, s));
     h->tiles_ready = true;
-    if (h->plan.cl > 1) {
-      TRY(build_cluster_layout<T>(h));
-      h->plan.cld = h->cld;
-    }
+    TRY(plan_layout<T>(h));
   }
   // G(R_a, R_a) into S
   CK(cudaMemsetAsync(B.S, 0, sizeof(T) * std::max<int64_t>(soff[nagg], 1), s));
@@ -2257,12 +2353,14 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
   int best_cl = 1;
   float best_ms = 1e30f;
   int tried = 0;
-  for (int cl = 1; cl <= 2; ++cl)
+  for (int mode = 1; mode <= 3; ++mode)
   for (size_t st : cand) {
-    if (h->sweep_cl_opt && cl != h->sweep_cl_opt) continue;
+    if (h->sweep_cl_opt && mode != h->sweep_cl_opt) continue;
+    const int cl = mode == 1 ? 1 : 2, la = mode == 3 ? 1 : 0;
+    if (la && st < la_max_unit<T>(h)) continue;
     if (band_sweep_stages(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, sizeof(T), (uint32_t)st) < 2) continue;
-    if (band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, (uint32_t)st) <= 0) continue;
-    dd_status rc = set_sweep_plan<T>(h, st, cl);
+    if (band_sweep_slots<T>(h->max_n, h->max_kl, h->max_ku2, h->tb, cl, (uint32_t)st, la) <= 0) continue;
+    dd_status rc = set_sweep_plan<T>(h, st, mode);
     if (rc != DD_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
     float tmin = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {
@@ -2276,7 +2374,7 @@ dd_status autotune_sweeps(DDHandle *h, double *y, double *x) {
       if (rep > 0) tmin = std::min(tmin, ms);
     }
     ++tried;
-    if (tmin < best_ms) { best_ms = tmin; best = st; best_cl = cl; }
+    if (tmin < best_ms) { best_ms = tmin; best = st; best_cl = mode; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2313,7 +2411,7 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   h->krylov_threads = o.krylov_threads > 0 ? o.krylov_threads : 512;
   h->krylov_per_sm = o.krylov_ctas_per_sm > 0 ? o.krylov_ctas_per_sm : (h->krylov_threads == 512 ? 1 : 2);
   h->time_kernels = o.time_kernels != 0 && !h->use_graph;
-  if (o.sweep_cluster < 0 || o.sweep_cluster > 2) { h->err = "sweep_cluster must be 0, 1 or 2"; return DD_ERR_INVALID_ARG; }
+  if (o.sweep_cluster < 0 || o.sweep_cluster > 3) { h->err = "sweep_cluster must be 0, 1, 2 or 3"; return DD_ERR_INVALID_ARG; }
   h->sweep_cl_opt = o.sweep_cluster;
   h->sweep_pf_opt = o.sweep_prefetch;
   if (!(o.ilu_tol >= 0.0) || !std::isfinite(o.ilu_tol)) { h->err = "ilu_tol must be finite and >= 0"; return DD_ERR_INVALID_ARG; }

@@ -31,7 +31,8 @@ struct BandInfo {
   int32_t row0;     // first row in the permuted interior numbering
   int32_t tile0;    // index of the first sweep tile in the packed tile tables
   int32_t jf0, njf; // forward jobs [jf0, jf0 + njf) of the sweep ring
-  int32_t jb0, njb; // backward jobs
+  int32_t jb0, njb; // backward jobs (in the lookahead split: CTA 0's)
+  int32_t jl0, njl; // lookahead split: CTA 1's backward jobs
 };
 
 __host__ __device__ inline int bi_wd(const BandInfo &b) { return 2 * b.kl + b.ku + 1; }
@@ -50,6 +51,9 @@ struct TileMeta {
   // 2-CTA sweeps: byte offsets of CTA p's forward slice (its K rows, then
   // the tile's src) and backward slice (its Kb rows) in the cluster layout
   int64_t cfo[2], cbo[2];
+  // 2-CTA lookahead sweeps: byte offsets of CTA p's columns of the backward
+  // tile (la_cols) in the lookahead layout
+  int64_t lao[2];
 };
 
 // a job of the sweep ring: tiles [lo, hi) of one subdomain, one bulk copy
@@ -58,6 +62,22 @@ struct SweepJob {
 };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
+// Columns of a backward tile (wu wide, tb rows) that CTA p of a lookahead
+// pair takes: p = 0 the first la_split columns, p = 1 the rest.  CTA 0's
+// share always holds the columns of b_T and of the next tile's x (those its
+// step depends on at once); CTA 1's only x at least two tiles ahead, known
+// one step earlier.  Beyond that the split halves the row.  wu and tb are
+// multiples of 4, so every slice row is a multiple of 16 bytes.
+__host__ __device__ inline int la_split(int wu, int tb) {
+  const int half = ((wu >> 1) + 3) & ~3;
+  const int s = half > 2 * tb ? half : 2 * tb;
+  return s < wu ? s : wu;
+}
+__host__ __device__ inline int la_cols(int wu, int tb, int p) {
+  const int s = la_split(wu, tb);
+  return p == 0 ? s : wu - s;
+}
 
 // Sweeps split over a cluster of cl CTAs (cl = 1 or 2): CTA p of the cluster
 // takes forward-tile rows [fwd_split(wl, p), fwd_split(wl, p + 1)) and
@@ -111,6 +131,12 @@ struct SweepPlan {
   int pf = 0;
   // cl = 2: the tiles in the cluster layout (TileMeta cfo / cbo)
   const unsigned char *cld = nullptr;
+  // cl = 2 with la = 1: the lookahead split instead (CTA 0 runs the forward
+  // sweep alone and the near columns of every backward step, CTA 1 the far
+  // columns one step ahead); backward slices in lad (TileMeta lao), 8 TB
+  // threads per CTA
+  int la = 0;
+  const unsigned char *lad = nullptr;
 };
 
 // Device-side error word: first failure wins.
@@ -219,15 +245,21 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
                                   const T *e_val, const T *z2, const T *z1, const int32_t *perm,
                                   double *x, DevStatus *st, cudaStream_t s);
 // subdomains the sweep kernels hold resident at once (CTAs for cl = 1,
-// clusters for cl = 2) at this stage size; 0: they do not fit
+// clusters for cl = 2; la = 1 the lookahead split's 8 TB-thread clusters) at
+// this stage size; 0: they do not fit
 template <typename T>
-int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes);
+int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes, int la = 0);
 // The 2-CTA sweep layout: bytes of CTA p's forward / backward slice of a tile,
 // and the copy of every tile's slices to cld at TileMeta cfo / cbo
 void cluster_slice_bytes(const TileMeta &mt, int tb, int elem_size, int p, int64_t &fwd, int64_t &bwd);
 template <typename T>
 cudaError_t launch_cluster_pack(int ntiles, int tb, const TileMeta *tm, const T *ltile, const T *utile,
                                 const int32_t *srcs, unsigned char *cld, cudaStream_t s);
+// The lookahead sweep layout: CTA p's columns of every backward tile
+// (la_cols) copied to lad at TileMeta lao[p]
+template <typename T>
+cudaError_t launch_la_pack(int ntiles, int tb, const TileMeta *tm, const T *utile, unsigned char *lad,
+                           cudaStream_t s);
 // X = A_jj^-1 X in place; X column-major with leading dimension n_j starting
 // at x_off[j], ncols[j] columns.
 template <typename T>

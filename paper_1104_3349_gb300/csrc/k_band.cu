@@ -1031,6 +1031,12 @@ struct SweepCtx {
   uint64_t *xbar = nullptr;
   uint32_t pxb = 0, pxbar = 0;  // the peer's xb and xbar (shared::cluster addresses)
   uint32_t sstep = 0;
+  // lookahead sweeps: messages of earlier tasks in each direction (x from
+  // CTA 0, partial sums from CTA 1), tasks finished, and the two task-end
+  // flag words (own, and the peer's shared::cluster address)
+  uint32_t ubase = 0, vbase = 0, ntask = 0;
+  int32_t *okw = nullptr;
+  uint32_t pokw = 0;
   __device__ void init(T *xb_, uint64_t *xbar_, int max_kl, int tb) {
     cid = (int)blockIdx.x / CL;
     if (CL > 1) {
@@ -1046,6 +1052,8 @@ struct SweepCtx {
       }
       pxb = map_peer(smem_u32(xb_), (uint32_t)(rank ^ 1));
       pxbar = map_peer(smem_u32(xbar_), (uint32_t)(rank ^ 1));
+      okw = reinterpret_cast<int32_t *>(xbar_ + 2);  // 8 spare bytes after the two message barriers
+      pokw = map_peer(smem_u32(okw), (uint32_t)(rank ^ 1));
       cluster_barrier();  // the peer's barriers are set up before any message
     }
   }
@@ -1244,6 +1252,270 @@ __device__ bool sweep_cluster(const BandInfo &b, const TileMeta *__restrict__ tm
   jbase += nj;
   return ok;
 }
+// ---------------------------------------------------------------------------
+// The lookahead split of one subdomain's sweeps over a 2-CTA cluster.
+// CTA 0 runs the forward sweep alone, on the one-CTA tiles: a forward step
+// can take pivot rows from anywhere in its window, so splitting its rows
+// costs a wait for the peer every step.  The backward step t,
+//   x_t = Kb [b_t; x_{t+1}; x_{t+2}; ...],
+// is split by columns instead (la_split): CTA 0 takes the columns of b_t and
+// x_{t+1} (and more, to balance the bytes), CTA 1 only columns of x_{t+2}
+// and beyond, which are final one step before x_{t+1}.  So CTA 1 forms its
+// partial sums s_t one step ahead and sends them to CTA 0 (message
+// nst - 1 - t, every t); CTA 0 adds them to its own and sends x_t to CTA 1
+// (message nst - 1 - t, t >= 2), which needs it for s_{t-2}.  Each side
+// waits only for a message the other sent a step earlier.  Every message of
+// a task is sent and taken whatever happens (a copy that stayed out, or a
+// peer flag of 0, only clears the flag), and the pair decides together at
+// the end of each task whether to go on, so no message is in flight when
+// either CTA stops.  A CTA takes message k of a direction from slot k & 1
+// after taking message k - 2 from it; the peer sends message k only after
+// receiving something the CTA sent after that take, so no slot is
+// overwritten before it is read.  Each CTA streams its own job list, sized
+// by its own slices.  Sums are formed in another order than in the one-CTA
+// sweep, so the results agree to rounding, not bit for bit.
+// ---------------------------------------------------------------------------
+template <typename T, int TB>
+__device__ __forceinline__ uint32_t la_bytes(const TileMeta &mt, int rank) {
+  return (uint32_t)(TB * la_cols(mt.wu, TB, rank) * sizeof(T));
+}
+
+// job q of CTA rank's list into its stage: rank 0 the forward jobs (the
+// one-CTA tiles), then its backward slices; rank 1 its backward slices only.
+// A job whose slices are all empty copies nothing; its arrival alone
+// completes the stage's phase.
+template <typename T, int TB>
+__device__ __forceinline__ void issue_job_la(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs, int q,
+                                             const T *ltile, const int32_t *srcs, const unsigned char *lad,
+                                             unsigned char *stage, uint64_t *bar, int rank, uint32_t stage_bytes,
+                                             DevStatus *st) {
+  if (rank == 0 && q < b.njf) {
+    issue_job<T, TB, 1>(b, tm, jobs, q, ltile, nullptr, srcs, stage, bar, 0, stage_bytes, st);
+    return;
+  }
+  const SweepJob jb = jobs[b.jb0 + (rank == 0 ? q - b.njf : q)];
+  const TileMeta &a = tm[b.tile0 + jb.lo], &z = tm[b.tile0 + jb.hi - 1];
+  const uint32_t tot = (uint32_t)(z.lao[rank] - a.lao[rank]) + la_bytes<T, TB>(z, rank);
+  mbar_expect_tx(bar, tot);
+  if (tot) bulk_g2s_checked(stage, 0, lad + a.lao[rank], tot, stage_bytes, bar, st);
+}
+
+template <typename T, int TB>
+__device__ __forceinline__ void issue_first_jobs_la(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
+                                                    const T *ltile, const int32_t *srcs, const unsigned char *lad,
+                                                    unsigned char *ring, uint32_t stage_bytes, int nstages,
+                                                    uint64_t *bars, uint32_t jbase, int rank, DevStatus *st) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const int nj = rank == 0 ? b.njf + b.njb : b.njb;
+  for (int q = 0; q < nstages && q < nj; ++q) {
+    const int sq = (int)((jbase + q) % nstages);
+    issue_job_la<T, TB>(b, tm, jobs, q, ltile, srcs, lad, ring + (size_t)sq * stage_bytes, &bars[sq], rank,
+                        stage_bytes, st);
+  }
+}
+
+__device__ __forceinline__ int32_t ld_peer_i32(uint32_t raddr) {
+  int32_t v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(raddr) : "memory");
+  return v;
+}
+
+// 16 lanes' partial sums of one output row into every one of them
+template <typename T>
+__device__ __forceinline__ T sum16(T acc) {
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+  return acc;
+}
+
+// Forward sweep (CTA 0) and backward sweep (both CTAs) of one subdomain in
+// the lookahead split.  vec / xout / win as in the one-CTA sweep; CTA 1's
+// xout holds the x it has received.  Returns the pair's combined outcome
+// (false: a wait of either CTA expired).
+template <typename T, int TB>
+__device__ bool sweep_lookahead(const BandInfo &b, const TileMeta *__restrict__ tm,
+                                const SweepJob *__restrict__ jobs, const T *__restrict__ ltile,
+                                const int32_t *__restrict__ srcs, const unsigned char *__restrict__ lad, T *vec,
+                                T *xout, T *win, unsigned char *ring, uint32_t stage_bytes, int nstages,
+                                uint64_t *bars, uint32_t &jbase, int task, DevStatus *st, uint32_t first_wait,
+                                SweepCtx<T, 2> &cx, int wext, int vext) {
+  using CV = typename Chunk<T>::V;
+  constexpr int CN = Chunk<T>::N;
+  const int tid = threadIdx.x, nt = blockDim.x, rank = cx.rank, nst = b.nst;
+  const int nj = rank == 0 ? b.njf + b.njb : b.njb;
+  const int i0 = 2 * (tid >> 4), h = tid & 15;  // backward: rows i0, i0 + 1, lane h of their 16
+  bool ok = true;    // every copy in time (the same in every thread)
+  bool okm = true;   // every message this thread waited for came, flagged by the peer
+  bool live = true;  // the ring still copies (false once a copy stayed out twice the bound)
+  int qdead = nj;    // the job at which the ring stopped
+  for (int q = 0; q < nj; ++q) {
+    const uint32_t gq = jbase + q;
+    const int sidx = (int)(gq % nstages);
+    unsigned char *stage = ring + (size_t)sidx * stage_bytes;
+    const uint32_t par = (gq / nstages) & 1u;
+    // the first wait may be shortened by the timeout test hook; a second,
+    // full one then tells a late copy (the stage may be reused) from a lost
+    // one (the ring stops)
+    bool w1 = false, w2 = false;
+    if (live) {
+      w1 = mbar_wait_bounded(&bars[sidx], par, gq == 0 ? first_wait : DD_WAIT_LIMIT);
+      w2 = w1 || mbar_wait_bounded(&bars[sidx], par);
+    }
+    if (!__syncthreads_and(w1)) ok = false;
+    const bool have = __syncthreads_and(w2) != 0;
+    if (!have && live) {
+      live = false;
+      qdead = q;
+    }
+    const bool fwd = rank == 0 && q < b.njf;
+    const SweepJob jb = fwd ? jobs[b.jf0 + q] : jobs[b.jb0 + (rank == 0 ? q - b.njf : q)];
+    const TileMeta &a = tm[b.tile0 + jb.lo];
+    if (fwd) {
+      const TileMeta &z = tm[b.tile0 + jb.hi - 1];
+      const size_t kbytes = (size_t)(z.lofs + (int64_t)z.wl * TB - a.lofs) * sizeof(T);
+      for (int t = jb.lo; t < jb.hi; ++t) {
+        // forward tile t: w <- [0; w_B] + K w_T on the exchanged window
+        const TileMeta &mt = tm[b.tile0 + t];
+        const int c0 = t * TB, WL = mt.wl;
+        const T *K = reinterpret_cast<const T *>(stage + (mt.lofs - a.lofs) * sizeof(T));
+        const int32_t *src = reinterpret_cast<const int32_t *>(stage + kbytes) + (mt.sofs - a.sofs);
+        const bool wok = dd_check(st, WL <= wext && c0 + WL <= vext, 21);
+        if (!wok) ok = false;
+        const bool run = have && wok;
+        if (run)
+          for (int e = tid; e < WL; e += nt)
+            if (dd_check(st, (unsigned)src[e] < (unsigned)WL, 22)) win[e] = vec[c0 + src[e]];
+        __syncthreads();
+        if (run)
+          for (int r = tid; r < WL; r += nt) {
+            const CV *kr = reinterpret_cast<const CV *>(K + r * TB);
+            const CV *wv = reinterpret_cast<const CV *>(win);
+            T a0 = (r < TB) ? T(0) : win[r], a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+            for (int ch = 0; ch < TB / CN; ch += 4) {
+              a0 = Chunk<T>::fmadd(kr[ch ^ (r & 7)], wv[ch], a0);
+              a1 = Chunk<T>::fmadd(kr[(ch + 1) ^ (r & 7)], wv[ch + 1], a1);
+              a2 = Chunk<T>::fmadd(kr[(ch + 2) ^ (r & 7)], wv[ch + 2], a2);
+              a3 = Chunk<T>::fmadd(kr[(ch + 3) ^ (r & 7)], wv[ch + 3], a3);
+            }
+            vec[c0 + r] = (a0 + a1) + (a2 + a3);
+          }
+        __syncthreads();
+      }
+    } else if (rank == 0) {
+      for (int t = jb.hi - 1; t >= jb.lo; --t) {
+        // backward tile t: CTA 0's columns (b_t, x_{t+1}, ...), each pair
+        // of rows by 16 lanes, plus CTA 1's partial sums s_t
+        const TileMeta &mt = tm[b.tile0 + t];
+        const int r0 = t * TB, WA = la_cols(mt.wu, TB, 0), nch = WA / CN;
+        const T *Kb = reinterpret_cast<const T *>(stage + (mt.lao[0] - a.lao[0]));
+        const bool bok = dd_check(st, r0 + mt.wu <= vext, 23);
+        if (!bok) ok = false;
+        T acc0 = T(0), acc1 = T(0);
+        if (have && bok) {
+          // column c of Kb multiplies b_t (c < TB) or x = xout[r0 + c]
+          const CV *k0 = reinterpret_cast<const CV *>(Kb + (int64_t)i0 * WA);
+          const CV *k1 = reinterpret_cast<const CV *>(Kb + (int64_t)(i0 + 1) * WA);
+          const CV *bv = reinterpret_cast<const CV *>(vec + r0);
+          const CV *xv = reinterpret_cast<const CV *>(xout + r0);
+          for (int ch = h; ch < nch; ch += 16) {
+            const CV w = ch < TB / CN ? bv[ch] : xv[ch];
+            acc0 = Chunk<T>::fmadd(k0[ch], w, acc0);
+            acc1 = Chunk<T>::fmadd(k1[ch], w, acc1);
+          }
+        }
+        acc0 = sum16(acc0);
+        acc1 = sum16(acc1);
+        const uint32_t v = cx.vbase + (uint32_t)(nst - 1 - t), u = cx.ubase + (uint32_t)(nst - 1 - t);
+        if (tid == 0) cx.arm(v, TB);
+        if (h < 2) {
+          // s_t straight from the message buffer; x_t out, and to CTA 1
+          const int row = i0 + h;
+          const bool got = mbar_wait_cluster(&cx.xbar[v & 1u], (v >> 1) & 1u);
+          const T *msg = cx.xb + (int)(v & 1u) * cx.msg;
+          if (!got || msg[0] == T(0)) okm = false;
+          const T x = (h == 0 ? acc0 : acc1) + msg[1 + row];
+          xout[r0 + row] = x;
+          if (t >= 2) {
+            cx.put(u, 1 + row, x);
+            if (tid == 0) cx.put(u, 0, (ok && okm) ? T(1) : T(0));
+          }
+        }
+        __syncthreads();  // x_t in xout before the next step reads it
+      }
+    } else {
+      for (int t = jb.hi - 1; t >= jb.lo; --t) {
+        // backward tile t, CTA 1's columns (x_{t+2} and beyond): s_t
+        const TileMeta &mt = tm[b.tile0 + t];
+        const int r0 = t * TB, WS = la_split(mt.wu, TB), WB = mt.wu - WS, nch = WB / CN;
+        const T *Kb = reinterpret_cast<const T *>(stage + (mt.lao[1] - a.lao[1]));
+        if (t + 2 <= nst - 1) {
+          // x_{t+2} into xout, by the threads that copy it
+          const uint32_t u = cx.ubase + (uint32_t)(nst - 3 - t);
+          if (tid == 0) cx.arm(u, TB);
+          if (tid < TB) {
+            const bool got = mbar_wait_cluster(&cx.xbar[u & 1u], (u >> 1) & 1u);
+            const T *msg = cx.xb + (int)(u & 1u) * cx.msg;
+            if (!got || msg[0] == T(0)) okm = false;
+            xout[r0 + 2 * TB + tid] = msg[1 + tid];
+          }
+          __syncthreads();
+        }
+        const bool bok = dd_check(st, r0 + mt.wu <= vext, 23);
+        if (!bok) ok = false;
+        T acc0 = T(0), acc1 = T(0);
+        if (have && bok) {
+          const CV *k0 = reinterpret_cast<const CV *>(Kb + (int64_t)i0 * WB);
+          const CV *k1 = reinterpret_cast<const CV *>(Kb + (int64_t)(i0 + 1) * WB);
+          const CV *xv = reinterpret_cast<const CV *>(xout + r0 + WS);
+          for (int ch = h; ch < nch; ch += 16) {
+            const CV w = xv[ch];
+            acc0 = Chunk<T>::fmadd(k0[ch], w, acc0);
+            acc1 = Chunk<T>::fmadd(k1[ch], w, acc1);
+          }
+        }
+        acc0 = sum16(acc0);
+        acc1 = sum16(acc1);
+        const uint32_t v = cx.vbase + (uint32_t)(nst - 1 - t);
+        if (h < 2) cx.put(v, 1 + i0 + h, h == 0 ? acc0 : acc1);
+        if (tid == 0) cx.put(v, 0, (ok && okm) ? T(1) : T(0));
+      }
+    }
+    // the stage is free once every thread has finished the job's steps
+    __syncthreads();
+    if (tid == 0 && live && q + nstages < nj) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_job_la<T, TB>(b, tm, jobs, q + nstages, ltile, srcs, lad, stage, &bars[sidx], rank, stage_bytes, st);
+    }
+  }
+  if (!live) {
+    // the copies still in flight (jobs qdead .. qdead + nstages - 1), bounded
+    const int last_issued = min(nj - 1, qdead + nstages - 1);
+    for (int j = qdead; j <= last_issued; ++j) {
+      const uint32_t gj = jbase + j;
+      mbar_wait_bounded(&bars[gj % nstages], (gj / nstages) & 1u);
+    }
+  }
+  ok = __syncthreads_and(ok && okm) != 0;
+  if (!ok && tid == 0 && atomicCAS(&st->code, 0, (int)DD_ERR_TIMEOUT) == 0) st->block = task;
+  jbase += nj;
+  cx.vbase += (uint32_t)nst;
+  cx.ubase += (uint32_t)max(nst - 2, 0);
+  // the pair's outcome: each CTA's flag into slot ntask & 1, a cluster
+  // barrier, the peer's flag read back (a slot is rewritten two tasks later,
+  // after a barrier the peer reaches only once it has read it)
+  __shared__ int32_t pair_ok;
+  const uint32_t slot = cx.ntask & 1u;
+  if (tid == 0) cx.okw[slot] = ok ? 1 : 0;
+  cluster_barrier();
+  if (tid == 0) pair_ok = (ok && ld_peer_i32(cx.pokw + 4u * slot) != 0) ? 1 : 0;
+  __syncthreads();
+  ++cx.ntask;
+  return pair_ok != 0;
+}
+
 // shared-memory layout: [bars | vec | xout | win | tile table | job table | ring]
 template <typename T, int TB>
 __device__ __forceinline__ void carve(unsigned char *smraw, int max_n, int pad, int max_kl,
@@ -1282,6 +1554,22 @@ __device__ __forceinline__ BandInfo stage_tables(BandInfo b, const TileMeta *__r
   return b;
 }
 
+// CTA 1 of a lookahead pair: the tile table and its own backward jobs,
+// rebased as its only jobs
+__device__ __forceinline__ BandInfo stage_tables_la1(BandInfo b, const TileMeta *__restrict__ tm,
+                                                     const SweepJob *__restrict__ jobs, TileMeta *tms,
+                                                     SweepJob *jbs) {
+  for (int t = threadIdx.x; t < b.nst; t += blockDim.x) tms[t] = tm[b.tile0 + t];
+  for (int q = threadIdx.x; q < b.njl; q += blockDim.x) jbs[q] = jobs[b.jl0 + q];
+  b.tile0 = 0;
+  b.jf0 = 0;
+  b.njf = 0;
+  b.jb0 = 0;
+  b.njb = b.njl;
+  b.jl0 = 0;
+  return b;
+}
+
 __device__ __forceinline__ void init_bars(uint64_t *bars, int nstages) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) mbar_init(&bars[s], 1);
@@ -1297,7 +1585,7 @@ __device__ __forceinline__ void task_range(const int32_t *sched_off, int &t0, in
   t1 = sched_off ? sched_off[cid + 1] : cid + 1;
 }
 
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA>
 __device__ __forceinline__ bool run_sweep(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
                                           const T *ltile, const T *utile, const int32_t *srcs,
                                           const unsigned char *cld, T *vec, T *xout, T *win,
@@ -1307,13 +1595,30 @@ __device__ __forceinline__ bool run_sweep(const BandInfo &b, const TileMeta *tm,
   if constexpr (CL == 1)
     return sweep_pipelined<T, TB>(b, tm, jobs, ltile, utile, srcs, vec, xout, win, ring, stage_bytes,
                                   nstages, bars, jbase, task, true, st, first_wait, wext, vext, pf);
+  else if constexpr (LA)
+    return sweep_lookahead<T, TB>(b, tm, jobs, ltile, srcs, cld, vec, xout, win, ring, stage_bytes, nstages, bars,
+                                  jbase, task, st, first_wait, cx, wext, vext);
   else
     return sweep_cluster<T, TB>(b, tm, jobs, cld, vec, xout, win, ring, stage_bytes, nstages, bars, jbase, task,
                                 st, first_wait, cx, wext, vext);
 }
 
+// the first jobs of a task into the ring (thread 0)
+template <typename T, int TB, int CL, int LA>
+__device__ __forceinline__ void start_task(const BandInfo &b, const TileMeta *tm, const SweepJob *jobs,
+                                           const T *ltile, const T *utile, const int32_t *srcs,
+                                           const unsigned char *cld, unsigned char *ring, uint32_t stage_bytes,
+                                           int nstages, uint64_t *bars, uint32_t jbase, int rank, DevStatus *st,
+                                           int pf) {
+  if constexpr (LA)
+    issue_first_jobs_la<T, TB>(b, tm, jobs, ltile, srcs, cld, ring, stage_bytes, nstages, bars, jbase, rank, st);
+  else
+    issue_first_jobs<T, TB, CL>(b, tm, jobs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, rank, st,
+                                pf, cld);
+}
+
 // z = A_jj^-1 y_j with y gathered from the original numbering.
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA>
 __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -1346,11 +1651,12 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     const BandInfo bg = info[task];
     if (bg.n == 0 || (act && !act[task_sys[task]])) continue;  // empty, or its system is done
     __syncthreads();  // the previous task's reads of the tables and vectors are done
-    const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+    const BandInfo b = (LA && cx.rank == 1) ? stage_tables_la1(bg, tm, jobs, tms, jbs)
+                                            : stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();  // the tables are staged: start the first copies, then gather y
     if (threadIdx.x == 0)
-      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
-                                  pf, cld);
+      start_task<T, TB, CL, LA>(b, tms, jbs, ltile, utile, srcs, cld, ring, stage_bytes, nstages, bars, jbase,
+                                cx.rank, st, pf);
     const int ntot = b.nst * TB + pad;
     // y gathered through perm: eight indices, then eight values, in flight
     // per thread (a chain of dependent loads per element took ~8 us)
@@ -1375,11 +1681,14 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
     }
     __syncthreads();
     // a failed sweep stops both CTAs of a cluster at the same step
-    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes, nstages,
-                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
+    if (!run_sweep<T, TB, CL, LA>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes,
+                                  nstages, bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
       break;
-    // both CTAs of a cluster hold the whole result: each writes its share
-    for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) z[b.row0 + i] = xout[i];
+    // both CTAs of a row-split cluster hold the whole result: each writes its
+    // share; in the lookahead split CTA 0 holds it
+    const int wr = LA ? 0 : cx.rank, wn = LA ? 1 : CL;
+    if (wr == cx.rank)
+      for (int i = threadIdx.x + wr * blockDim.x; i < b.n; i += wn * blockDim.x) z[b.row0 + i] = xout[i];
   }
   // no CTA of a cluster leaves while its peer may still address its shared
   // memory (every message sent has been taken by then)
@@ -1387,7 +1696,7 @@ __global__ void band_solve_fwd_kernel(const BandInfo *__restrict__ info, int max
 }
 
 // x1 = z1 - A_jj^-1 (E z2)_j, scattered to x in the original numbering.
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA>
 __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max_n, int max_kl,
                                       int max_ku2, int max_tiles, int max_jobs, int nstages,
                                       uint32_t stage_bytes,
@@ -1423,11 +1732,12 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
     const BandInfo bg = info[task];
     if (bg.n == 0 || (act && !act[task_sys[task]])) continue;
     __syncthreads();
-    const BandInfo b = stage_tables(bg, tm, jobs, tms, jbs);
+    const BandInfo b = (LA && cx.rank == 1) ? stage_tables_la1(bg, tm, jobs, tms, jbs)
+                                            : stage_tables(bg, tm, jobs, tms, jbs);
     __syncthreads();
     if (threadIdx.x == 0)
-      issue_first_jobs<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, ring, stage_bytes, nstages, bars, jbase, cx.rank, st,
-                                  pf, cld);
+      start_task<T, TB, CL, LA>(b, tms, jbs, ltile, utile, srcs, cld, ring, stage_bytes, nstages, bars, jbase,
+                                cx.rank, st, pf);
     const int ntot = b.nst * TB + pad;
     // (E z2) of the subdomain's rows: the row bounds of eight rows, then their
     // entries, loaded before use (rows of E hold 0-2 entries)
@@ -1456,13 +1766,15 @@ __global__ void band_solve_bwd_kernel(const BandInfo *__restrict__ info, int max
       }
     }
     __syncthreads();
-    if (!run_sweep<T, TB, CL>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes, nstages,
-                              bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
+    if (!run_sweep<T, TB, CL, LA>(b, tms, jbs, ltile, utile, srcs, cld, vec, xout, win, ring, stage_bytes,
+                                  nstages, bars, jbase, task, st, first_wait, cx, TB + max_kl + 8, ntot, pf))
       break;
-    for (int i = threadIdx.x + cx.rank * blockDim.x; i < b.n; i += CL * blockDim.x) {
-      const int r = b.row0 + i;
-      x[perm[r]] = double(z1[r] - xout[i]);
-    }
+    const int wr = LA ? 0 : cx.rank, wn = LA ? 1 : CL;
+    if (wr == cx.rank)
+      for (int i = threadIdx.x + wr * blockDim.x; i < b.n; i += wn * blockDim.x) {
+        const int r = b.row0 + i;
+        x[perm[r]] = double(z1[r] - xout[i]);
+      }
   }
   if (CL > 1) cluster_barrier();
 }
@@ -1618,7 +1930,9 @@ static size_t sweep_base_bytes(int max_n, int max_kl, int max_ku2, size_t es, in
   used += sizeof(TileMeta) * (size_t)max_tiles + sizeof(SweepJob) * (size_t)max_jobs;
   return (used + 127) & ~(size_t)127;
 }
-#define DD_SMEM_LIMIT (227 * 1024)
+// dynamic shared memory of a sweep CTA: the 227 KB a block may hold, less
+// 256 bytes for the kernels' static shared variables
+#define DD_SMEM_LIMIT (227 * 1024 - 256)
 #define DD_MAX_STAGES 4
 // stages of the ring at this stage size (0: two do not fit) for tiles of tb
 // columns swept by clusters of cl CTAs
@@ -1759,6 +2073,35 @@ cudaError_t launch_cluster_pack(int ntiles, int tb, const TileMeta *tm, const T 
   return cudaGetLastError();
 }
 
+// The backward tiles in the layout of the lookahead sweeps: CTA p's columns
+// of tile t (la_cols), row by row, at byte lao[p].  Rows, column offsets and
+// widths are multiples of 16 bytes; one CTA per (tile, p).
+template <typename T, int TB>
+__global__ void la_pack_kernel(int ntiles, const TileMeta *__restrict__ tm, const T *__restrict__ utile,
+                               unsigned char *lad) {
+  const int t = blockIdx.x, p = blockIdx.y;
+  if (t >= ntiles) return;
+  const TileMeta mt = tm[t];
+  const int c0 = p == 0 ? 0 : la_split(mt.wu, TB), w = la_cols(mt.wu, TB, p);
+  const int v16 = w * (int)sizeof(T) / 16;
+  uint4 *dst = reinterpret_cast<uint4 *>(lad + mt.lao[p]);
+  for (int e = threadIdx.x; e < TB * v16; e += blockDim.x) {
+    const int r = e / v16, k = e % v16;
+    dst[e] = reinterpret_cast<const uint4 *>(utile + mt.uofs + (int64_t)r * mt.wu + c0)[k];
+  }
+}
+
+template <typename T>
+cudaError_t launch_la_pack(int ntiles, int tb, const TileMeta *tm, const T *utile, unsigned char *lad,
+                           cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const dim3 grid(ntiles, 2);
+  if (tb == 64) la_pack_kernel<T, 64><<<grid, 128, 0, s>>>(ntiles, tm, utile, lad);
+  else if (tb == 32) la_pack_kernel<T, 32><<<grid, 128, 0, s>>>(ntiles, tm, utile, lad);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 // one sweep launch: a plain grid, or clusters of cl CTAs
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_sweep(void (*kernel)(KArgs...), int grid, int threads, size_t smem, int cl,
@@ -1784,7 +2127,7 @@ static size_t sweep_smem(int max_n, int max_kl, int max_ku2, int ns, uint32_t st
   return sweep_base_bytes(max_n, max_kl, max_ku2, sizeof(T), TB, CL, mt, mj) + (size_t)ns * stage_bytes;
 }
 
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA = 0>
 static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
                           int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
                           const int32_t *src, const double *y, const int32_t *perm, T *z, DevStatus *st,
@@ -1792,16 +2135,17 @@ static cudaError_t fwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   const int mt = max_n / TB, mj = 2 * mt;
   const int grid = pl.sched_off ? pl.grid : m * CL;
   const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, pl.stage_bytes);
-  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T, TB, CL>, smem);
+  cudaError_t e = ensure_smem(band_solve_fwd_kernel<T, TB, CL, LA>, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  return launch_sweep(band_solve_fwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
-                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, pl.cld, y, perm, z, pl.sched,
-                      pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
+  return launch_sweep(band_solve_fwd_kernel<T, TB, CL, LA>, grid, LA ? 8 * TB : 8 * TB / CL, smem, CL, s, d_info,
+                      max_n, max_kl, max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src,
+                      LA ? pl.lad : pl.cld, y, perm, z, pl.sched, pl.sched_off, pl.task_sys, pl.act, st,
+                      pl.first_wait, pl.pf);
 }
 
-// tile width and cluster size of a plan: 8 TB / cl threads per CTA
-static inline int plan_tb(const SweepPlan &pl) { return pl.threads * pl.cl / 8; }
+// tile width of a plan: 8 TB / cl threads per CTA (8 TB in the lookahead split)
+static inline int plan_tb(const SweepPlan &pl) { return pl.la ? pl.threads / 8 : pl.threads * pl.cl / 8; }
 
 template <typename T>
 cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int max_kl,
@@ -1813,6 +2157,13 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, pl.cl, sizeof(T), pl.stage_bytes);
   if (ns < 2) return cudaErrorInvalidValue;
   // the backward tile step maps exactly 8 threads to each of the CTA's rows
+  if (pl.la && pl.cl == 2 && tb == 64)
+    return fwd_tb<T, 64, 2, 1>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st,
+                               s);
+  if (pl.la && pl.cl == 2 && tb == 32)
+    return fwd_tb<T, 32, 2, 1>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st,
+                               s);
+  if (pl.la) return cudaErrorInvalidValue;
   if (tb == 64 && pl.cl == 1)
     return fwd_tb<T, 64, 1>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, y, perm, z, st, s);
   if (tb == 64 && pl.cl == 2)
@@ -1824,7 +2175,7 @@ cudaError_t launch_band_solve_fwd(const BandInfo *d_info, int m, int max_n, int 
   return cudaErrorInvalidValue;
 }
 
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA = 0>
 static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, int max_ku2, const SweepPlan &pl,
                           int ns, const TileMeta *tm, const SweepJob *jobs, const T *ltile, const T *utile,
                           const int32_t *src, const int32_t *e_ptr, const int32_t *e_col, const T *e_val,
@@ -1833,12 +2184,13 @@ static cudaError_t bwd_tb(const BandInfo *d_info, int m, int max_n, int max_kl, 
   const int mt = max_n / TB, mj = 2 * mt;
   const int grid = pl.sched_off ? pl.grid : m * CL;
   const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, pl.stage_bytes);
-  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T, TB, CL>, smem);
+  cudaError_t e = ensure_smem(band_solve_bwd_kernel<T, TB, CL, LA>, smem);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  return launch_sweep(band_solve_bwd_kernel<T, TB, CL>, grid, 8 * TB / CL, smem, CL, s, d_info, max_n, max_kl,
-                      max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src, pl.cld, e_ptr, e_col, e_val, z2,
-                      z1, perm, x, pl.sched, pl.sched_off, pl.task_sys, pl.act, st, pl.first_wait, pl.pf);
+  return launch_sweep(band_solve_bwd_kernel<T, TB, CL, LA>, grid, LA ? 8 * TB : 8 * TB / CL, smem, CL, s, d_info,
+                      max_n, max_kl, max_ku2, mt, mj, ns, pl.stage_bytes, tm, jobs, ltile, utile, src,
+                      LA ? pl.lad : pl.cld, e_ptr, e_col, e_val, z2, z1, perm, x, pl.sched, pl.sched_off, pl.task_sys,
+                      pl.act, st, pl.first_wait, pl.pf);
 }
 
 template <typename T>
@@ -1851,14 +2203,16 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
   const int tb = plan_tb(pl);
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, pl.cl, sizeof(T), pl.stage_bytes);
   if (ns < 2) return cudaErrorInvalidValue;
-#define DD_BWD_CASE(TBV, CLV)                                                                           \
-  if (tb == TBV && pl.cl == CLV)                                                                       \
-    return bwd_tb<T, TBV, CLV>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, e_ptr, \
-                               e_col, e_val, z2, z1, perm, x, st, s);
-  DD_BWD_CASE(64, 1)
-  DD_BWD_CASE(64, 2)
-  DD_BWD_CASE(32, 1)
-  DD_BWD_CASE(32, 2)
+#define DD_BWD_CASE(TBV, CLV, LAV)                                                                  \
+  if (tb == TBV && pl.cl == CLV && pl.la == LAV)                                                        \
+    return bwd_tb<T, TBV, CLV, LAV>(d_info, m, max_n, max_kl, max_ku2, pl, ns, tm, jobs, ltile, utile, src, \
+                                    e_ptr, e_col, e_val, z2, z1, perm, x, st, s);
+  DD_BWD_CASE(64, 1, 0)
+  DD_BWD_CASE(64, 2, 0)
+  DD_BWD_CASE(32, 1, 0)
+  DD_BWD_CASE(32, 2, 0)
+  DD_BWD_CASE(64, 2, 1)
+  DD_BWD_CASE(32, 2, 1)
 #undef DD_BWD_CASE
   return cudaErrorInvalidValue;
 }
@@ -1866,26 +2220,28 @@ cudaError_t launch_band_solve_bwd(const BandInfo *d_info, int m, int max_n, int 
 // Subdomains the sweep kernels hold resident at once at this stage size
 // (both kernels; the smaller): CTAs per SM times SMs for cl = 1, the device's
 // active clusters for cl = 2.  0 when they do not fit.
-template <typename T, int TB, int CL>
+template <typename T, int TB, int CL, int LA = 0>
 static int slots_tb(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_bytes) {
   const size_t smem = sweep_smem<T, TB, CL>(max_n, max_kl, max_ku2, ns, stage_bytes);
-  if (ensure_smem(band_solve_fwd_kernel<T, TB, CL>, smem) != cudaSuccess) return 0;
-  if (ensure_smem(band_solve_bwd_kernel<T, TB, CL>, smem) != cudaSuccess) return 0;
+  if (ensure_smem(band_solve_fwd_kernel<T, TB, CL, LA>, smem) != cudaSuccess) return 0;
+  if (ensure_smem(band_solve_bwd_kernel<T, TB, CL, LA>, smem) != cudaSuccess) return 0;
   int a = 0, b = 0;
   if (CL == 1) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T, TB, CL>, 8 * TB, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, band_solve_fwd_kernel<T, TB, CL, LA>, 8 * TB, smem) !=
+        cudaSuccess)
       return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T, TB, CL>, 8 * TB, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, band_solve_bwd_kernel<T, TB, CL, LA>, 8 * TB, smem) !=
+        cudaSuccess)
       return 0;
     return (a < b ? a : b) * sms;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL * 64);
-  cfg.blockDim = dim3(8 * TB / CL);
+  cfg.blockDim = dim3(LA ? 8 * TB : 8 * TB / CL);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1894,15 +2250,21 @@ static int slots_tb(int max_n, int max_kl, int max_ku2, int ns, uint32_t stage_b
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaOccupancyMaxActiveClusters(&a, band_solve_fwd_kernel<T, TB, CL>, &cfg) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveClusters(&b, band_solve_bwd_kernel<T, TB, CL>, &cfg) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveClusters(&a, band_solve_fwd_kernel<T, TB, CL, LA>, &cfg) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveClusters(&b, band_solve_bwd_kernel<T, TB, CL, LA>, &cfg) != cudaSuccess) return 0;
   return a < b ? a : b;
 }
 
 template <typename T>
-int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes) {
+int band_sweep_slots(int max_n, int max_kl, int max_ku2, int tb, int cl, uint32_t stage_bytes, int la) {
   const int ns = band_sweep_stages(max_n, max_kl, max_ku2, tb, cl, sizeof(T), stage_bytes);
   if (ns < 2) return 0;
+  if (la) {
+    if (cl != 2) return 0;
+    if (tb == 64) return slots_tb<T, 64, 2, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
+    if (tb == 32) return slots_tb<T, 32, 2, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
+    return 0;
+  }
   if (tb == 64 && cl == 1) return slots_tb<T, 64, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
   if (tb == 64 && cl == 2) return slots_tb<T, 64, 2>(max_n, max_kl, max_ku2, ns, stage_bytes);
   if (tb == 32 && cl == 1) return slots_tb<T, 32, 1>(max_n, max_kl, max_ku2, ns, stage_bytes);
@@ -1955,7 +2317,9 @@ cudaError_t launch_band_solve_multi(const BandInfo *d_info, int m, const int32_t
       const BandInfo *, int, int, int, int, const SweepPlan &, const TileMeta *,                   \
       const SweepJob *, const T *, const T *, const int32_t *, const int32_t *, const int32_t *,    \
       const T *, const T *, const T *, const int32_t *, double *, DevStatus *, cudaStream_t);      \
-  template int band_sweep_slots<T>(int, int, int, int, int, uint32_t);                              \
+  template int band_sweep_slots<T>(int, int, int, int, int, uint32_t, int);                         \
+  template cudaError_t launch_la_pack<T>(int, int, const TileMeta *, const T *, unsigned char *,     \
+                                         cudaStream_t);                                             \
   template cudaError_t launch_cluster_pack<T>(int, int, const TileMeta *, const T *, const T *,    \
                                               const int32_t *, unsigned char *, cudaStream_t);      \
   template cudaError_t launch_band_solve_multi<T>(const BandInfo *, int, const int32_t *,          \

@@ -39,7 +39,7 @@ def _systems(ws):
     return [(w.A, w.part, w.m, w.perm, w.agg) for w in ws]
 
 
-@pytest.mark.parametrize("cl", [1, 2])
+@pytest.mark.parametrize("cl", [1, 2, 3])
 def test_batched_apply_matches_each_oracle(env, small_batch, cl):
     """1664 subdomains on persistent task lists, one CTA or a 2-CTA cluster each."""
     torch, dd, dev = env

@@ -38,7 +38,7 @@ for grid, m, sz in ((32, 4, 64), (20, 4, 33), (12, 8, 16)):
             continue
         xr = R.apply(y)
         for prec in (0, 1):
-            for cl in (1, 2):
+            for cl in (1, 2, 3):
                 P = dd.DD(w.A, w.part, w.m, name, perm=w.perm, agg_offsets=agg, prec=prec, sweep_cluster=cl, **kw)
                 xd = torch.full_like(yd, float("nan"))
                 P.apply(yd, xd)

@@ -86,3 +86,27 @@ def test_setup_is_deterministic(full, prec):
         its.append(r["iters"])
     assert its[0] == its[1]
     assert np.array_equal(xs[0].view(np.uint64), xs[1].view(np.uint64))
+
+
+def test_lookahead_fp32_full_size(full):
+    """The lookahead split of the sweeps at full size, FP32 (in FP64 its ring
+    stages and message buffers do not fit beside the vectors): the apply
+    agrees with one CTA per subdomain to FP32 rounding and with the oracle
+    within 1e-4; FGMRES takes the oracle's iterations +-1."""
+    torch, dd, dev, w, agg, y, xr, ro = full
+    yd = torch.from_numpy(y).to(dev)
+    xs = []
+    for mode in (1, 3):
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=dd.DD_FP32, sweep_cluster=mode)
+        assert P.stats()["sweep_cluster"] == mode
+        xd = torch.full_like(yd, float("nan"))
+        P.apply(yd, xd)
+        assert P.check_status() == 0
+        xs.append(xd.cpu().numpy())
+        if mode == 3:
+            bd = torch.from_numpy(w.b).to(dev)
+            r = P.gmres(bd, torch.zeros_like(bd), tol=1e-8, restart=50, maxit=3000)
+            assert r["status"] == 0 and abs(r["iters"] - ro["iters"]) <= 1, (r["iters"], ro["iters"])
+        P.close()
+    assert np.linalg.norm(xs[0] - xs[1]) <= 1e-5 * np.linalg.norm(xs[0])
+    assert np.linalg.norm(xs[1] - xr) <= 1e-4 * np.linalg.norm(xr)

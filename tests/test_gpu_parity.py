@@ -250,6 +250,39 @@ def test_cluster_sweeps_equal_single_cta(torch_dev, prec, grid, m, sz):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("grid,m,sz", [(32, 4, 64), (20, 4, 33), (6, 2, 5), (48, 4, 128), (40, 16, 96)])
+def test_lookahead_sweeps_match_oracle(torch_dev, prec, grid, m, sz):
+    """The lookahead split (CTA 0 the forward sweep and the near columns of
+    each backward step, CTA 1 the far columns a step ahead) sums the
+    backward rows in another order than one CTA: the applies agree to
+    rounding, and with the oracle to the usual bars."""
+    torch, dev = torch_dev
+    from paper_1104_3349_gb300 import dd
+    w = W.make_workload("t", grid, 0.02, 1.0, W.WIND_FOURIER, grid, m, sz=sz)
+    try:
+        R = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=w.agg)
+    except O.OracleError:
+        pytest.skip("no preconditioner for this partition")
+    y = W.uniform(2, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xs = []
+    for mode in (1, 3):
+        P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=w.agg, prec=prec, sweep_cluster=mode)
+        assert P.stats()["sweep_cluster"] == mode
+        xd = torch.full_like(yd, float("nan"))
+        for _ in range(2):  # a second apply reuses the ring's phases and the message slots
+            P.apply(yd, xd)
+        assert P.check_status() == 0
+        xs.append(xd.cpu().numpy())
+        P.close()
+    d = np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[0])
+    assert d <= (1e-13 if prec == 0 else 1e-5), d
+    xr = R.apply(y)
+    err = np.linalg.norm(xs[1] - xr) / np.linalg.norm(xr)
+    assert err <= (1e-10 if prec == 0 else 1e-4), err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("grid,m,sz", [(32, 4, 64), (20, 4, 33), (6, 2, 5)])
 def test_l2_prefetch_changes_no_bit(torch_dev, prec, grid, m, sz):
     """The sweeps' L2 prefetch is a hint: off (the default) and distances 1,

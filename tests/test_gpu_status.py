@@ -29,10 +29,12 @@ def env():
     return torch, dd, torch.device("cuda:0"), w, R
 
 
-@pytest.mark.parametrize("cl", [1, 2])
+@pytest.mark.parametrize("cl", [1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_timeout_is_reported_and_cleared(env, prec, cl):
-    """cl = 2: both CTAs of every cluster stop after the same cluster barrier."""
+    """cl = 2: both CTAs of every cluster stop after the same cluster barrier;
+    cl = 3 (the lookahead split): both finish the task's message exchange,
+    agree on the outcome at its end, and the next apply is unaffected."""
     torch, dd, dev, w, R = env
     P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=w.agg, prec=prec, sweep_cluster=cl)
     y = W.uniform(1, w.A.n)
