@@ -506,6 +506,174 @@ __global__ void __launch_bounds__(DD_GJ_PANEL_THREADS, 1) bgj_panel_reg_kernel(i
   bgj_panel_tail<T, NB, NO>(Wg, L11, LD, s_q, c0, nbe, nbo);
 }
 
+// (2') The whole NO-column slab of an outer step at once (FP32, rows of W
+// below k0 up to DD_GJ_CL * DD_GJ_SLAB_THREADS): LU with partial pivoting,
+// column by column, over a cluster of DD_GJ_CL CTAs.  Thread t of CTA r
+// holds the slab row that starts at position r * DD_GJ_SLAB_THREADS + t,
+// all NO entries in registers.  Rows never move while the slab is factored:
+// each thread tracks where the interchanges so far have put its row, and
+// stores the row there at the end.  Per pivot column c:
+//   - every warp's best candidate among the rows at positions >= c (largest
+//     |entry|, then lowest position) publishes its whole row in a slot of
+//     shared memory; warp 0 reduces the CTA's warps to one candidate;
+//   - one cluster barrier; warp 0 of every CTA reads the CTAs' candidates
+//     through distributed shared memory, reduces them to the same pivot and
+//     copies the pivot row;
+//   - the interchange of positions c and p_c goes to ipiv; every other row
+//     at a position >= c takes its multiplier (one reciprocal per column)
+//     and its rank-one update.
+// Slots, candidates and the pivot row copy alternate between two buffers
+// by column parity: a buffer is rewritten two columns later, after a
+// cluster barrier that every reader of it has passed.  The outcome of the
+// pivot test is the same in every CTA, so all of them take the same cluster
+// barriers; a last one keeps every CTA resident until the others have read
+// its slots.  The result is that of the four panel steps and three trailing
+// updates, with the rank-one updates in another order.
+#define DD_GJ_CL 8
+#define DD_GJ_SLAB_THREADS 512
+__device__ __forceinline__ int32_t ld_cluster_i32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void gj_cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <int NO>
+__global__ void __launch_bounds__(DD_GJ_SLAB_THREADS, 1) bgj_slab_kernel(int k0, const int32_t *__restrict__ P,
+                                                                      float *scratch,
+                                                                      const int64_t *__restrict__ poff,
+                                                                      int32_t *ipiv, const float *__restrict__ amax,
+                                                                      double pivtol, int32_t *failed, DevStatus *st,
+                                                                      int code) {
+  constexpr int NT = DD_GJ_SLAB_THREADS, NW = NT / 32;
+  static_assert(NO % 4 == 0 && NO / 4 <= 32 && DD_GJ_CL <= 32, "one warp copies a row and reduces the CTAs");
+  const int rank = (int)(blockIdx.x % DD_GJ_CL), b = (int)(blockIdx.x / DD_GJ_CL);
+  const int p = P[b];
+  if (k0 >= p || failed[b]) return;  // the same in every CTA of the cluster, before any barrier
+  const int rows_all = p - k0, nbo = min(NO, rows_all);
+  float *Wg = gj_base<float, NO>(scratch, poff, b);
+  __shared__ __align__(16) float slot[2][NW][NO];
+  __shared__ __align__(16) float prow[2][NO];
+  __shared__ float wv[NW];
+  __shared__ int wpos[NW];
+  __shared__ int32_t cand[2][4];  // the CTA's candidate: |value| bits, position, warp
+  __shared__ int s_pc[2], s_ok[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int mypos = rank * NT + tid;
+  const bool has = mypos < rows_all;
+  float a[NO];
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(Wg + (int64_t)(has ? mypos : 0) * NO);
+#pragma unroll
+    for (int v = 0; v < NO / 4; ++v) {
+      const float4 q = has ? src[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      a[4 * v] = q.x;
+      a[4 * v + 1] = q.y;
+      a[4 * v + 2] = q.z;
+      a[4 * v + 3] = q.w;
+    }
+  }
+  const float thresh = (float)pivtol * amax[b];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < NO; ++c) {
+    if (!ok || c >= nbo) continue;  // the same in every thread of the cluster
+    const int buf = c & 1;
+    const bool act = has && mypos >= c;
+    float v = act ? fabsf(a[c]) : -1.f;
+    int L = act ? mypos : INT_MAX, unused = 0;
+    warp_argmax(v, L, unused);
+    if (act && mypos == L) {
+      float4 *dst = reinterpret_cast<float4 *>(slot[buf][warp]);
+#pragma unroll
+      for (int q = 0; q < NO / 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+    }
+    if (lane == 0) {
+      wv[warp] = v;
+      wpos[warp] = L;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float bv = lane < NW ? wv[lane] : -1.f;
+      int bl = lane < NW ? wpos[lane] : INT_MAX, bw = lane;
+      warp_argmax(bv, bl, bw);
+      if (lane == 0) {
+        cand[buf][0] = __float_as_int(bv);
+        cand[buf][1] = bl;
+        cand[buf][2] = bw;
+      }
+    }
+    gj_cluster_barrier();
+    if (warp == 0) {
+      float cv = -1.f;
+      int cl = INT_MAX, pay = 0;
+      if (lane < DD_GJ_CL) {
+        const uint32_t ra = cluster_addr(&cand[buf][0], (uint32_t)lane);
+        cv = __int_as_float(ld_cluster_i32(ra));
+        cl = ld_cluster_i32(ra + 4);
+        pay = lane * NW + ld_cluster_i32(ra + 8);
+      }
+      warp_argmax(cv, cl, pay);
+      if (lane < NO / 4) {
+        const uint32_t ra = cluster_addr(&slot[buf][pay % NW][4 * lane], (uint32_t)(pay / NW));
+        reinterpret_cast<float4 *>(prow[buf])[lane] = ld_cluster_f4(ra);
+      }
+      if (lane == 0) {
+        s_pc[buf] = cl;
+        s_ok[buf] = cv > thresh ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    const int pc = s_pc[buf];
+    if (!s_ok[buf]) {
+      ok = false;
+      continue;
+    }
+    if (rank == 0 && tid == 0) ipiv[poff[b] + k0 + c] = k0 + pc;
+    if (act) {
+      if (mypos == pc) {
+        mypos = c;  // the pivot row: row c of U
+      } else {
+        if (mypos == c) mypos = pc;  // the row exchanged with the pivot row
+        const float l = a[c] * (1.f / prow[buf][c]);
+        a[c] = l;
+#pragma unroll
+        for (int q = c + 1; q < NO; ++q) a[q] -= l * prow[buf][q];
+      }
+    }
+  }
+  gj_cluster_barrier();  // every CTA has read the others' slots
+  if (!ok) {
+    if (rank == 0 && tid == 0) {
+      failed[b] = 1;
+      set_status2(st, code, b);
+    }
+    return;
+  }
+  if (has) {
+    float4 *dst = reinterpret_cast<float4 *>(Wg + (int64_t)mypos * NO);
+#pragma unroll
+    for (int q = 0; q < NO / 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+  }
+}
+
 // (2b) W(i, j) -= L21(i, :) U12(:, j) for the rows below and the columns
 // right of step s; CTA x takes 64 rows
 template <typename T, int NB, int NO>
@@ -1157,7 +1325,31 @@ int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size) {
 int64_t gj_launch_count(int pmax, int elem_size) {
   const int nb = elem_size == 8 ? BgjNB<double>::value : BgjNB<float>::value;
   const int no = elem_size == 8 ? BgjNO<double>::value : BgjNO<float>::value;
-  return (int64_t)(2 * (no / nb) + 6) * ((pmax + no - 1) / no) + 2;
+  int64_t n = 2;
+  for (int k0 = 0; k0 < pmax; k0 += no)  // FP32 slabs that fit a cluster: copy, slab and six launches
+    n += (elem_size == 4 && pmax - k0 <= DD_GJ_CL * DD_GJ_SLAB_THREADS) ? 8 : 2 * (no / nb) + 6;
+  return n;
+}
+
+// One launch of the slab kernel: a cluster of DD_GJ_CL CTAs per block
+template <int NO>
+static cudaError_t launch_gj_slab(int nblk, int k0, const int32_t *d_p, float *scratch, const int64_t *d_poff,
+                                  int32_t *ipiv, const float *amax, double pivtol, int32_t *failed, DevStatus *st,
+                                  int code, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nblk * DD_GJ_CL));
+  cfg.blockDim = dim3(DD_GJ_SLAB_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = DD_GJ_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bgj_slab_kernel<NO>, k0, d_p, scratch, d_poff, ipiv, amax, pivtol, failed, st,
+                            code);
 }
 // Explicit inverse of every block (in place), blocked Gauss-Jordan; blocks
 // that fail the pivot test are flagged and reported through st.
@@ -1186,7 +1378,17 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
   const dim3 ug((pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, (pmax + DD_BGJ_TILE - 1) / DD_BGJ_TILE, nblk);
   for (int k0 = 0; k0 < pmax; k0 += NO) {
     bgj_copy_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
-    for (int sp = 0; sp < NO / NB; ++sp) {
+    bool slab = false;
+    if constexpr (sizeof(T) == 4) {
+      // the whole slab in one launch when its rows fit a cluster's threads
+      if (pmax - k0 <= DD_GJ_CL * DD_GJ_SLAB_THREADS) {
+        e = launch_gj_slab<NO>(nblk, k0, d_p, reinterpret_cast<float *>(scratch), d_poff, ipiv,
+                               reinterpret_cast<const float *>(amax), pivtol, failed, st, status_code, s);
+        if (e != cudaSuccess) return e;
+        slab = true;
+      }
+    }
+    for (int sp = 0; sp < NO / NB && !slab; ++sp) {
       // the panel's rows in registers when they fit DD_GJ_REG_RPT per thread
       const int rpt = (pmax - k0 - NB * sp + DD_GJ_PANEL_THREADS - 1) / DD_GJ_PANEL_THREADS;
 #define DD_GJ_REG(R)                                                                                     \
