@@ -235,6 +235,11 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
     __syncthreads();
   }
 
+  // In shared memory the window slides: the part of panel t's window that
+  // panel t + 1 still needs (rows and columns NB on) moves up and left by NB,
+  // and only the NB new rows and columns come from the band.  The values a
+  // reload would bring are the same: every update stays inside the band.
+  const bool slide = __isShared(W);
   for (int t = 0; t < b.ntiles; ++t) {
     const int c0 = t * DD_NB;
     const int nbe = min(DD_NB, n - c0);
@@ -242,23 +247,43 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
     // copy (positions outside the band or the matrix are filled with zeros by
     // a zero source size), all in flight before one wait: the warp-per-row
     // loads below waited ~30 times per panel for a dependent round of loads.
-    if (__isShared(W)) {
-      for (int r = warp; r < R; r += nw) {
-        const int gr = c0 + r;
-        const T *arow = A + (int64_t)min(gr, n - 1) * wd;
-        T *wrow = W + r * ldw;
-        for (int c = lane; c < Cw; c += 32) {
-          const int gc = c0 + c, off = c - r + kl;
-          const bool ok = gr < n && gc < n && off >= 0 && off < wd;
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(wrow + c);
-          const T *src = ok ? arow + off : arow;
-          if (sizeof(T) == 4)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0)
-                         : "memory");
-          else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(src), "r"(ok ? 8 : 0)
-                         : "memory");
+    if (slide) {
+      auto load_rect = [&](int ra, int rz, int ca, int cz) {
+        for (int r = ra + warp; r < rz; r += nw) {
+          const int gr = c0 + r;
+          const T *arow = A + (int64_t)min(gr, n - 1) * wd;
+          T *wrow = W + r * ldw;
+          for (int c = ca + lane; c < cz; c += 32) {
+            const int gc = c0 + c, off = c - r + kl;
+            const bool ok = gr < n && gc < n && off >= 0 && off < wd;
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(wrow + c);
+            const T *src = ok ? arow + off : arow;
+            if (sizeof(T) == 4)
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0)
+                           : "memory");
+            else
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(src), "r"(ok ? 8 : 0)
+                           : "memory");
+          }
         }
+      };
+      if (t == 0) {
+        load_rect(0, R, 0, Cw);
+      } else {
+        // rows [0, R - NB) x columns [0, Cw - NB) <- rows [NB, R) x columns
+        // [NB, Cw), NB rows at a time: a block's source rows are the next
+        // block's destination, which is written after a barrier
+        const int sw = Cw - DD_NB;
+        for (int rb = 0; rb < R - DD_NB; rb += DD_NB) {
+          const int nr = min(DD_NB, R - DD_NB - rb);
+          for (int e = tid; e < nr * sw; e += nt) {
+            const int r = rb + e / sw, c = e % sw;
+            W[r * ldw + c] = W[(r + DD_NB) * ldw + c + DD_NB];
+          }
+          __syncthreads();
+        }
+        load_rect(R - DD_NB, R, 0, Cw);          // the new rows
+        load_rect(0, R - DD_NB, Cw - DD_NB, Cw);  // the new columns of the others
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
     } else
@@ -441,11 +466,20 @@ __device__ void band_lu_task(const BandInfo &b, int task, T *band, T *ltraw, int
     T *lt = ltraw + b.lraw_off + (int64_t)t * bi_lraw_elems(b);
     for (int c = warp; c < DD_NB; c += nw)  // column c of the multipliers
       for (int r = lane; r < R; r += 32) lt[(int64_t)c * R + r] = (r > c && c < nbe) ? W[r * ldw + c] : T(0);
-    for (int r = warp; r < R; r += nw) {
+    // (sliding window: the panel's NB rows are final; the whole band row,
+    // with zeros where the multipliers of earlier panels were)
+    for (int r = warp; r < (slide ? DD_NB : R); r += nw) {
       const int gr = c0 + r;
       if (gr >= n) continue;
       T *arow = A + (int64_t)gr * wd;
       const T *wrow = W + r * ldw;
+      if (slide) {
+        for (int off = lane; off < wd; off += 32) {
+          const int gc = gr - kl + off, c = gc - c0;
+          if (gc >= 0 && gc < n) arow[off] = (c < 0 || (c < DD_NB && r > c)) ? T(0) : wrow[c];
+        }
+        continue;
+      }
       for (int c = lane; c < Cw; c += 32) {
         const int gc = c0 + c, off = c - r + kl;
         if (gc < n && off >= 0 && off < wd) arow[off] = (c < DD_NB && r > c) ? T(0) : wrow[c];
