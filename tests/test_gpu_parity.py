@@ -197,6 +197,58 @@ def test_singular_interior_block_reported(torch_dev):
     assert eo.value.bad_block == eg.value.bad_block
 
 
+@pytest.mark.parametrize("layout", ["singles", "pair"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_singular_schur_block_reported(torch_dev, prec, layout):
+    """An aggregate that holds a pressure node whose S_hat row is zero (no
+    interior neighbour, no coupled interface node in the aggregate) gives a
+    singular S_hat block.  singles: every interface node its own aggregate;
+    pair: three aggregates, the singular one of two nodes, so that the
+    factorisation stops at its second pivot column (in FP32 inside the
+    cluster slab kernel, whose other clusters finish).  The oracle refuses
+    them, the device reports DD_ERR_SINGULAR_SCHUR for a block that the
+    oracle also finds singular, and a valid setup in the same process still
+    matches the oracle."""
+    torch, dev = torch_dev
+    from paper_1104_3349_gb300 import dd
+    w = W.cavity32()
+    nG = int((w.part < 0).sum())
+    agg = np.asarray(list(range(nG + 1)), np.int32)
+    Ro = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=agg, raise_on_error=False)
+    st_o, b0 = Ro.status, Ro.bad_block
+    Ro.close()
+    assert st_o == 4
+    if layout == "pair":
+        agg = np.asarray([0, b0 - 1, b0 + 1, nG], np.int32)
+        Ro = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=agg, raise_on_error=False)
+        st_o = Ro.status
+        Ro.close()
+        if st_o != 4:
+            pytest.skip("the pair around the singular node is not singular")
+    with pytest.raises(dd.DDError) as eg:
+        dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+    assert eg.value.status == 4
+    bad = eg.value.bad_block
+    assert 0 <= bad < len(agg) - 1
+    # that block alone, as its own partition of the interface, is singular
+    # for the oracle too
+    lo, hi = int(agg[bad]), int(agg[bad + 1])
+    one = np.asarray(sorted({0, lo, hi, nG}), np.int32)
+    Rb = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=one, raise_on_error=False)
+    assert Rb.status == 4 and int(one[Rb.bad_block]) == lo
+    Rb.close()
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=w.agg, prec=prec)
+    R = O.OracleDD(w.A, w.part, w.m, O.MSCE_INF, perm=w.perm, agg_offsets=w.agg)
+    y = W.uniform(4, w.A.n)
+    yd = torch.from_numpy(y).to(dev)
+    xd = torch.full_like(yd, float("nan"))
+    P.apply(yd, xd)
+    assert P.check_status() == 0
+    xr = R.apply(y)
+    assert np.linalg.norm(xd.cpu().numpy() - xr) <= (1e-10 if prec == 0 else 1e-4) * np.linalg.norm(xr)
+    P.close()
+
+
 def test_invalid_partition_rejected(torch_dev, cav32):
     torch, dev = torch_dev
     from paper_1104_3349_gb300 import dd
