@@ -413,7 +413,7 @@ def run_variants(args, dev):
         "one_by_one_ms": round(e0.elapsed_time(e1), 1), "sweep_grid": int(st["sweep_grid"]),
         "stage_bytes": int(st["stage_bytes"]), "autotune_candidates": int(st["tuned"]),
         "graphs": int(st["graphs"]), "launches": int(st["launches"])}
-    for name, fn in (("learned", run_learned), ("ilu", run_ilu)):
+    for name, fn in (("learned", run_learned), ("ilu", run_ilu), ("fp32_tf32", run_tf32)):
         try:  # one variant's failure leaves the others' numbers
             out[name] = fn(args, dev)
         except Exception as e:  # noqa: BLE001
@@ -448,6 +448,32 @@ def run_ilu(args, dev):
     return {"workload": WORKLOAD, "preconditioner": "fp32 factors, FP64 FGMRES(50)",
             "note": "the packed sweep tiles are dense between their trimmed bounds, so dropped entries inside "
                     "them still stream", **res}
+
+
+def run_tf32(args, dev):
+    """The headline workload with DD_FP32_TF32 (the dense block inverses'
+    rank-64 updates on the TF32 tensor cores, three TF32 terms per product)
+    against DD_FP32: setup + solve, the second run of each."""
+    import torch
+    from paper_1104_3349_gb300 import dd, workload as W
+    w = W.fourier256()
+    agg = W.aggregates(w.A, w.part, w.perm, SZ)
+    b = torch.from_numpy(w.b).to(dev)
+    res = {}
+    for name, prec in (("fp32", dd.DD_FP32), ("fp32_tf32", dd.DD_FP32_TF32)):
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
+            x = torch.empty_like(b)
+            r = P.gmres(b, x, tol=TOL, restart=RESTART, maxit=MAXIT)
+            e1.record()
+            torch.cuda.synchronize()
+            st = P.stats()
+            P.close()
+        res[name] = {"ms": round(e0.elapsed_time(e1), 2), "setup_ms": round(st["setup_ms"], 2),
+                     "iters": r["iters"], "status": r["status"], "relres": r["relres"]}
+    return {"workload": WORKLOAD, **res}
 
 
 WEIGHTS = os.path.join(ROOT, "paper_1104_3349_gb300", "weights", "schur_mlp.bin")

@@ -81,7 +81,13 @@ typedef enum {
 
 typedef enum {
   DD_FP64 = 0,     /* preconditioner factors and apply in FP64                 */
-  DD_FP32 = 1      /* factors and apply in FP32 (FP64 in/out); Krylov in FP64  */
+  DD_FP32 = 1,     /* factors and apply in FP32 (FP64 in/out); Krylov in FP64  */
+  DD_FP32_TF32 = 2 /* DD_FP32, with the rank-64 updates of the dense block
+                      inverses (S_hat, MSCN / MSCE(r) blocks) on the TF32
+                      tensor cores, every product in three TF32 terms
+                      (hi*hi + hi*lo + lo*hi, FP32 accumulation); close to
+                      FP32 but not bitwise equal to DD_FP32.  Reported as
+                      DD_FP32 by the handle                               */
 } dd_prec;
 
 /* C in CSR form, original numbering (host, copied). */
@@ -109,7 +115,7 @@ typedef struct {
 } dd_partition;
 
 typedef struct {
-  dd_prec prec;       /* DD_FP64 or DD_FP32                                    */
+  dd_prec prec;       /* DD_FP64, DD_FP32 or DD_FP32_TF32                      */
   double pivot_tol;   /* relative pivot test |pivot| <= tol * max|block|;
                          <= 0 selects 1e-14 (FP64) / 1e-7 (FP32)              */
   int32_t use_graph;  /* 1: gmres_solve replays one captured CUDA graph per

@@ -43,6 +43,7 @@ struct DDHandle {
   SweepPlan plan;              // sweep ring stage size, threads and persistent schedule
   uint32_t first_wait = 0xffffffffu;  // test hook: polls of each sweep CTA's first wait
   int sweep_cl_opt = 0;        // opts.sweep_cluster: 0 choose, 1, 2 or 3
+  int gj_tc = 0;               // DD_FP32_TF32: Gauss-Jordan updates on TF32 tensor cores
   int sweep_pf_opt = 0;        // opts.sweep_prefetch: k > 0 k jobs, else none
   int overlap = 0, radius = 0; // opts.overlap (overlapped kinds), opts.radius (DD_MSCE)
   double ilu_tol = 0.0;        // opts.ilu_tol: drop tolerance of the incomplete interior LU (0: exact)
@@ -966,7 +967,7 @@ dd_status learned_blocks(DDHandle *h, const dd_csr *csr, HostBlocks &hb, const s
   CK(cudaMemsetAsync(h->st_probe, 0, sizeof(DevStatus), s));
   CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.S, B.amax, s));
   CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.S, h->ipiv, h->poff, B.amax, h->failed, B.gj,
-                          pivtol, h->st_probe, DD_ERR_SINGULAR_SCHUR, s));
+                          pivtol, h->st_probe, DD_ERR_SINGULAR_SCHUR, s, h->gj_tc));
   std::vector<int32_t> failed(nagg, 0);
   if (nagg) CK(cudaMemcpyAsync(failed.data(), h->failed, sizeof(int32_t) * nagg, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1000,7 +1001,7 @@ dd_status learned_blocks(DDHandle *h, const dd_csr *csr, HostBlocks &hb, const s
   TRY(dalloc(h, &famax, fb.size()));
   CK(launch_block_amax<T>((int)fb.size(), d_fpp, d_fo, S2, famax, s));
   CK(launch_gj_inverse<T>((int)fb.size(), d_fpp, d_fo, fpmax, S2, h->ipiv, d_fpo, famax, d_ff, B.gj, pivtol,
-                          h->st, DD_ERR_SINGULAR_SCHUR, s));
+                          h->st, DD_ERR_SINGULAR_SCHUR, s, h->gj_tc));
   for (size_t q = 0; q < fb.size(); ++q)
     CK(cudaMemcpyAsync(B.S + soff[fb[q]], S2 + soff[fb[q]], sizeof(T) * (size_t)p[fb[q]] * p[fb[q]],
                        cudaMemcpyDeviceToDevice, s));
@@ -1147,7 +1148,7 @@ dd_status principal_blocks(DDHandle *h, const dd_csr *csr, const HostBlocks &hb,
   CK(launch_scatter_coo<T>((int64_t)fi.size(), d_i, d_v, B.Fm, s));
   CK(launch_block_amax<T>(nb, d_p, d_soff, B.Dm, amax, s));
   CK(launch_gj_inverse<T>(nb, d_p, d_soff, pmax, B.Dm, ipiv, d_poff, amax, failed, gj, pivtol, h->st,
-                          DD_ERR_SINGULAR_SCHUR, s));
+                          DD_ERR_SINGULAR_SCHUR, s, h->gj_tc));
   if (!rowsum) {
     CK(launch_block_gemm<T>(nb, d_p, d_soff, pmax, B.Dm, B.Em, B.Tm, T(1), T(0), s));
     CK(launch_block_gemm<T>(nb, d_p, d_soff, pmax, B.Fm, B.Tm, S, T(-1), T(1), s));
@@ -1363,7 +1364,7 @@ dd_status msce_radius_blocks(DDHandle *h, const dd_csr *csr, const HostBlocks &h
   TRY(dalloc(h, &amax, nb));
   CK(launch_block_amax<T>(nb, d_bd, d_doff, Dr, amax, s));
   CK(launch_gj_inverse<T>(nb, d_bd, d_doff, dmax, Dr, ipiv, d_poff, amax, failed, gj, pivtol, h->st,
-                          DD_ERR_SINGULAR_SCHUR, s));
+                          DD_ERR_SINGULAR_SCHUR, s, h->gj_tc));
   // T_b = D_r^-1 E_b (d x p), then S_a -= F_b T_b (p x p)
   std::vector<int32_t> dims1, dims2;
   std::vector<int64_t> offs1, offs2;
@@ -1780,7 +1781,7 @@ dd_status setup_device(DDHandle *h, const dd_csr *csr, const dd_partition *pt, H
   // ---- explicit inverses of the S_hat blocks
   CK(launch_block_amax<T>(nagg, h->d_p, h->s_off, B.S, B.amax, s));
   CK(launch_gj_inverse<T>(nagg, h->d_p, h->s_off, h->pmax, B.S, h->ipiv, h->poff, B.amax,
-                          h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s));
+                          h->failed, B.gj, pivtol, h->st, DD_ERR_SINGULAR_SCHUR, s, h->gj_tc));
   TRY(dalloc(h, &B.z1, std::max(nI, 1)));
   TRY(dalloc(h, &B.z2, std::max(nG, 1)));
   TRY(dalloc(h, &B.t, std::max(nG, 1)));
@@ -2397,8 +2398,14 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
     if (!o.mlp_weights) { h->err = "DD_LEARNED needs opts.mlp_weights"; return DD_ERR_INVALID_ARG; }
     h->mlp_path = o.mlp_weights;
   }
-  if (o.prec != DD_FP64 && o.prec != DD_FP32) { h->err = "unknown precision"; return DD_ERR_INVALID_ARG; }
-  h->prec = o.prec;
+  if (o.prec != DD_FP64 && o.prec != DD_FP32 && o.prec != DD_FP32_TF32) {
+    h->err = "unknown precision";
+    return DD_ERR_INVALID_ARG;
+  }
+  // DD_FP32_TF32 is the FP32 preconditioner with its dense block inverses'
+  // rank-64 updates on the TF32 tensor cores
+  h->gj_tc = o.prec == DD_FP32_TF32 ? 1 : 0;
+  h->prec = o.prec == DD_FP32_TF32 ? DD_FP32 : o.prec;
   h->kind = approx;
   h->use_graph = o.use_graph != 0;
   if (o.krylov_threads != 0 && o.krylov_threads != 256 && o.krylov_threads != 512) {
@@ -2419,7 +2426,7 @@ dd_status setup_handle(DDHandle *h, const dd_csr *csr, const dd_partition *parti
   if (o.overlap < 0 || o.radius < 0) { h->err = "overlap and radius must be >= 0"; return DD_ERR_INVALID_ARG; }
   h->overlap = o.overlap;
   h->radius = o.radius;
-  const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (o.prec == DD_FP32 ? 1e-7 : 1e-14);
+  const double pivtol = o.pivot_tol > 0 ? o.pivot_tol : (h->prec == DD_FP32 ? 1e-7 : 1e-14);
   const int R = o.max_restart > 0 ? o.max_restart : 50;
   if (R > 120) { h->err = "max_restart must be <= 120"; return DD_ERR_INVALID_ARG; }
   HostBlocks hb;

@@ -274,7 +274,8 @@ cudaError_t launch_block_amax(int nblk, const int32_t *d_p, const int64_t *d_off
                               T *amax, cudaStream_t s);
 // In-place explicit inverses (Gauss-Jordan, partial pivoting); ipiv holds
 // p[b] entries per block at poff[b]; failing blocks are flagged and reported
-// through st with status_code.
+// through st with status_code.  tc = 1 (FP32 only): the rank-64 updates on
+// TF32 tensor cores, each product in three TF32 terms (DD_FP32_TF32).
 // scratch (elements of T) of launch_gj_inverse for nblk blocks of total size sum_p
 int64_t gj_scratch_elems(int nblk, int64_t sum_p, int elem_size);
 // kernel launches of one launch_gj_inverse call for blocks of size <= pmax
@@ -283,7 +284,7 @@ template <typename T>
 cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
                               int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
                               T *scratch, double pivtol, DevStatus *st, int status_code,
-                              cudaStream_t s);
+                              cudaStream_t s, int tc = 0);
 template <typename T>
 cudaError_t launch_scatter_coo(int64_t nnz, const int64_t *idx, const double *val, T *dst,
                                cudaStream_t s);

@@ -915,10 +915,38 @@ __global__ void __launch_bounds__(256) bgj_pcol_kernel(int k0, const int32_t *__
 #define DD_BGJ_TILE 64
 #define DD_BGJ_RT 4
 #define DD_BGJ_UPD_THREADS ((DD_BGJ_TILE / DD_BGJ_RT) * (DD_BGJ_TILE / DD_BGJ_RT))
-// Rank-NB update of one 64 x 64 tile: each of the 256 threads owns 4
+
+// TF32 tensor-core products with near-FP32 accuracy (the DD_FP32_TF32
+// precision): x = hi + lo with hi the TF32 rounding of x and lo that of the
+// remainder; a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi (the a_lo b_lo term and
+// the rounding of the lo parts are below FP32's unit roundoff relative to
+// a b), accumulated in FP32 by the tensor cores.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+// c += a b for one m16n8k8 fragment (a 16 x 8 row-major, b 8 x 8 column-
+// major, c 16 x 8, in the register layouts of the warp-level mma)
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Rank-NB update of one 64 x 64 tile from a transposed P column chunk and an
+// R row chunk staged in shared memory.  Each of the 256 threads owns 4
 // consecutive rows by 4 consecutive columns and accumulates the outer
-// products of a transposed P column chunk and an R row chunk in registers.
-template <typename T, int NB>
+// products in registers; with TC (FP32 only, DD_FP32_TF32) each of the 8
+// warps takes a 16 x 32 block as four m16n8 fragments on the tensor cores,
+// every product in three TF32 terms (split_tf32).
+template <typename T, int NB, int TC = 0>
 __global__ void __launch_bounds__(DD_BGJ_UPD_THREADS, 3) bgj_update_kernel(int k0, const int32_t *__restrict__ P,
                                                          const int64_t *__restrict__ off, T *A,
                                                          const T *__restrict__ scratch,
@@ -983,22 +1011,52 @@ __global__ void __launch_bounds__(DD_BGJ_UPD_THREADS, 3) bgj_update_kernel(int k
   }
   __syncthreads();
   constexpr int RT = DD_BGJ_RT, TH = DD_BGJ_TILE / DD_BGJ_RT;
+  constexpr bool TCU = TC && sizeof(T) == 4 && NB % 8 == 0 && DD_BGJ_UPD_THREADS == 256 && DD_BGJ_TILE == 64;
   const int tr = tid / TH, tc = tid % TH;
   const int rb = RT * tr, qb = RT * tc;
+  // TCU: warp w holds rows mb + g, mb + g + 8 and columns nb + 8 j + 2 t4,
+  // + 1 of fragment j (g = lane / 4, t4 = lane % 4)
+  const int g = (tid & 31) >> 2, t4 = tid & 3;
+  const int mb = 16 * ((tid >> 5) & 3), nb = 32 * (tid >> 7);
+  float cf[4][4];
   T acc[RT][RT];
+  if constexpr (TCU) {
 #pragma unroll
-  for (int x = 0; x < RT; ++x)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int y = 0; y < RT; ++y) acc[x][y] = T(0);
-#pragma unroll 8
-  for (int c = 0; c < NB; ++c) {
-    T pv[RT], rv[RT];
+      for (int e = 0; e < 4; ++e) cf[j][e] = 0.f;
+#pragma unroll 2
+    for (int k0 = 0; k0 < NB; k0 += 8) {
+      uint32_t ah[4], al[4];
+      split_tf32((float)Pt[k0 + t4][mb + g], ah[0], al[0]);
+      split_tf32((float)Pt[k0 + t4][mb + g + 8], ah[1], al[1]);
+      split_tf32((float)Pt[k0 + t4 + 4][mb + g], ah[2], al[2]);
+      split_tf32((float)Pt[k0 + t4 + 4][mb + g + 8], ah[3], al[3]);
 #pragma unroll
-    for (int x = 0; x < RT; ++x) { pv[x] = Pt[c][rb + x]; rv[x] = Rs[c][qb + x]; }
+      for (int j = 0; j < 4; ++j) {
+        uint32_t bh[2], bl[2];
+        split_tf32((float)Rs[k0 + t4][nb + 8 * j + g], bh[0], bl[0]);
+        split_tf32((float)Rs[k0 + t4 + 4][nb + 8 * j + g], bh[1], bl[1]);
+        mma_tf32(cf[j], al, bh);
+        mma_tf32(cf[j], ah, bl);
+        mma_tf32(cf[j], ah, bh);
+      }
+    }
+  } else {
 #pragma unroll
     for (int x = 0; x < RT; ++x)
 #pragma unroll
-      for (int y = 0; y < RT; ++y) acc[x][y] += pv[x] * rv[y];
+      for (int y = 0; y < RT; ++y) acc[x][y] = T(0);
+#pragma unroll 8
+    for (int c = 0; c < NB; ++c) {
+      T pv[RT], rv[RT];
+#pragma unroll
+      for (int x = 0; x < RT; ++x) { pv[x] = Pt[c][rb + x]; rv[x] = Rs[c][qb + x]; }
+#pragma unroll
+      for (int x = 0; x < RT; ++x)
+#pragma unroll
+        for (int y = 0; y < RT; ++y) acc[x][y] += pv[x] * rv[y];
+    }
   }
   // Epilogue through shared memory (over Pt, no longer read), CH rows at a
   // time, so that consecutive threads update consecutive columns of A.
@@ -1008,7 +1066,15 @@ __global__ void __launch_bounds__(DD_BGJ_UPD_THREADS, 3) bgj_update_kernel(int k
   T *S = &Pt[0][0];
   for (int h = 0; h < DD_BGJ_TILE; h += CH) {
     __syncthreads();
-    if (rb >= h && rb < h + CH) {
+    if constexpr (TCU) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = mb + g + 8 * (e >> 1), q = nb + 8 * j + 2 * t4 + (e & 1);
+          if (r >= h && r < h + CH) S[(r - h) * SL + q] = (T)cf[j][e];
+        }
+    } else if (rb >= h && rb < h + CH) {
 #pragma unroll
       for (int x = 0; x < RT; ++x)
 #pragma unroll
@@ -1357,7 +1423,7 @@ template <typename T>
 cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off, int pmax, T *A,
                               int32_t *ipiv, const int64_t *d_poff, const T *amax, int32_t *failed,
                               T *scratch, double pivtol, DevStatus *st, int status_code,
-                              cudaStream_t s) {
+                              cudaStream_t s, int tc) {
   if (nblk <= 0) return cudaSuccess;
   constexpr int NB = BgjNB<T>::value, NO = BgjNO<T>::value;
   static_assert(NO % NB == 0 && NO <= DD_BGJ_TILE, "outer block of whole inner panels");
@@ -1416,7 +1482,10 @@ cudaError_t launch_gj_inverse(int nblk, const int32_t *d_p, const int64_t *d_off
     bgj_a11inv_kernel<T, NO><<<ag, 1024, 0, s>>>(k0, d_p, scratch, d_poff, failed);
     bgj_rowblock_kernel<T, NO><<<rg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
     bgj_pcol_kernel<T, NO><<<cg, 256, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
-    bgj_update_kernel<T, NO><<<ug, DD_BGJ_UPD_THREADS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    if (tc && sizeof(T) == 4)
+      bgj_update_kernel<T, NO, 1><<<ug, DD_BGJ_UPD_THREADS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
+    else
+      bgj_update_kernel<T, NO><<<ug, DD_BGJ_UPD_THREADS, 0, s>>>(k0, d_p, d_off, A, scratch, d_poff, failed);
   }
   // the composite column permutation in the (now free) scratch, then the rows
   int32_t *cidx = reinterpret_cast<int32_t *>(scratch);
@@ -1526,7 +1595,7 @@ cudaError_t launch_schur_apply(int nagg, const int32_t *agg_off, const int64_t *
                                             cudaStream_t);                                         \
   template cudaError_t launch_gj_inverse<T>(int, const int32_t *, const int64_t *, int, T *,      \
                                             int32_t *, const int64_t *, const T *, int32_t *, T *, \
-                                            double, DevStatus *, int, cudaStream_t);              \
+                                            double, DevStatus *, int, cudaStream_t, int);         \
   template cudaError_t launch_scatter_coo<T>(int64_t, const int64_t *, const double *, T *,       \
                                              cudaStream_t);                                        \
   template cudaError_t launch_assemble_overlapped<T>(int, int, const int32_t *, const int32_t *,          \

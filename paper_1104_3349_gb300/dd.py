@@ -27,7 +27,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
 DD_EXACT, DD_MSCE_INF, DD_MSCN, DD_MSCNR, DD_LUM = 0, 1, 2, 3, 4
-DD_FP64, DD_FP32 = 0, 1
+DD_FP64, DD_FP32, DD_FP32_TF32 = 0, 1, 2
 STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_INVALID_ARG", 2: "DD_ERR_INVALID_PARTITION",
                 3: "DD_ERR_SINGULAR_BLOCK", 4: "DD_ERR_SINGULAR_SCHUR", 5: "DD_ERR_NOT_CONVERGED",
                 6: "DD_ERR_NONFINITE", 7: "DD_ERR_TIMEOUT", 8: "DD_ERR_OOM", 9: "DD_ERR_CUDA",

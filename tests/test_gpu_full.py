@@ -110,3 +110,17 @@ def test_lookahead_fp32_full_size(full):
         P.close()
     assert np.linalg.norm(xs[0] - xs[1]) <= 1e-5 * np.linalg.norm(xs[0])
     assert np.linalg.norm(xs[1] - xr) <= 1e-4 * np.linalg.norm(xr)
+
+
+def test_tf32_full_size_iterations(full):
+    """DD_FP32_TF32 at full size: FGMRES(50) reaches 1e-8 within +-2
+    iterations of the oracle's count (true residual recomputed on the host)."""
+    torch, dd, dev, w, agg, y, xr, ro = full
+    P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=dd.DD_FP32_TF32)
+    bd = torch.from_numpy(w.b).to(dev)
+    xd = torch.zeros_like(bd)
+    r = P.gmres(bd, xd, tol=1e-8, restart=50, maxit=3000)
+    P.close()
+    print(f"DD_FP32_TF32: {r['iters']} iterations, oracle {ro['iters']}")
+    assert r["status"] == 0 and abs(r["iters"] - ro["iters"]) <= 2, (r["iters"], ro["iters"])
+    assert np.linalg.norm(w.b - O.spmv(w.A, xd.cpu().numpy())) <= 1e-8 * np.linalg.norm(w.b)
