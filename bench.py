@@ -154,7 +154,7 @@ def run_ours(args):
     dd.build()
     dd.load()
     w, agg = make_inputs()
-    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    prec = {"fp32": dd.DD_FP32, "fp32_tf32": dd.DD_FP32_TF32}.get(args.prec, dd.DD_FP64)
     b_host = torch.from_numpy(w.b).pin_memory()
     b = b_host.to(dev)
     x = torch.empty_like(b)
@@ -574,7 +574,7 @@ def apply_only(args):
     from paper_1104_3349_gb300 import dd
     dd.build()
     w, agg = make_inputs()
-    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    prec = {"fp32": dd.DD_FP32, "fp32_tf32": dd.DD_FP32_TF32}.get(args.prec, dd.DD_FP64)
     P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
     y = torch.from_numpy(w.b).cuda()
     x = torch.empty_like(y)
@@ -591,7 +591,7 @@ def solve_only(args):
     from paper_1104_3349_gb300 import dd
     dd.build()
     w, agg = make_inputs()
-    prec = dd.DD_FP32 if args.prec == "fp32" else dd.DD_FP64
+    prec = {"fp32": dd.DD_FP32, "fp32_tf32": dd.DD_FP32_TF32}.get(args.prec, dd.DD_FP64)
     P = dd.DD(w.A, w.part, w.m, "msce_inf", perm=w.perm, agg_offsets=agg, prec=prec)
     b = torch.from_numpy(w.b).cuda()
     x = torch.empty_like(b)
@@ -606,7 +606,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32_tf32"],
+                    help="preconditioner precision")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-variants", action="store_true",
