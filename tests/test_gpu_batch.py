@@ -66,11 +66,15 @@ def test_batched_apply_matches_each_oracle(env, small_batch, cl):
     P.close()
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batched_gmres_matches_each_oracle(env, small_batch, use_graph):
+@pytest.mark.parametrize("use_graph,cl", [(False, 0), (True, 0), (False, 3)])
+def test_batched_gmres_matches_each_oracle(env, small_batch, use_graph, cl):
+    """cl = 3: the lookahead sweeps on persistent task lists, with the
+    systems that have converged skipped by both CTAs of every pair."""
     torch, dd, dev = env
     ws = small_batch
-    P = dd.DDBatch(_systems(ws), "msce_inf", max_restart=30, use_graph=use_graph)
+    P = dd.DDBatch(_systems(ws), "msce_inf", max_restart=30, use_graph=use_graph, sweep_cluster=cl)
+    if cl:
+        assert P.stats()["sweep_cluster"] == cl
     bs = [torch.from_numpy(w.b).to(dev) for w in ws]
     xs = [torch.zeros_like(b) for b in bs]
     rc, out = P.gmres(bs, xs, tol=1e-8, restart=30)
